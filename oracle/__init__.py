@@ -1,0 +1,158 @@
+"""Plain FP64 CPU oracle of sFFT-DT -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The GPU library never calls it and
+shares no code with it.  The C source (``sfft_oracle.c``) follows Algorithm 1
+and Sec. II-B of the paper step by step; this module only builds it with gcc
+and marshals numpy arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_SOURCES = ["sfft_oracle.c"]
+_lock = threading.Lock()
+_lib = None
+
+ITER, FIXED = 0, 1
+
+# Validation tolerances, keyed to the precision of the *input*: a complex128
+# signal is exactly sparse to ~1e-16, a complex64 one only to its rounding
+# (~1e-7 relative), and the thresholds sit between that floor and O(1).
+# root_tol is only a sanity bound (the root must lie near the unit circle):
+# for adjacent aliases the Hankel system has condition ~1e4-1e5 and the root
+# moves by ~1e-3 while its nearest candidate stays right; the residual test
+# (res_tol, in data units) is the discriminating check.
+TOL_FP64 = dict(zero_tol=1e-10, root_tol=0.1, res_tol=1e-9)
+TOL_MIXED = dict(zero_tol=1e-6, root_tol=0.1, res_tol=1e-6)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liboracle.so with gcc."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "sfft_oracle.h")])
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Params(C.Structure):
+    _fields_ = [("N", C.c_int64), ("M0", C.c_int64), ("a_max", C.c_int32),
+                ("max_iters", C.c_int32), ("mode", C.c_int32), ("pad_", C.c_int32),
+                ("zero_tol", C.c_double), ("root_tol", C.c_double), ("res_tol", C.c_double)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P = C.POINTER
+            lib.orc_fft.argtypes = [C.c_int64, P(C.c_double), C.c_int]
+            lib.orc_dft_brute.argtypes = [C.c_int64, P(C.c_double), P(C.c_double), C.c_int]
+            lib.orc_syndrome.argtypes = [P(C.c_double), C.c_int64, C.c_int64, C.c_int64,
+                                         P(C.c_double)]
+            lib.orc_poly_roots.argtypes = [C.c_int, P(C.c_double), P(C.c_double)]
+            lib.orc_decode.argtypes = [C.c_int, P(C.c_double), C.c_int, C.c_int64, C.c_int64,
+                                       C.c_int64, C.c_double, C.c_double, C.c_double,
+                                       P(C.c_int64), P(C.c_double)]
+            lib.orc_exact.argtypes = [P(C.c_double), P(_Params), C.c_int64, P(C.c_int64),
+                                      P(C.c_double), P(C.c_int64)]
+            lib.orc_exact.restype = C.c_int64
+            _lib = lib
+    return _lib
+
+
+def _c128(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a), dtype=np.complex128)
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def fft(a, sign: int = -1) -> np.ndarray:
+    """Unnormalised radix-2 FFT (sign -1 forward, +1 inverse)."""
+    a = _c128(a).copy()
+    if _load().orc_fft(a.size, _dp(a), int(sign)) != 0:
+        raise ValueError("length must be a power of two")
+    return a
+
+
+def dft_brute(a, sign: int = -1) -> np.ndarray:
+    a = _c128(a)
+    out = np.empty_like(a)
+    _load().orc_dft_brute(a.size, _dp(a), _dp(out), int(sign))
+    return out
+
+
+def syndrome(x, d: int, shift: int) -> np.ndarray:
+    """Y_{d,shift} = d * FFT_{N/d}(x[n d + shift])  (Eq. (2))."""
+    x = _c128(x)
+    N = x.size
+    Y = np.empty(N // d, dtype=np.complex128)
+    if _load().orc_syndrome(_dp(x), N, int(d), int(shift), _dp(Y)) != 0:
+        raise ValueError("bad sizes")
+    return Y
+
+
+def poly_roots(c) -> np.ndarray:
+    """Roots of z^a + c[a-1] z^{a-1} + ... + c[0], 1 <= a <= 4."""
+    c = _c128(c)
+    z = np.empty(c.size, dtype=np.complex128)
+    if _load().orc_poly_roots(c.size, _dp(c), _dp(z)) != 0:
+        raise ValueError("degree must be 1..4")
+    return z
+
+
+def decode(a: int, m, k: int, M: int, N: int, theta: float, root_tol: float, res_tol: float):
+    """SynDec of one bin: returns (ok, s[a], p[a])."""
+    m = _c128(m)
+    s = np.zeros(4, dtype=np.int64)
+    p = np.zeros(4, dtype=np.complex128)
+    ok = _load().orc_decode(int(a), _dp(m), m.size, int(k), int(M), int(N), float(theta),
+                            float(root_tol), float(res_tol),
+                            s.ctypes.data_as(C.POINTER(C.c_int64)), _dp(p))
+    return bool(ok), s[:a].copy(), p[:a].copy()
+
+
+def exact(x, M0: int, a_max: int = 4, mode: int = ITER, max_iters: int | None = None,
+          zero_tol: float | None = None, root_tol: float | None = None,
+          res_tol: float | None = None, cap: int | None = None):
+    """Whole exactly-K-sparse sFFT-DT.  x of any complex dtype is upcast to
+    complex128.  Default tolerances are TOL_MIXED for complex64 input and
+    TOL_FP64 otherwise.  Returns (idx int64 sorted, val complex128, unresolved)."""
+    x_in = np.asarray(x)
+    tol = TOL_MIXED if x_in.dtype == np.complex64 else TOL_FP64
+    x = _c128(x_in)
+    N = x.size
+    prm = _Params(N=N, M0=int(M0), a_max=int(a_max),
+                  max_iters=int(a_max if max_iters is None else max_iters), mode=int(mode),
+                  pad_=0,
+                  zero_tol=float(tol["zero_tol"] if zero_tol is None else zero_tol),
+                  root_tol=float(tol["root_tol"] if root_tol is None else root_tol),
+                  res_tol=float(tol["res_tol"] if res_tol is None else res_tol))
+    if cap is None:
+        cap = int(M0) * int(a_max)
+    idx = np.zeros(cap, dtype=np.int64)
+    val = np.zeros(cap, dtype=np.complex128)
+    unres = C.c_int64(0)
+    n = _load().orc_exact(_dp(x), C.byref(prm), int(cap),
+                          idx.ctypes.data_as(C.POINTER(C.c_int64)), _dp(val), C.byref(unres))
+    if n < 0:
+        raise ValueError("bad parameters")
+    n = min(int(n), cap)
+    return idx[:n].copy(), val[:n].copy(), int(unres.value)

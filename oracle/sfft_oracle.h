@@ -1,0 +1,76 @@
+/*
+ * sfft_oracle.h -- plain FP64 CPU oracle of sFFT-DT (Hsieh, Lu, Pei).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This oracle exists to check the GPU library.
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+ * call it; the library never links or calls it, and it shares no code,
+ * header, table or constant with the GPU path.
+ *
+ * Conventions (reading of Sec. II-A and Eq. (1)-(2)):
+ *   X[s] = sum_n x[n] e^{-2 pi i s n/N}   (unnormalised DFT)
+ *   omega = e^{+2 pi i / N}
+ *   Y_{d,l}[k] = d * FFT_M(x[n d + l])[k] = sum_{j<d} X[k + jM] omega^{(k+jM) l}
+ * so the syndromes m_l of bin k are moments sum_j p_j z_j^l with p_j = X[s_j]
+ * and z_j = omega^{s_j} (Eq. (3)).
+ */
+#ifndef SFFT_ORACLE_H
+#define SFFT_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Complex arrays are interleaved (re, im) doubles. */
+
+/* In-place radix-2 FFT, unnormalised; sign = -1 forward, +1 inverse.
+ * n must be a power of two.  Returns 0, or -1 on bad n. */
+int orc_fft(int64_t n, double* a, int sign);
+
+/* O(n^2) DFT straight from the definition (for pinning orc_fft). */
+int orc_dft_brute(int64_t n, const double* in, double* out, int sign);
+
+/* Syndrome spectrum of one shift (Eq. (2), Alg. 1 lines 03-06):
+ *   Y[k] = d * sum_{n<M} x[n d + shift] e^{-2 pi i k n / M},  M = N/d.
+ * Returns 0, or -1 on bad sizes. */
+int orc_syndrome(const double* x, int64_t N, int64_t d, int64_t shift, double* Y);
+
+/* Roots of z^a + c[a-1] z^{a-1} + ... + c[0] for 1 <= a <= 4 by the
+ * analytical solutions (quadratic, Cardano, Ferrari).  Returns 0 / -1. */
+int orc_poly_roots(int a, const double* c, double* z);
+
+/* SynDec of one bin (Sec. II-B steps (i)-(iii), Alg. 1 lines 23-35).
+ *   a      number of aliases assumed (1..4)
+ *   m      n_m syndromes m_0..m_{n_m-1} of bin k (n_m >= 2a)
+ *   k, M, N  bin index, number of bins, signal length
+ *   theta  zero threshold; root_tol, res_tol  validation tolerances
+ * On success writes s_out[a] (ascending) and p_out[a] and returns 1;
+ * returns 0 when the bin does not decode with a aliases. */
+int orc_decode(int a, const double* m, int n_m, int64_t k, int64_t M, int64_t N,
+               double theta, double root_tol, double res_tol,
+               int64_t* s_out, double* p_out);
+
+enum { ORC_ITER = 0, ORC_FIXED = 1 };
+
+typedef struct {
+  int64_t N;          /* signal length (power of two)                        */
+  int64_t M0;         /* number of bins at the first level, d0 = N / M0       */
+  int32_t a_max;      /* largest alias count decoded (1..4)                  */
+  int32_t max_iters;  /* ITER: number of levels (<= a_max)                    */
+  int32_t mode;       /* ORC_ITER (Algorithm 1) or ORC_FIXED (non-iterative)  */
+  int32_t pad_;
+  double zero_tol;    /* theta = zero_tol * max_k |Y_{d0,0}[k]|               */
+  double root_tol;    /* |z_j - omega^{s_j}| bound                            */
+  double res_tol;     /* ||m - Z p||_inf <= res_tol * ||m||_inf               */
+} orc_exact_params;
+
+/* Whole exactly-K-sparse transform.  Writes up to cap (s, X[s]) pairs sorted
+ * by s into idx / val, the number of unresolved bins into *unresolved, and
+ * returns the number of recovered frequencies (or -1 on bad parameters). */
+int64_t orc_exact(const double* x, const orc_exact_params* p, int64_t cap,
+                  int64_t* idx, double* val, int64_t* unresolved);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
