@@ -1,0 +1,171 @@
+/*
+ * sft.h -- C ABI of the GB300 (sm_103a) sparse FFT by downsampling in time
+ * (sFFT-DT, Hsieh, Lu and Pei).
+ *
+ * Problem (Sec. II-A, Eq. (1)-(2)).  Given x in C^N, recover the K-sparse
+ * spectrum X[s] = sum_n x[n] e^{-2 pi i s n / N} (unnormalised DFT; x is its
+ * inverse with 1/N).  The signal is downsampled in time, x_{d,l}[n] =
+ * x[n d + l], and each length-M = N/d FFT, scaled by d, gives per bin k the
+ * syndromes m_l = Y_{d,l}[k] = sum_{s in S_k} X[s] omega^{s l} with
+ * omega = e^{2 pi i / N} and S_k = {k + tM : 0 <= t < d} (Eq. (3)).  A bin
+ * holding a <= 4 non-zero frequencies is decoded from 2a syndromes
+ * (Sec. II-B): Hankel locator solve (Eq. (4)-(5)), roots of the locator
+ * polynomial snapped to the candidate set S_k, least-squares value solve.
+ *
+ * Modes.
+ *   SFT_EXACT_ITER   Algorithm 1: level l = 0..max_iters-1 works at
+ *                    d_l = 2^l d with M_l = M / 2^l bins, computes the two
+ *                    new shifts 2l, 2l+1, folds the syndromes held from
+ *                    earlier levels (Y_{2d,j}[k] = Y_{d,j}[k] + Y_{d,j}[k+M/2]),
+ *                    removes the frequencies already solved (SubFreq) and
+ *                    decodes every active bin with a = l + 1.
+ *   SFT_EXACT_FIXED  the non-iterative method (Fig. 1(b)): all 2 a_max shifts
+ *                    at d, each active bin decoded once with the smallest
+ *                    a <= a_max that validates.
+ *
+ * Precision.
+ *   SFT_FP64   input complex128 (interleaved re, im doubles); FFTs, folds,
+ *              peels and solves in FP64.
+ *   SFT_MIXED  input complex64 (interleaved re, im floats); the FFTs run on
+ *              the FP32 pipes in compensated (float-float) arithmetic, which
+ *              keeps FP64-grade syndromes; folds, peels and the per-bin
+ *              Hankel / root / value solves run in FP64.
+ *
+ * Conventions of every entry point.
+ *   - Pointers marked "device" must be CUDA device (or managed) memory on
+ *     the current device; "host" pointers are ordinary host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *     Device entry points are asynchronous on that stream; errors of the
+ *     launch itself are returned, errors of the kernels surface on the
+ *     stream (check with cudaStreamSynchronize).
+ *   - A plan is not thread-safe: calls on one plan must not overlap on the
+ *     GPU (they share its workspace).  Use one plan per concurrent stream.
+ *   - No C++ exception crosses this boundary.
+ */
+#ifndef SFT_H
+#define SFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SFT_OK = 0,
+  SFT_EINVAL = 1,       /* bad argument: sizes, pointers, parameters      */
+  SFT_ENOMEM = 2,       /* device or host allocation failed               */
+  SFT_ECUDA = 3,        /* a CUDA call failed (see sft_last_cuda_error)   */
+  SFT_ETIMEOUT = 4,     /* a bounded device wait gave up                  */
+  SFT_EUNSUPPORTED = 5  /* valid request this build does not implement    */
+} sft_status;
+
+typedef enum { SFT_EXACT_ITER = 0, SFT_EXACT_FIXED = 1, SFT_GENERAL = 2 } sft_mode;
+typedef enum { SFT_FP64 = 0, SFT_MIXED = 1 } sft_precision;
+
+/* Parameters as the paper states the problem (Algorithm 1 inputs: x, K;
+ * initialisation d, a_m). */
+typedef struct {
+  int64_t N;           /* signal length; power of two, 2^3 .. 2^30            */
+  int64_t K;           /* sparsity; the result capacity must be >= K         */
+  int64_t d;           /* (initial) downsampling factor; d | N, M = N/d a     */
+                       /* power of two, M <= 8192 in this build              */
+  int32_t a_max;       /* largest alias count decoded, 1..4 (paper: a_m = 4)  */
+  int32_t max_iters;   /* ITER: number of levels, 1..a_max (0 -> a_max);     */
+                       /* M / 2^(max_iters-1) must be >= 1                   */
+  int32_t mode;        /* sft_mode                                           */
+  int32_t precision;   /* sft_precision                                      */
+  int32_t n_cs_shifts; /* SFT_GENERAL only (random shifts r); 0 -> 3 a_max    */
+  int32_t reserved_;   /* must be 0                                          */
+  uint64_t seed;       /* SFT_GENERAL only: draws the random shifts          */
+  double zero_tol;     /* bin active iff |m| > zero_tol * max_k |Y_{d,0}[k]| */
+  double root_tol;     /* a root must lie within root_tol of its candidate    */
+  double res_tol;      /* accept iff ||m - Z p||_inf <= res_tol ||m||_inf     */
+} sft_params;
+
+/* Fills *p with the paper's defaults for (N, K, d, mode, precision):
+ * a_max = 4, max_iters = 4, and tolerances keyed to the input precision
+ * (FP64: zero 1e-10, root 0.1, residual 1e-9; MIXED: 1e-6, 0.1, 1e-6).
+ * Returns SFT_EINVAL for a NULL pointer, SFT_OK otherwise (validation of
+ * the sizes happens in sft_plan_create). */
+sft_status sft_params_default(sft_params* p, int64_t N, int64_t K, int64_t d, int32_t mode,
+                              int32_t precision);
+
+/* Result buffers, owned by the caller.  For n_signals signals:
+ *   idx        device int64  [n_signals * cap]   recovered locations s
+ *   val        device double [n_signals * cap * 2] recovered X[s] (re, im)
+ *   count      device int64  [n_signals]         entries written per signal
+ *                                                 (<= cap; see `overflow`)
+ *   unresolved device int32  [n_signals]         bins left unsolved
+ *   overflow   device int32  [n_signals]         1 if more than cap entries
+ *                                                 were recovered (extra dropped)
+ * Entries of one signal are ordered by bin s mod (N/d), then by s. */
+typedef struct {
+  int64_t cap;
+  int64_t* idx;
+  double* val;
+  int64_t* count;
+  int32_t* unresolved;
+  int32_t* overflow;
+} sft_result;
+
+typedef struct sft_plan_s* sft_plan_t;
+
+/* Validates *p and creates a plan for batches of up to max_signals signals
+ * of that shape: uploads the twiddle / omega tables and allocates the
+ * workspace (plan-owned device memory, see sft_plan_workspace_bytes).
+ * Must be called with the target device current.  Returns SFT_EINVAL,
+ * SFT_EUNSUPPORTED (e.g. SFT_GENERAL, M > 8192), SFT_ENOMEM or SFT_ECUDA. */
+sft_status sft_plan_create(const sft_params* p, int64_t max_signals, sft_plan_t* out);
+
+/* Frees the plan and its device memory (synchronises the device). */
+void sft_plan_destroy(sft_plan_t plan);
+
+/* Device bytes the plan holds (tables + workspace). */
+size_t sft_plan_workspace_bytes(sft_plan_t plan);
+
+/* Exactly K-sparse transform of n_signals signals (Algorithm 1, or the
+ * non-iterative variant), all on the GPU.
+ *   x         device, n_signals signals of N complex values each (complex128
+ *             for SFT_FP64, complex64 for SFT_MIXED); signal b starts at
+ *             element b * x_stride (x_stride >= N, in complex elements)
+ *   r         result buffers (device pointers inside), cap >= K
+ * Asynchronous on `stream`.  1 <= n_signals <= max_signals of the plan. */
+sft_status sft_exact(sft_plan_t plan, int64_t n_signals, const void* x, int64_t x_stride,
+                     const sft_result* r, void* stream);
+
+/* Same transform from and to HOST memory: copies the n_signals inputs to
+ * the device (plan-owned staging buffer), runs sft_exact, copies the
+ * results back into the host arrays of `r_host` (same layout as
+ * sft_result, but host pointers) and synchronises `stream` before
+ * returning.  Pinned host memory gives full copy bandwidth. */
+sft_status sft_exact_host(sft_plan_t plan, int64_t n_signals, const void* x_host,
+                          int64_t x_stride, const sft_result* r_host, void* stream);
+
+/* Number of kernel launches one sft_exact call of this plan issues. */
+int32_t sft_plan_launches_per_call(sft_plan_t plan);
+
+/* Per-stage timing.  With profiling enabled, every launch of an sft_exact
+ * call on this plan is bracketed by CUDA events recorded on the call's
+ * stream.  sft_plan_stage_times synchronises the device, sums the elapsed
+ * times per stage name since the previous read (or since profiling was
+ * enabled), writes up to `cap` entries (names are static strings, ms is the
+ * total, launches the number of launches summed) and resets the record.
+ * *n receives the number of stages.  Profiling adds one event pair per launch. */
+sft_status sft_plan_set_profiling(sft_plan_t plan, int32_t enable);
+sft_status sft_plan_stage_times(sft_plan_t plan, int32_t cap, const char** names, double* ms,
+                                int64_t* launches, int32_t* n);
+
+/* Human-readable name of a status code (static storage). */
+const char* sft_strerror(sft_status s);
+
+/* Detail of the last error this library reported in the calling thread: the
+ * CUDA error text for SFT_ECUDA, the offending argument for SFT_EINVAL
+ * (static per-thread storage; "" if none). */
+const char* sft_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFT_H */

@@ -1,0 +1,377 @@
+// sft_api.cu -- the C ABI (include/sft.h): parameter validation, plans
+// (device tables + workspace), and the device / host entry points.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sft_internal.h"
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+void note_cuda(cudaError_t e) {
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e),
+                cudaGetErrorString(e));
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int64_t v) {
+  int l = 0;
+  while ((int64_t(1) << l) < v) ++l;
+  return l;
+}
+
+constexpr int64_t kMaxFusedM = 8192;  // largest M one CTA transforms in this build
+
+sft_status fill_defaults(sft_params* p) {
+  if (p->a_max == 0) p->a_max = 4;
+  if (p->max_iters == 0) p->max_iters = p->a_max;
+  const bool fp64 = p->precision == SFT_FP64;
+  if (!(p->zero_tol > 0)) p->zero_tol = fp64 ? 1e-10 : 1e-6;
+  if (!(p->root_tol > 0)) p->root_tol = 0.1;
+  if (!(p->res_tol > 0)) p->res_tol = fp64 ? 1e-9 : 1e-6;
+  return SFT_OK;
+}
+
+sft_status validate(const sft_params& p) {
+  if (!is_pow2(p.N) || p.N < 8 || p.N > (int64_t(1) << 30)) return SFT_EINVAL;
+  if (p.K < 0 || p.K > p.N) return SFT_EINVAL;
+  if (!is_pow2(p.d) || p.d > p.N) return SFT_EINVAL;
+  if (p.a_max < 1 || p.a_max > 4) return SFT_EINVAL;
+  if (p.precision != SFT_FP64 && p.precision != SFT_MIXED) return SFT_EINVAL;
+  if (p.mode == SFT_GENERAL) return SFT_EUNSUPPORTED;
+  if (p.mode != SFT_EXACT_ITER && p.mode != SFT_EXACT_FIXED) return SFT_EINVAL;
+  if (p.reserved_ != 0) return SFT_EINVAL;
+  const int64_t M0 = p.N / p.d;
+  if (p.mode == SFT_EXACT_ITER) {
+    if (p.max_iters < 1 || p.max_iters > p.a_max) return SFT_EINVAL;
+    if ((M0 >> (p.max_iters - 1)) < 1) return SFT_EINVAL;
+  }
+  if (M0 > kMaxFusedM) return SFT_EUNSUPPORTED;
+  return SFT_OK;
+}
+
+template <class T>
+cudaError_t dalloc(T** ptr, size_t count, size_t* total) {
+  *total += count * sizeof(T);
+  return cudaMalloc(reinterpret_cast<void**>(ptr), count * sizeof(T));
+}
+
+void free_plan_memory(sft_plan_s* P) {
+  void* ptrs[] = {P->tab.om_hi, P->tab.om_lo, P->tab.tw, P->ws.held[0], P->ws.held[1],
+                  P->ws.T[0], P->ws.T[1], P->ws.zero_base, P->ws.slot_s, P->ws.slot_p,
+                  P->x_stage, P->r_stage};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+}
+
+// omega^e = e^{2 pi i e / N} and e^{-2 pi i q / M0}, rounded from long double
+cudaError_t upload_tables(sft_plan_s* P, size_t* total) {
+  const int64_t N = P->p.N, M0 = P->M0;
+  const int lo_bits = P->log2N / 2;
+  const int64_t n_lo = int64_t(1) << lo_bits, n_hi = N >> lo_bits;
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  std::vector<double2> lo(n_lo), hi(n_hi);
+  for (int64_t i = 0; i < n_lo; ++i) {
+    long double t = two_pi * (long double)i / (long double)N;
+    lo[i] = make_double2((double)cosl(t), (double)sinl(t));
+  }
+  for (int64_t i = 0; i < n_hi; ++i) {
+    long double t = two_pi * (long double)(i << lo_bits) / (long double)N;
+    hi[i] = make_double2((double)cosl(t), (double)sinl(t));
+  }
+  cudaError_t e;
+  if ((e = dalloc(&P->tab.om_lo, n_lo, total)) != cudaSuccess) return e;
+  if ((e = dalloc(&P->tab.om_hi, n_hi, total)) != cudaSuccess) return e;
+  P->tab.om_lo_bits = lo_bits;
+  if ((e = cudaMemcpy(P->tab.om_lo, lo.data(), n_lo * sizeof(double2), cudaMemcpyHostToDevice)))
+    return e;
+  if ((e = cudaMemcpy(P->tab.om_hi, hi.data(), n_hi * sizeof(double2), cudaMemcpyHostToDevice)))
+    return e;
+  if (P->p.precision == SFT_FP64) {
+    std::vector<double2> tw(M0);
+    for (int64_t q = 0; q < M0; ++q) {
+      long double t = two_pi * (long double)q / (long double)M0;
+      tw[q] = make_double2((double)cosl(t), (double)-sinl(t));
+    }
+    double2* d;
+    if ((e = dalloc(&d, M0, total)) != cudaSuccess) return e;
+    P->tab.tw = d;
+    return cudaMemcpy(d, tw.data(), M0 * sizeof(double2), cudaMemcpyHostToDevice);
+  }
+  std::vector<float4> tw(M0);
+  for (int64_t q = 0; q < M0; ++q) {
+    long double t = two_pi * (long double)q / (long double)M0;
+    long double c = cosl(t), s = -sinl(t);
+    float ch = (float)c, sh = (float)s;
+    tw[q] = make_float4(ch, (float)(c - (long double)ch), sh, (float)(s - (long double)sh));
+  }
+  float4* d;
+  if ((e = dalloc(&d, M0, total)) != cudaSuccess) return e;
+  P->tab.tw = d;
+  return cudaMemcpy(d, tw.data(), M0 * sizeof(float4), cudaMemcpyHostToDevice);
+}
+
+cudaError_t alloc_workspace(sft_plan_s* P, size_t* total) {
+  const int64_t B = P->max_signals, M0 = P->M0;
+  sft::Workspace& W = P->ws;
+  W.held_elems = P->p.mode == SFT_EXACT_FIXED ? 2 * P->p.a_max * M0 : 2 * M0;
+  cudaError_t e;
+  for (int i = 0; i < 2; ++i) {
+    if (i == 1 && P->p.mode == SFT_EXACT_FIXED) break;  // FIXED uses one buffer
+    if ((e = dalloc(&W.held[i], (size_t)(B * W.held_elems), total)) != cudaSuccess) return e;
+    if ((e = dalloc(&W.T[i], (size_t)(B * M0), total)) != cudaSuccess) return e;
+  }
+  // zeroed per call: ymax2 [B] | flags [B] (8-byte slots) | slot_cnt [B*M0]
+  const size_t zbytes = (size_t)B * 16 + (size_t)(B * M0);
+  char* z;
+  if ((e = dalloc(&z, zbytes, total)) != cudaSuccess) return e;
+  W.zero_base = z;
+  W.ymax2 = reinterpret_cast<unsigned long long*>(z);
+  W.flags = reinterpret_cast<int32_t*>(z + (size_t)B * 8);
+  W.slot_cnt = reinterpret_cast<uint8_t*>(z + (size_t)B * 16);
+  if ((e = dalloc(&W.slot_s, (size_t)(B * M0 * 4), total)) != cudaSuccess) return e;
+  if ((e = dalloc(&W.slot_p, (size_t)(B * M0 * 4), total)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+size_t zero_region_bytes(const sft_plan_s* P) {
+  return (size_t)P->max_signals * 16 + (size_t)(P->max_signals * P->M0);
+}
+
+}  // namespace
+
+extern "C" {
+
+sft_status sft_params_default(sft_params* p, int64_t N, int64_t K, int64_t d, int32_t mode,
+                              int32_t precision) {
+  if (!p) return SFT_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->N = N;
+  p->K = K;
+  p->d = d;
+  p->a_max = 4;
+  p->max_iters = 4;
+  p->mode = mode;
+  p->precision = precision;
+  fill_defaults(p);
+  return SFT_OK;
+}
+
+sft_status sft_plan_create(const sft_params* pin, int64_t max_signals, sft_plan_t* out) {
+  if (!pin || !out || max_signals < 1) return SFT_EINVAL;
+  *out = nullptr;
+  sft_params p = *pin;
+  fill_defaults(&p);
+  sft_status st = validate(p);
+  if (st != SFT_OK) return st;
+  sft_plan_s* P = new (std::nothrow) sft_plan_s();
+  if (!P) return SFT_ENOMEM;
+  P->p = p;
+  P->max_signals = max_signals;
+  P->M0 = p.N / p.d;
+  P->log2N = ilog2(p.N);
+  P->log2M0 = ilog2(P->M0);
+  P->levels = p.mode == SFT_EXACT_ITER ? p.max_iters : 1;
+  size_t total = 0;
+  cudaError_t e = upload_tables(P, &total);
+  if (e == cudaSuccess) e = alloc_workspace(P, &total);
+  if (e == cudaSuccess) e = sft::prepare_kernels(P);
+  if (e != cudaSuccess) {
+    note_cuda(e);
+    free_plan_memory(P);
+    delete P;
+    return e == cudaErrorMemoryAllocation ? SFT_ENOMEM : SFT_ECUDA;
+  }
+  P->device_bytes = total;
+  *out = P;
+  return SFT_OK;
+}
+
+static void drop_stage_recs(sft_plan_s* P);
+static void free_event_pool(sft_plan_s* P);
+
+void sft_plan_destroy(sft_plan_t P) {
+  if (!P) return;
+  cudaDeviceSynchronize();
+  drop_stage_recs(P);
+  free_event_pool(P);
+  free_plan_memory(P);
+  delete P;
+}
+
+size_t sft_plan_workspace_bytes(sft_plan_t P) { return P ? P->device_bytes : 0; }
+
+int32_t sft_plan_launches_per_call(sft_plan_t P) { return P ? sft::launches_per_call(P) : 0; }
+
+static sft_status reject(const char* fmt, long long a, long long b) {
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), fmt, a, b);
+  return SFT_EINVAL;
+}
+
+static sft_status check_call(sft_plan_t P, int64_t n, const void* x, int64_t x_stride,
+                             const sft_result* r) {
+  if (!P || !x || !r) return reject("NULL plan, input or result (%lld %lld)", 0, 0);
+  if (n < 1 || n > P->max_signals)
+    return reject("n_signals %lld outside [1, max_signals = %lld]", n, P->max_signals);
+  if (x_stride < P->p.N) return reject("x_stride %lld < N %lld", x_stride, P->p.N);
+  if (r->cap < P->p.K || r->cap < 1) return reject("result cap %lld < K %lld", r->cap, P->p.K);
+  if (!r->idx || !r->val || !r->count || !r->unresolved || !r->overflow)
+    return reject("NULL result array (%lld %lld)", 0, 0);
+  return SFT_OK;
+}
+
+sft_status sft_exact(sft_plan_t P, int64_t n, const void* x, int64_t x_stride,
+                     const sft_result* r, void* stream) {
+  sft_status st = check_call(P, n, x, x_stride, r);
+  if (st != SFT_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(P->ws.zero_base, 0, zero_region_bytes(P), s);
+  if (e == cudaSuccess) e = sft::launch_exact(P, n, x, x_stride, r, s);
+  if (e != cudaSuccess) {
+    note_cuda(e);
+    return SFT_ECUDA;
+  }
+  return SFT_OK;
+}
+
+sft_status sft_exact_host(sft_plan_t P, int64_t n, const void* x_host, int64_t x_stride,
+                          const sft_result* rh, void* stream) {
+  sft_status st = check_call(P, n, x_host, x_stride, rh);
+  if (st != SFT_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t elem = P->p.precision == SFT_FP64 ? 16 : 8;
+  const size_t xbytes = (size_t)n * (size_t)P->p.N * elem;
+  const int64_t cap = rh->cap;
+  const size_t rbytes = (size_t)n * (size_t)cap * 24 + (size_t)n * 16;
+  cudaError_t e = cudaSuccess;
+  if (P->x_stage_bytes < xbytes) {
+    if (P->x_stage) cudaFree(P->x_stage);
+    P->x_stage = nullptr;
+    P->x_stage_bytes = 0;
+    if ((e = cudaMalloc(&P->x_stage, xbytes)) != cudaSuccess) {
+      note_cuda(e);
+      return SFT_ENOMEM;
+    }
+    P->x_stage_bytes = xbytes;
+  }
+  if (P->r_stage_bytes < rbytes) {
+    if (P->r_stage) cudaFree(P->r_stage);
+    P->r_stage = nullptr;
+    P->r_stage_bytes = 0;
+    if ((e = cudaMalloc(&P->r_stage, rbytes)) != cudaSuccess) {
+      note_cuda(e);
+      return SFT_ENOMEM;
+    }
+    P->r_stage_bytes = rbytes;
+  }
+  // inputs: one copy when the host signals are packed, one per signal if not
+  const char* xh = static_cast<const char*>(x_host);
+  if (x_stride == P->p.N) {
+    e = cudaMemcpyAsync(P->x_stage, xh, xbytes, cudaMemcpyHostToDevice, s);
+  } else {
+    const size_t row = (size_t)P->p.N * elem;
+    e = cudaMemcpy2DAsync(P->x_stage, row, xh, (size_t)x_stride * elem, row, (size_t)n,
+                          cudaMemcpyHostToDevice, s);
+  }
+  char* rs = static_cast<char*>(P->r_stage);
+  sft_result rd;
+  rd.cap = cap;
+  rd.idx = reinterpret_cast<int64_t*>(rs);
+  rd.val = reinterpret_cast<double*>(rs + (size_t)n * cap * 8);
+  rd.count = reinterpret_cast<int64_t*>(rs + (size_t)n * cap * 24);
+  rd.unresolved = reinterpret_cast<int32_t*>(rs + (size_t)n * cap * 24 + (size_t)n * 8);
+  rd.overflow = reinterpret_cast<int32_t*>(rs + (size_t)n * cap * 24 + (size_t)n * 12);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->ws.zero_base, 0, zero_region_bytes(P), s);
+  if (e == cudaSuccess) e = sft::launch_exact(P, n, P->x_stage, P->p.N, &rd, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(rh->idx, rd.idx, (size_t)n * cap * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(rh->val, rd.val, (size_t)n * cap * 16, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(rh->count, rd.count, (size_t)n * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(rh->unresolved, rd.unresolved, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(rh->overflow, rd.overflow, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    note_cuda(e);
+    return SFT_ECUDA;
+  }
+  return SFT_OK;
+}
+
+static void drop_stage_recs(sft_plan_s* P) {
+  P->stage_recs.clear();
+  P->events_used = 0;
+}
+
+static void free_event_pool(sft_plan_s* P) {
+  for (cudaEvent_t e : P->event_pool) cudaEventDestroy(e);
+  P->event_pool.clear();
+  P->events_used = 0;
+}
+
+sft_status sft_plan_set_profiling(sft_plan_t P, int32_t enable) {
+  if (!P) return SFT_EINVAL;
+  if (!enable) {
+    cudaDeviceSynchronize();
+    drop_stage_recs(P);
+  }
+  P->profiling = enable != 0;
+  return SFT_OK;
+}
+
+sft_status sft_plan_stage_times(sft_plan_t P, int32_t cap, const char** names, double* ms,
+                                int64_t* launches, int32_t* n) {
+  if (!P || !n || cap < 0 || (cap > 0 && (!names || !ms || !launches))) return SFT_EINVAL;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    note_cuda(e);
+    return SFT_ECUDA;
+  }
+  std::vector<const char*> nm;
+  std::vector<double> tot;
+  std::vector<int64_t> cnt;
+  for (auto& r : P->stage_recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.t0, r.t1) != cudaSuccess) continue;
+    size_t i = 0;
+    while (i < nm.size() && std::strcmp(nm[i], r.name) != 0) ++i;
+    if (i == nm.size()) {
+      nm.push_back(r.name);
+      tot.push_back(0.0);
+      cnt.push_back(0);
+    }
+    tot[i] += t;
+    cnt[i] += 1;
+  }
+  drop_stage_recs(P);
+  *n = (int32_t)nm.size();
+  for (int32_t i = 0; i < cap && i < (int32_t)nm.size(); ++i) {
+    names[i] = nm[i];
+    ms[i] = tot[i];
+    launches[i] = cnt[i];
+  }
+  return SFT_OK;
+}
+
+const char* sft_strerror(sft_status s) {
+  switch (s) {
+    case SFT_OK: return "SFT_OK";
+    case SFT_EINVAL: return "SFT_EINVAL: invalid argument";
+    case SFT_ENOMEM: return "SFT_ENOMEM: allocation failed";
+    case SFT_ECUDA: return "SFT_ECUDA: CUDA call failed";
+    case SFT_ETIMEOUT: return "SFT_ETIMEOUT: bounded device wait expired";
+    case SFT_EUNSUPPORTED: return "SFT_EUNSUPPORTED: not supported by this build";
+  }
+  return "unknown sft_status";
+}
+
+const char* sft_last_cuda_error(void) { return g_cuda_err; }
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// sft_fft.cuh -- CTA-wide FFT of one length-M sequence held in shared memory.
+//
+// Stockham autosort formulation, forward (e^{-2 pi i k n / M}), natural order
+// in and out.  M = 2^m is factored into radix-16 passes plus one radix-2/4/8
+// pass.  In every pass each thread loads its R inputs (stride M/R) into
+// registers, applies the inter-pass twiddles, runs an R-point DFT in
+// registers (radix-2 decimation in frequency, constant twiddles), and stores
+// the R outputs.  All loads of a pass complete before any store (barrier),
+// so one M-point buffer suffices.
+//
+// Pass with radix R after sub-transforms of length Ns (Ns = product of the
+// earlier radices): group j (0 <= j < M/R), kk = j mod Ns,
+//   v[r] = buf[j + r M/R] * e^{-2 pi i r kk / (Ns R)}
+//   V    = DFT_R(v)
+//   buf[(j - kk) R + kk + r Ns] = V[r]
+// The inter-pass twiddles come from a table of e^{-2 pi i q / Mt} (Mt >= M,
+// Mt a power of two), indexed at q = r kk (Mt / (Ns R)).
+#pragma once
+
+#include "sft_common.cuh"
+
+namespace sft {
+
+// In-register DFT of R = 2, 4, 8 or 16 points: radix-2 DIF stages, then the
+// bit-reversal permutation (compile-time register renaming).
+template <class F, int R>
+__device__ __forceinline__ void dft_reg(typename F::V* v) {
+#pragma unroll
+  for (int h = R / 2; h >= 1; h >>= 1) {
+#pragma unroll
+    for (int blk = 0; blk < R; blk += 2 * h) {
+#pragma unroll
+      for (int j = 0; j < h; ++j) {
+        typename F::V a = v[blk + j], b = v[blk + j + h];
+        v[blk + j] = F::add(a, b);
+        typename F::V t = F::sub(a, b);
+        const int m = j * (8 / h);  // e^{-2 pi i j / (2h)} = e^{-2 pi i m / 16}
+        if (m == 0) {
+          v[blk + j + h] = t;
+        } else if (m == 4) {
+          v[blk + j + h] = F::mul_mi(t);
+        } else {
+          v[blk + j + h] = F::mul_c16(t, m);
+        }
+      }
+    }
+  }
+  // bit reversal of the R outputs
+  constexpr int LOG = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    int r = 0;
+#pragma unroll
+    for (int b = 0; b < LOG; ++b) r |= ((i >> b) & 1) << (LOG - 1 - b);
+    if (r > i) {
+      typename F::V t = v[i];
+      v[i] = v[r];
+      v[r] = t;
+    }
+  }
+}
+
+// One Stockham pass of radix R over buf[0..M).  Each thread owns up to
+// G = 16 / R groups (group j = tid + g * nthr).
+template <class F, int R>
+__device__ __forceinline__ void stockham_pass(char* buf, int M, int Ns, int log2Mt,
+                                              const typename F::Tw* __restrict__ tw, int tid,
+                                              int nthr) {
+  constexpr int G = 16 / R;
+  const int groups = M / R;
+  typename F::V v[G][R];
+  const int twstep_log = log2Mt - (31 - __clz(Ns * R));  // log2(Mt / (Ns R))
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int j = tid + g * nthr;
+    if (j < groups) {
+      const int kk = j & (Ns - 1);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        v[g][r] = F::ld(buf, M, j + r * groups);
+        if (r > 0 && Ns > 1) v[g][r] = F::mul_tw(v[g][r], __ldg(tw + ((r * kk) << twstep_log)));
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int j = tid + g * nthr;
+    if (j < groups) {
+      const int kk = j & (Ns - 1);
+      dft_reg<F, R>(v[g]);
+      const int base = (j - kk) * R + kk;
+#pragma unroll
+      for (int r = 0; r < R; ++r) F::st(buf, M, base + r * Ns, v[g][r]);
+    }
+  }
+  __syncthreads();
+}
+
+// Forward FFT of buf[0..M), M = 2^log2M (1 <= log2M <= 13 here), executed by
+// nthr threads (nthr * 16 >= M).  Caller synchronises before the call.
+template <class F>
+__device__ void cta_fft(char* buf, int log2M, int log2Mt, const typename F::Tw* __restrict__ tw,
+                        int tid, int nthr) {
+  const int M = 1 << log2M;
+  int Ns = 1;
+  int rem = log2M;
+  while (rem >= 4) {
+    stockham_pass<F, 16>(buf, M, Ns, log2Mt, tw, tid, nthr);
+    Ns <<= 4;
+    rem -= 4;
+  }
+  if (rem == 3) stockham_pass<F, 8>(buf, M, Ns, log2Mt, tw, tid, nthr);
+  if (rem == 2) stockham_pass<F, 4>(buf, M, Ns, log2Mt, tw, tid, nthr);
+  if (rem == 1) stockham_pass<F, 2>(buf, M, Ns, log2Mt, tw, tid, nthr);
+}
+
+}  // namespace sft

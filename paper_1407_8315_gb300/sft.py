@@ -1,0 +1,254 @@
+"""Thin Python binding of the C ABI in include/sft.h.
+
+Argument marshalling only: every step of the transform runs in the CUDA
+library (libsft.so); PyTorch supplies device memory and streams.  The names
+mirror the C entry points (sft_params_default, sft_plan_create, sft_exact,
+sft_exact_host, ...); `Plan` is a small convenience wrapper around them.
+
+There is no CPU fallback: if the library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from collections import namedtuple
+
+import numpy as np
+
+from . import _build_lib
+
+SFT_OK, SFT_EINVAL, SFT_ENOMEM, SFT_ECUDA, SFT_ETIMEOUT, SFT_EUNSUPPORTED = range(6)
+SFT_EXACT_ITER, SFT_EXACT_FIXED, SFT_GENERAL = 0, 1, 2
+SFT_FP64, SFT_MIXED = 0, 1
+
+_MODES = {"iter": SFT_EXACT_ITER, "fixed": SFT_EXACT_FIXED, "general": SFT_GENERAL}
+_PRECS = {"fp64": SFT_FP64, "mixed": SFT_MIXED}
+
+
+class sft_params(C.Structure):
+    _fields_ = [("N", C.c_int64), ("K", C.c_int64), ("d", C.c_int64), ("a_max", C.c_int32),
+                ("max_iters", C.c_int32), ("mode", C.c_int32), ("precision", C.c_int32),
+                ("n_cs_shifts", C.c_int32), ("reserved_", C.c_int32), ("seed", C.c_uint64),
+                ("zero_tol", C.c_double), ("root_tol", C.c_double), ("res_tol", C.c_double)]
+
+
+class sft_result(C.Structure):
+    _fields_ = [("cap", C.c_int64), ("idx", C.c_void_p), ("val", C.c_void_p),
+                ("count", C.c_void_p), ("unresolved", C.c_void_p), ("overflow", C.c_void_p)]
+
+
+EXPORTS = ["sft_params_default", "sft_plan_create", "sft_plan_destroy", "sft_plan_workspace_bytes",
+           "sft_exact", "sft_exact_host", "sft_plan_launches_per_call", "sft_strerror",
+           "sft_last_cuda_error", "sft_plan_set_profiling", "sft_plan_stage_times"]
+
+_lib = None
+
+
+class SftError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        lib = load()
+        msg = lib.sft_strerror(status).decode()
+        detail = lib.sft_last_cuda_error().decode()
+        if detail:
+            msg += " (" + detail + ")"
+        super().__init__(f"{what}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build_lib.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libsft.so (raises if it was not built and build_if_missing is False)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build_lib.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library {path} is missing; build it with "
+                               "paper_1407_8315_gb300.build() (there is no CPU fallback)")
+        _build_lib.build()
+    lib = C.CDLL(path)
+    P = C.POINTER
+    lib.sft_params_default.argtypes = [P(sft_params), C.c_int64, C.c_int64, C.c_int64, C.c_int32,
+                                       C.c_int32]
+    lib.sft_plan_create.argtypes = [P(sft_params), C.c_int64, P(C.c_void_p)]
+    lib.sft_plan_destroy.argtypes = [C.c_void_p]
+    lib.sft_plan_destroy.restype = None
+    lib.sft_plan_workspace_bytes.argtypes = [C.c_void_p]
+    lib.sft_plan_workspace_bytes.restype = C.c_size_t
+    lib.sft_exact.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, P(sft_result),
+                              C.c_void_p]
+    lib.sft_exact_host.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, P(sft_result),
+                                   C.c_void_p]
+    lib.sft_plan_launches_per_call.argtypes = [C.c_void_p]
+    lib.sft_plan_launches_per_call.restype = C.c_int32
+    lib.sft_plan_set_profiling.argtypes = [C.c_void_p, C.c_int32]
+    lib.sft_plan_stage_times.argtypes = [C.c_void_p, C.c_int32, P(C.c_char_p), P(C.c_double),
+                                         P(C.c_int64), P(C.c_int32)]
+    lib.sft_strerror.argtypes = [C.c_int]
+    lib.sft_strerror.restype = C.c_char_p
+    lib.sft_last_cuda_error.argtypes = []
+    lib.sft_last_cuda_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != SFT_OK:
+        raise SftError(status, what)
+
+
+def sft_params_default(N, K, d, mode="iter", precision="mixed") -> sft_params:
+    p = sft_params()
+    _check(load().sft_params_default(C.byref(p), int(N), int(K), int(d),
+                                     _MODES.get(mode, mode), _PRECS.get(precision, precision)),
+           "sft_params_default")
+    return p
+
+
+def sft_plan_create(params: sft_params, max_signals: int = 1) -> int:
+    h = C.c_void_p()
+    _check(load().sft_plan_create(C.byref(params), int(max_signals), C.byref(h)), "sft_plan_create")
+    return h.value
+
+
+def sft_plan_destroy(handle: int):
+    load().sft_plan_destroy(C.c_void_p(handle))
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+Result = namedtuple("Result", "idx val count unresolved overflow")
+
+
+def sft_exact(handle: int, x, cap: int, out: Result | None = None, stream=None) -> Result:
+    """x: torch tensor [B, N] (complex128 for fp64 plans, complex64 for mixed)
+    on the current CUDA device.  Returns device tensors (idx int64 [B, cap],
+    val complex128 [B, cap], count int64 [B], unresolved int32 [B],
+    overflow int32 [B])."""
+    import torch
+    if x.dim() == 1:
+        x = x.unsqueeze(0)
+    if not x.is_cuda:
+        raise ValueError("sft_exact needs a CUDA tensor (use sft_exact_host for host data)")
+    if x.stride(1) != 1:
+        raise ValueError("signals must be contiguous along N")
+    B = x.shape[0]
+    if out is None:
+        dev = x.device
+        out = Result(torch.empty((B, cap), dtype=torch.int64, device=dev),
+                     torch.empty((B, cap), dtype=torch.complex128, device=dev),
+                     torch.empty(B, dtype=torch.int64, device=dev),
+                     torch.empty(B, dtype=torch.int32, device=dev),
+                     torch.empty(B, dtype=torch.int32, device=dev))
+    r = sft_result(cap, out.idx.data_ptr(), out.val.data_ptr(), out.count.data_ptr(),
+                   out.unresolved.data_ptr(), out.overflow.data_ptr())
+    # a single row has no meaningful pitch (numpy/torch may report 0 for it)
+    pitch = x.stride(0) if B > 1 else x.shape[1]
+    _check(load().sft_exact(C.c_void_p(handle), B, C.c_void_p(x.data_ptr()), pitch,
+                            C.byref(r), C.c_void_p(_stream_ptr(stream))), "sft_exact")
+    return out
+
+
+def sft_exact_host(handle: int, x: np.ndarray, cap: int, out: Result | None = None,
+                   stream=None) -> Result:
+    """Host-memory variant: x is a numpy array [B, N]; results come back as
+    numpy arrays.  The library copies in, computes and copies out."""
+    if x.ndim == 1:
+        x = x[None, :]
+    if x.strides[1] != x.itemsize:
+        raise ValueError("signals must be contiguous along N")
+    B = x.shape[0]
+    if out is None:
+        out = Result(np.empty((B, cap), np.int64), np.empty((B, cap), np.complex128),
+                     np.empty(B, np.int64), np.empty(B, np.int32), np.empty(B, np.int32))
+    r = sft_result(cap, out.idx.ctypes.data, out.val.ctypes.data, out.count.ctypes.data,
+                   out.unresolved.ctypes.data, out.overflow.ctypes.data)
+    pitch = x.strides[0] // x.itemsize if B > 1 else x.shape[1]
+    _check(load().sft_exact_host(C.c_void_p(handle), B, C.c_void_p(x.ctypes.data),
+                                 pitch, C.byref(r),
+                                 C.c_void_p(_stream_ptr(stream))), "sft_exact_host")
+    return out
+
+
+def sft_plan_set_profiling(handle: int, enable: bool):
+    _check(load().sft_plan_set_profiling(C.c_void_p(handle), int(bool(enable))),
+           "sft_plan_set_profiling")
+
+
+def sft_plan_stage_times(handle: int) -> dict:
+    """{stage name: (total ms, launches)} since the previous read; resets."""
+    cap = 32
+    names = (C.c_char_p * cap)()
+    ms = (C.c_double * cap)()
+    cnt = (C.c_int64 * cap)()
+    n = C.c_int32(0)
+    _check(load().sft_plan_stage_times(C.c_void_p(handle), cap, names, ms, cnt, C.byref(n)),
+           "sft_plan_stage_times")
+    return {names[i].decode(): (ms[i], int(cnt[i])) for i in range(min(n.value, cap))}
+
+
+class Plan:
+    """Convenience owner of one sft plan."""
+
+    def __init__(self, N, K, d, mode="iter", precision="mixed", max_signals=1, a_max=4,
+                 max_iters=0, zero_tol=0.0, root_tol=0.0, res_tol=0.0):
+        p = sft_params_default(N, K, d, mode, precision)
+        p.a_max = int(a_max)
+        p.max_iters = int(max_iters) if max_iters else int(a_max)
+        if zero_tol:
+            p.zero_tol = float(zero_tol)
+        if root_tol:
+            p.root_tol = float(root_tol)
+        if res_tol:
+            p.res_tol = float(res_tol)
+        self.params = p
+        self.N, self.K, self.d = int(N), int(K), int(d)
+        self.M = self.N // self.d
+        self.precision = precision
+        self.max_signals = int(max_signals)
+        self.handle = None
+        self.handle = sft_plan_create(p, max_signals)
+
+    @property
+    def dtype_np(self):
+        return np.complex128 if self.precision in ("fp64", SFT_FP64) else np.complex64
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(load().sft_plan_workspace_bytes(C.c_void_p(self.handle)))
+
+    @property
+    def launches_per_call(self) -> int:
+        return int(load().sft_plan_launches_per_call(C.c_void_p(self.handle)))
+
+    def exact(self, x, cap=None, out=None, stream=None) -> Result:
+        return sft_exact(self.handle, x, cap or max(self.K, 1), out, stream)
+
+    def exact_host(self, x, cap=None, out=None, stream=None) -> Result:
+        return sft_exact_host(self.handle, x, cap or max(self.K, 1), out, stream)
+
+    def set_profiling(self, enable: bool = True):
+        sft_plan_set_profiling(self.handle, enable)
+
+    def stage_times(self) -> dict:
+        return sft_plan_stage_times(self.handle)
+
+    def close(self):
+        if self.handle:
+            sft_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,78 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports
+every entry point include/sft.h declares; argument validation that happens
+before any CUDA call is checked here (no compute)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(sft_\w+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1407_8315_gb300 as pkg
+    pkg.build()
+    from paper_1407_8315_gb300 import sft
+    return sft.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"sft_plan_create", "sft_exact", "sft_exact_host", "sft_plan_destroy"} <= names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header(lib):
+    from paper_1407_8315_gb300 import sft
+    assert set(sft.EXPORTS) <= _declared()
+
+
+def test_strerror(lib):
+    from paper_1407_8315_gb300 import sft
+    assert lib.sft_strerror(sft.SFT_OK) == b"SFT_OK"
+    assert b"EINVAL" in lib.sft_strerror(sft.SFT_EINVAL)
+
+
+def test_params_default(lib):
+    from paper_1407_8315_gb300 import sft
+    p = sft.sft_params_default(1 << 22, 4096, 512, "iter", "mixed")
+    assert (p.N, p.K, p.d, p.a_max, p.max_iters) == (1 << 22, 4096, 512, 4, 4)
+    assert p.zero_tol == 1e-6 and p.res_tol == 1e-6 and p.root_tol == 0.1
+    p = sft.sft_params_default(1 << 16, 64, 256, "fixed", "fp64")
+    assert p.zero_tol == 1e-10 and p.res_tol == 1e-9
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("N", 1000, 1), ("N", 4, 1), ("d", 3, 1), ("d", 1 << 23, 1), ("a_max", 5, 1),
+    ("max_iters", 5, 1), ("mode", 7, 1), ("precision", 9, 1), ("reserved_", 1, 1),
+    ("mode", 2, 5),          # SFT_GENERAL: not in this build
+    ("d", 64, 5),            # M = 2^16 bins: above the one-CTA FFT size
+])
+def test_plan_create_rejects_before_touching_the_gpu(lib, field, value, status):
+    from paper_1407_8315_gb300 import sft
+    p = sft.sft_params_default(1 << 22, 4096, 512, "iter", "mixed")
+    setattr(p, field, value)
+    h = C.c_void_p()
+    assert lib.sft_plan_create(C.byref(p), 1, C.byref(h)) == status
+    assert h.value is None
+
+
+def test_null_arguments(lib):
+    h = C.c_void_p()
+    assert lib.sft_plan_create(None, 1, C.byref(h)) == 1
+    assert lib.sft_params_default(None, 8, 1, 1, 0, 0) == 1
+    assert lib.sft_exact(None, 1, None, 0, None, None) == 1
+    assert lib.sft_plan_workspace_bytes(None) == 0

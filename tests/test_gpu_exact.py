@@ -1,0 +1,193 @@
+"""GPU parity of the exactly K-sparse transform against the FP64 oracle, through
+the C ABI.  Supports must match bit-exactly; values within 1e-10 relative on
+the FP64 path and 1e-4 relative (the bulk-FP32 bound) on the mixed path."""
+import numpy as np
+import pytest
+
+import siggen
+
+pytestmark = pytest.mark.gpu
+
+FP64_VAL_TOL = 1e-10
+MIXED_VAL_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1407_8315_gb300 as pkg
+    pkg.build()
+    return torch
+
+
+def _tol_of(plan):
+    p = plan.params
+    return dict(zero_tol=p.zero_tol, root_tol=p.root_tol, res_tol=p.res_tol)
+
+
+def _run_gpu(torch, plan, xs, cap):
+    x = torch.from_numpy(np.ascontiguousarray(xs)).cuda()
+    out = plan.exact(x, cap)
+    torch.cuda.synchronize()
+    return [t.cpu().numpy() for t in out]
+
+
+def _compare(orc, plan, xs, mode, cap, val_tol, mmax=None):
+    """Run the oracle on every signal of xs and compare with the GPU result."""
+    import torch
+    idx, val, cnt, unres, ovf = _run_gpu(torch, plan, xs, cap)
+    om = orc.ITER if mode == "iter" else orc.FIXED
+    tol = _tol_of(plan)
+    worst = 0.0
+    for b in range(xs.shape[0]):
+        oi, ov, ou = orc.exact(xs[b], plan.M, plan.params.a_max, om,
+                               max_iters=plan.params.max_iters, cap=cap, **tol)
+        n = int(cnt[b])
+        gi, gv = idx[b, :n], val[b, :n]
+        order = np.argsort(gi, kind="stable")
+        gi, gv = gi[order], gv[order]
+        assert ovf[b] == 0
+        np.testing.assert_array_equal(gi, oi, err_msg=f"signal {b}: supports differ")
+        assert unres[b] == ou, f"signal {b}: unresolved {unres[b]} vs {ou}"
+        if n:
+            rel = np.abs(gv - ov) / np.maximum(np.abs(ov), 1e-300)
+            worst = max(worst, float(rel.max()))
+    assert worst <= val_tol, worst
+    return worst
+
+
+@pytest.mark.parametrize("mode", ["iter", "fixed"])
+def test_plain_fp64_unit_magnitudes(gpu, orc, mode):
+    """N = 2^16 complex128, K = 64, |X| = 1, M = 256 (d = 256), FP64 path."""
+    from paper_1407_8315_gb300 import Plan
+    N, K, M = 1 << 16, 64, 256
+    plan = Plan(N, K, N // M, mode, "fp64", max_signals=8)
+    xs = np.stack([siggen.exact_signal(N, K, s)[0] for s in range(8)])
+    _compare(orc, plan, xs, mode, cap=4 * M, val_tol=FP64_VAL_TOL)
+
+
+@pytest.mark.parametrize("mode", ["iter", "fixed"])
+def test_mixed_full_size(gpu, orc, mode):
+    """N = 2^22 complex64, K = 4096, |X| ~ U[1,10], M = 2^13: the headline
+    configuration, four signals in one batch."""
+    from paper_1407_8315_gb300 import Plan
+    N, K, M = 1 << 22, 4096, 1 << 13
+    plan = Plan(N, K, N // M, mode, "mixed", max_signals=4)
+    xs, _, _ = siggen.batch_exact(N, K, range(100, 104), mag=(1, 10), dtype=np.complex64)
+    _compare(orc, plan, xs, mode, cap=2 * K, val_tol=MIXED_VAL_TOL)
+
+
+@pytest.mark.parametrize("mode", ["iter", "fixed"])
+def test_fp64_full_size(gpu, orc, mode):
+    from paper_1407_8315_gb300 import Plan
+    N, K, M = 1 << 22, 4096, 1 << 13
+    plan = Plan(N, K, N // M, mode, "fp64", max_signals=2)
+    xs = np.stack([siggen.exact_signal(N, K, s, mag=(1, 10))[0] for s in (7, 8)])
+    _compare(orc, plan, xs, mode, cap=2 * K, val_tol=FP64_VAL_TOL)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("N,K,M", [(1 << 10, 6, 32), (1 << 12, 100, 256), (1 << 14, 600, 1024),
+                                   (1 << 18, 2048, 4096), (1 << 13, 2000, 8192)])
+def test_sizes_span_tiles(gpu, orc, prec, N, K, M):
+    """Bins per block 128: M = 32 is a partial block, M = 8192 the largest
+    one-CTA FFT; K / M from 0.2 to 0.5 exercises every level."""
+    from paper_1407_8315_gb300 import Plan
+    dt = np.complex128 if prec == "fp64" else np.complex64
+    for mode in ("iter", "fixed"):
+        plan = Plan(N, K, N // M, mode, prec, max_signals=3)
+        xs, _, _ = siggen.batch_exact(N, K, [N + K + i for i in range(3)], mag=(1, 10), dtype=dt)
+        _compare(orc, plan, xs, mode, cap=4 * M,
+                 val_tol=FP64_VAL_TOL if prec == "fp64" else MIXED_VAL_TOL)
+
+
+def test_fig1_worked_example_on_gpu(gpu, orc):
+    from paper_1407_8315_gb300 import Plan
+    x = siggen.tone_signal(8, [0, 2, 4], [1.0, 2.0j, -3.0 + 0.5j])[None, :]
+    plan = Plan(8, 3, 2, "iter", "fp64", a_max=2, max_iters=1)
+    idx, val, cnt, unres, _ = _run_gpu(gpu, plan, x, 8)
+    assert idx[0, :cnt[0]].tolist() == [2] and unres[0] == 1
+    plan = Plan(8, 3, 2, "iter", "fp64", a_max=2, max_iters=2)
+    idx, val, cnt, unres, _ = _run_gpu(gpu, plan, x, 8)
+    assert sorted(idx[0, :cnt[0]].tolist()) == [0, 2, 4] and unres[0] == 0
+    plan = Plan(8, 3, 2, "fixed", "fp64", a_max=2)
+    idx, val, cnt, unres, _ = _run_gpu(gpu, plan, x, 8)
+    assert sorted(idx[0, :cnt[0]].tolist()) == [0, 2, 4] and unres[0] == 0
+
+
+def test_zero_signal_and_single_tone(gpu):
+    from paper_1407_8315_gb300 import Plan
+    N, M = 1 << 12, 64
+    plan = Plan(N, 4, N // M, "iter", "mixed", max_signals=2)
+    xs = np.zeros((2, N), np.complex64)
+    xs[1] = siggen.tone_signal(N, [1234], [3 - 4j], np.complex64)
+    idx, val, cnt, unres, ovf = _run_gpu(gpu, plan, xs, 4)
+    assert cnt[0] == 0 and unres[0] == 0
+    assert cnt[1] == 1 and idx[1, 0] == 1234 and abs(val[1, 0] - (3 - 4j)) < 1e-5
+
+
+def test_capacity_overflow_is_flagged(gpu):
+    from paper_1407_8315_gb300 import Plan
+    N, K, M = 1 << 14, 200, 1024
+    plan = Plan(N, K, N // M, "iter", "fp64")
+    x = siggen.exact_signal(N, K, 5, mag=(1, 10))[0][None, :]
+    import torch
+    xt = torch.from_numpy(x).cuda()
+    full = plan.exact(xt, 1024)
+    small = plan.exact(xt, 256)  # cap >= K still required
+    torch.cuda.synchronize()
+    n_full = int(full.count[0])
+    assert n_full > 150
+    # a plan whose K promises more than cap is rejected up front
+    with pytest.raises(Exception):
+        plan.exact(xt, 100)
+    assert int(small.count[0]) == min(n_full, 256)
+    assert int(small.overflow[0]) == (1 if n_full > 256 else 0)
+
+
+def test_batch_equals_single(gpu):
+    """Signals in one batch do not interact."""
+    from paper_1407_8315_gb300 import Plan
+    N, K, M = 1 << 16, 512, 1024
+    plan = Plan(N, K, N // M, "iter", "mixed", max_signals=5)
+    xs, _, _ = siggen.batch_exact(N, K, range(5), mag=(1, 10), dtype=np.complex64)
+    bi, bv, bc, bu, _ = _run_gpu(gpu, plan, xs, 2048)
+    for b in range(5):
+        si, sv, sc, su, _ = _run_gpu(gpu, plan, xs[b:b + 1], 2048)
+        assert sc[0] == bc[b] and su[0] == bu[b]
+        np.testing.assert_array_equal(si[0, :sc[0]], bi[b, :bc[b]])
+        np.testing.assert_array_equal(sv[0, :sc[0]], bv[b, :bc[b]])
+
+
+def test_host_entry_matches_device_entry(gpu):
+    from paper_1407_8315_gb300 import Plan
+    N, K, M = 1 << 18, 1024, 2048
+    plan = Plan(N, K, N // M, "iter", "mixed", max_signals=3)
+    xs, _, _ = siggen.batch_exact(N, K, range(3), mag=(1, 10), dtype=np.complex64)
+    di, dv, dc, du, do = _run_gpu(gpu, plan, xs, 2 * K)
+    h = plan.exact_host(xs, 2 * K)
+    np.testing.assert_array_equal(h.count, dc)
+    np.testing.assert_array_equal(h.unresolved, du)
+    for b in range(3):
+        np.testing.assert_array_equal(h.idx[b, :dc[b]], di[b, :dc[b]])
+        np.testing.assert_array_equal(h.val[b, :dc[b]], dv[b, :dc[b]])
+
+
+def test_strided_batch(gpu, orc):
+    """x_stride > N: signals read from a wider row pitch."""
+    from paper_1407_8315_gb300 import Plan
+    import torch
+    N, K, M = 1 << 14, 300, 1024
+    plan = Plan(N, K, N // M, "iter", "fp64", max_signals=2)
+    xs = np.stack([siggen.exact_signal(N, K, s, mag=(1, 10))[0] for s in (1, 2)])
+    wide = np.zeros((2, N + 96), np.complex128)
+    wide[:, :N] = xs
+    xt = torch.from_numpy(wide).cuda()[:, :N]
+    out = plan.exact(xt, 4 * M)
+    torch.cuda.synchronize()
+    for b in range(2):
+        oi, _, _ = orc.exact(xs[b], M, 4, orc.ITER, **_tol_of(plan), cap=4 * M)
+        gi = np.sort(out.idx[b, :int(out.count[b])].cpu().numpy())
+        np.testing.assert_array_equal(gi, oi)
