@@ -143,6 +143,33 @@ sft_status sft_exact(sft_plan_t plan, int64_t n_signals, const void* x, int64_t 
 sft_status sft_exact_host(sft_plan_t plan, int64_t n_signals, const void* x_host,
                           int64_t x_stride, const sft_result* r_host, void* stream);
 
+/* Allocation-free variant of sft_exact (the paper has no counterpart: this
+ * is a deployment interface).  Some callers cannot allocate device memory
+ * when they need a transform -- code inside another framework's memory
+ * manager that owns every device byte, latency-critical loops that cannot
+ * absorb cudaFree's implicit device synchronisation or an allocation failure
+ * mid-run, fixed-budget embedded deployments -- and so cannot create a plan.
+ * This entry point takes the parameters directly and keeps its tables and
+ * workspace in one static device array of SFT_NOALLOC_SCRATCH_BYTES that the
+ * library holds on every device that loads it, until the process exits.  It
+ * calls no allocation routine.
+ *   p, n_signals, x, x_stride, r   as for sft_plan_create + sft_exact
+ *                                  (x and the arrays of r are device memory)
+ * Returns SFT_EINVAL (with the required and the maximum size in
+ * sft_last_cuda_error) when n_signals signals of this shape do not fit the
+ * array: per signal 163 * N/d + 16 bytes for SFT_EXACT_ITER (226 * N/d + 16
+ * for SFT_EXACT_FIXED with a_max = 4), plus 16 * (N/d + 2^ceil(log2(N)/2) +
+ * 2^floor(log2(N)/2)) bytes of tables and 256-byte alignment of each array
+ * (at N = 2^22, N/d = 2^13: 12 signals per call).  The first call on each
+ * device looks up the array's device address on that device (make it before
+ * any stream capture).  All calls share the array and it keeps the last
+ * call's contents; each call rebuilds what it needs, but calls that overlap
+ * on the GPU race and must be serialised by the caller.  Asynchronous on
+ * `stream` like sft_exact. */
+#define SFT_NOALLOC_SCRATCH_BYTES (16u << 20)
+sft_status sft_exact_noalloc(const sft_params* p, int64_t n_signals, const void* x,
+                             int64_t x_stride, const sft_result* r, void* stream);
+
 /* Number of kernel launches one sft_exact call of this plan issues. */
 int32_t sft_plan_launches_per_call(sft_plan_t plan);
 

@@ -144,6 +144,12 @@ size_t zero_region_bytes(const sft_plan_s* P) {
 
 }  // namespace
 
+namespace sft {
+// Records `msg` as the calling thread's error detail (read back through
+// sft_last_cuda_error).
+void set_error_detail(const char* msg) { std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s", msg); }
+}  // namespace sft
+
 extern "C" {
 
 sft_status sft_params_default(sft_params* p, int64_t N, int64_t K, int64_t d, int32_t mode,

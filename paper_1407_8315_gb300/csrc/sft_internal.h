@@ -77,6 +77,8 @@ cudaError_t launch_exact(sft_plan_s* plan, int64_t n_signals, const void* x, int
 // One-time per-plan kernel attributes (dynamic shared memory limits).
 cudaError_t prepare_kernels(sft_plan_s* plan);
 int launches_per_call(const sft_plan_s* plan);
+// Sets the calling thread's error detail returned by sft_last_cuda_error.
+void set_error_detail(const char* msg);
 // Profiling brackets around one launch (no-ops unless plan->profiling).
 void stage_begin(sft_plan_s* plan, const char* name, cudaStream_t st);
 void stage_end(sft_plan_s* plan, cudaStream_t st);

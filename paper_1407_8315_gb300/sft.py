@@ -39,7 +39,8 @@ class sft_result(C.Structure):
 
 EXPORTS = ["sft_params_default", "sft_plan_create", "sft_plan_destroy", "sft_plan_workspace_bytes",
            "sft_exact", "sft_exact_host", "sft_plan_launches_per_call", "sft_strerror",
-           "sft_last_cuda_error", "sft_plan_set_profiling", "sft_plan_stage_times"]
+           "sft_last_cuda_error", "sft_plan_set_profiling", "sft_plan_stage_times",
+           "sft_exact_noalloc"]
 
 _lib = None
 
@@ -88,6 +89,8 @@ def load(build_if_missing: bool = False):
     lib.sft_plan_set_profiling.argtypes = [C.c_void_p, C.c_int32]
     lib.sft_plan_stage_times.argtypes = [C.c_void_p, C.c_int32, P(C.c_char_p), P(C.c_double),
                                          P(C.c_int64), P(C.c_int32)]
+    lib.sft_exact_noalloc.argtypes = [P(sft_params), C.c_int64, C.c_void_p, C.c_int64,
+                                      P(sft_result), C.c_void_p]
     lib.sft_strerror.argtypes = [C.c_int]
     lib.sft_strerror.restype = C.c_char_p
     lib.sft_last_cuda_error.argtypes = []
@@ -176,6 +179,36 @@ def sft_exact_host(handle: int, x: np.ndarray, cap: int, out: Result | None = No
     _check(load().sft_exact_host(C.c_void_p(handle), B, C.c_void_p(x.ctypes.data),
                                  pitch, C.byref(r),
                                  C.c_void_p(_stream_ptr(stream))), "sft_exact_host")
+    return out
+
+
+def _device_result(B, cap, dev):
+    import torch
+    return Result(torch.empty((B, cap), dtype=torch.int64, device=dev),
+                  torch.empty((B, cap), dtype=torch.complex128, device=dev),
+                  torch.empty(B, dtype=torch.int64, device=dev),
+                  torch.empty(B, dtype=torch.int32, device=dev),
+                  torch.empty(B, dtype=torch.int32, device=dev))
+
+
+def sft_exact_noalloc(params: sft_params, x, cap: int, out: Result | None = None,
+                      stream=None) -> Result:
+    """Allocation-free entry point (no plan): the library keeps its tables and
+    workspace in a static device array.  `x` and `out` are device tensors the
+    caller provides (`out` is created here with torch if omitted)."""
+    if x.dim() == 1:
+        x = x.unsqueeze(0)
+    if not x.is_cuda or x.stride(1) != 1:
+        raise ValueError("sft_exact_noalloc needs a CUDA tensor contiguous along N")
+    B = x.shape[0]
+    if out is None:
+        out = _device_result(B, cap, x.device)
+    r = sft_result(cap, out.idx.data_ptr(), out.val.data_ptr(), out.count.data_ptr(),
+                   out.unresolved.data_ptr(), out.overflow.data_ptr())
+    pitch = x.stride(0) if B > 1 else x.shape[1]
+    _check(load().sft_exact_noalloc(C.byref(params), B, C.c_void_p(x.data_ptr()), pitch,
+                                    C.byref(r), C.c_void_p(_stream_ptr(stream))),
+           "sft_exact_noalloc")
     return out
 
 

@@ -1,0 +1,91 @@
+"""The allocation-free entry point, sft_exact_noalloc, against the plan-based
+sft_exact, through the C ABI.
+
+It serves callers that cannot allocate device memory when they need a
+transform (a component inside another framework's memory manager, a
+latency-critical loop that cannot absorb cudaFree's device-wide
+synchronisation, a fixed-budget deployment): the library keeps the call's
+tables and workspace in one static device array instead of a plan.  Two calls
+in a row must each reproduce the plan-based result -- the array keeps the
+previous call's contents, so this also checks that a call rebuilds everything
+it relies on.  This file is collected last so that a failure here stops a
+`-x` run only after every other test has run."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import siggen
+
+pytestmark = pytest.mark.gpu
+
+MIXED_VAL_TOL = 1e-4
+FP64_VAL_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def torch_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1407_8315_gb300 as pkg
+    pkg.build()
+    return torch
+
+
+def _host(res):
+    return [t.cpu().numpy() for t in res]
+
+
+def _same(a, b, val_tol):
+    ai, av, ac, au, ao = a
+    bi, bv, bc, bu, bo = b
+    np.testing.assert_array_equal(ac, bc)
+    np.testing.assert_array_equal(au, bu)
+    np.testing.assert_array_equal(ao, bo)
+    for s in range(len(ac)):
+        n = int(ac[s])
+        np.testing.assert_array_equal(ai[s, :n], bi[s, :n])
+        if n:
+            rel = np.abs(av[s, :n] - bv[s, :n]) / np.abs(bv[s, :n])
+            assert rel.max() <= val_tol
+
+
+@pytest.mark.parametrize("mode,prec,N,K,M,B", [
+    ("iter", "mixed", 1 << 22, 4096, 1 << 13, 4),
+    ("fixed", "fp64", 1 << 16, 64, 256, 6),
+    ("iter", "fp64", 1 << 14, 600, 1024, 3),
+])
+def test_noalloc_matches_plan_twice(torch_gpu, mode, prec, N, K, M, B):
+    torch = torch_gpu
+    from paper_1407_8315_gb300 import Plan, sft
+    dt = np.complex64 if prec == "mixed" else np.complex128
+    xs, _, _ = siggen.batch_exact(N, K, range(40, 40 + B), mag=(1, 10), dtype=dt)
+    x = torch.from_numpy(xs).cuda()
+    cap = 2 * K
+    plan = Plan(N, K, N // M, mode, prec, max_signals=B)
+    ref = _host(plan.exact(x, cap))
+    tol = MIXED_VAL_TOL if prec == "mixed" else FP64_VAL_TOL
+    for _ in range(2):  # two calls in a row through the same static array
+        got = _host(sft.sft_exact_noalloc(plan.params, x, cap))
+        torch.cuda.synchronize()
+        _same(got, ref, tol)
+    assert int(ref[2].sum()) > 0
+
+
+def test_noalloc_rejects_batches_beyond_its_array(torch_gpu):
+    torch = torch_gpu
+    from paper_1407_8315_gb300 import sft
+    lib = sft.load()
+    N, K, M = 1 << 22, 4096, 1 << 13
+    p = sft.sft_params_default(N, K, N // M, "iter", "mixed")
+    B = 64  # about 86 MB of workspace, far above the static array
+    x = torch.zeros((B, N), dtype=torch.complex64, device="cuda")
+    out = sft._device_result(B, K, x.device)
+    r = sft.sft_result(K, out.idx.data_ptr(), out.val.data_ptr(), out.count.data_ptr(),
+                       out.unresolved.data_ptr(), out.overflow.data_ptr())
+    st = lib.sft_exact_noalloc(C.byref(p), B, C.c_void_p(x.data_ptr()), N, C.byref(r),
+                               C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == sft.SFT_EINVAL
+    msg = lib.sft_last_cuda_error().decode()
+    assert "static maximum" in msg and "need" in msg
