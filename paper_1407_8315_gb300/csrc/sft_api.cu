@@ -61,9 +61,7 @@ cudaError_t dalloc(T** ptr, size_t count, size_t* total) {
 }
 
 void free_plan_memory(sft_plan_s* P) {
-  void* ptrs[] = {P->tab.om_hi, P->tab.om_lo, P->tab.tw, P->ws.held[0], P->ws.held[1],
-                  P->ws.T[0], P->ws.T[1], P->ws.zero_base, P->ws.slot_s, P->ws.slot_p,
-                  P->x_stage, P->r_stage};
+  void* ptrs[] = {P->tab.om_hi, P->tab.om_lo, P->tab.tw, P->ws_base, P->x_stage, P->r_stage};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -116,30 +114,14 @@ cudaError_t upload_tables(sft_plan_s* P, size_t* total) {
 }
 
 cudaError_t alloc_workspace(sft_plan_s* P, size_t* total) {
-  const int64_t B = P->max_signals, M0 = P->M0;
-  sft::Workspace& W = P->ws;
-  W.held_elems = P->p.mode == SFT_EXACT_FIXED ? 2 * P->p.a_max * M0 : 2 * M0;
-  cudaError_t e;
-  for (int i = 0; i < 2; ++i) {
-    if (i == 1 && P->p.mode == SFT_EXACT_FIXED) break;  // FIXED uses one buffer
-    if ((e = dalloc(&W.held[i], (size_t)(B * W.held_elems), total)) != cudaSuccess) return e;
-    if ((e = dalloc(&W.T[i], (size_t)(B * M0), total)) != cudaSuccess) return e;
-  }
-  // zeroed per call: ymax2 [B] | flags [B] (8-byte slots) | slot_cnt [B*M0]
-  const size_t zbytes = (size_t)B * 16 + (size_t)(B * M0);
-  char* z;
-  if ((e = dalloc(&z, zbytes, total)) != cudaSuccess) return e;
-  W.zero_base = z;
-  W.ymax2 = reinterpret_cast<unsigned long long*>(z);
-  W.flags = reinterpret_cast<int32_t*>(z + (size_t)B * 8);
-  W.slot_cnt = reinterpret_cast<uint8_t*>(z + (size_t)B * 16);
-  if ((e = dalloc(&W.slot_s, (size_t)(B * M0 * 4), total)) != cudaSuccess) return e;
-  if ((e = dalloc(&W.slot_p, (size_t)(B * M0 * 4), total)) != cudaSuccess) return e;
+  const size_t bytes =
+      sft::layout_workspace(nullptr, nullptr, P->max_signals, P->M0, P->p.mode, P->p.a_max);
+  char* base = nullptr;
+  cudaError_t e = dalloc(&base, bytes, total);
+  if (e != cudaSuccess) return e;
+  P->ws_base = base;
+  sft::layout_workspace(&P->ws, base, P->max_signals, P->M0, P->p.mode, P->p.a_max);
   return cudaSuccess;
-}
-
-size_t zero_region_bytes(const sft_plan_s* P) {
-  return (size_t)P->max_signals * 16 + (size_t)(P->max_signals * P->M0);
 }
 
 }  // namespace
@@ -235,7 +217,7 @@ sft_status sft_exact(sft_plan_t P, int64_t n, const void* x, int64_t x_stride,
   sft_status st = check_call(P, n, x, x_stride, r);
   if (st != SFT_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemsetAsync(P->ws.zero_base, 0, zero_region_bytes(P), s);
+  cudaError_t e = cudaMemsetAsync(P->ws.zero_base, 0, P->ws.zero_bytes, s);
   if (e == cudaSuccess) e = sft::launch_exact(P, n, x, x_stride, r, s);
   if (e != cudaSuccess) {
     note_cuda(e);
@@ -291,7 +273,7 @@ sft_status sft_exact_host(sft_plan_t P, int64_t n, const void* x_host, int64_t x
   rd.count = reinterpret_cast<int64_t*>(rs + (size_t)n * cap * 24);
   rd.unresolved = reinterpret_cast<int32_t*>(rs + (size_t)n * cap * 24 + (size_t)n * 8);
   rd.overflow = reinterpret_cast<int32_t*>(rs + (size_t)n * cap * 24 + (size_t)n * 12);
-  if (e == cudaSuccess) e = cudaMemsetAsync(P->ws.zero_base, 0, zero_region_bytes(P), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->ws.zero_base, 0, P->ws.zero_bytes, s);
   if (e == cudaSuccess) e = sft::launch_exact(P, n, P->x_stage, P->p.N, &rd, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(rh->idx, rd.idx, (size_t)n * cap * 8, cudaMemcpyDeviceToHost, s);

@@ -1,5 +1,5 @@
 // sft_decode.cuh -- per-bin syndrome decoding in FP64 (Sec. II-B, the SynDec
-// function of Algorithm 1), run by one thread per bin.
+// function of Algorithm 1), one thread per (active) bin.
 //
 // Given n_m >= 2a syndromes m_i = sum_j p_j z_j^i of bin k (Eq. (3)):
 //  (i)   solve the a x a Hankel system sum_j c_j m_{i+j} = -m_{a+i}
@@ -12,11 +12,50 @@
 //        squares sense (normal equations).
 // Accept iff every root lies within root_tol of omega^{s_j}, the s_j are
 // distinct, every |p_j| > theta and ||m - Z p||_inf <= res_tol ||m||_inf.
+//
+// GB300 executes FP64 at a small fraction of its FP32 rate, so the FP64
+// work per bin is kept lean: magnitudes are compared squared (no hypot),
+// complex quotients use one reciprocal, the candidate index of a root comes
+// from an FP32 angle unless that angle lies near the midpoint of two
+// candidates (then the FP64 formula decides, as in the oracle), and cube
+// roots are an FP32 estimate polished by FP64 Newton steps (any cube root
+// gives the same three roots of the cubic).
 #pragma once
 
 #include "sft_common.cuh"
 
 namespace sft {
+
+__device__ __forceinline__ cdbl crcp(cdbl b) {
+  const double inv = 1.0 / norm2(b);
+  return cdbl{b.x * inv, -b.y * inv};
+}
+__device__ __forceinline__ cdbl csqrt_fast(cdbl v) {
+  const double r = sqrt(norm2(v));
+  if (r == 0.0) return cdbl{0.0, 0.0};
+  if (v.x >= 0.0) {
+    const double t = sqrt(0.5 * (r + v.x));
+    return cdbl{t, v.y * (0.5 / t)};
+  }
+  const double t = sqrt(0.5 * (r - v.x));
+  return cdbl{fabs(v.y) * (0.5 / t), copysign(t, v.y)};
+}
+// a cube root of v: FP32 polar estimate, two FP64 Newton steps
+// u <- (2u + v / u^2) / 3
+__device__ __forceinline__ cdbl ccbrt_any(cdbl v) {
+  if (v.x == 0.0 && v.y == 0.0) return cdbl{0.0, 0.0};
+  const float rf = cbrtf((float)sqrt(norm2(v)));
+  const float th = atan2f((float)v.y, (float)v.x) * (1.0f / 3.0f);
+  float sf, cf;
+  sincosf(th, &sf, &cf);
+  cdbl u{(double)(rf * cf), (double)(rf * sf)};
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const cdbl u2 = u * u;
+    u = (u * 2.0 + v * crcp(u2)) * (1.0 / 3.0);
+  }
+  return u;
+}
 
 // Gaussian elimination with partial pivoting on an n x n system (n <= 4).
 // A is row-major and destroyed.  Fails on a pivot below 1e-14 of max |A|.
@@ -26,40 +65,40 @@ __device__ __forceinline__ bool solve_small(cdbl* A, cdbl* b, cdbl* x) {
 #pragma unroll
   for (int i = 0; i < n * n; ++i) amax2 = fmax(amax2, norm2(A[i]));
   if (!(amax2 > 0.0)) return false;
+  cdbl inv[n];
 #pragma unroll
   for (int col = 0; col < n; ++col) {
     int piv = col;
     double best = norm2(A[col * n + col]);
 #pragma unroll
     for (int r = col + 1; r < n; ++r) {
-      double v = norm2(A[r * n + col]);
+      const double v = norm2(A[r * n + col]);
       if (v > best) {
         best = v;
         piv = r;
       }
     }
     if (!(best > 1e-28 * amax2)) return false;
-    // swap rows col and piv (predicated moves keep the indexing static)
 #pragma unroll
     for (int r = col + 1; r < n; ++r) {
       if (r == piv) {
 #pragma unroll
         for (int c = 0; c < n; ++c) {
-          cdbl t = A[col * n + c];
+          const cdbl t = A[col * n + c];
           A[col * n + c] = A[r * n + c];
           A[r * n + c] = t;
         }
-        cdbl t = b[col];
+        const cdbl t = b[col];
         b[col] = b[r];
         b[r] = t;
       }
     }
-    const cdbl dv = A[col * n + col];
+    inv[col] = crcp(A[col * n + col]);
 #pragma unroll
     for (int r = col + 1; r < n; ++r) {
-      cdbl f = cdivd(A[r * n + col], dv);
+      const cdbl f = A[r * n + col] * inv[col];
 #pragma unroll
-      for (int c = col; c < n; ++c) A[r * n + c] = A[r * n + c] - f * A[col * n + c];
+      for (int c = col + 1; c < n; ++c) A[r * n + c] = A[r * n + c] - f * A[col * n + c];
       b[r] = b[r] - f * b[col];
     }
   }
@@ -68,7 +107,7 @@ __device__ __forceinline__ bool solve_small(cdbl* A, cdbl* b, cdbl* x) {
     cdbl acc = b[r];
 #pragma unroll
     for (int c = r + 1; c < n; ++c) acc = acc - A[r * n + c] * x[c];
-    x[r] = cdivd(acc, A[r * n + r]);
+    x[r] = acc * inv[r];
   }
   return true;
 }
@@ -76,15 +115,15 @@ __device__ __forceinline__ bool solve_small(cdbl* A, cdbl* b, cdbl* x) {
 // z^2 + b z + c = 0 in the cancellation-free form q = -(b + sgn sqrt(D))/2,
 // roots q and c/q.
 __device__ __forceinline__ void quad_roots(cdbl b, cdbl c, cdbl* z) {
-  cdbl sq = csqrtd(b * b - c * 4.0);
-  cdbl qp = b + sq, qm = b - sq;
-  cdbl q = (norm2(qp) >= norm2(qm) ? qp : qm) * -0.5;
+  const cdbl sq = csqrt_fast(b * b - c * 4.0);
+  const cdbl qp = b + sq, qm = b - sq;
+  const cdbl q = (norm2(qp) >= norm2(qm) ? qp : qm) * -0.5;
   if (q.x == 0.0 && q.y == 0.0) {
     z[0] = z[1] = mk(0.0, 0.0);
     return;
   }
   z[0] = q;
-  z[1] = cdivd(c, q);
+  z[1] = c * crcp(q);
 }
 
 // z^3 + c2 z^2 + c1 z + c0 = 0: shift z = y - c2/3 to y^3 + p y + q = 0;
@@ -94,14 +133,15 @@ __device__ __forceinline__ void cubic_roots(cdbl c2, cdbl c1, cdbl c0, cdbl* z) 
   const cdbl sh = c2 * (1.0 / 3.0);
   const cdbl p = c1 - c2 * c2 * (1.0 / 3.0);
   const cdbl q = c2 * c2 * c2 * (2.0 / 27.0) - c2 * c1 * (1.0 / 3.0) + c0;
-  const cdbl sD = csqrtd(q * q * 0.25 + p * p * p * (1.0 / 27.0));
+  const cdbl sD = csqrt_fast(q * q * 0.25 + p * p * p * (1.0 / 27.0));
   const cdbl w1 = q * -0.5 + sD, w2 = q * -0.5 - sD;
-  const cdbl u = ccbrtd(norm2(w1) >= norm2(w2) ? w1 : w2);
-  const cdbl br[3] = {mk(1.0, 0.0), mk(-0.5, 0.86602540378443864676), mk(-0.5, -0.86602540378443864676)};
+  const cdbl u = ccbrt_any(norm2(w1) >= norm2(w2) ? w1 : w2);
+  const cdbl br[3] = {mk(1.0, 0.0), mk(-0.5, 0.86602540378443864676),
+                      mk(-0.5, -0.86602540378443864676)};
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    cdbl uj = u * br[j];
-    cdbl vj = (uj.x == 0.0 && uj.y == 0.0) ? mk(0.0, 0.0) : cdivd(-p, uj * 3.0);
+    const cdbl uj = u * br[j];
+    const cdbl vj = (uj.x == 0.0 && uj.y == 0.0) ? mk(0.0, 0.0) : (-p) * crcp(uj * 3.0);
     z[j] = uj + vj - sh;
   }
 }
@@ -125,13 +165,13 @@ __device__ __forceinline__ void quartic_roots(cdbl c3, cdbl c2, cdbl c1, cdbl c0
   if (m.x == 0.0 && m.y == 0.0) {
     cdbl w[2];
     quad_roots(p, r, w);
-    y[0] = csqrtd(w[0]);
+    y[0] = csqrt_fast(w[0]);
     y[1] = -y[0];
-    y[2] = csqrtd(w[1]);
+    y[2] = csqrt_fast(w[1]);
     y[3] = -y[2];
   } else {
-    const cdbl s = csqrtd(m * 2.0);
-    const cdbl qs = cdivd(q, s * 2.0);
+    const cdbl s = csqrt_fast(m * 2.0);
+    const cdbl qs = q * crcp(s * 2.0);
     quad_roots(-s, p * 0.5 + m + qs, y);
     quad_roots(s, p * 0.5 + m - qs, y + 2);
   }
@@ -144,112 +184,171 @@ struct BinGeom {
   OmegaTab om;
 };
 
-struct Tol {
-  double theta, root_tol, res_tol;
+// Thresholds, squared: theta^2, root_tol^2, res_tol^2.
+struct Tol2 {
+  double theta2, root2, res2;
 };
 
-// Decode bin k with `a` aliases from m[0..nm).  On success fills s[0..a)
-// (ascending), p[0..a) and returns true.
-template <int a>
-__device__ __forceinline__ bool decode_bin(const cdbl* m, int nm, int64_t k, const BinGeom& g,
-                                           const Tol& tol, int64_t* s, cdbl* p) {
-  cdbl H[a * a], rhs[a], c[a];
-#pragma unroll
-  for (int i = 0; i < a; ++i) {
-#pragma unroll
-    for (int j = 0; j < a; ++j) H[i * a + j] = m[i + j];
-    rhs[i] = -m[a + i];
-  }
-  if (!solve_small<a>(H, rhs, c)) return false;
-
-  cdbl z[4];
-  if constexpr (a == 1) {
-    z[0] = -c[0];
-  } else if constexpr (a == 2) {
-    quad_roots(c[1], c[0], z);
-  } else if constexpr (a == 3) {
-    cubic_roots(c[2], c[1], c[0], z);
+// Location of root z: the member k + tM of S_k nearest to it, i.e.
+// t = round((arg(z) N / (2 pi) - k) / M) mod d.  The FP32 estimate is exact
+// unless it falls within its error bound of a midpoint; then the oracle's
+// FP64 formula decides.
+__device__ __forceinline__ int64_t snap_root(cdbl z, int64_t k, const BinGeom& g) {
+  const float inv2pi = 0.15915494309189533577f;
+  const float ang = atan2f((float)z.y, (float)z.x);
+  const float df = (float)g.d;
+  const float q = fmaf(ang, df * inv2pi, -(float)k / (float)g.M);
+  const float fr = q - rintf(q);
+  const float margin = fmaxf(1e-3f, 8e-7f * df);
+  double tf;
+  if (fabsf(fabsf(fr) - 0.5f) < margin) {
+    const double pos = atan2(z.y, z.x) * 0.15915494309189533577 * (double)g.N;
+    tf = rint((pos - (double)k) / (double)g.M);
   } else {
-    quartic_roots(c[3], c[2], c[1], c[0], z);
+    tf = (double)rintf(q);
   }
+  int64_t t = ((int64_t)tf) % g.d;
+  if (t < 0) t += g.d;
+  return k + t * g.M;
+}
 
-  const double inv2pi = 0.15915494309189533577;  // 1 / (2 pi)
+// Decode bin k with `a` aliases from m[0..nm).  On success fills s[0..a)
+// (ascending), p[0..a), replaces m[0..nm) by the residual m - Z p and
+// returns true; on failure m is unchanged.
+template <int a, int nm>
+__device__ __forceinline__ bool decode_bin(cdbl* m, int64_t k, const BinGeom& g, const Tol2& tol,
+                                           int64_t* s, cdbl* p) {
+  static_assert(nm >= 2 * a && nm <= 8, "need 2a <= nm <= 8 syndromes");
+  if constexpr (a == 1) {
+    // c_0 = -m_1 / m_0, the single root z = m_1 / m_0 (Sec. II-A)
+    if (m[0].x == 0.0 && m[0].y == 0.0) return false;
+    const cdbl z = m[1] * crcp(m[0]);
+    if (!(isfinite(z.x) && isfinite(z.y)) || (z.x == 0.0 && z.y == 0.0)) return false;
+    s[0] = snap_root(z, k, g);
+    const cdbl w = omega_pow(g.om, s[0]);
+    if (!(norm2(z - w) <= tol.root2)) return false;
+    // least squares over all equations: Z^H Z = nm, p = (1/nm) sum conj(w^i) m_i
+    cdbl acc = m[0], wp = w;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    if (j < a) {
+    for (int i = 1; i < nm; ++i) {
+      acc = acc + conjd(wp) * m[i];
+      wp = wp * w;
+    }
+    p[0] = acc * (1.0 / (double)nm);
+    if (!(norm2(p[0]) > tol.theta2)) return false;
+    double mmax2 = 0.0, rmax2 = 0.0;
+    cdbl r[nm];
+    wp = mk(1.0, 0.0);
+#pragma unroll
+    for (int i = 0; i < nm; ++i) {
+      r[i] = m[i] - p[0] * wp;
+      wp = wp * w;
+      mmax2 = fmax(mmax2, norm2(m[i]));
+      rmax2 = fmax(rmax2, norm2(r[i]));
+    }
+    if (!(rmax2 <= tol.res2 * mmax2)) return false;
+#pragma unroll
+    for (int i = 0; i < nm; ++i) m[i] = r[i];
+    return true;
+  } else {
+    cdbl H[a * a], rhs[a], c[a];
+#pragma unroll
+    for (int i = 0; i < a; ++i) {
+#pragma unroll
+      for (int j = 0; j < a; ++j) H[i * a + j] = m[i + j];
+      rhs[i] = -m[a + i];
+    }
+    if (!solve_small<a>(H, rhs, c)) return false;
+
+    cdbl z[4];
+    if constexpr (a == 2) {
+      quad_roots(c[1], c[0], z);
+    } else if constexpr (a == 3) {
+      cubic_roots(c[2], c[1], c[0], z);
+    } else {
+      quartic_roots(c[3], c[2], c[1], c[0], z);
+    }
+    cdbl w[a];
+#pragma unroll
+    for (int j = 0; j < a; ++j) {
       if (!(isfinite(z[j].x) && isfinite(z[j].y)) || (z[j].x == 0.0 && z[j].y == 0.0)) return false;
-      const double pos = atan2(z[j].y, z[j].x) * inv2pi * (double)g.N;
-      const double tf = rint((pos - (double)k) / (double)g.M);
-      int64_t t = ((int64_t)tf) % g.d;
-      if (t < 0) t += g.d;
-      s[j] = k + t * g.M;
-      const cdbl w = omega_pow(g.om, s[j]);
-      if (!(absd(z[j] - w) <= tol.root_tol)) return false;
+      s[j] = snap_root(z[j], k, g);
+      w[j] = omega_pow(g.om, s[j]);
+      if (!(norm2(z[j] - w[j]) <= tol.root2)) return false;
     }
-  }
-  // ascending (4-input sorting network; unused slots sort last), distinct
-#pragma unroll
-  for (int j = 0; j < 4; ++j)
-    if (j >= a) s[j] = INT64_MAX;
-  auto cswap = [](int64_t& u, int64_t& v) {
-    if (u > v) {
-      int64_t t = u;
-      u = v;
-      v = t;
-    }
-  };
-  cswap(s[0], s[1]);
-  cswap(s[2], s[3]);
-  cswap(s[0], s[2]);
-  cswap(s[1], s[3]);
-  cswap(s[1], s[2]);
-#pragma unroll
-  for (int j = 1; j < 4; ++j)
-    if (j < a && s[j] == s[j - 1]) return false;
-
-  // normal equations (Z^H Z) p = Z^H m over all nm equations, Z_ij = omega^{s_j i}
-  cdbl G[16], gr[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    gr[u] = mk(0.0, 0.0);
-#pragma unroll
-    for (int v = 0; v < 4; ++v) G[u * 4 + v] = mk(0.0, 0.0);
-  }
-  for (int i = 0; i < nm; ++i) {
-    cdbl zi[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (j < a) zi[j] = omega_pow(g.om, s[j] * (int64_t)i);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (u < a) {
-        gr[u] = gr[u] + conjd(zi[u]) * m[i];
-#pragma unroll
-        for (int v = 0; v < 4; ++v)
-          if (v < a) G[u * 4 + v] = G[u * 4 + v] + conjd(zi[u]) * zi[v];
+    // ascending locations (sorting network on (s, w) pairs), distinct
+    auto cswap = [&](int u, int v) {
+      if (s[u] > s[v]) {
+        const int64_t ts = s[u];
+        s[u] = s[v];
+        s[v] = ts;
+        const cdbl tw = w[u];
+        w[u] = w[v];
+        w[v] = tw;
       }
+    };
+    if constexpr (a == 2) {
+      cswap(0, 1);
+    } else if constexpr (a == 3) {
+      cswap(0, 1);
+      cswap(1, 2);
+      cswap(0, 1);
+    } else {
+      cswap(0, 1);
+      cswap(2, 3);
+      cswap(0, 2);
+      cswap(1, 3);
+      cswap(1, 2);
     }
-  }
-  cdbl Gs[a * a];
 #pragma unroll
-  for (int u = 0; u < a; ++u)
-#pragma unroll
-    for (int v = 0; v < a; ++v) Gs[u * a + v] = G[u * 4 + v];
-  if (!solve_small<a>(Gs, gr, p)) return false;
+    for (int j = 1; j < a; ++j)
+      if (s[j] == s[j - 1]) return false;
 
+    // normal equations (Z^H Z) p = Z^H m over all nm equations, Z_ij = w_j^i
+    cdbl G[a * a], gr[a], wp[a];
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
-    if (j < a && !(absd(p[j]) > tol.theta)) return false;
-  double mmax = 0.0, rmax = 0.0;
-  for (int i = 0; i < nm; ++i) {
-    cdbl fit = mk(0.0, 0.0);
+    for (int u = 0; u < a; ++u) {
+      gr[u] = mk(0.0, 0.0);
+      wp[u] = mk(1.0, 0.0);
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (j < a) fit = fit + p[j] * omega_pow(g.om, s[j] * (int64_t)i);
-    mmax = fmax(mmax, absd(m[i]));
-    rmax = fmax(rmax, absd(m[i] - fit));
+      for (int v = 0; v < a; ++v) G[u * a + v] = mk(0.0, 0.0);
+    }
+#pragma unroll
+    for (int i = 0; i < nm; ++i) {
+#pragma unroll
+      for (int u = 0; u < a; ++u) {
+        gr[u] = gr[u] + conjd(wp[u]) * m[i];
+#pragma unroll
+        for (int v = 0; v < a; ++v) G[u * a + v] = G[u * a + v] + conjd(wp[u]) * wp[v];
+      }
+#pragma unroll
+      for (int u = 0; u < a; ++u) wp[u] = wp[u] * w[u];
+    }
+    if (!solve_small<a>(G, gr, p)) return false;
+#pragma unroll
+    for (int j = 0; j < a; ++j)
+      if (!(norm2(p[j]) > tol.theta2)) return false;
+    double mmax2 = 0.0, rmax2 = 0.0;
+    cdbl r[nm];
+#pragma unroll
+    for (int u = 0; u < a; ++u) wp[u] = mk(1.0, 0.0);
+#pragma unroll
+    for (int i = 0; i < nm; ++i) {
+      cdbl fit = mk(0.0, 0.0);
+#pragma unroll
+      for (int j = 0; j < a; ++j) {
+        fit = fit + p[j] * wp[j];
+        wp[j] = wp[j] * w[j];
+      }
+      r[i] = m[i] - fit;
+      mmax2 = fmax(mmax2, norm2(m[i]));
+      rmax2 = fmax(rmax2, norm2(r[i]));
+    }
+    if (!(rmax2 <= tol.res2 * mmax2)) return false;
+#pragma unroll
+    for (int i = 0; i < nm; ++i) m[i] = r[i];
+    return true;
   }
-  return rmax <= tol.res_tol * mmax;
 }
 
 }  // namespace sft

@@ -5,13 +5,19 @@
 //   ITER, level l = 0 .. L-1 (M = M0 / 2^l, d = 2^l d0):
 //     k_gather_fft   shifts 2l, 2l+1:  Y_{d,j} = d FFT_M(x[n d + j])
 //                    (Alg. 1 lines 03-06), written into the level's buffer
-//     k_iter_level   one thread per bin: fold the held syndromes
+//     k_iter_fold    one thread per bin: fold the held syndromes
 //                    (Y_{2d,j}[k] = Y_{d,j}[k] + Y_{d,j}[k + M]), SubFreq on
 //                    the two new shifts (lines 17-22), the activity test
-//                    (line 09), SynDec with a = l + 1 (lines 23-35)
-//   FIXED: k_gather_fft for the 2 a_max shifts at d0, then k_fixed_decode.
+//                    (line 09); active bins are queued
+//     k_iter_decode  SynDec with a = l + 1 (lines 23-35) over the queue, so
+//                    the FP64-heavy decode runs with full warps
+//   FIXED: k_gather_fft for the 2 a_max shifts at d0, k_fixed_scan (queue
+//          the active bins), k_fixed_round for a = 1 .. a_max (the bins no
+//          smaller a decoded).
 //   k_finalize       compacts the recovered frequencies into the result.
+#include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 #include "sft_decode.cuh"
 #include "sft_fft.cuh"
@@ -32,10 +38,18 @@ __global__ void __launch_bounds__(512) k_gather_fft(
   const int M = 1 << log2M;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const typename F::In* xs = x + (int64_t)b * x_stride;
-  // x_{d,shift}[n] = x[(n d + shift) mod N]
-  for (int n = tid; n < M; n += nthr) {
-    const int64_t e = ((int64_t)n * d + shift) & (N - 1);
-    F::st(smem, M, n, F::from_in(__ldg(xs + e)));
+  // x_{d,shift}[n] = x[(n d + shift) mod N]: every load of the thread is
+  // issued before the first store (at most 16 per thread)
+  typename F::In v[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int n = tid + i * nthr;
+    if (n < M) v[i] = __ldg(xs + (((int64_t)n * d + shift) & (N - 1)));
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int n = tid + i * nthr;
+    if (n < M) F::st(smem, M, n, F::from_in(v[i]));
   }
   __syncthreads();
   cta_fft<F>(smem, log2M, log2Mt, tw, tid, nthr);
@@ -106,64 +120,102 @@ __device__ __forceinline__ void file_solution(const int64_t* s, const cdbl* p, i
   }
 }
 
+// Append (b, k) to a device queue when `pred`; one atomic per warp.  Every
+// lane of the warp must call this (inactive lanes with pred = false).
+__device__ __forceinline__ void queue_push(bool pred, int b, int k, int2* q, int* count) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned mask = __ballot_sync(0xffffffffu, pred);
+  if (mask == 0u) return;
+  const int leader = __ffs(mask) - 1;
+  int base = 0;
+  if ((int)lane == leader) base = atomicAdd(count, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (pred) q[base + __popc(mask & ((1u << lane) - 1u))] = make_int2(b, k);
+}
+
+constexpr int kFoldThreads = 256;
+constexpr int kDecThreads = 128;
+
+// Level l, phase 1, one thread per bin: fold the held syndromes, SubFreq on
+// the two new shifts, activity test (line 09), write the syndromes back and
+// queue the active bins for decoding.
 template <int A>
-__global__ void __launch_bounds__(128) k_iter_level(LevelArgs g) {
+__global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* queue, int* qcount) {
   constexpr int l = A - 1, nm = 2 * A;
   const int b = blockIdx.y;
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= g.M) return;
   const int64_t M = g.M, M0 = g.M0;
-  const double2* prev = g.prev + (int64_t)b * g.held_elems;
-  double2* cur = g.cur + (int64_t)b * g.held_elems;
-  uint8_t* cnt = g.slot_cnt + (int64_t)b * M0;
-  int64_t* ss = g.slot_s + (int64_t)b * M0 * 4;
-  double2* sp = g.slot_p + (int64_t)b * M0 * 4;
-
-  cdbl m[nm];
-  // fold the syndromes held from level l-1 (length 2M) to length M
+  const int64_t k = (int64_t)blockIdx.x * kFoldThreads + threadIdx.x;
+  bool active = false;
+  if (k < M) {
+    const double2* prev = g.prev + (int64_t)b * g.held_elems;
+    double2* cur = g.cur + (int64_t)b * g.held_elems;
+    const uint8_t* cnt = g.slot_cnt + (int64_t)b * M0;
+    const int64_t* ss = g.slot_s + (int64_t)b * M0 * 4;
+    const double2* sp = g.slot_p + (int64_t)b * M0 * 4;
+    cdbl m[nm];
+    // fold the syndromes held from level l-1 (length 2M) to length M
 #pragma unroll
-  for (int j = 0; j < 2 * l; ++j) m[j] = ld2(prev + j * 2 * M + k) + ld2(prev + j * 2 * M + k + M);
-  m[2 * l] = ld2(cur + (2 * l) * M + k);
-  m[2 * l + 1] = ld2(cur + (2 * l + 1) * M + k);
-  // SubFreq: remove every frequency recovered at earlier levels from the
-  // two new shifts; they are filed under the level-0 bins k + i M
-  if (l > 0) {
-    const int64_t nsub = M0 / M;
-    for (int64_t i = 0; i < nsub; ++i) {
-      const int64_t k0 = k + i * M;
-      const int c = cnt[k0];
-      for (int e = 0; e < c; ++e) {
-        const int64_t s = ss[k0 * 4 + e];
-        const cdbl p = ld2(sp + k0 * 4 + e);
-        m[2 * l] = m[2 * l] - p * omega_pow(g.om, s * (2 * l));
-        m[2 * l + 1] = m[2 * l + 1] - p * omega_pow(g.om, s * (2 * l + 1));
+    for (int j = 0; j < 2 * l; ++j) m[j] = ld2(prev + j * 2 * M + k) + ld2(prev + j * 2 * M + k + M);
+    m[2 * l] = ld2(cur + (2 * l) * M + k);
+    m[2 * l + 1] = ld2(cur + (2 * l + 1) * M + k);
+    // SubFreq: remove every frequency recovered at earlier levels from the
+    // two new shifts; they are filed under the level-0 bins k + u M
+    if (l > 0) {
+      const int64_t nsub = M0 / M;
+      for (int64_t u = 0; u < nsub; ++u) {
+        const int64_t k0 = k + u * M;
+        const int c = cnt[k0];
+        for (int e = 0; e < c; ++e) {
+          const int64_t sl = ss[k0 * 4 + e];
+          const cdbl p = ld2(sp + k0 * 4 + e);
+          m[2 * l] = m[2 * l] - p * omega_pow(g.om, sl * (2 * l));
+          m[2 * l + 1] = m[2 * l + 1] - p * omega_pow(g.om, sl * (2 * l + 1));
+        }
       }
     }
+    uint8_t t = 0;
+    if (l > 0) t = (uint8_t)(g.Tprev[(int64_t)b * M0 + k] | g.Tprev[(int64_t)b * M0 + k + M]);
+    const double theta2 = g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]);
+    active = t || norm2(m[2 * l]) > theta2 || norm2(m[2 * l + 1]) > theta2;
+#pragma unroll
+    for (int j = 0; j < nm; ++j) cur[j * M + k] = make_double2(m[j].x, m[j].y);
+    if (!active) g.Tcur[(int64_t)b * M0 + k] = 0;
   }
-  uint8_t t = 0;
-  if (l > 0) t = (uint8_t)(g.Tprev[(int64_t)b * M0 + k] | g.Tprev[(int64_t)b * M0 + k + M]);
-  const double theta = g.zero_tol * sqrt(__longlong_as_double((long long)g.ymax2[b]));
-  const bool active = t || absd(m[2 * l]) > theta || absd(m[2 * l + 1]) > theta;
-  if (active) {
-    BinGeom geom{g.N, M, g.d, g.om};
-    Tol tol{theta, g.root_tol, g.res_tol};
+  queue_push(active, b, (int)k, queue, qcount);
+}
+
+// Level l, phase 2: decode the queued bins with a = l + 1 (lines 23-35),
+// grid-stride over the queue so that every warp is full.
+template <int A>
+__global__ void __launch_bounds__(kDecThreads) k_iter_decode(LevelArgs g, const int2* queue,
+                                                             const int* qcount) {
+  constexpr int nm = 2 * A;
+  const int n = *qcount;
+  const Tol2 tolr{0.0, g.root_tol * g.root_tol, g.res_tol * g.res_tol};
+  const BinGeom geom{g.N, g.M, g.d, g.om};
+  for (int e = blockIdx.x * kDecThreads + threadIdx.x; e < n; e += gridDim.x * kDecThreads) {
+    const int2 q = queue[e];
+    const int b = q.x;
+    const int64_t k = q.y, M = g.M, M0 = g.M0;
+    double2* cur = g.cur + (int64_t)b * g.held_elems;
+    Tol2 tol = tolr;
+    tol.theta2 = g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]);
+    cdbl m[nm];
+#pragma unroll
+    for (int j = 0; j < nm; ++j) m[j] = ld2(cur + j * M + k);
     int64_t s[4];
     cdbl p[4];
-    if (decode_bin<A>(m, nm, k, geom, tol, s, p)) {
-      file_solution<A>(s, p, M0, cnt, ss, sp, g.flags + b);
+    uint8_t t = 1;
+    if (decode_bin<A, nm>(m, k, geom, tol, s, p)) {
+      file_solution<A>(s, p, M0, g.slot_cnt + (int64_t)b * M0, g.slot_s + (int64_t)b * M0 * 4,
+                       g.slot_p + (int64_t)b * M0 * 4, g.flags + b);
       // the recovered terms leave every syndrome held for this bin
 #pragma unroll
-      for (int j = 0; j < A; ++j)
-#pragma unroll
-        for (int i = 0; i < nm; ++i) m[i] = m[i] - p[j] * omega_pow(g.om, s[j] * i);
+      for (int j = 0; j < nm; ++j) cur[j * M + k] = make_double2(m[j].x, m[j].y);
       t = 0;
-    } else {
-      t = 1;
     }
+    g.Tcur[(int64_t)b * M0 + k] = t;
   }
-#pragma unroll
-  for (int j = 0; j < nm; ++j) cur[j * M + k] = make_double2(m[j].x, m[j].y);
-  g.Tcur[(int64_t)b * M0 + k] = t;
 }
 
 // ---------------------------------------------- non-iterative decode (FIXED)
@@ -182,49 +234,59 @@ struct FixedArgs {
   OmegaTab om;
 };
 
-template <int A>
-__device__ __forceinline__ bool try_fixed(const cdbl* m, int nm, int64_t k, const BinGeom& geom,
-                                          const Tol& tol, int64_t M0, uint8_t* cnt, int64_t* ss,
-                                          double2* sp, int32_t* flag) {
-  int64_t s[4];
-  cdbl p[4];
-  if (!decode_bin<A>(m, nm, k, geom, tol, s, p)) return false;
-  file_solution<A>(s, p, M0, cnt, ss, sp, flag);
-  return true;
+// activity of every bin (any of the 2 a_max syndromes above theta)
+template <int NM>
+__global__ void __launch_bounds__(kFoldThreads) k_fixed_scan(FixedArgs g, int2* queue, int* qcount) {
+  const int b = blockIdx.y;
+  const int64_t M = g.M;
+  const int64_t k = (int64_t)blockIdx.x * kFoldThreads + threadIdx.x;
+  bool active = false;
+  if (k < M) {
+    const double2* Y = g.Y + (int64_t)b * g.held_elems;
+    const double theta2 = g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]);
+#pragma unroll
+    for (int j = 0; j < NM; ++j) active = active || norm2(ld2(Y + j * M + k)) > theta2;
+    g.T[(int64_t)b * M + k] = 0;
+  }
+  queue_push(active, b, (int)k, queue, qcount);
 }
 
-__global__ void __launch_bounds__(128) k_fixed_decode(FixedArgs g) {
-  const int b = blockIdx.y;
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= g.M) return;
+// round a: decode the queued bins with a aliases; failures go to the next
+// round's queue, or are marked unsolved after the last round (a = a_max)
+template <int A, int NM>
+__global__ void __launch_bounds__(kDecThreads) k_fixed_round(FixedArgs g, const int2* qin,
+                                                             const int* nin, int2* qout,
+                                                             int* nout) {
+  const int n = *nin;
+  const BinGeom geom{g.N, g.M, g.d, g.om};
   const int64_t M = g.M;
-  const int nm = 2 * g.a_max;
-  const double2* Y = g.Y + (int64_t)b * g.held_elems;
-  cdbl m[8];
-  const double theta = g.zero_tol * sqrt(__longlong_as_double((long long)g.ymax2[b]));
-  bool active = false;
+  for (int e0 = blockIdx.x * kDecThreads; e0 < n; e0 += gridDim.x * kDecThreads) {
+    const int e = e0 + threadIdx.x;
+    bool fail = false;
+    int b = 0, k = 0;
+    if (e < n) {
+      const int2 q = qin[e];
+      b = q.x;
+      k = q.y;
+      const double2* Y = g.Y + (int64_t)b * g.held_elems;
+      const Tol2 tol{g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]),
+                     g.root_tol * g.root_tol, g.res_tol * g.res_tol};
+      cdbl m[NM];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    if (j < nm) {
-      m[j] = ld2(Y + j * M + k);
-      active = active || absd(m[j]) > theta;
+      for (int j = 0; j < NM; ++j) m[j] = ld2(Y + j * M + k);
+      int64_t s[4];
+      cdbl p[4];
+      if (decode_bin<A, NM>(m, k, geom, tol, s, p)) {
+        file_solution<A>(s, p, M, g.slot_cnt + (int64_t)b * M, g.slot_s + (int64_t)b * M * 4,
+                         g.slot_p + (int64_t)b * M * 4, g.flags + b);
+      } else if (qout == nullptr) {
+        g.T[(int64_t)b * M + k] = 1;
+      } else {
+        fail = true;
+      }
     }
+    if (qout != nullptr) queue_push(fail, b, k, qout, nout);
   }
-  uint8_t t = 0;
-  if (active) {
-    BinGeom geom{g.N, M, g.d, g.om};
-    Tol tol{theta, g.root_tol, g.res_tol};
-    uint8_t* cnt = g.slot_cnt + (int64_t)b * M;
-    int64_t* ss = g.slot_s + (int64_t)b * M * 4;
-    double2* sp = g.slot_p + (int64_t)b * M * 4;
-    int32_t* fl = g.flags + b;
-    bool ok = try_fixed<1>(m, nm, k, geom, tol, M, cnt, ss, sp, fl);
-    if (!ok && g.a_max >= 2) ok = try_fixed<2>(m, nm, k, geom, tol, M, cnt, ss, sp, fl);
-    if (!ok && g.a_max >= 3) ok = try_fixed<3>(m, nm, k, geom, tol, M, cnt, ss, sp, fl);
-    if (!ok && g.a_max >= 4) ok = try_fixed<4>(m, nm, k, geom, tol, M, cnt, ss, sp, fl);
-    t = ok ? 0 : 1;
-  }
-  g.T[(int64_t)b * M + k] = t;
 }
 
 // ------------------------------------------------------------- finalize
@@ -323,8 +385,8 @@ cudaError_t prepare_kernels(sft_plan_s* P) {
 }
 
 int launches_per_call(const sft_plan_s* P) {
-  if (P->p.mode == SFT_EXACT_FIXED) return 3;
-  return 2 * P->levels + 1;
+  if (P->p.mode == SFT_EXACT_FIXED) return 1 + 1 + P->p.a_max + 1;
+  return 3 * P->levels + 1;
 }
 
 static cudaEvent_t pool_event(sft_plan_s* P) {
@@ -373,6 +435,11 @@ cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
   int64_t M_last = P->M0;
   const uint8_t* T_last = W.T[0];
 
+  // grid of the grid-stride queue decoders: a few CTAs per SM
+  int dev = 0, nsm = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+
   if (P->p.mode == SFT_EXACT_FIXED) {
     const int nsh = 2 * P->p.a_max;
     if (fp64)
@@ -382,10 +449,55 @@ cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
     FixedArgs g{P->p.N, P->M0, d0, P->p.a_max, W.held[0], W.held_elems, W.T[0], W.slot_cnt,
                 W.slot_s, W.slot_p, W.ymax2, W.flags, P->p.zero_tol, P->p.root_tol,
                 P->p.res_tol, om};
-    dim3 grid((unsigned)((P->M0 + 127) / 128), (unsigned)B);
-    stage_begin(P, "decode_fixed", st);
-    k_fixed_decode<<<grid, 128, 0, st>>>(g);
+    dim3 sgrid((unsigned)((P->M0 + kFoldThreads - 1) / kFoldThreads), (unsigned)B);
+    const int64_t maxq = B * P->M0;
+    const unsigned dgrid =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>((maxq + kDecThreads - 1) / kDecThreads, 8 * nsm));
+    int2* q0 = W.queue[0];
+    int2* q1 = W.queue[1];
+    int* c = W.qcount;
+    stage_begin(P, "decode_fixed_scan", st);
+    switch (P->p.a_max) {
+      case 1: k_fixed_scan<2><<<sgrid, kFoldThreads, 0, st>>>(g, q0, c); break;
+      case 2: k_fixed_scan<4><<<sgrid, kFoldThreads, 0, st>>>(g, q0, c); break;
+      case 3: k_fixed_scan<6><<<sgrid, kFoldThreads, 0, st>>>(g, q0, c); break;
+      default: k_fixed_scan<8><<<sgrid, kFoldThreads, 0, st>>>(g, q0, c); break;
+    }
     stage_end(P, st);
+    static const char* rnames[] = {"decode_fixed_a1", "decode_fixed_a2", "decode_fixed_a3",
+                                   "decode_fixed_a4"};
+    // round a reads queue (a-1)&1 / counter a-1, writes queue a&1 / counter a
+    auto round = [&](auto a_tag, auto nm_tag) {
+      constexpr int A = decltype(a_tag)::value, NM = decltype(nm_tag)::value;
+      const bool last = A == P->p.a_max;
+      stage_begin(P, rnames[A - 1], st);
+      k_fixed_round<A, NM><<<dgrid, kDecThreads, 0, st>>>(
+          g, (A & 1) ? q0 : q1, c + (A - 1), last ? nullptr : ((A & 1) ? q1 : q0),
+          last ? nullptr : c + A);
+      stage_end(P, st);
+    };
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    using I3 = std::integral_constant<int, 3>;
+    using I4 = std::integral_constant<int, 4>;
+    switch (P->p.a_max) {
+      case 1: round(I1{}, std::integral_constant<int, 2>{}); break;
+      case 2:
+        round(I1{}, std::integral_constant<int, 4>{});
+        round(I2{}, std::integral_constant<int, 4>{});
+        break;
+      case 3:
+        round(I1{}, std::integral_constant<int, 6>{});
+        round(I2{}, std::integral_constant<int, 6>{});
+        round(I3{}, std::integral_constant<int, 6>{});
+        break;
+      default:
+        round(I1{}, std::integral_constant<int, 8>{});
+        round(I2{}, std::integral_constant<int, 8>{});
+        round(I3{}, std::integral_constant<int, 8>{});
+        round(I4{}, std::integral_constant<int, 8>{});
+        break;
+    }
   } else {
     int64_t M = P->M0, d = d0;
     for (int l = 0; l < P->levels; ++l) {
@@ -403,14 +515,28 @@ cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
       LevelArgs g{P->p.N, M, d, P->M0, prev, cur, W.held_elems, W.T[(l + 1) & 1], W.T[l & 1],
                   W.slot_cnt, W.slot_s, W.slot_p, W.ymax2, W.flags, P->p.zero_tol,
                   P->p.root_tol, P->p.res_tol, om};
-      dim3 grid((unsigned)((M + 127) / 128), (unsigned)B);
+      int2* q = W.queue[l & 1];
+      int* c = W.qcount + l;
+      dim3 fgrid((unsigned)((M + kFoldThreads - 1) / kFoldThreads), (unsigned)B);
+      const int64_t maxq = B * M;
+      const unsigned dgrid = (unsigned)std::max<int64_t>(
+          1, std::min<int64_t>((maxq + kDecThreads - 1) / kDecThreads, 8 * nsm));
+      static const char* fnames[] = {"fold_l0", "fold_l1", "fold_l2", "fold_l3"};
       static const char* dnames[] = {"decode_l0", "decode_l1", "decode_l2", "decode_l3"};
+      stage_begin(P, fnames[l], st);
+      switch (l) {
+        case 0: k_iter_fold<1><<<fgrid, kFoldThreads, 0, st>>>(g, q, c); break;
+        case 1: k_iter_fold<2><<<fgrid, kFoldThreads, 0, st>>>(g, q, c); break;
+        case 2: k_iter_fold<3><<<fgrid, kFoldThreads, 0, st>>>(g, q, c); break;
+        default: k_iter_fold<4><<<fgrid, kFoldThreads, 0, st>>>(g, q, c); break;
+      }
+      stage_end(P, st);
       stage_begin(P, dnames[l], st);
       switch (l) {
-        case 0: k_iter_level<1><<<grid, 128, 0, st>>>(g); break;
-        case 1: k_iter_level<2><<<grid, 128, 0, st>>>(g); break;
-        case 2: k_iter_level<3><<<grid, 128, 0, st>>>(g); break;
-        default: k_iter_level<4><<<grid, 128, 0, st>>>(g); break;
+        case 0: k_iter_decode<1><<<dgrid, kDecThreads, 0, st>>>(g, q, c); break;
+        case 1: k_iter_decode<2><<<dgrid, kDecThreads, 0, st>>>(g, q, c); break;
+        case 2: k_iter_decode<3><<<dgrid, kDecThreads, 0, st>>>(g, q, c); break;
+        default: k_iter_decode<4><<<dgrid, kDecThreads, 0, st>>>(g, q, c); break;
       }
       stage_end(P, st);
       M_last = M;

@@ -11,26 +11,75 @@
 
 namespace sft {
 
-// Device workspace of one plan for up to `max_signals` signals.  Per signal:
+// Device workspace of one call for up to B signals.  Per signal:
 //   held[2]   ping-pong syndrome buffers, `held_elems` double2 each
 //             (ITER level l keeps rows j < 2l+2 of length M_l; FIXED keeps
 //             2 a_max rows of length M0)
 //   T[2]      unsolved-bin flags per level, M0 bytes each
+//   queue[2]  active (signal, bin) pairs awaiting decoding, M0 int2 each
 //   slot_*    frequencies recovered so far, filed by their level-0 bin
 //             k0 = s mod M0 (at most 4 per bin): count, location, value
 //   ymax2     bit pattern of max_k |Y_{d,0}[k]|^2 (zero threshold)
 //   flags     bit 0: a level-0 bin received more than 4 frequencies
+// plus qcount[16], the queue fill counters of one call.  ymax2, flags,
+// qcount and slot_cnt form one contiguous region cleared before each call.
 struct Workspace {
   double2* held[2] = {nullptr, nullptr};
   int64_t held_elems = 0;
   uint8_t* T[2] = {nullptr, nullptr};
+  int2* queue[2] = {nullptr, nullptr};
   uint8_t* slot_cnt = nullptr;
   int64_t* slot_s = nullptr;
   double2* slot_p = nullptr;
   unsigned long long* ymax2 = nullptr;
   int32_t* flags = nullptr;
-  void* zero_base = nullptr;  // ymax2 | flags | slot_cnt, cleared per call
+  int32_t* qcount = nullptr;
+  void* zero_base = nullptr;  // ymax2 | flags | qcount | slot_cnt
+  size_t zero_bytes = 0;
 };
+
+// Lays the workspace of B signals out from `base` (or only sizes it when
+// base is null) and returns its byte size; every array is 256-byte aligned.
+inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, int mode,
+                               int a_max) {
+  auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+  const int64_t held_elems = mode == SFT_EXACT_FIXED ? 2 * a_max * M0 : 2 * M0;
+  size_t off = 0;
+  size_t o_held[2], o_T[2], o_q[2];
+  for (int i = 0; i < 2; ++i) {
+    o_held[i] = off;
+    off = al(off + (size_t)(B * held_elems) * 16);
+    o_T[i] = off;
+    off = al(off + (size_t)(B * M0));
+    o_q[i] = off;
+    off = al(off + (size_t)(B * M0) * 8);
+  }
+  const size_t o_zero = off;
+  const size_t zero_bytes = (size_t)B * 16 + 64 + (size_t)(B * M0);
+  off = al(off + zero_bytes);
+  const size_t o_ss = off;
+  off = al(off + (size_t)(B * M0 * 4) * 8);
+  const size_t o_sp = off;
+  off = al(off + (size_t)(B * M0 * 4) * 16);
+  if (W != nullptr && base != nullptr) {
+    W->held_elems = held_elems;
+    for (int i = 0; i < 2; ++i) {
+      W->held[i] = reinterpret_cast<double2*>(base + o_held[i]);
+      W->T[i] = reinterpret_cast<uint8_t*>(base + o_T[i]);
+      W->queue[i] = reinterpret_cast<int2*>(base + o_q[i]);
+    }
+    char* z = base + o_zero;
+    W->zero_base = z;
+    W->zero_bytes = zero_bytes;
+    W->ymax2 = reinterpret_cast<unsigned long long*>(z);
+    W->flags = reinterpret_cast<int32_t*>(z + (size_t)B * 8);
+    W->qcount = reinterpret_cast<int32_t*>(z + (size_t)B * 16);
+    W->slot_cnt = reinterpret_cast<uint8_t*>(z + (size_t)B * 16 + 64);
+    W->slot_s = reinterpret_cast<int64_t*>(base + o_ss);
+    W->slot_p = reinterpret_cast<double2*>(base + o_sp);
+  }
+  return off;
+}
 
 struct Tables {
   double2* om_hi = nullptr;  // omega^(i << lo_bits)
@@ -57,6 +106,7 @@ struct sft_plan_s {
   int levels = 0;  // ITER: max_iters; FIXED: 1
   sft::Tables tab;
   sft::Workspace ws;
+  void* ws_base = nullptr;  // one allocation holding the workspace
   size_t device_bytes = 0;
   // staging for the host entry point (allocated on first use)
   void* x_stage = nullptr;

@@ -143,8 +143,6 @@ extern "C" sft_status sft_exact_noalloc(const sft_params* pin, int64_t n, const 
   const int log2N = lg2(p.N);
   const int lo_bits = log2N / 2;
   const int64_t n_lo = int64_t(1) << lo_bits, n_hi = p.N >> lo_bits;
-  const int64_t held_elems = p.mode == SFT_EXACT_FIXED ? 2 * p.a_max * M0 : 2 * M0;
-  const int nheld = p.mode == SFT_EXACT_FIXED ? 1 : 2;
   size_t off = 0;
   const size_t o_lo = off;
   off = align256(off + n_lo * 16);
@@ -152,20 +150,8 @@ extern "C" sft_status sft_exact_noalloc(const sft_params* pin, int64_t n, const 
   off = align256(off + n_hi * 16);
   const size_t o_tw = off;
   off = align256(off + M0 * 16);
-  size_t o_held[2] = {0, 0}, o_T[2] = {0, 0};
-  for (int i = 0; i < nheld; ++i) {
-    o_held[i] = off;
-    off = align256(off + (size_t)(n * held_elems) * 16);
-    o_T[i] = off;
-    off = align256(off + (size_t)(n * M0));
-  }
-  const size_t o_zero = off;
-  const size_t zero_bytes = (size_t)n * 16 + (size_t)(n * M0);
-  off = align256(off + zero_bytes);
-  const size_t o_ss = off;
-  off = align256(off + (size_t)(n * M0 * 4) * 8);
-  const size_t o_sp = off;
-  off = align256(off + (size_t)(n * M0 * 4) * 16);
+  const size_t o_ws = off;
+  off += sft::layout_workspace(nullptr, nullptr, n, M0, p.mode, p.a_max);
   if (off > (size_t)SFT_NOALLOC_SCRATCH_BYTES) {
     std::snprintf(noalloc_msg(), 256,
                   "sft_exact_noalloc: %lld signals of N/d = %lld need %zu bytes of scratch; the "
@@ -195,17 +181,7 @@ extern "C" sft_status sft_exact_noalloc(const sft_params* pin, int64_t n, const 
   P.tab.om_hi = reinterpret_cast<double2*>(base + o_hi);
   P.tab.om_lo_bits = lo_bits;
   P.tab.tw = base + o_tw;
-  P.ws.held_elems = held_elems;
-  for (int i = 0; i < nheld; ++i) {
-    P.ws.held[i] = reinterpret_cast<double2*>(base + o_held[i]);
-    P.ws.T[i] = reinterpret_cast<uint8_t*>(base + o_T[i]);
-  }
-  P.ws.zero_base = base + o_zero;
-  P.ws.ymax2 = reinterpret_cast<unsigned long long*>(base + o_zero);
-  P.ws.flags = reinterpret_cast<int32_t*>(base + o_zero + (size_t)n * 8);
-  P.ws.slot_cnt = reinterpret_cast<uint8_t*>(base + o_zero + (size_t)n * 16);
-  P.ws.slot_s = reinterpret_cast<int64_t*>(base + o_ss);
-  P.ws.slot_p = reinterpret_cast<double2*>(base + o_sp);
+  sft::layout_workspace(&P.ws, base + o_ws, n, M0, p.mode, p.a_max);
 
   const int64_t nt = n_lo > n_hi ? n_lo : n_hi;
   const int64_t ntab = nt > M0 ? nt : M0;
@@ -213,7 +189,7 @@ extern "C" sft_status sft_exact_noalloc(const sft_params* pin, int64_t n, const 
       P.tab.om_lo, n_lo, P.tab.om_hi, n_hi, lo_bits, p.N, P.tab.tw, M0, fp64 ? 0 : 1);
   e = cudaGetLastError();
   // counters and thresholds that the kernels accumulate into start at zero
-  if (e == cudaSuccess) e = cudaMemsetAsync(P.ws.zero_base, 0, zero_bytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.ws.zero_base, 0, P.ws.zero_bytes, st);
   if (e == cudaSuccess) e = sft::launch_exact(&P, n, x, x_stride, r, st);
   if (e != cudaSuccess) {
     std::snprintf(noalloc_msg(), 256, "launch: %s", cudaGetErrorString(e));
