@@ -157,10 +157,11 @@ sft_status sft_exact_host(sft_plan_t plan, int64_t n_signals, const void* x_host
  *                                  (x and the arrays of r are device memory)
  * Returns SFT_EINVAL (with the required and the maximum size in
  * sft_last_cuda_error) when n_signals signals of this shape do not fit the
- * array: per signal 163 * N/d + 16 bytes for SFT_EXACT_ITER (226 * N/d + 16
- * for SFT_EXACT_FIXED with a_max = 4), plus 16 * (N/d + 2^ceil(log2(N)/2) +
- * 2^floor(log2(N)/2)) bytes of tables and 256-byte alignment of each array
- * (at N = 2^22, N/d = 2^13: 12 signals per call).  The first call on each
+ * array: per signal 179 * N/d + 16 bytes for SFT_EXACT_ITER (242 * N/d + 16
+ * for SFT_EXACT_FIXED with a_max = 4), plus 16 * (N/d + 2 * (2^ceil(log2(N)/2)
+ * + 2^floor(log2(N)/2))) bytes of tables, 64 bytes of counters and 256-byte
+ * alignment of each array (at N = 2^22, N/d = 2^13: 11 signals per call).
+ * The first call on each
  * device looks up the array's device address on that device (make it before
  * any stream capture).  All calls share the array and it keeps the last
  * call's contents; each call rebuilds what it needs, but calls that overlap

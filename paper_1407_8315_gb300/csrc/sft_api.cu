@@ -61,7 +61,8 @@ cudaError_t dalloc(T** ptr, size_t count, size_t* total) {
 }
 
 void free_plan_memory(sft_plan_s* P) {
-  void* ptrs[] = {P->tab.om_hi, P->tab.om_lo, P->tab.tw, P->ws_base, P->x_stage, P->r_stage};
+  void* ptrs[] = {P->tab.om_hi,    P->tab.om_lo,    P->tab.tw,  P->tab.om_hi_ff,
+                  P->tab.om_lo_ff, P->ws_base,      P->x_stage, P->r_stage};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -89,6 +90,22 @@ cudaError_t upload_tables(sft_plan_s* P, size_t* total) {
     return e;
   if ((e = cudaMemcpy(P->tab.om_hi, hi.data(), n_hi * sizeof(double2), cudaMemcpyHostToDevice)))
     return e;
+  if (P->p.precision != SFT_FP64) {
+    // the same omega tables split into float-float for the FP32 peels
+    auto split = [](double2 v) {
+      const float xh = (float)v.x, yh = (float)v.y;
+      return make_float4(xh, (float)(v.x - (double)xh), yh, (float)(v.y - (double)yh));
+    };
+    std::vector<float4> lof(n_lo), hif(n_hi);
+    for (int64_t i = 0; i < n_lo; ++i) lof[i] = split(lo[i]);
+    for (int64_t i = 0; i < n_hi; ++i) hif[i] = split(hi[i]);
+    if ((e = dalloc(&P->tab.om_lo_ff, n_lo, total)) != cudaSuccess) return e;
+    if ((e = dalloc(&P->tab.om_hi_ff, n_hi, total)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(P->tab.om_lo_ff, lof.data(), n_lo * sizeof(float4), cudaMemcpyHostToDevice)))
+      return e;
+    if ((e = cudaMemcpy(P->tab.om_hi_ff, hif.data(), n_hi * sizeof(float4), cudaMemcpyHostToDevice)))
+      return e;
+  }
   if (P->p.precision == SFT_FP64) {
     std::vector<double2> tw(M0);
     for (int64_t q = 0; q < M0; ++q) {

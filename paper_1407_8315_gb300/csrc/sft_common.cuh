@@ -119,6 +119,7 @@ struct F64 {
     double2 t = reinterpret_cast<const double2*>(sm)[i];
     return V{t.x, t.y};
   }
+  typedef double2 Out;
   __device__ static __forceinline__ double2 out(V v, double scale) {
     return make_double2(v.rx * scale, v.ry * scale);
   }
@@ -215,9 +216,53 @@ struct FF {
     float2 l = reinterpret_cast<const float2*>(sm)[M + i];
     return V{h.x, l.x, h.y, l.y};
   }
-  __device__ static __forceinline__ double2 out(V v, double scale) {
-    return make_double2(((double)v.rh + (double)v.rl) * scale, ((double)v.ih + (double)v.il) * scale);
+  // syndromes leave the FFT as float-float quadruples scaled by d (a power
+  // of two, so the scaling is exact and stays on the FP32 pipes)
+  typedef float4 Out;
+  __device__ static __forceinline__ float4 out(V v, float scale) {
+    return make_float4(v.rh * scale, v.rl * scale, v.ih * scale, v.il * scale);
+  }
+  __device__ static __forceinline__ float out_norm_hi(float4 o) { return o.x * o.x + o.z * o.z; }
+  __device__ static __forceinline__ V from4(float4 o) { return V{o.x, o.y, o.z, o.w}; }
+  __device__ static __forceinline__ float4 to4(V v) { return make_float4(v.rh, v.rl, v.ih, v.il); }
+  __device__ static __forceinline__ V mulv(V a, V b) { return mul4(a, b.rh, b.rl, b.ih, b.il); }
+};
+
+// Storage of held syndromes and recovered values: FP64 pairs on the plain
+// path, float-float quadruples (hi, lo of re, hi, lo of im) on the mixed path;
+// 16 bytes either way.  to_d/from_d convert for the FP64 solves.
+template <class F>
+struct Store;
+template <>
+struct Store<F64> {
+  typedef double2 T;
+  __device__ static __forceinline__ cdbl to_d(double2 v) { return cdbl{v.x, v.y}; }
+  __device__ static __forceinline__ double2 from_d(cdbl c) { return make_double2(c.x, c.y); }
+};
+template <>
+struct Store<FF> {
+  typedef float4 T;
+  __device__ static __forceinline__ cdbl to_d(float4 v) {
+    return cdbl{(double)v.x + (double)v.y, (double)v.z + (double)v.w};
+  }
+  __device__ static __forceinline__ float4 from_d(cdbl c) {
+    const float xh = (float)c.x, yh = (float)c.y;
+    return make_float4(xh, (float)(c.x - (double)xh), yh, (float)(c.y - (double)yh));
   }
 };
+
+// omega^e as a float-float product of two table entries (mixed path)
+struct OmegaTabFF {
+  const float4* hi;
+  const float4* lo;
+  int lo_bits;
+  int64_t mask;
+};
+__device__ __forceinline__ FF::V omega_ff(const OmegaTabFF& t, int64_t e) {
+  const int64_t r = e & t.mask;
+  const float4 a = __ldg(t.hi + (r >> t.lo_bits));
+  const float4 b = __ldg(t.lo + (r & ((int64_t(1) << t.lo_bits) - 1)));
+  return FF::mul4(FF::from4(a), b.x, b.y, b.z, b.w);
+}
 
 }  // namespace sft

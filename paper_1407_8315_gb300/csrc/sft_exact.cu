@@ -15,6 +15,12 @@
 //          the active bins), k_fixed_round for a = 1 .. a_max (the bins no
 //          smaller a decoded).
 //   k_finalize       compacts the recovered frequencies into the result.
+//
+// Two arithmetic flavours F (sft_common.cuh): F64 everywhere on the plain
+// path; on the mixed path (FF) the FFT, the folds, the peels and the
+// activity tests run in float-float on the FP32 pipes, held syndromes and
+// recovered values are stored as float-float, and only the per-bin solves
+// (sft_decode.cuh) run in FP64.
 #include <algorithm>
 #include <cstdio>
 #include <type_traits>
@@ -29,9 +35,10 @@ namespace sft {
 template <class F>
 __global__ void __launch_bounds__(512) k_gather_fft(
     const typename F::In* __restrict__ x, int64_t x_stride, int64_t N, int64_t d, int log2M,
-    int shift0, int log2Mt, const typename F::Tw* __restrict__ tw, double2* __restrict__ out,
+    int shift0, int log2Mt, const typename F::Tw* __restrict__ tw, void* __restrict__ out_v,
     int64_t out_sig, int64_t out_row, int row0, unsigned long long* __restrict__ ymax2) {
   extern __shared__ __align__(16) char smem[];
+  typedef typename F::Out Out;
   const int b = blockIdx.y;
   const int js = blockIdx.x;
   const int64_t shift = shift0 + js;
@@ -53,13 +60,22 @@ __global__ void __launch_bounds__(512) k_gather_fft(
   }
   __syncthreads();
   cta_fft<F>(smem, log2M, log2Mt, tw, tid, nthr);
-  double2* o = out + (int64_t)b * out_sig + (int64_t)(row0 + js) * out_row;
-  const double scale = (double)d;
+  Out* o = reinterpret_cast<Out*>(out_v) + (int64_t)b * out_sig + (int64_t)(row0 + js) * out_row;
   double lmax = 0.0;
-  for (int k = tid; k < M; k += nthr) {
-    const double2 v = F::out(F::ld(smem, M, k), scale);
-    o[k] = v;
-    lmax = fmax(lmax, v.x * v.x + v.y * v.y);
+  if constexpr (std::is_same<F, F64>::value) {
+    for (int k = tid; k < M; k += nthr) {
+      const double2 w = F::out(F::ld(smem, M, k), (double)d);
+      o[k] = w;
+      lmax = fmax(lmax, w.x * w.x + w.y * w.y);
+    }
+  } else {
+    float fmax_hi = 0.0f;
+    for (int k = tid; k < M; k += nthr) {
+      const float4 w = F::out(F::ld(smem, M, k), (float)d);
+      o[k] = w;
+      fmax_hi = fmaxf(fmax_hi, F::out_norm_hi(w));
+    }
+    lmax = (double)fmax_hi;
   }
   if (ymax2 != nullptr && shift == 0) {
     // block max of |Y_{d,0}|^2 -> per-signal atomic max on the bit pattern
@@ -70,10 +86,10 @@ __global__ void __launch_bounds__(512) k_gather_fft(
     if ((tid & 31) == 0) wmax[tid >> 5] = lmax;
     __syncthreads();
     if (tid < 32) {
-      double v = tid < (nthr >> 5) ? wmax[tid] : 0.0;
+      double w = tid < (nthr >> 5) ? wmax[tid] : 0.0;
 #pragma unroll
-      for (int o2 = 16; o2 > 0; o2 >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o2));
-      if (tid == 0) atomicMax(ymax2 + b, (unsigned long long)__double_as_longlong(v));
+      for (int o2 = 16; o2 > 0; o2 >>= 1) w = fmax(w, __shfl_xor_sync(0xffffffffu, w, o2));
+      if (tid == 0) atomicMax(ymax2 + b, (unsigned long long)__double_as_longlong(w));
     }
   }
 }
@@ -81,38 +97,34 @@ __global__ void __launch_bounds__(512) k_gather_fft(
 // ------------------------------------------------- per-level decode (ITER)
 struct LevelArgs {
   int64_t N, M, d, M0;
-  const double2* prev;  // level l-1 rows, length 2M
-  double2* cur;         // level l rows, length M
+  const void* prev;  // level l-1 rows, length 2M (Store<F>::T)
+  void* cur;         // level l rows, length M
   int64_t held_elems;
   const uint8_t* Tprev;
   uint8_t* Tcur;
   uint8_t* slot_cnt;
   int64_t* slot_s;
-  double2* slot_p;
+  void* slot_p;  // Store<F>::T
   const unsigned long long* ymax2;
   int32_t* flags;
   double zero_tol, root_tol, res_tol;
   OmegaTab om;
+  OmegaTabFF omff;
 };
-
-__device__ __forceinline__ cdbl ld2(const double2* p) {
-  double2 v = *p;
-  return mk(v.x, v.y);
-}
 
 // File the a recovered frequencies of one decode event under their level-0
 // bins (the calling thread owns every level-0 bin congruent to its bin).
-template <int A>
+template <class F, int A>
 __device__ __forceinline__ void file_solution(const int64_t* s, const cdbl* p, int64_t M0,
-                                              uint8_t* cnt, int64_t* ss, double2* sp,
-                                              int32_t* flag) {
+                                              uint8_t* cnt, int64_t* ss,
+                                              typename Store<F>::T* sp, int32_t* flag) {
 #pragma unroll
   for (int j = 0; j < A; ++j) {
     const int64_t k0 = s[j] & (M0 - 1);
     const int c = cnt[k0];
     if (c < 4) {
       ss[k0 * 4 + c] = s[j];
-      sp[k0 * 4 + c] = make_double2(p[j].x, p[j].y);
+      sp[k0 * 4 + c] = Store<F>::from_d(p[j]);
       cnt[k0] = (uint8_t)(c + 1);
     } else {
       atomicOr(flag, 1);
@@ -133,52 +145,90 @@ __device__ __forceinline__ void queue_push(bool pred, int b, int k, int2* q, int
   if (pred) q[base + __popc(mask & ((1u << lane) - 1u))] = make_int2(b, k);
 }
 
+// |m|^2 > theta^2 decided from the float-float hi parts when they are
+// clearly on one side (relative error of the hi-part norm < 1e-6), in FP64
+// otherwise -- the same decision the FP64 comparison takes.
+__device__ __forceinline__ bool above_ff(const FF::V& m, double theta2) {
+  const float nh = m.rh * m.rh + m.ih * m.ih;
+  const float t2 = (float)theta2;
+  if (nh > t2 * 1.0001f) return true;
+  if (nh < t2 * 0.9999f) return false;
+  const double x = (double)m.rh + (double)m.rl, y = (double)m.ih + (double)m.il;
+  return x * x + y * y > theta2;
+}
+
 constexpr int kFoldThreads = 256;
 constexpr int kDecThreads = 128;
 
 // Level l, phase 1, one thread per bin: fold the held syndromes, SubFreq on
 // the two new shifts, activity test (line 09), write the syndromes back and
 // queue the active bins for decoding.
-template <int A>
+template <class F, int A>
 __global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* queue, int* qcount) {
   constexpr int l = A - 1, nm = 2 * A;
+  typedef typename Store<F>::T T;
   const int b = blockIdx.y;
   const int64_t M = g.M, M0 = g.M0;
   const int64_t k = (int64_t)blockIdx.x * kFoldThreads + threadIdx.x;
   bool active = false;
   if (k < M) {
-    const double2* prev = g.prev + (int64_t)b * g.held_elems;
-    double2* cur = g.cur + (int64_t)b * g.held_elems;
+    const T* prev = reinterpret_cast<const T*>(g.prev) + (int64_t)b * g.held_elems;
+    T* cur = reinterpret_cast<T*>(g.cur) + (int64_t)b * g.held_elems;
     const uint8_t* cnt = g.slot_cnt + (int64_t)b * M0;
     const int64_t* ss = g.slot_s + (int64_t)b * M0 * 4;
-    const double2* sp = g.slot_p + (int64_t)b * M0 * 4;
-    cdbl m[nm];
-    // fold the syndromes held from level l-1 (length 2M) to length M
-#pragma unroll
-    for (int j = 0; j < 2 * l; ++j) m[j] = ld2(prev + j * 2 * M + k) + ld2(prev + j * 2 * M + k + M);
-    m[2 * l] = ld2(cur + (2 * l) * M + k);
-    m[2 * l + 1] = ld2(cur + (2 * l + 1) * M + k);
-    // SubFreq: remove every frequency recovered at earlier levels from the
-    // two new shifts; they are filed under the level-0 bins k + u M
-    if (l > 0) {
-      const int64_t nsub = M0 / M;
-      for (int64_t u = 0; u < nsub; ++u) {
-        const int64_t k0 = k + u * M;
-        const int c = cnt[k0];
-        for (int e = 0; e < c; ++e) {
-          const int64_t sl = ss[k0 * 4 + e];
-          const cdbl p = ld2(sp + k0 * 4 + e);
-          m[2 * l] = m[2 * l] - p * omega_pow(g.om, sl * (2 * l));
-          m[2 * l + 1] = m[2 * l + 1] - p * omega_pow(g.om, sl * (2 * l + 1));
-        }
-      }
-    }
+    const T* sp = reinterpret_cast<const T*>(g.slot_p) + (int64_t)b * M0 * 4;
     uint8_t t = 0;
     if (l > 0) t = (uint8_t)(g.Tprev[(int64_t)b * M0 + k] | g.Tprev[(int64_t)b * M0 + k + M]);
     const double theta2 = g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]);
-    active = t || norm2(m[2 * l]) > theta2 || norm2(m[2 * l + 1]) > theta2;
+    const int64_t nsub = M0 / M;
+    if constexpr (std::is_same<F, F64>::value) {
+      cdbl m[nm];
+      // fold the syndromes held from level l-1 (length 2M) to length M
 #pragma unroll
-    for (int j = 0; j < nm; ++j) cur[j * M + k] = make_double2(m[j].x, m[j].y);
+      for (int j = 0; j < 2 * l; ++j)
+        m[j] = Store<F>::to_d(prev[j * 2 * M + k]) + Store<F>::to_d(prev[j * 2 * M + k + M]);
+      m[2 * l] = Store<F>::to_d(cur[(2 * l) * M + k]);
+      m[2 * l + 1] = Store<F>::to_d(cur[(2 * l + 1) * M + k]);
+      // SubFreq: remove every frequency recovered at earlier levels from the
+      // two new shifts; they are filed under the level-0 bins k + u M
+      if (l > 0) {
+        for (int64_t u = 0; u < nsub; ++u) {
+          const int64_t k0 = k + u * M;
+          const int c = cnt[k0];
+          for (int e = 0; e < c; ++e) {
+            const int64_t sl = ss[k0 * 4 + e];
+            const cdbl p = Store<F>::to_d(sp[k0 * 4 + e]);
+            m[2 * l] = m[2 * l] - p * omega_pow(g.om, sl * (2 * l));
+            m[2 * l + 1] = m[2 * l + 1] - p * omega_pow(g.om, sl * (2 * l + 1));
+          }
+        }
+      }
+      active = t || norm2(m[2 * l]) > theta2 || norm2(m[2 * l + 1]) > theta2;
+#pragma unroll
+      for (int j = 0; j < nm; ++j) cur[j * M + k] = Store<F>::from_d(m[j]);
+    } else {
+      FF::V m[nm];
+#pragma unroll
+      for (int j = 0; j < 2 * l; ++j)
+        m[j] = FF::add(FF::from4(prev[j * 2 * M + k]), FF::from4(prev[j * 2 * M + k + M]));
+      m[2 * l] = FF::from4(cur[(2 * l) * M + k]);
+      m[2 * l + 1] = FF::from4(cur[(2 * l + 1) * M + k]);
+      if (l > 0) {
+        for (int64_t u = 0; u < nsub; ++u) {
+          const int64_t k0 = k + u * M;
+          const int c = cnt[k0];
+          for (int e = 0; e < c; ++e) {
+            const int64_t sl = ss[k0 * 4 + e];
+            const FF::V p = FF::from4(sp[k0 * 4 + e]);
+            m[2 * l] = FF::sub(m[2 * l], FF::mulv(p, omega_ff(g.omff, sl * (2 * l))));
+            m[2 * l + 1] = FF::sub(m[2 * l + 1], FF::mulv(p, omega_ff(g.omff, sl * (2 * l + 1))));
+          }
+        }
+      }
+      active = t || above_ff(m[2 * l], theta2) || above_ff(m[2 * l + 1], theta2);
+#pragma unroll
+      for (int j = 0; j < nm; ++j) cur[j * M + k] = FF::to4(m[j]);
+    }
     if (!active) g.Tcur[(int64_t)b * M0 + k] = 0;
   }
   queue_push(active, b, (int)k, queue, qcount);
@@ -186,32 +236,32 @@ __global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* q
 
 // Level l, phase 2: decode the queued bins with a = l + 1 (lines 23-35),
 // grid-stride over the queue so that every warp is full.
-template <int A>
+template <class F, int A>
 __global__ void __launch_bounds__(kDecThreads) k_iter_decode(LevelArgs g, const int2* queue,
                                                              const int* qcount) {
   constexpr int nm = 2 * A;
+  typedef typename Store<F>::T T;
   const int n = *qcount;
-  const Tol2 tolr{0.0, g.root_tol * g.root_tol, g.res_tol * g.res_tol};
   const BinGeom geom{g.N, g.M, g.d, g.om};
   for (int e = blockIdx.x * kDecThreads + threadIdx.x; e < n; e += gridDim.x * kDecThreads) {
     const int2 q = queue[e];
     const int b = q.x;
     const int64_t k = q.y, M = g.M, M0 = g.M0;
-    double2* cur = g.cur + (int64_t)b * g.held_elems;
-    Tol2 tol = tolr;
-    tol.theta2 = g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]);
+    T* cur = reinterpret_cast<T*>(g.cur) + (int64_t)b * g.held_elems;
+    const Tol2 tol{g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]),
+                   g.root_tol * g.root_tol, g.res_tol * g.res_tol};
     cdbl m[nm];
 #pragma unroll
-    for (int j = 0; j < nm; ++j) m[j] = ld2(cur + j * M + k);
+    for (int j = 0; j < nm; ++j) m[j] = Store<F>::to_d(cur[j * M + k]);
     int64_t s[4];
     cdbl p[4];
     uint8_t t = 1;
     if (decode_bin<A, nm>(m, k, geom, tol, s, p)) {
-      file_solution<A>(s, p, M0, g.slot_cnt + (int64_t)b * M0, g.slot_s + (int64_t)b * M0 * 4,
-                       g.slot_p + (int64_t)b * M0 * 4, g.flags + b);
+      file_solution<F, A>(s, p, M0, g.slot_cnt + (int64_t)b * M0, g.slot_s + (int64_t)b * M0 * 4,
+                          reinterpret_cast<T*>(g.slot_p) + (int64_t)b * M0 * 4, g.flags + b);
       // the recovered terms leave every syndrome held for this bin
 #pragma unroll
-      for (int j = 0; j < nm; ++j) cur[j * M + k] = make_double2(m[j].x, m[j].y);
+      for (int j = 0; j < nm; ++j) cur[j * M + k] = Store<F>::from_d(m[j]);
       t = 0;
     }
     g.Tcur[(int64_t)b * M0 + k] = t;
@@ -222,12 +272,12 @@ __global__ void __launch_bounds__(kDecThreads) k_iter_decode(LevelArgs g, const 
 struct FixedArgs {
   int64_t N, M, d;
   int a_max;
-  const double2* Y;  // 2 a_max rows of length M
+  const void* Y;  // 2 a_max rows of length M (Store<F>::T)
   int64_t held_elems;
   uint8_t* T;
   uint8_t* slot_cnt;
   int64_t* slot_s;
-  double2* slot_p;
+  void* slot_p;
   const unsigned long long* ymax2;
   int32_t* flags;
   double zero_tol, root_tol, res_tol;
@@ -235,17 +285,23 @@ struct FixedArgs {
 };
 
 // activity of every bin (any of the 2 a_max syndromes above theta)
-template <int NM>
+template <class F, int NM>
 __global__ void __launch_bounds__(kFoldThreads) k_fixed_scan(FixedArgs g, int2* queue, int* qcount) {
+  typedef typename Store<F>::T T;
   const int b = blockIdx.y;
   const int64_t M = g.M;
   const int64_t k = (int64_t)blockIdx.x * kFoldThreads + threadIdx.x;
   bool active = false;
   if (k < M) {
-    const double2* Y = g.Y + (int64_t)b * g.held_elems;
+    const T* Y = reinterpret_cast<const T*>(g.Y) + (int64_t)b * g.held_elems;
     const double theta2 = g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]);
 #pragma unroll
-    for (int j = 0; j < NM; ++j) active = active || norm2(ld2(Y + j * M + k)) > theta2;
+    for (int j = 0; j < NM; ++j) {
+      if constexpr (std::is_same<F, F64>::value)
+        active = active || norm2(Store<F>::to_d(Y[j * M + k])) > theta2;
+      else
+        active = active || above_ff(FF::from4(Y[j * M + k]), theta2);
+    }
     g.T[(int64_t)b * M + k] = 0;
   }
   queue_push(active, b, (int)k, queue, qcount);
@@ -253,10 +309,11 @@ __global__ void __launch_bounds__(kFoldThreads) k_fixed_scan(FixedArgs g, int2* 
 
 // round a: decode the queued bins with a aliases; failures go to the next
 // round's queue, or are marked unsolved after the last round (a = a_max)
-template <int A, int NM>
+template <class F, int A, int NM>
 __global__ void __launch_bounds__(kDecThreads) k_fixed_round(FixedArgs g, const int2* qin,
                                                              const int* nin, int2* qout,
                                                              int* nout) {
+  typedef typename Store<F>::T T;
   const int n = *nin;
   const BinGeom geom{g.N, g.M, g.d, g.om};
   const int64_t M = g.M;
@@ -268,17 +325,17 @@ __global__ void __launch_bounds__(kDecThreads) k_fixed_round(FixedArgs g, const 
       const int2 q = qin[e];
       b = q.x;
       k = q.y;
-      const double2* Y = g.Y + (int64_t)b * g.held_elems;
+      const T* Y = reinterpret_cast<const T*>(g.Y) + (int64_t)b * g.held_elems;
       const Tol2 tol{g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]),
                      g.root_tol * g.root_tol, g.res_tol * g.res_tol};
       cdbl m[NM];
 #pragma unroll
-      for (int j = 0; j < NM; ++j) m[j] = ld2(Y + j * M + k);
+      for (int j = 0; j < NM; ++j) m[j] = Store<F>::to_d(Y[j * M + k]);
       int64_t s[4];
       cdbl p[4];
       if (decode_bin<A, NM>(m, k, geom, tol, s, p)) {
-        file_solution<A>(s, p, M, g.slot_cnt + (int64_t)b * M, g.slot_s + (int64_t)b * M * 4,
-                         g.slot_p + (int64_t)b * M * 4, g.flags + b);
+        file_solution<F, A>(s, p, M, g.slot_cnt + (int64_t)b * M, g.slot_s + (int64_t)b * M * 4,
+                            reinterpret_cast<T*>(g.slot_p) + (int64_t)b * M * 4, g.flags + b);
       } else if (qout == nullptr) {
         g.T[(int64_t)b * M + k] = 1;
       } else {
@@ -294,7 +351,7 @@ struct FinArgs {
   int64_t M0, M_last;
   const uint8_t* slot_cnt;
   const int64_t* slot_s;
-  const double2* slot_p;
+  const void* slot_p;
   const uint8_t* T_last;
   const int32_t* flags;
   int64_t cap;
@@ -333,11 +390,14 @@ __device__ __forceinline__ int block_excl_scan(int v, int* total) {
   return before;
 }
 
+template <class F>
 __global__ void __launch_bounds__(1024) k_finalize(FinArgs g) {
+  typedef typename Store<F>::T T;
   const int b = blockIdx.x;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int64_t M0 = g.M0;
   const uint8_t* cnt = g.slot_cnt + (int64_t)b * M0;
+  const T* sp = reinterpret_cast<const T*>(g.slot_p);
   const int64_t chunk = (M0 + nthr - 1) / nthr;
   const int64_t lo = min((int64_t)tid * chunk, M0), hi = min(lo + chunk, M0);
   int mine = 0;
@@ -351,14 +411,15 @@ __global__ void __launch_bounds__(1024) k_finalize(FinArgs g) {
     for (int e = 0; e < c; ++e, ++pos) {
       if (pos < g.cap) {
         idx[pos] = g.slot_s[((int64_t)b * M0 + k0) * 4 + e];
-        val[pos] = g.slot_p[((int64_t)b * M0 + k0) * 4 + e];
+        const cdbl v = Store<F>::to_d(sp[((int64_t)b * M0 + k0) * 4 + e]);
+        val[pos] = make_double2(v.x, v.y);
       }
     }
   }
   // unresolved bins at the last level
   int un = 0;
-  const uint8_t* T = g.T_last + (int64_t)b * M0;
-  for (int64_t k = tid; k < g.M_last; k += nthr) un += T[k];
+  const uint8_t* T_ = g.T_last + (int64_t)b * M0;
+  for (int64_t k = tid; k < g.M_last; k += nthr) un += T_[k];
   int un_total = 0;
   (void)block_excl_scan(un, &un_total);
   if (tid == 0) {
@@ -411,142 +472,157 @@ void stage_end(sft_plan_s* P, cudaStream_t st) {
 }
 
 template <class F>
-static void launch_gather_fft(const sft_plan_s* P, int64_t B, const void* x, int64_t x_stride,
-                              int64_t d, int log2M, int shift0, int nshift, double2* out,
+static void launch_gather_fft(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride,
+                              int64_t d, int log2M, int shift0, int nshift, void* out,
                               int64_t out_row, int row0, bool want_ymax, cudaStream_t st) {
   dim3 grid(nshift, (unsigned)B);
   const int nthr = fft_threads(log2M);
   const size_t smem = (size_t)(1 << log2M) * F::kBytesPerPoint;
   static const char* names[] = {"gather_fft_l0", "gather_fft_l1", "gather_fft_l2", "gather_fft_l3"};
-  stage_begin(const_cast<sft_plan_s*>(P), nshift > 2 ? "gather_fft_fixed" : names[shift0 / 2], st);
+  stage_begin(P, nshift > 2 ? "gather_fft_fixed" : names[shift0 / 2], st);
   k_gather_fft<F><<<grid, nthr, smem, st>>>(
       reinterpret_cast<const typename F::In*>(x), x_stride, P->p.N, d, log2M, shift0, P->log2M0,
       reinterpret_cast<const typename F::Tw*>(P->tab.tw), out, P->ws.held_elems, out_row, row0,
       want_ymax ? P->ws.ymax2 : nullptr);
-  stage_end(const_cast<sft_plan_s*>(P), st);
+  stage_end(P, st);
+}
+
+template <class F>
+static void launch_fixed(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride,
+                         const OmegaTab& om, int nsm, cudaStream_t st) {
+  const Workspace& W = P->ws;
+  const int nsh = 2 * P->p.a_max;
+  launch_gather_fft<F>(P, B, x, x_stride, P->p.d, P->log2M0, 0, nsh, W.held[0], P->M0, 0, true, st);
+  FixedArgs g{P->p.N, P->M0, P->p.d, P->p.a_max, W.held[0], W.held_elems, W.T[0], W.slot_cnt,
+              W.slot_s, W.slot_p, W.ymax2, W.flags, P->p.zero_tol, P->p.root_tol,
+              P->p.res_tol, om};
+  dim3 sgrid((unsigned)((P->M0 + kFoldThreads - 1) / kFoldThreads), (unsigned)B);
+  const int64_t maxq = B * P->M0;
+  const unsigned dgrid = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((maxq + kDecThreads - 1) / kDecThreads, 8 * (int64_t)nsm));
+  int2* q0 = W.queue[0];
+  int2* q1 = W.queue[1];
+  int* c = W.qcount;
+  stage_begin(P, "decode_fixed_scan", st);
+  switch (P->p.a_max) {
+    case 1: k_fixed_scan<F, 2><<<sgrid, kFoldThreads, 0, st>>>(g, q0, c); break;
+    case 2: k_fixed_scan<F, 4><<<sgrid, kFoldThreads, 0, st>>>(g, q0, c); break;
+    case 3: k_fixed_scan<F, 6><<<sgrid, kFoldThreads, 0, st>>>(g, q0, c); break;
+    default: k_fixed_scan<F, 8><<<sgrid, kFoldThreads, 0, st>>>(g, q0, c); break;
+  }
+  stage_end(P, st);
+  static const char* rnames[] = {"decode_fixed_a1", "decode_fixed_a2", "decode_fixed_a3",
+                                 "decode_fixed_a4"};
+  // round a reads queue (a-1)&1 / counter a-1, writes queue a&1 / counter a
+  auto round = [&](auto a_tag, auto nm_tag) {
+    constexpr int A = decltype(a_tag)::value, NM = decltype(nm_tag)::value;
+    const bool last = A == P->p.a_max;
+    stage_begin(P, rnames[A - 1], st);
+    k_fixed_round<F, A, NM><<<dgrid, kDecThreads, 0, st>>>(
+        g, (A & 1) ? q0 : q1, c + (A - 1), last ? nullptr : ((A & 1) ? q1 : q0),
+        last ? nullptr : c + A);
+    stage_end(P, st);
+  };
+  using I1 = std::integral_constant<int, 1>;
+  using I2 = std::integral_constant<int, 2>;
+  using I3 = std::integral_constant<int, 3>;
+  using I4 = std::integral_constant<int, 4>;
+  switch (P->p.a_max) {
+    case 1: round(I1{}, std::integral_constant<int, 2>{}); break;
+    case 2:
+      round(I1{}, std::integral_constant<int, 4>{});
+      round(I2{}, std::integral_constant<int, 4>{});
+      break;
+    case 3:
+      round(I1{}, std::integral_constant<int, 6>{});
+      round(I2{}, std::integral_constant<int, 6>{});
+      round(I3{}, std::integral_constant<int, 6>{});
+      break;
+    default:
+      round(I1{}, std::integral_constant<int, 8>{});
+      round(I2{}, std::integral_constant<int, 8>{});
+      round(I3{}, std::integral_constant<int, 8>{});
+      round(I4{}, std::integral_constant<int, 8>{});
+      break;
+  }
+}
+
+template <class F>
+static void launch_iter(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride,
+                        const OmegaTab& om, int nsm, cudaStream_t st, int64_t* M_last,
+                        const uint8_t** T_last) {
+  const Workspace& W = P->ws;
+  const OmegaTabFF omff{P->tab.om_hi_ff, P->tab.om_lo_ff, P->tab.om_lo_bits, P->p.N - 1};
+  int64_t M = P->M0, d = P->p.d;
+  for (int l = 0; l < P->levels; ++l) {
+    if (l > 0) {
+      M >>= 1;
+      d <<= 1;
+    }
+    const int log2M = P->log2M0 - l;
+    void* cur = W.held[l & 1];
+    const void* prev = W.held[(l + 1) & 1];
+    launch_gather_fft<F>(P, B, x, x_stride, d, log2M, 2 * l, 2, cur, M, 2 * l, l == 0, st);
+    LevelArgs g{P->p.N, M, d, P->M0, prev, cur, W.held_elems, W.T[(l + 1) & 1], W.T[l & 1],
+                W.slot_cnt, W.slot_s, W.slot_p, W.ymax2, W.flags, P->p.zero_tol,
+                P->p.root_tol, P->p.res_tol, om, omff};
+    int2* q = W.queue[l & 1];
+    int* c = W.qcount + l;
+    dim3 fgrid((unsigned)((M + kFoldThreads - 1) / kFoldThreads), (unsigned)B);
+    const int64_t maxq = B * M;
+    const unsigned dgrid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((maxq + kDecThreads - 1) / kDecThreads, 8 * (int64_t)nsm));
+    static const char* fnames[] = {"fold_l0", "fold_l1", "fold_l2", "fold_l3"};
+    static const char* dnames[] = {"decode_l0", "decode_l1", "decode_l2", "decode_l3"};
+    stage_begin(P, fnames[l], st);
+    switch (l) {
+      case 0: k_iter_fold<F, 1><<<fgrid, kFoldThreads, 0, st>>>(g, q, c); break;
+      case 1: k_iter_fold<F, 2><<<fgrid, kFoldThreads, 0, st>>>(g, q, c); break;
+      case 2: k_iter_fold<F, 3><<<fgrid, kFoldThreads, 0, st>>>(g, q, c); break;
+      default: k_iter_fold<F, 4><<<fgrid, kFoldThreads, 0, st>>>(g, q, c); break;
+    }
+    stage_end(P, st);
+    stage_begin(P, dnames[l], st);
+    switch (l) {
+      case 0: k_iter_decode<F, 1><<<dgrid, kDecThreads, 0, st>>>(g, q, c); break;
+      case 1: k_iter_decode<F, 2><<<dgrid, kDecThreads, 0, st>>>(g, q, c); break;
+      case 2: k_iter_decode<F, 3><<<dgrid, kDecThreads, 0, st>>>(g, q, c); break;
+      default: k_iter_decode<F, 4><<<dgrid, kDecThreads, 0, st>>>(g, q, c); break;
+    }
+    stage_end(P, st);
+    *M_last = M;
+    *T_last = W.T[l & 1];
+  }
 }
 
 cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride,
                          const sft_result* r, cudaStream_t st) {
   const Workspace& W = P->ws;
-  OmegaTab om{P->tab.om_hi, P->tab.om_lo, P->tab.om_lo_bits, P->p.N - 1};
+  const OmegaTab om{P->tab.om_hi, P->tab.om_lo, P->tab.om_lo_bits, P->p.N - 1};
   const bool fp64 = P->p.precision == SFT_FP64;
-  const int64_t d0 = P->p.d;
-  int64_t M_last = P->M0;
-  const uint8_t* T_last = W.T[0];
-
-  // grid of the grid-stride queue decoders: a few CTAs per SM
   int dev = 0, nsm = 152;
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-
+  int64_t M_last = P->M0;
+  const uint8_t* T_last = W.T[0];
   if (P->p.mode == SFT_EXACT_FIXED) {
-    const int nsh = 2 * P->p.a_max;
     if (fp64)
-      launch_gather_fft<F64>(P, B, x, x_stride, d0, P->log2M0, 0, nsh, W.held[0], P->M0, 0, true, st);
+      launch_fixed<F64>(P, B, x, x_stride, om, nsm, st);
     else
-      launch_gather_fft<FF>(P, B, x, x_stride, d0, P->log2M0, 0, nsh, W.held[0], P->M0, 0, true, st);
-    FixedArgs g{P->p.N, P->M0, d0, P->p.a_max, W.held[0], W.held_elems, W.T[0], W.slot_cnt,
-                W.slot_s, W.slot_p, W.ymax2, W.flags, P->p.zero_tol, P->p.root_tol,
-                P->p.res_tol, om};
-    dim3 sgrid((unsigned)((P->M0 + kFoldThreads - 1) / kFoldThreads), (unsigned)B);
-    const int64_t maxq = B * P->M0;
-    const unsigned dgrid =
-        (unsigned)std::max<int64_t>(1, std::min<int64_t>((maxq + kDecThreads - 1) / kDecThreads, 8 * nsm));
-    int2* q0 = W.queue[0];
-    int2* q1 = W.queue[1];
-    int* c = W.qcount;
-    stage_begin(P, "decode_fixed_scan", st);
-    switch (P->p.a_max) {
-      case 1: k_fixed_scan<2><<<sgrid, kFoldThreads, 0, st>>>(g, q0, c); break;
-      case 2: k_fixed_scan<4><<<sgrid, kFoldThreads, 0, st>>>(g, q0, c); break;
-      case 3: k_fixed_scan<6><<<sgrid, kFoldThreads, 0, st>>>(g, q0, c); break;
-      default: k_fixed_scan<8><<<sgrid, kFoldThreads, 0, st>>>(g, q0, c); break;
-    }
-    stage_end(P, st);
-    static const char* rnames[] = {"decode_fixed_a1", "decode_fixed_a2", "decode_fixed_a3",
-                                   "decode_fixed_a4"};
-    // round a reads queue (a-1)&1 / counter a-1, writes queue a&1 / counter a
-    auto round = [&](auto a_tag, auto nm_tag) {
-      constexpr int A = decltype(a_tag)::value, NM = decltype(nm_tag)::value;
-      const bool last = A == P->p.a_max;
-      stage_begin(P, rnames[A - 1], st);
-      k_fixed_round<A, NM><<<dgrid, kDecThreads, 0, st>>>(
-          g, (A & 1) ? q0 : q1, c + (A - 1), last ? nullptr : ((A & 1) ? q1 : q0),
-          last ? nullptr : c + A);
-      stage_end(P, st);
-    };
-    using I1 = std::integral_constant<int, 1>;
-    using I2 = std::integral_constant<int, 2>;
-    using I3 = std::integral_constant<int, 3>;
-    using I4 = std::integral_constant<int, 4>;
-    switch (P->p.a_max) {
-      case 1: round(I1{}, std::integral_constant<int, 2>{}); break;
-      case 2:
-        round(I1{}, std::integral_constant<int, 4>{});
-        round(I2{}, std::integral_constant<int, 4>{});
-        break;
-      case 3:
-        round(I1{}, std::integral_constant<int, 6>{});
-        round(I2{}, std::integral_constant<int, 6>{});
-        round(I3{}, std::integral_constant<int, 6>{});
-        break;
-      default:
-        round(I1{}, std::integral_constant<int, 8>{});
-        round(I2{}, std::integral_constant<int, 8>{});
-        round(I3{}, std::integral_constant<int, 8>{});
-        round(I4{}, std::integral_constant<int, 8>{});
-        break;
-    }
+      launch_fixed<FF>(P, B, x, x_stride, om, nsm, st);
   } else {
-    int64_t M = P->M0, d = d0;
-    for (int l = 0; l < P->levels; ++l) {
-      if (l > 0) {
-        M >>= 1;
-        d <<= 1;
-      }
-      const int log2M = P->log2M0 - l;
-      double2* cur = W.held[l & 1];
-      const double2* prev = W.held[(l + 1) & 1];
-      if (fp64)
-        launch_gather_fft<F64>(P, B, x, x_stride, d, log2M, 2 * l, 2, cur, M, 2 * l, l == 0, st);
-      else
-        launch_gather_fft<FF>(P, B, x, x_stride, d, log2M, 2 * l, 2, cur, M, 2 * l, l == 0, st);
-      LevelArgs g{P->p.N, M, d, P->M0, prev, cur, W.held_elems, W.T[(l + 1) & 1], W.T[l & 1],
-                  W.slot_cnt, W.slot_s, W.slot_p, W.ymax2, W.flags, P->p.zero_tol,
-                  P->p.root_tol, P->p.res_tol, om};
-      int2* q = W.queue[l & 1];
-      int* c = W.qcount + l;
-      dim3 fgrid((unsigned)((M + kFoldThreads - 1) / kFoldThreads), (unsigned)B);
-      const int64_t maxq = B * M;
-      const unsigned dgrid = (unsigned)std::max<int64_t>(
-          1, std::min<int64_t>((maxq + kDecThreads - 1) / kDecThreads, 8 * nsm));
-      static const char* fnames[] = {"fold_l0", "fold_l1", "fold_l2", "fold_l3"};
-      static const char* dnames[] = {"decode_l0", "decode_l1", "decode_l2", "decode_l3"};
-      stage_begin(P, fnames[l], st);
-      switch (l) {
-        case 0: k_iter_fold<1><<<fgrid, kFoldThreads, 0, st>>>(g, q, c); break;
-        case 1: k_iter_fold<2><<<fgrid, kFoldThreads, 0, st>>>(g, q, c); break;
-        case 2: k_iter_fold<3><<<fgrid, kFoldThreads, 0, st>>>(g, q, c); break;
-        default: k_iter_fold<4><<<fgrid, kFoldThreads, 0, st>>>(g, q, c); break;
-      }
-      stage_end(P, st);
-      stage_begin(P, dnames[l], st);
-      switch (l) {
-        case 0: k_iter_decode<1><<<dgrid, kDecThreads, 0, st>>>(g, q, c); break;
-        case 1: k_iter_decode<2><<<dgrid, kDecThreads, 0, st>>>(g, q, c); break;
-        case 2: k_iter_decode<3><<<dgrid, kDecThreads, 0, st>>>(g, q, c); break;
-        default: k_iter_decode<4><<<dgrid, kDecThreads, 0, st>>>(g, q, c); break;
-      }
-      stage_end(P, st);
-      M_last = M;
-      T_last = W.T[l & 1];
-    }
+    if (fp64)
+      launch_iter<F64>(P, B, x, x_stride, om, nsm, st, &M_last, &T_last);
+    else
+      launch_iter<FF>(P, B, x, x_stride, om, nsm, st, &M_last, &T_last);
   }
   FinArgs f{P->M0, M_last, W.slot_cnt, W.slot_s, W.slot_p, T_last, W.flags, r->cap, r->idx,
             reinterpret_cast<double2*>(r->val), r->count, r->unresolved, r->overflow};
   stage_begin(P, "finalize", st);
-  k_finalize<<<(unsigned)B, 1024, 0, st>>>(f);
+  if (fp64)
+    k_finalize<F64><<<(unsigned)B, 1024, 0, st>>>(f);
+  else
+    k_finalize<FF><<<(unsigned)B, 1024, 0, st>>>(f);
   stage_end(P, st);
   return cudaGetLastError();
 }

@@ -24,13 +24,13 @@ namespace sft {
 // plus qcount[16], the queue fill counters of one call.  ymax2, flags,
 // qcount and slot_cnt form one contiguous region cleared before each call.
 struct Workspace {
-  double2* held[2] = {nullptr, nullptr};
+  void* held[2] = {nullptr, nullptr};  // double2 or float-float float4 elements
   int64_t held_elems = 0;
   uint8_t* T[2] = {nullptr, nullptr};
   int2* queue[2] = {nullptr, nullptr};
   uint8_t* slot_cnt = nullptr;
   int64_t* slot_s = nullptr;
-  double2* slot_p = nullptr;
+  void* slot_p = nullptr;  // double2 (FP64 path) or float-float float4 (mixed path)
   unsigned long long* ymax2 = nullptr;
   int32_t* flags = nullptr;
   int32_t* qcount = nullptr;
@@ -44,13 +44,16 @@ inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, 
                                int a_max) {
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
   const int64_t held_elems = mode == SFT_EXACT_FIXED ? 2 * a_max * M0 : 2 * M0;
+  const int nbuf = mode == SFT_EXACT_FIXED ? 1 : 2;  // FIXED keeps one level
   size_t off = 0;
-  size_t o_held[2], o_T[2], o_q[2];
+  size_t o_held[2] = {0, 0}, o_T[2] = {0, 0}, o_q[2];
   for (int i = 0; i < 2; ++i) {
-    o_held[i] = off;
-    off = al(off + (size_t)(B * held_elems) * 16);
-    o_T[i] = off;
-    off = al(off + (size_t)(B * M0));
+    if (i < nbuf) {
+      o_held[i] = off;
+      off = al(off + (size_t)(B * held_elems) * 16);
+      o_T[i] = off;
+      off = al(off + (size_t)(B * M0));
+    }
     o_q[i] = off;
     off = al(off + (size_t)(B * M0) * 8);
   }
@@ -64,8 +67,8 @@ inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, 
   if (W != nullptr && base != nullptr) {
     W->held_elems = held_elems;
     for (int i = 0; i < 2; ++i) {
-      W->held[i] = reinterpret_cast<double2*>(base + o_held[i]);
-      W->T[i] = reinterpret_cast<uint8_t*>(base + o_T[i]);
+      W->held[i] = i < nbuf ? base + o_held[i] : nullptr;
+      W->T[i] = i < nbuf ? reinterpret_cast<uint8_t*>(base + o_T[i]) : nullptr;
       W->queue[i] = reinterpret_cast<int2*>(base + o_q[i]);
     }
     char* z = base + o_zero;
@@ -76,7 +79,7 @@ inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, 
     W->qcount = reinterpret_cast<int32_t*>(z + (size_t)B * 16);
     W->slot_cnt = reinterpret_cast<uint8_t*>(z + (size_t)B * 16 + 64);
     W->slot_s = reinterpret_cast<int64_t*>(base + o_ss);
-    W->slot_p = reinterpret_cast<double2*>(base + o_sp);
+    W->slot_p = base + o_sp;
   }
   return off;
 }
@@ -86,6 +89,8 @@ struct Tables {
   double2* om_lo = nullptr;  // omega^i, i < 2^lo_bits
   int om_lo_bits = 0;
   void* tw = nullptr;        // e^{-2 pi i q / M0}: double2 (FP64) or float4 (FF)
+  float4* om_hi_ff = nullptr;  // the omega tables as float-float (mixed path only)
+  float4* om_lo_ff = nullptr;
 };
 
 }  // namespace sft

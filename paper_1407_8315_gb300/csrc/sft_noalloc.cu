@@ -55,17 +55,25 @@ int lg2(int64_t v) {
 // Tables of omega^e (two-level) and of the FFT twiddles e^{-2 pi i q / M0},
 // written into the scratch by the device (the plan path computes the same
 // values on the host; both are correctly rounded to within an ulp).
+__device__ __forceinline__ float4 ff_split(double c, double s) {
+  const float ch = (float)c, sh = (float)s;
+  return make_float4(ch, (float)(c - (double)ch), sh, (float)(s - (double)sh));
+}
+
 __global__ void k_noalloc_tables(double2* om_lo, int64_t n_lo, double2* om_hi, int64_t n_hi,
-                                 int lo_bits, int64_t N, void* tw, int64_t M0, int ff) {
+                                 int lo_bits, int64_t N, void* tw, int64_t M0, int ff,
+                                 float4* om_lo_ff, float4* om_hi_ff) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double s, c;
   if (i < n_lo) {
     sincospi(2.0 * (double)i / (double)N, &s, &c);
     om_lo[i] = make_double2(c, s);
+    if (ff) om_lo_ff[i] = ff_split(c, s);
   }
   if (i < n_hi) {
     sincospi(2.0 * (double)(i << lo_bits) / (double)N, &s, &c);
     om_hi[i] = make_double2(c, s);
+    if (ff) om_hi_ff[i] = ff_split(c, s);
   }
   if (i < M0) {
     sincospi(2.0 * (double)i / (double)M0, &s, &c);
@@ -150,6 +158,10 @@ extern "C" sft_status sft_exact_noalloc(const sft_params* pin, int64_t n, const 
   off = align256(off + n_hi * 16);
   const size_t o_tw = off;
   off = align256(off + M0 * 16);
+  const size_t o_loff = off;
+  off = align256(off + n_lo * 16);
+  const size_t o_hiff = off;
+  off = align256(off + n_hi * 16);
   const size_t o_ws = off;
   off += sft::layout_workspace(nullptr, nullptr, n, M0, p.mode, p.a_max);
   if (off > (size_t)SFT_NOALLOC_SCRATCH_BYTES) {
@@ -181,12 +193,15 @@ extern "C" sft_status sft_exact_noalloc(const sft_params* pin, int64_t n, const 
   P.tab.om_hi = reinterpret_cast<double2*>(base + o_hi);
   P.tab.om_lo_bits = lo_bits;
   P.tab.tw = base + o_tw;
+  P.tab.om_lo_ff = reinterpret_cast<float4*>(base + o_loff);
+  P.tab.om_hi_ff = reinterpret_cast<float4*>(base + o_hiff);
   sft::layout_workspace(&P.ws, base + o_ws, n, M0, p.mode, p.a_max);
 
   const int64_t nt = n_lo > n_hi ? n_lo : n_hi;
   const int64_t ntab = nt > M0 ? nt : M0;
   k_noalloc_tables<<<(unsigned)((ntab + 255) / 256), 256, 0, st>>>(
-      P.tab.om_lo, n_lo, P.tab.om_hi, n_hi, lo_bits, p.N, P.tab.tw, M0, fp64 ? 0 : 1);
+      P.tab.om_lo, n_lo, P.tab.om_hi, n_hi, lo_bits, p.N, P.tab.tw, M0, fp64 ? 0 : 1,
+      P.tab.om_lo_ff, P.tab.om_hi_ff);
   e = cudaGetLastError();
   // counters and thresholds that the kernels accumulate into start at zero
   if (e == cudaSuccess) e = cudaMemsetAsync(P.ws.zero_base, 0, P.ws.zero_bytes, st);
