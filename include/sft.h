@@ -135,11 +135,16 @@ size_t sft_plan_workspace_bytes(sft_plan_t plan);
 sft_status sft_exact(sft_plan_t plan, int64_t n_signals, const void* x, int64_t x_stride,
                      const sft_result* r, void* stream);
 
-/* Same transform from and to HOST memory: copies the n_signals inputs to
- * the device (plan-owned staging buffer), runs sft_exact, copies the
- * results back into the host arrays of `r_host` (same layout as
- * sft_result, but host pointers) and synchronises `stream` before
- * returning.  Pinned host memory gives full copy bandwidth. */
+/* Same transform from and to HOST memory (`x_host` and the arrays of
+ * `r_host`, same layout as sft_result, are host pointers); synchronises
+ * `stream` before returning.
+ *   - If x_host is page-locked (cudaHostAlloc, cudaHostRegister, torch
+ *     pin_memory) the kernels read the samples in place over the host link:
+ *     only the samples of the shifts cross it, a small fraction of each
+ *     signal.  Otherwise the inputs are first copied whole into a
+ *     plan-owned device staging buffer.
+ *   - If every result array is page-locked the kernels write the results in
+ *     place; otherwise they are staged on the device and copied back. */
 sft_status sft_exact_host(sft_plan_t plan, int64_t n_signals, const void* x_host,
                           int64_t x_stride, const sft_result* r_host, void* stream);
 

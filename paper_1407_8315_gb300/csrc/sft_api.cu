@@ -243,65 +243,94 @@ sft_status sft_exact(sft_plan_t P, int64_t n, const void* x, int64_t x_stride,
   return SFT_OK;
 }
 
+// Device address of page-locked host memory (nullptr for pageable memory).
+static void* mapped(const void* h) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of a failed query
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 sft_status sft_exact_host(sft_plan_t P, int64_t n, const void* x_host, int64_t x_stride,
                           const sft_result* rh, void* stream) {
   sft_status st = check_call(P, n, x_host, x_stride, rh);
   if (st != SFT_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t elem = P->p.precision == SFT_FP64 ? 16 : 8;
-  const size_t xbytes = (size_t)n * (size_t)P->p.N * elem;
   const int64_t cap = rh->cap;
-  const size_t rbytes = (size_t)n * (size_t)cap * 24 + (size_t)n * 16;
   cudaError_t e = cudaSuccess;
-  if (P->x_stage_bytes < xbytes) {
-    if (P->x_stage) cudaFree(P->x_stage);
-    P->x_stage = nullptr;
-    P->x_stage_bytes = 0;
-    if ((e = cudaMalloc(&P->x_stage, xbytes)) != cudaSuccess) {
-      note_cuda(e);
-      return SFT_ENOMEM;
+
+  // inputs: read in place when page-locked (the kernels touch only the
+  // samples of the shifts, a small fraction of each signal), else staged
+  const void* xd = mapped(x_host);
+  if (xd == nullptr) {
+    const size_t xbytes = (size_t)n * (size_t)P->p.N * elem;
+    if (P->x_stage_bytes < xbytes) {
+      if (P->x_stage) cudaFree(P->x_stage);
+      P->x_stage = nullptr;
+      P->x_stage_bytes = 0;
+      if ((e = cudaMalloc(&P->x_stage, xbytes)) != cudaSuccess) {
+        note_cuda(e);
+        return SFT_ENOMEM;
+      }
+      P->x_stage_bytes = xbytes;
     }
-    P->x_stage_bytes = xbytes;
-  }
-  if (P->r_stage_bytes < rbytes) {
-    if (P->r_stage) cudaFree(P->r_stage);
-    P->r_stage = nullptr;
-    P->r_stage_bytes = 0;
-    if ((e = cudaMalloc(&P->r_stage, rbytes)) != cudaSuccess) {
-      note_cuda(e);
-      return SFT_ENOMEM;
+    const char* xh = static_cast<const char*>(x_host);
+    if (x_stride == P->p.N || n == 1) {
+      e = cudaMemcpyAsync(P->x_stage, xh, xbytes, cudaMemcpyHostToDevice, s);
+    } else {
+      const size_t row = (size_t)P->p.N * elem;
+      e = cudaMemcpy2DAsync(P->x_stage, row, xh, (size_t)x_stride * elem, row, (size_t)n,
+                            cudaMemcpyHostToDevice, s);
     }
-    P->r_stage_bytes = rbytes;
+    xd = P->x_stage;
+    x_stride = P->p.N;
   }
-  // inputs: one copy when the host signals are packed, one per signal if not
-  const char* xh = static_cast<const char*>(x_host);
-  if (x_stride == P->p.N) {
-    e = cudaMemcpyAsync(P->x_stage, xh, xbytes, cudaMemcpyHostToDevice, s);
-  } else {
-    const size_t row = (size_t)P->p.N * elem;
-    e = cudaMemcpy2DAsync(P->x_stage, row, xh, (size_t)x_stride * elem, row, (size_t)n,
-                          cudaMemcpyHostToDevice, s);
-  }
-  char* rs = static_cast<char*>(P->r_stage);
+
+  // results: written in place when every array is page-locked, else staged
   sft_result rd;
   rd.cap = cap;
-  rd.idx = reinterpret_cast<int64_t*>(rs);
-  rd.val = reinterpret_cast<double*>(rs + (size_t)n * cap * 8);
-  rd.count = reinterpret_cast<int64_t*>(rs + (size_t)n * cap * 24);
-  rd.unresolved = reinterpret_cast<int32_t*>(rs + (size_t)n * cap * 24 + (size_t)n * 8);
-  rd.overflow = reinterpret_cast<int32_t*>(rs + (size_t)n * cap * 24 + (size_t)n * 12);
+  rd.idx = static_cast<int64_t*>(mapped(rh->idx));
+  rd.val = static_cast<double*>(mapped(rh->val));
+  rd.count = static_cast<int64_t*>(mapped(rh->count));
+  rd.unresolved = static_cast<int32_t*>(mapped(rh->unresolved));
+  rd.overflow = static_cast<int32_t*>(mapped(rh->overflow));
+  const bool in_place = rd.idx && rd.val && rd.count && rd.unresolved && rd.overflow;
+  if (!in_place) {
+    const size_t rbytes = (size_t)n * (size_t)cap * 24 + (size_t)n * 16;
+    if (P->r_stage_bytes < rbytes) {
+      if (P->r_stage) cudaFree(P->r_stage);
+      P->r_stage = nullptr;
+      P->r_stage_bytes = 0;
+      if ((e = cudaMalloc(&P->r_stage, rbytes)) != cudaSuccess) {
+        note_cuda(e);
+        return SFT_ENOMEM;
+      }
+      P->r_stage_bytes = rbytes;
+    }
+    char* rs = static_cast<char*>(P->r_stage);
+    rd.idx = reinterpret_cast<int64_t*>(rs);
+    rd.val = reinterpret_cast<double*>(rs + (size_t)n * cap * 8);
+    rd.count = reinterpret_cast<int64_t*>(rs + (size_t)n * cap * 24);
+    rd.unresolved = reinterpret_cast<int32_t*>(rs + (size_t)n * cap * 24 + (size_t)n * 8);
+    rd.overflow = reinterpret_cast<int32_t*>(rs + (size_t)n * cap * 24 + (size_t)n * 12);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(P->ws.zero_base, 0, P->ws.zero_bytes, s);
-  if (e == cudaSuccess) e = sft::launch_exact(P, n, P->x_stage, P->p.N, &rd, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(rh->idx, rd.idx, (size_t)n * cap * 8, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(rh->val, rd.val, (size_t)n * cap * 16, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(rh->count, rd.count, (size_t)n * 8, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(rh->unresolved, rd.unresolved, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(rh->overflow, rd.overflow, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = sft::launch_exact(P, n, xd, x_stride, &rd, s);
+  if (!in_place) {
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(rh->idx, rd.idx, (size_t)n * cap * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(rh->val, rd.val, (size_t)n * cap * 16, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(rh->count, rd.count, (size_t)n * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(rh->unresolved, rd.unresolved, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(rh->overflow, rd.overflow, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     note_cuda(e);

@@ -82,6 +82,13 @@ __device__ __forceinline__ cdbl omega_pow(const OmegaTab& t, int64_t e) {
 }
 
 // ------------------------------------------------------- FFT value traits
+// Shared-memory slot of FFT element i: one spare slot per 16 elements, so
+// that the first Stockham pass (thread j writes elements 16j .. 16j+15)
+// does not hit one bank with every lane of a half-warp.
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+// padded length of an M-point buffer
+__host__ __device__ __forceinline__ int padded(int M) { return M + (M >> 4); }
+
 // Constant twiddles e^{-2 pi i m/16}, m = 0..7, for the in-register radix-16
 // butterflies (correctly rounded double literals).
 #define SFT_C1 0.92387953251128675613
@@ -113,10 +120,10 @@ struct F64 {
   __device__ static __forceinline__ V mul_mi(V a) { return V{a.ry, -a.rx}; }  // * (-i)
   __device__ static __forceinline__ V from_in(In v) { return V{v.x, v.y}; }
   __device__ static __forceinline__ void st(char* sm, int M, int i, V v) {
-    reinterpret_cast<double2*>(sm)[i] = make_double2(v.rx, v.ry);
+    reinterpret_cast<double2*>(sm)[pad16(i)] = make_double2(v.rx, v.ry);
   }
   __device__ static __forceinline__ V ld(const char* sm, int M, int i) {
-    double2 t = reinterpret_cast<const double2*>(sm)[i];
+    double2 t = reinterpret_cast<const double2*>(sm)[pad16(i)];
     return V{t.x, t.y};
   }
   typedef double2 Out;
@@ -208,12 +215,12 @@ struct FF {
   __device__ static __forceinline__ V from_in(In v) { return V{v.x, 0.f, v.y, 0.f}; }
   // shared memory: hi plane (float2) followed by lo plane (float2)
   __device__ static __forceinline__ void st(char* sm, int M, int i, V v) {
-    reinterpret_cast<float2*>(sm)[i] = make_float2(v.rh, v.ih);
-    reinterpret_cast<float2*>(sm)[M + i] = make_float2(v.rl, v.il);
+    reinterpret_cast<float2*>(sm)[pad16(i)] = make_float2(v.rh, v.ih);
+    reinterpret_cast<float2*>(sm)[padded(M) + pad16(i)] = make_float2(v.rl, v.il);
   }
   __device__ static __forceinline__ V ld(const char* sm, int M, int i) {
-    float2 h = reinterpret_cast<const float2*>(sm)[i];
-    float2 l = reinterpret_cast<const float2*>(sm)[M + i];
+    float2 h = reinterpret_cast<const float2*>(sm)[pad16(i)];
+    float2 l = reinterpret_cast<const float2*>(sm)[padded(M) + pad16(i)];
     return V{h.x, l.x, h.y, l.y};
   }
   // syndromes leave the FFT as float-float quadruples scaled by d (a power
@@ -238,6 +245,7 @@ struct Store<F64> {
   typedef double2 T;
   __device__ static __forceinline__ cdbl to_d(double2 v) { return cdbl{v.x, v.y}; }
   __device__ static __forceinline__ double2 from_d(cdbl c) { return make_double2(c.x, c.y); }
+  __device__ static __forceinline__ double2 from_d_small(cdbl c) { return make_double2(c.x, c.y); }
 };
 template <>
 struct Store<FF> {
@@ -248,6 +256,11 @@ struct Store<FF> {
   __device__ static __forceinline__ float4 from_d(cdbl c) {
     const float xh = (float)c.x, yh = (float)c.y;
     return make_float4(xh, (float)(c.x - (double)xh), yh, (float)(c.y - (double)yh));
+  }
+  // for residuals of accepted decodes (|r| <= res_tol |m|): the hi parts
+  // alone carry them to well below the float-float precision of |m|
+  __device__ static __forceinline__ float4 from_d_small(cdbl c) {
+    return make_float4((float)c.x, 0.0f, (float)c.y, 0.0f);
   }
 };
 

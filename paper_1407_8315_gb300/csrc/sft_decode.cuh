@@ -26,8 +26,19 @@
 
 namespace sft {
 
+// 1/x: FP32 seed refined by two Newton steps r <- r + r (1 - x r) (each
+// doubles the correct bits: 2^-23 -> 2^-46 -> below an FP64 ulp); an exact
+// FP64 division when x lies outside the float range.
+__device__ __forceinline__ double rcp_d(double x) {
+  double r = (double)__frcp_rn((float)x);
+  if (!(fabs(r) > 1e-37 && fabs(r) < 1e37)) return 1.0 / x;
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
 __device__ __forceinline__ cdbl crcp(cdbl b) {
-  const double inv = 1.0 / norm2(b);
+  const double inv = rcp_d(norm2(b));
   return cdbl{b.x * inv, -b.y * inv};
 }
 __device__ __forceinline__ cdbl csqrt_fast(cdbl v) {
@@ -228,28 +239,42 @@ __device__ __forceinline__ bool decode_bin(cdbl* m, int64_t k, const BinGeom& g,
     const cdbl w = omega_pow(g.om, s[0]);
     if (!(norm2(z - w) <= tol.root2)) return false;
     // least squares over all equations: Z^H Z = nm, p = (1/nm) sum conj(w^i) m_i
-    cdbl acc = m[0], wp = w;
+    if constexpr (nm == 2) {
+      // p = (m0 + conj(w) m1) / 2; the residuals are r0 = (m0 - conj(w) m1)/2
+      // and r1 = m1 - p w = -w r0, so |r1| = |r0|
+      const cdbl t = conjd(w) * m[1];
+      p[0] = (m[0] + t) * 0.5;
+      if (!(norm2(p[0]) > tol.theta2)) return false;
+      const cdbl r0 = (m[0] - t) * 0.5;
+      const double mmax2 = fmax(norm2(m[0]), norm2(m[1]));
+      if (!(norm2(r0) <= tol.res2 * mmax2)) return false;
+      m[0] = r0;
+      m[1] = -(w * r0);
+      return true;
+    } else {
+      cdbl acc = m[0], wp = w;
 #pragma unroll
-    for (int i = 1; i < nm; ++i) {
-      acc = acc + conjd(wp) * m[i];
-      wp = wp * w;
+      for (int i = 1; i < nm; ++i) {
+        acc = acc + conjd(wp) * m[i];
+        wp = wp * w;
+      }
+      p[0] = acc * (1.0 / (double)nm);
+      if (!(norm2(p[0]) > tol.theta2)) return false;
+      double mmax2 = 0.0, rmax2 = 0.0;
+      cdbl r[nm];
+      wp = mk(1.0, 0.0);
+#pragma unroll
+      for (int i = 0; i < nm; ++i) {
+        r[i] = m[i] - p[0] * wp;
+        wp = wp * w;
+        mmax2 = fmax(mmax2, norm2(m[i]));
+        rmax2 = fmax(rmax2, norm2(r[i]));
+      }
+      if (!(rmax2 <= tol.res2 * mmax2)) return false;
+#pragma unroll
+      for (int i = 0; i < nm; ++i) m[i] = r[i];
+      return true;
     }
-    p[0] = acc * (1.0 / (double)nm);
-    if (!(norm2(p[0]) > tol.theta2)) return false;
-    double mmax2 = 0.0, rmax2 = 0.0;
-    cdbl r[nm];
-    wp = mk(1.0, 0.0);
-#pragma unroll
-    for (int i = 0; i < nm; ++i) {
-      r[i] = m[i] - p[0] * wp;
-      wp = wp * w;
-      mmax2 = fmax(mmax2, norm2(m[i]));
-      rmax2 = fmax(rmax2, norm2(r[i]));
-    }
-    if (!(rmax2 <= tol.res2 * mmax2)) return false;
-#pragma unroll
-    for (int i = 0; i < nm; ++i) m[i] = r[i];
-    return true;
   } else {
     cdbl H[a * a], rhs[a], c[a];
 #pragma unroll

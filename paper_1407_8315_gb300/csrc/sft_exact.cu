@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kDecThreads) k_iter_decode(LevelArgs g, const 
                           reinterpret_cast<T*>(g.slot_p) + (int64_t)b * M0 * 4, g.flags + b);
       // the recovered terms leave every syndrome held for this bin
 #pragma unroll
-      for (int j = 0; j < nm; ++j) cur[j * M + k] = Store<F>::from_d(m[j]);
+      for (int j = 0; j < nm; ++j) cur[j * M + k] = Store<F>::from_d_small(m[j]);
       t = 0;
     }
     g.Tcur[(int64_t)b * M0 + k] = t;
@@ -436,7 +436,7 @@ static int fft_threads(int log2M) {
 }
 
 cudaError_t prepare_kernels(sft_plan_s* P) {
-  const int smem = (int)(P->M0 * 16);
+  const int smem = padded((int)P->M0) * 16;
   cudaError_t e;
   if (P->p.precision == SFT_FP64)
     e = cudaFuncSetAttribute(k_gather_fft<F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -477,7 +477,7 @@ static void launch_gather_fft(sft_plan_s* P, int64_t B, const void* x, int64_t x
                               int64_t out_row, int row0, bool want_ymax, cudaStream_t st) {
   dim3 grid(nshift, (unsigned)B);
   const int nthr = fft_threads(log2M);
-  const size_t smem = (size_t)(1 << log2M) * F::kBytesPerPoint;
+  const size_t smem = (size_t)padded(1 << log2M) * F::kBytesPerPoint;
   static const char* names[] = {"gather_fft_l0", "gather_fft_l1", "gather_fft_l2", "gather_fft_l3"};
   stage_begin(P, nshift > 2 ? "gather_fft_fixed" : names[shift0 / 2], st);
   k_gather_fft<F><<<grid, nthr, smem, st>>>(

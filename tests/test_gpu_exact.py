@@ -175,6 +175,32 @@ def test_host_entry_matches_device_entry(gpu):
         np.testing.assert_array_equal(h.val[b, :dc[b]], dv[b, :dc[b]])
 
 
+def test_host_entry_page_locked_in_place(gpu):
+    """Page-locked inputs and results: the kernels read the samples and write
+    the results in place in host memory; identical to the device entry."""
+    import torch
+    from paper_1407_8315_gb300 import Plan, sft
+    N, K, M = 1 << 18, 1024, 2048
+    plan = Plan(N, K, N // M, "iter", "mixed", max_signals=3)
+    xs, _, _ = siggen.batch_exact(N, K, range(3), mag=(1, 10), dtype=np.complex64)
+    di, dv, dc, du, do = _run_gpu(gpu, plan, xs, 2 * K)
+    px = torch.empty((3, N), dtype=torch.complex64, pin_memory=True)
+    px.numpy()[:] = xs
+    cap = 2 * K
+    out = sft.Result(torch.empty((3, cap), dtype=torch.int64, pin_memory=True).numpy(),
+                     torch.empty((3, cap), dtype=torch.complex128, pin_memory=True).numpy(),
+                     torch.empty(3, dtype=torch.int64, pin_memory=True).numpy(),
+                     torch.empty(3, dtype=torch.int32, pin_memory=True).numpy(),
+                     torch.empty(3, dtype=torch.int32, pin_memory=True).numpy())
+    for _ in range(2):
+        h = plan.exact_host(px.numpy(), cap, out)
+        np.testing.assert_array_equal(h.count, dc)
+        np.testing.assert_array_equal(h.unresolved, du)
+        for b in range(3):
+            np.testing.assert_array_equal(h.idx[b, :dc[b]], di[b, :dc[b]])
+            np.testing.assert_array_equal(h.val[b, :dc[b]], dv[b, :dc[b]])
+
+
 def test_strided_batch(gpu, orc):
     """x_stride > N: signals read from a wider row pitch."""
     from paper_1407_8315_gb300 import Plan
