@@ -70,7 +70,7 @@ typedef struct {
   int64_t N;           /* signal length; power of two, 2^3 .. 2^30            */
   int64_t K;           /* sparsity; the result capacity must be >= K         */
   int64_t d;           /* (initial) downsampling factor; d | N, M = N/d a     */
-                       /* power of two, M <= 8192 in this build              */
+                       /* power of two, M <= 2^26 (M > 8192: four-step FFT)  */
   int32_t a_max;       /* largest alias count decoded, 1..4 (paper: a_m = 4)  */
   int32_t max_iters;   /* ITER: number of levels, 1..a_max (0 -> a_max);     */
                        /* M / 2^(max_iters-1) must be >= 1                   */
@@ -116,7 +116,7 @@ typedef struct sft_plan_s* sft_plan_t;
  * of that shape: uploads the twiddle / omega tables and allocates the
  * workspace (plan-owned device memory, see sft_plan_workspace_bytes).
  * Must be called with the target device current.  Returns SFT_EINVAL,
- * SFT_EUNSUPPORTED (e.g. SFT_GENERAL, M > 8192), SFT_ENOMEM or SFT_ECUDA. */
+ * SFT_EUNSUPPORTED (e.g. M > 2^26), SFT_ENOMEM or SFT_ECUDA. */
 sft_status sft_plan_create(const sft_params* p, int64_t max_signals, sft_plan_t* out);
 
 /* Frees the plan and its device memory (synchronises the device). */

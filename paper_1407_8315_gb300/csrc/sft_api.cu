@@ -24,7 +24,7 @@ int ilog2(int64_t v) {
   return l;
 }
 
-constexpr int64_t kMaxFusedM = 8192;  // largest M one CTA transforms in this build
+constexpr int64_t kMaxM = int64_t(1) << 26;  // largest M = N/d (four-step FFT of 2^13 x 2^13)
 
 sft_status fill_defaults(sft_params* p) {
   if (p->a_max == 0) p->a_max = 4;
@@ -50,7 +50,7 @@ sft_status validate(const sft_params& p) {
     if (p.max_iters < 1 || p.max_iters > p.a_max) return SFT_EINVAL;
     if ((M0 >> (p.max_iters - 1)) < 1) return SFT_EINVAL;
   }
-  if (M0 > kMaxFusedM) return SFT_EUNSUPPORTED;
+  if (M0 > kMaxM) return SFT_EUNSUPPORTED;
   return SFT_OK;
 }
 

@@ -130,6 +130,8 @@ struct F64 {
   __device__ static __forceinline__ double2 out(V v, double scale) {
     return make_double2(v.rx * scale, v.ry * scale);
   }
+  __device__ static __forceinline__ V from_out(double2 o) { return V{o.x, o.y}; }
+  __device__ static __forceinline__ double out_norm(double2 o) { return o.x * o.x + o.y * o.y; }
 };
 
 struct FF {
@@ -230,6 +232,8 @@ struct FF {
     return make_float4(v.rh * scale, v.rl * scale, v.ih * scale, v.il * scale);
   }
   __device__ static __forceinline__ float out_norm_hi(float4 o) { return o.x * o.x + o.z * o.z; }
+  __device__ static __forceinline__ double out_norm(float4 o) { return (double)out_norm_hi(o); }
+  __device__ static __forceinline__ V from_out(float4 o) { return V{o.x, o.y, o.z, o.w}; }
   __device__ static __forceinline__ V from4(float4 o) { return V{o.x, o.y, o.z, o.w}; }
   __device__ static __forceinline__ float4 to4(V v) { return make_float4(v.rh, v.rl, v.ih, v.il); }
   __device__ static __forceinline__ V mulv(V a, V b) { return mul4(a, b.rh, b.rl, b.ih, b.il); }

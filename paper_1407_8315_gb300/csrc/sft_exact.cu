@@ -94,6 +94,103 @@ __global__ void __launch_bounds__(512) k_gather_fft(
   }
 }
 
+// ------------------------------------------- four-step FFT for M > 8192
+// M = M1 M2 with n = n1 M2 + n2 and k = k1 + M1 k2:
+//   A[k1][n2] = sum_{n1} x_d[n1 M2 + n2] e^{-2 pi i n1 k1 / M1}        (cols)
+//   Y[k1 + M1 k2] = sum_{n2} A[k1][n2] e^{-2 pi i n2 k1 / M} e^{-2 pi i n2 k2 / M2}
+// k_fft4_cols runs 8192/M1 column FFTs per CTA (each on M1/16 threads) and
+// writes twiddled rows W[k1][n2]; k_fft4_rows runs 8192/M2 row FFTs per CTA
+// and writes Y (times d).  Both move data in coalesced runs.
+constexpr int kFft4Points = 8192;
+
+template <class F>
+__global__ void __launch_bounds__(512) k_fft4_cols(
+    const typename F::In* __restrict__ x, int64_t x_stride, int64_t N, int64_t d, int log2M1,
+    int log2M2, int shift0, int log2Mt, const typename F::Tw* __restrict__ tw,
+    typename F::Out* __restrict__ W, int64_t w_sig, int nshift) {
+  extern __shared__ __align__(16) char smem[];
+  const int b = blockIdx.z, js = blockIdx.y;
+  const int64_t shift = shift0 + js;
+  const int M1 = 1 << log2M1, M2 = 1 << log2M2;
+  const int log2M = log2M1 + log2M2;
+  const int CB = kFft4Points >> log2M1;  // columns per CTA
+  const int tpg = M1 / 16;               // threads per column
+  const int tid = threadIdx.x, g = tid / tpg, t = tid % tpg;
+  const int c0 = blockIdx.x * CB;
+  const typename F::In* xs = x + (int64_t)b * x_stride;
+  char* buf = smem + (size_t)g * padded(M1) * F::kBytesPerPoint;
+  typename F::In v[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int64_t n = (int64_t)(t + i * tpg) * M2 + c0 + g;
+    v[i] = __ldg(xs + ((n * d + shift) & (N - 1)));
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) F::st(buf, M1, t + i * tpg, F::from_in(v[i]));
+  __syncthreads();
+  cta_fft<F>(buf, log2M1, log2Mt, tw, t, tpg);
+  // twiddle e^{-2 pi i n2 k1 / M} (table of e^{-2 pi i q / Mt}, Mt >= M)
+  for (int i = 0; i < 16; ++i) {
+    const int k1 = t + i * tpg;
+    const int64_t q = ((int64_t)(c0 + g) * k1) & ((int64_t(1) << log2M) - 1);
+    F::st(buf, M1, k1, F::mul_tw(F::ld(buf, M1, k1), __ldg(tw + (q << (log2Mt - log2M)))));
+  }
+  __syncthreads();
+  typename F::Out* Wo = W + (int64_t)b * w_sig + (int64_t)js * ((int64_t)M1 * M2);
+  for (int idx = tid; idx < CB * M1; idx += blockDim.x) {
+    const int k1 = idx / CB, c = idx % CB;
+    const char* bc = smem + (size_t)c * padded(M1) * F::kBytesPerPoint;
+    Wo[(int64_t)k1 * M2 + c0 + c] = F::out(F::ld(bc, M1, k1), 1);
+  }
+}
+
+template <class F>
+__global__ void __launch_bounds__(512) k_fft4_rows(
+    const typename F::Out* __restrict__ W, int64_t w_sig, int log2M1, int log2M2, int64_t d,
+    int log2Mt, const typename F::Tw* __restrict__ tw, void* __restrict__ out_v, int64_t out_sig,
+    int64_t out_row, int row0, unsigned long long* __restrict__ ymax2, int shift0) {
+  extern __shared__ __align__(16) char smem[];
+  typedef typename F::Out Out;
+  const int b = blockIdx.z, js = blockIdx.y;
+  const int M1 = 1 << log2M1, M2 = 1 << log2M2;
+  const int RB = kFft4Points >> log2M2;  // rows per CTA
+  const int tpg = M2 / 16;
+  const int tid = threadIdx.x, g = tid / tpg, t = tid % tpg;
+  const int r0 = blockIdx.x * RB;
+  const Out* Wi = W + (int64_t)b * w_sig + (int64_t)js * ((int64_t)M1 * M2);
+  for (int idx = tid; idx < RB * M2; idx += blockDim.x) {
+    const int gg = idx / M2, c = idx % M2;
+    char* bg = smem + (size_t)gg * padded(M2) * F::kBytesPerPoint;
+    F::st(bg, M2, c, F::from_out(Wi[(int64_t)(r0 + gg) * M2 + c]));
+  }
+  __syncthreads();
+  char* buf = smem + (size_t)g * padded(M2) * F::kBytesPerPoint;
+  cta_fft<F>(buf, log2M2, log2Mt, tw, t, tpg);
+  __syncthreads();
+  Out* o = reinterpret_cast<Out*>(out_v) + (int64_t)b * out_sig + (int64_t)(row0 + js) * out_row;
+  double lmax = 0.0;
+  for (int idx = tid; idx < RB * M2; idx += blockDim.x) {
+    const int k2 = idx / RB, gg = idx % RB;
+    const char* bg = smem + (size_t)gg * padded(M2) * F::kBytesPerPoint;
+    const Out w = F::out(F::ld(bg, M2, k2), d);
+    o[(int64_t)(r0 + gg) + (int64_t)M1 * k2] = w;
+    lmax = fmax(lmax, F::out_norm(w));
+  }
+  if (ymax2 != nullptr && shift0 + js == 0) {
+    __shared__ double wmax[32];
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o2));
+    if ((tid & 31) == 0) wmax[tid >> 5] = lmax;
+    __syncthreads();
+    if (tid < 32) {
+      double w = tid < (int)(blockDim.x >> 5) ? wmax[tid] : 0.0;
+#pragma unroll
+      for (int o2 = 16; o2 > 0; o2 >>= 1) w = fmax(w, __shfl_xor_sync(0xffffffffu, w, o2));
+      if (tid == 0) atomicMax(ymax2 + b, (unsigned long long)__double_as_longlong(w));
+    }
+  }
+}
+
 // ------------------------------------------------- per-level decode (ITER)
 struct LevelArgs {
   int64_t N, M, d, M0;
@@ -435,19 +532,28 @@ static int fft_threads(int log2M) {
   return M / 16 > 32 ? M / 16 : 32;
 }
 
-cudaError_t prepare_kernels(sft_plan_s* P) {
-  const int smem = padded((int)P->M0) * 16;
-  cudaError_t e;
-  if (P->p.precision == SFT_FP64)
-    e = cudaFuncSetAttribute(k_gather_fft<F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  else
-    e = cudaFuncSetAttribute(k_gather_fft<FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+template <class F>
+static cudaError_t prepare_kernels_t(int64_t M0) {
+  const int smem = padded((int)std::min<int64_t>(M0, kFft4Points)) * 16;
+  const int smem4 = padded(kFft4Points) * 16;
+  cudaError_t e = cudaFuncSetAttribute(k_gather_fft<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem);
+  if (e == cudaSuccess && M0 > kFft4Points)
+    e = cudaFuncSetAttribute(k_fft4_cols<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem4);
+  if (e == cudaSuccess && M0 > kFft4Points)
+    e = cudaFuncSetAttribute(k_fft4_rows<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem4);
   return e;
 }
 
+cudaError_t prepare_kernels(sft_plan_s* P) {
+  return P->p.precision == SFT_FP64 ? prepare_kernels_t<F64>(P->M0) : prepare_kernels_t<FF>(P->M0);
+}
+
 int launches_per_call(const sft_plan_s* P) {
-  if (P->p.mode == SFT_EXACT_FIXED) return 1 + 1 + P->p.a_max + 1;
-  return 3 * P->levels + 1;
+  if (P->p.mode == SFT_EXACT_FIXED) return (P->M0 > kFft4Points ? 2 : 1) + 1 + P->p.a_max + 1;
+  int fft = 0;
+  for (int l = 0; l < P->levels; ++l) fft += (P->M0 >> l) > kFft4Points ? 2 : 1;
+  return fft + 2 * P->levels + 1;
 }
 
 static cudaEvent_t pool_event(sft_plan_s* P) {
@@ -475,15 +581,39 @@ template <class F>
 static void launch_gather_fft(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride,
                               int64_t d, int log2M, int shift0, int nshift, void* out,
                               int64_t out_row, int row0, bool want_ymax, cudaStream_t st) {
-  dim3 grid(nshift, (unsigned)B);
-  const int nthr = fft_threads(log2M);
-  const size_t smem = (size_t)padded(1 << log2M) * F::kBytesPerPoint;
   static const char* names[] = {"gather_fft_l0", "gather_fft_l1", "gather_fft_l2", "gather_fft_l3"};
-  stage_begin(P, nshift > 2 ? "gather_fft_fixed" : names[shift0 / 2], st);
-  k_gather_fft<F><<<grid, nthr, smem, st>>>(
-      reinterpret_cast<const typename F::In*>(x), x_stride, P->p.N, d, log2M, shift0, P->log2M0,
-      reinterpret_cast<const typename F::Tw*>(P->tab.tw), out, P->ws.held_elems, out_row, row0,
-      want_ymax ? P->ws.ymax2 : nullptr);
+  static const char* cnames[] = {"gather_cols_l0", "gather_cols_l1", "gather_cols_l2",
+                                 "gather_cols_l3"};
+  static const char* rnames[] = {"fft_rows_l0", "fft_rows_l1", "fft_rows_l2", "fft_rows_l3"};
+  const int lvl = nshift > 2 ? 0 : shift0 / 2;
+  const auto* xin = reinterpret_cast<const typename F::In*>(x);
+  const auto* tw = reinterpret_cast<const typename F::Tw*>(P->tab.tw);
+  if ((1 << log2M) <= kFft4Points) {
+    dim3 grid(nshift, (unsigned)B);
+    const int nthr = fft_threads(log2M);
+    const size_t smem = (size_t)padded(1 << log2M) * F::kBytesPerPoint;
+    stage_begin(P, nshift > 2 ? "gather_fft_fixed" : names[lvl], st);
+    k_gather_fft<F><<<grid, nthr, smem, st>>>(xin, x_stride, P->p.N, d, log2M, shift0, P->log2M0,
+                                              tw, out, P->ws.held_elems, out_row, row0,
+                                              want_ymax ? P->ws.ymax2 : nullptr);
+    stage_end(P, st);
+    return;
+  }
+  // four-step: columns of length M1, rows of length M2, M1 >= M2
+  const int log2M2 = log2M / 2, log2M1 = log2M - log2M2;
+  const int64_t Mlev = int64_t(1) << log2M;
+  const unsigned ctas = (unsigned)(Mlev / kFft4Points);
+  const size_t smem = (size_t)padded(kFft4Points) * F::kBytesPerPoint;
+  auto* W = reinterpret_cast<typename F::Out*>(P->ws.fft4);
+  const int64_t w_sig = (int64_t)nshift * Mlev;
+  stage_begin(P, cnames[lvl], st);
+  k_fft4_cols<F><<<dim3(ctas, nshift, (unsigned)B), 512, smem, st>>>(
+      xin, x_stride, P->p.N, d, log2M1, log2M2, shift0, P->log2M0, tw, W, w_sig, nshift);
+  stage_end(P, st);
+  stage_begin(P, rnames[lvl], st);
+  k_fft4_rows<F><<<dim3(ctas, nshift, (unsigned)B), 512, smem, st>>>(
+      W, w_sig, log2M1, log2M2, d, P->log2M0, tw, out, P->ws.held_elems, out_row, row0,
+      want_ymax ? P->ws.ymax2 : nullptr, shift0);
   stage_end(P, st);
 }
 

@@ -36,6 +36,7 @@ struct Workspace {
   int32_t* qcount = nullptr;
   void* zero_base = nullptr;  // ymax2 | flags | qcount | slot_cnt
   size_t zero_bytes = 0;
+  void* fft4 = nullptr;  // four-step FFT intermediate (only when N/d > 8192)
 };
 
 // Lays the workspace of B signals out from `base` (or only sizes it when
@@ -64,6 +65,10 @@ inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, 
   off = al(off + (size_t)(B * M0 * 4) * 8);
   const size_t o_sp = off;
   off = al(off + (size_t)(B * M0 * 4) * 16);
+  // four-step FFT intermediate: one M0-point plane per shift of a launch
+  const int nsh = mode == SFT_EXACT_FIXED ? 2 * a_max : 2;
+  const size_t o_f4 = off;
+  if (M0 > 8192) off = al(off + (size_t)(B * nsh * M0) * 16);
   if (W != nullptr && base != nullptr) {
     W->held_elems = held_elems;
     for (int i = 0; i < 2; ++i) {
@@ -80,6 +85,7 @@ inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, 
     W->slot_cnt = reinterpret_cast<uint8_t*>(z + (size_t)B * 16 + 64);
     W->slot_s = reinterpret_cast<int64_t*>(base + o_ss);
     W->slot_p = base + o_sp;
+    W->fft4 = M0 > 8192 ? base + o_f4 : nullptr;
   }
   return off;
 }

@@ -59,7 +59,6 @@ def test_params_default(lib):
     ("N", 1000, 1), ("N", 4, 1), ("d", 3, 1), ("d", 1 << 23, 1), ("a_max", 5, 1),
     ("max_iters", 5, 1), ("mode", 7, 1), ("precision", 9, 1), ("reserved_", 1, 1),
     ("mode", 2, 5),          # SFT_GENERAL: not in this build
-    ("d", 64, 5),            # M = 2^16 bins: above the one-CTA FFT size
 ])
 def test_plan_create_rejects_before_touching_the_gpu(lib, field, value, status):
     from paper_1407_8315_gb300 import sft
@@ -68,6 +67,14 @@ def test_plan_create_rejects_before_touching_the_gpu(lib, field, value, status):
     h = C.c_void_p()
     assert lib.sft_plan_create(C.byref(p), 1, C.byref(h)) == status
     assert h.value is None
+
+
+def test_plan_create_rejects_too_many_bins(lib):
+    """N/d = 2^27 bins is above the four-step FFT limit (2^26)."""
+    from paper_1407_8315_gb300 import sft
+    p = sft.sft_params_default(1 << 28, 4096, 2, "iter", "mixed")
+    h = C.c_void_p()
+    assert lib.sft_plan_create(C.byref(p), 1, C.byref(h)) == sft.SFT_EUNSUPPORTED
 
 
 def test_null_arguments(lib):

@@ -90,10 +90,13 @@ def test_fp64_full_size(gpu, orc, mode):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("N,K,M", [(1 << 10, 6, 32), (1 << 12, 100, 256), (1 << 14, 600, 1024),
-                                   (1 << 18, 2048, 4096), (1 << 13, 2000, 8192)])
+                                   (1 << 18, 2048, 4096), (1 << 13, 2000, 8192),
+                                   (1 << 17, 6000, 1 << 14), (1 << 18, 7000, 1 << 15),
+                                   (1 << 20, 30000, 1 << 16)])
 def test_sizes_span_tiles(gpu, orc, prec, N, K, M):
-    """Bins per block 128: M = 32 is a partial block, M = 8192 the largest
-    one-CTA FFT; K / M from 0.2 to 0.5 exercises every level."""
+    """Fold blocks of 256 bins: M = 32 is a partial block; M = 8192 is the
+    largest one-CTA FFT and M >= 2^14 goes through the four-step FFT (every
+    level of M = 2^16 does); K / M from 0.2 to 0.5 exercises every level."""
     from paper_1407_8315_gb300 import Plan
     dt = np.complex128 if prec == "fp64" else np.complex64
     for mode in ("iter", "fixed"):
@@ -101,6 +104,17 @@ def test_sizes_span_tiles(gpu, orc, prec, N, K, M):
         xs, _, _ = siggen.batch_exact(N, K, [N + K + i for i in range(3)], mag=(1, 10), dtype=dt)
         _compare(orc, plan, xs, mode, cap=4 * M,
                  val_tol=FP64_VAL_TOL if prec == "fp64" else MIXED_VAL_TOL)
+
+
+@pytest.mark.parametrize("mode", ["iter", "fixed"])
+def test_large_single_signal(gpu, orc, mode):
+    """N = 2^27 complex64 (1 GiB), K = 2^16, M = 2^18 (d = 512): four-step
+    FFTs at every level."""
+    from paper_1407_8315_gb300 import Plan
+    N, K, M = 1 << 27, 1 << 16, 1 << 18
+    plan = Plan(N, K, N // M, mode, "mixed", max_signals=1)
+    xs = siggen.exact_signal(N, K, 2027, mag=(1, 10), dtype=np.complex64)[0][None, :]
+    _compare(orc, plan, xs, mode, cap=2 * K, val_tol=MIXED_VAL_TOL)
 
 
 def test_fig1_worked_example_on_gpu(gpu, orc):
