@@ -55,6 +55,12 @@ class _Params(C.Structure):
                 ("zero_tol", C.c_double), ("root_tol", C.c_double), ("res_tol", C.c_double)]
 
 
+class _GParams(C.Structure):
+    _fields_ = [("N", C.c_int64), ("K", C.c_int64), ("M", C.c_int64), ("a_max", C.c_int32),
+                ("r", C.c_int32), ("seed", C.c_uint64), ("keep", C.c_int32),
+                ("sp_iters", C.c_int32)]
+
+
 def _load():
     global _lib
     with _lock:
@@ -72,6 +78,15 @@ def _load():
             lib.orc_exact.argtypes = [P(C.c_double), P(_Params), C.c_int64, P(C.c_int64),
                                       P(C.c_double), P(C.c_int64)]
             lib.orc_exact.restype = C.c_int64
+            lib.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
+            lib.orc_splitmix64.restype = C.c_uint64
+            lib.orc_cs_shifts.argtypes = [C.c_uint64, C.c_int64, C.c_int, P(C.c_int64)]
+            lib.orc_hankel_svals.argtypes = [C.c_int, P(C.c_double), P(C.c_double)]
+            lib.orc_subspace_pursuit.argtypes = [C.c_int, C.c_int, P(C.c_double), P(C.c_double),
+                                                 C.c_int, C.c_int, P(C.c_double)]
+            lib.orc_general.argtypes = [P(C.c_double), P(_GParams), C.c_int64, P(C.c_int64),
+                                        P(C.c_double), P(C.c_ubyte)]
+            lib.orc_general.restype = C.c_int64
             _lib = lib
     return _lib
 
@@ -156,3 +171,59 @@ def exact(x, M0: int, a_max: int = 4, mode: int = ITER, max_iters: int | None = 
         raise ValueError("bad parameters")
     n = min(int(n), cap)
     return idx[:n].copy(), val[:n].copy(), int(unres.value)
+
+
+# --------------------------------------------- generally K-sparse (Alg. 2)
+def splitmix64(seed: int, i: int) -> int:
+    """Output i of the SplitMix64 stream of `seed`."""
+    return int(_load().orc_splitmix64(C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), i))
+
+
+def cs_shifts(seed: int, d: int, r: int) -> np.ndarray:
+    """The r distinct random shifts n_l in [0, d) drawn from `seed`."""
+    out = np.zeros(r, dtype=np.int64)
+    if _load().orc_cs_shifts(C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), int(d), int(r),
+                             out.ctypes.data_as(C.POINTER(C.c_int64))) != 0:
+        raise ValueError("need 0 <= r <= d")
+    return out
+
+
+def hankel_svals(m, n: int) -> np.ndarray:
+    """Singular values (descending) of the n x n Hankel matrix H_ij = m_{i+j}."""
+    m = _c128(m)
+    if m.size < 2 * n - 1:
+        raise ValueError("need 2n - 1 syndromes")
+    sv = np.zeros(n)
+    _load().orc_hankel_svals(int(n), _dp(m), sv.ctypes.data_as(C.POINTER(C.c_double)))
+    return sv
+
+
+def subspace_pursuit(Phi, y, ks: int, iters: int = 8) -> np.ndarray:
+    Phi = _c128(Phi)
+    y = _c128(y)
+    rows, cols = Phi.shape
+    b = np.zeros(cols, dtype=np.complex128)
+    n = _load().orc_subspace_pursuit(rows, cols, _dp(Phi), _dp(y), int(ks), int(iters), _dp(b))
+    if n < 0:
+        raise ValueError("subspace pursuit failed")
+    return b
+
+
+def general(x, M: int, K: int, a_max: int = 3, r: int | None = None, seed: int = 0,
+            keep: int = 2, sp_iters: int = 8, cap: int | None = None):
+    """Algorithm 2 on x (upcast to complex128).  Returns (idx, val, a_k)."""
+    x = _c128(x)
+    N = x.size
+    r = 3 * a_max if r is None else r
+    prm = _GParams(N=N, K=int(K), M=int(M), a_max=int(a_max), r=int(r),
+                   seed=int(seed) & 0xFFFFFFFFFFFFFFFF, keep=int(keep), sp_iters=int(sp_iters))
+    cap = int(K) * 2 + 16 if cap is None else int(cap)
+    idx = np.zeros(cap, dtype=np.int64)
+    val = np.zeros(cap, dtype=np.complex128)
+    ak = np.zeros(M, dtype=np.uint8)
+    n = _load().orc_general(_dp(x), C.byref(prm), cap, idx.ctypes.data_as(C.POINTER(C.c_int64)),
+                            _dp(val), ak.ctypes.data_as(C.POINTER(C.c_ubyte)))
+    if n < 0:
+        raise ValueError("bad parameters")
+    n = min(int(n), cap)
+    return idx[:n].copy(), val[:n].copy(), ak

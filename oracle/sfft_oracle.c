@@ -443,3 +443,307 @@ int64_t orc_exact(const double* xin, const orc_exact_params* prm, int64_t cap,
   free(T);
   return nS;
 }
+
+/* ===================================================================== */
+/*            generally K-sparse signals: Sec. III, Algorithm 2           */
+/* ===================================================================== */
+
+uint64_t orc_splitmix64(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+int orc_cs_shifts(uint64_t seed, int64_t d, int r, int64_t* out) {
+  if (d < 1 || r < 0 || r > d) return -1;
+  int64_t* a = (int64_t*)malloc((size_t)d * sizeof(int64_t));
+  if (!a) return -1;
+  for (int64_t i = 0; i < d; ++i) a[i] = i;
+  for (int i = 0; i < r; ++i) {
+    int64_t j = i + (int64_t)(orc_splitmix64(seed, (uint64_t)i) % (uint64_t)(d - i));
+    int64_t t = a[i];
+    a[i] = a[j];
+    a[j] = t;
+    out[i] = a[i];
+  }
+  free(a);
+  return 0;
+}
+
+/* One-sided Jacobi: rotate pairs of columns of A until every pair is
+ * orthogonal; the singular values are then the column norms. */
+int orc_hankel_svals(int n, const double* min, double* sv) {
+  if (n < 1 || n > 8) return -1;
+  const cplx* m = (const cplx*)min;
+  cplx A[64];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) A[i * n + j] = m[i + j];
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double alpha = 0, beta = 0;
+        cplx gamma = 0;
+        for (int i = 0; i < n; ++i) {
+          alpha += creal(conj(A[i * n + p]) * A[i * n + p]);
+          beta += creal(conj(A[i * n + q]) * A[i * n + q]);
+          gamma += conj(A[i * n + p]) * A[i * n + q];
+        }
+        double g = cabs(gamma);
+        if (!(g > 0) || !(alpha > 0) || !(beta > 0)) continue;
+        off = fmax(off, g / sqrt(alpha * beta));
+        if (!(g > 1e-15 * sqrt(alpha * beta))) continue;
+        /* make the inner product real: a_q <- e^{-i phi} a_q, then a real
+         * rotation with cot(2 theta) = (beta - alpha) / (2 |gamma|) */
+        cplx ph = gamma / g;
+        double zeta = (beta - alpha) / (2.0 * g);
+        double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        for (int i = 0; i < n; ++i) {
+          cplx ap = A[i * n + p], aq = A[i * n + q] * conj(ph);
+          A[i * n + p] = c * ap - s * aq;
+          A[i * n + q] = s * ap + c * aq;
+        }
+      }
+    if (off <= 1e-15) break;
+  }
+  for (int j = 0; j < n; ++j) {
+    double s2 = 0;
+    for (int i = 0; i < n; ++i) s2 += creal(conj(A[i * n + j]) * A[i * n + j]);
+    sv[j] = sqrt(s2);
+  }
+  for (int i = 1; i < n; ++i) /* descending */
+    for (int j = i; j > 0 && sv[j - 1] < sv[j]; --j) {
+      double t = sv[j];
+      sv[j] = sv[j - 1];
+      sv[j - 1] = t;
+    }
+  return 0;
+}
+
+/* indices of the ks largest values (ties: smaller index first), returned in
+ * ascending index order */
+static int top_ks(int n, const double* v, const unsigned char* allowed, int ks, int* out) {
+  unsigned char taken[64] = {0};
+  int cnt = 0;
+  for (int r = 0; r < ks; ++r) {
+    int best = -1;
+    for (int i = 0; i < n; ++i)
+      if ((!allowed || allowed[i]) && !taken[i] && (best < 0 || v[i] > v[best])) best = i;
+    if (best < 0) break;
+    taken[best] = 1;
+    ++cnt;
+  }
+  int w = 0;
+  for (int i = 0; i < n; ++i)
+    if (taken[i]) out[w++] = i;
+  return cnt;
+}
+
+/* least squares on the columns T of Phi (normal equations); fills the
+ * coefficients and the residual y - Phi_T x; returns |res|^2 or -1 */
+static double ls_on(int rows, int cols, const cplx* Phi, const cplx* y, const int* T, int nT,
+                    cplx* x, cplx* res) {
+  cplx G[64], g[8];
+  for (int u = 0; u < nT; ++u) {
+    g[u] = 0;
+    for (int v = 0; v < nT; ++v) G[u * nT + v] = 0;
+    for (int i = 0; i < rows; ++i) {
+      g[u] += conj(Phi[i * cols + T[u]]) * y[i];
+      for (int v = 0; v < nT; ++v) G[u * nT + v] += conj(Phi[i * cols + T[u]]) * Phi[i * cols + T[v]];
+    }
+  }
+  if (!solve_lin(nT, G, g, x)) return -1;
+  double rn = 0;
+  for (int i = 0; i < rows; ++i) {
+    cplx f = 0;
+    for (int u = 0; u < nT; ++u) f += Phi[i * cols + T[u]] * x[u];
+    res[i] = y[i] - f;
+    rn += creal(conj(res[i]) * res[i]);
+  }
+  return rn;
+}
+
+int orc_subspace_pursuit(int rows, int cols, const double* Phin, const double* yn, int ks,
+                         int iters, double* bout) {
+  const cplx* Phi = (const cplx*)Phin;
+  const cplx* y = (const cplx*)yn;
+  cplx* b = (cplx*)bout;
+  if (rows < 1 || rows > 32 || cols < 1 || cols > 32) return -1;
+  for (int j = 0; j < cols; ++j) b[j] = 0;
+  if (ks > cols) ks = cols;
+  if (ks <= 0) return 0;
+  double corr[32];
+  cplx res[32], x[8], xn[8], resn[32];
+  int T[8], nT;
+  /* initialisation: the ks columns most correlated with y */
+  for (int j = 0; j < cols; ++j) {
+    cplx c = 0;
+    for (int i = 0; i < rows; ++i) c += conj(Phi[i * cols + j]) * y[i];
+    corr[j] = cabs(c);
+  }
+  nT = top_ks(cols, corr, NULL, ks, T);
+  double rn = ls_on(rows, cols, Phi, y, T, nT, x, res);
+  if (rn < 0) return -1;
+  for (int it = 0; it < iters; ++it) {
+    /* expand by the ks columns most correlated with the residual */
+    for (int j = 0; j < cols; ++j) {
+      cplx c = 0;
+      for (int i = 0; i < rows; ++i) c += conj(Phi[i * cols + j]) * res[i];
+      corr[j] = cabs(c);
+    }
+    int add[8];
+    int na = top_ks(cols, corr, NULL, ks, add);
+    unsigned char in2[32] = {0};
+    for (int u = 0; u < nT; ++u) in2[T[u]] = 1;
+    for (int u = 0; u < na; ++u) in2[add[u]] = 1;
+    int T2[16], n2 = 0;
+    for (int j = 0; j < cols; ++j)
+      if (in2[j]) T2[n2++] = j;
+    /* least squares on the union, keep the ks largest coefficients */
+    cplx x2[16], r2[32];
+    if (ls_on(rows, cols, Phi, y, T2, n2, x2, r2) < 0) break;
+    double mag[32] = {0};
+    unsigned char allow[32] = {0};
+    for (int u = 0; u < n2; ++u) {
+      mag[T2[u]] = cabs(x2[u]);
+      allow[T2[u]] = 1;
+    }
+    int Tn[8];
+    int nn = top_ks(cols, mag, allow, ks, Tn);
+    double rnn = ls_on(rows, cols, Phi, y, Tn, nn, xn, resn);
+    if (rnn < 0 || rnn >= rn) break; /* no improvement: keep the previous support */
+    nT = nn;
+    for (int u = 0; u < nT; ++u) {
+      T[u] = Tn[u];
+      x[u] = xn[u];
+    }
+    for (int i = 0; i < rows; ++i) res[i] = resn[i];
+    rn = rnn;
+  }
+  for (int u = 0; u < nT; ++u) b[T[u]] = x[u];
+  return nT;
+}
+
+typedef struct {
+  double v;
+  int64_t i;
+} keyed;
+
+static int cmp_desc(const void* A, const void* B) {
+  const keyed* a = (const keyed*)A;
+  const keyed* b = (const keyed*)B;
+  if (a->v > b->v) return -1;
+  if (a->v < b->v) return 1;
+  return (a->i > b->i) - (a->i < b->i);
+}
+
+int64_t orc_general(const double* xin, const orc_general_params* p, int64_t cap, int64_t* idx,
+                    double* val, unsigned char* a_k_out) {
+  const int64_t N = p->N, M = p->M, K = p->K;
+  const int am = p->a_max, r = p->r;
+  if (!is_pow2(N) || !is_pow2(M) || M > N || am < 1 || am > 4 || r < 1 || r > 32 ||
+      p->keep < 1 || K < 0)
+    return -1;
+  const int64_t d = N / M;
+  if (r > d) return -1;
+  int64_t ns[32];
+  if (orc_cs_shifts(p->seed, d, r, ns) != 0) return -1;
+  const int nc = 2 * am;
+  cplx* Yc = (cplx*)malloc((size_t)nc * (size_t)M * sizeof(cplx));
+  cplx* Ys = (cplx*)malloc((size_t)r * (size_t)M * sizeof(cplx));
+  keyed* sv = (keyed*)malloc((size_t)M * (size_t)am * sizeof(keyed));
+  unsigned char* ak = (unsigned char*)calloc((size_t)M, 1);
+  entry* S = NULL;
+  int64_t nS = 0, capS = 0;
+  if (!Yc || !Ys || !sv || !ak) {
+    free(Yc);
+    free(Ys);
+    free(sv);
+    free(ak);
+    return -1;
+  }
+  /* Part 1 (lines 02-10): consecutive shifts 0..2a_m-1 and the r random
+   * shifts, each d * FFT_M */
+  for (int j = 0; j < nc; ++j) orc_syndrome(xin, N, d, j, (double*)&Yc[(size_t)j * M]);
+  for (int l = 0; l < r; ++l) orc_syndrome(xin, N, d, ns[l], (double*)&Ys[(size_t)l * M]);
+  /* Part 2 (lines 11-21): singular values of every bin's a_m x a_m Hankel
+   * matrix (m_0 .. m_{2a_m-2}, Eq. (26)); the K largest vote */
+  for (int64_t k = 0; k < M; ++k) {
+    cplx m[8];
+    double s[4];
+    for (int j = 0; j < 2 * am - 1; ++j) m[j] = Yc[(size_t)j * M + k];
+    orc_hankel_svals(am, (const double*)m, s);
+    for (int i = 0; i < am; ++i) {
+      sv[k * am + i].v = s[i];
+      sv[k * am + i].i = k * am + i;
+    }
+  }
+  qsort(sv, (size_t)(M * am), sizeof(keyed), cmp_desc);
+  const int64_t nvote = K < M * am ? K : M * am;
+  for (int64_t e = 0; e < nvote; ++e) ak[sv[e].i / am] += 1;
+  /* Parts 3-4 (lines 22-29): pruning Steps 2-3 and Subspace Pursuit */
+  for (int64_t k = 0; k < M; ++k) {
+    const int a = ak[k];
+    if (a == 0) continue;
+    cplx m[8];
+    for (int j = 0; j < 2 * a; ++j) m[j] = Yc[(size_t)j * M + k];
+    /* (a): the a x a Hankel system with the observed syndromes */
+    cplx H[16], rhs[4], c[4];
+    for (int i = 0; i < a; ++i) {
+      for (int j = 0; j < a; ++j) H[i * a + j] = m[i + j];
+      rhs[i] = -m[a + i];
+    }
+    if (!solve_lin(a, H, rhs, c)) continue;
+    /* (b)-(c): |P~(z)| at every candidate z = omega^{k + tM} of U_k; keep
+     * the min(d, keep * a) smallest (ties: smaller t) */
+    int64_t nkeep = (int64_t)p->keep * a < d ? (int64_t)p->keep * a : d;
+    if (nkeep > 32) nkeep = 32;
+    double* pv = (double*)malloc((size_t)d * sizeof(double));
+    unsigned char* tk = (unsigned char*)calloc((size_t)d, 1);
+    /* P(z) = z^a + c_{a-1} z^{a-1} + ... + c_0 by Horner */
+    for (int64_t t = 0; t < d; ++t) {
+      cplx z = omega_pow(N, k + t * M), P = 1;
+      for (int j = a - 1; j >= 0; --j) P = P * z + c[j];
+      pv[t] = cabs(P);
+    }
+    int64_t kept[32];
+    int nk = 0;
+    for (int64_t rr = 0; rr < nkeep; ++rr) {
+      int64_t best = -1;
+      for (int64_t t = 0; t < d; ++t)
+        if (!tk[t] && (best < 0 || pv[t] < pv[best])) best = t;
+      tk[best] = 1;
+    }
+    for (int64_t t = 0; t < d; ++t)
+      if (tk[t]) kept[nk++] = t;
+    free(pv);
+    free(tk);
+    /* Step 3: Phi_p[j][u] = omega^{(k + kept_u M) n_j}, y_j = Y_{n_j}[k] */
+    cplx Phi[32 * 32], y[32], b[32];
+    for (int j = 0; j < r; ++j) {
+      y[j] = Ys[(size_t)j * M + k];
+      for (int u = 0; u < nk; ++u) Phi[j * nk + u] = omega_pow(N, (k + kept[u] * M) * ns[j]);
+    }
+    int nz = orc_subspace_pursuit(r, nk, (const double*)Phi, (const double*)y, a, p->sp_iters,
+                                  (double*)b);
+    if (nz <= 0) continue;
+    for (int u = 0; u < nk; ++u)
+      if (b[u] != 0) push(&S, &nS, &capS, k + kept[u] * M, b[u]);
+  }
+  qsort(S, (size_t)nS, sizeof(entry), cmp_entry);
+  const int64_t nout = nS < cap ? nS : cap;
+  for (int64_t e = 0; e < nout; ++e) {
+    idx[e] = S[e].s;
+    val[2 * e] = creal(S[e].v);
+    val[2 * e + 1] = cimag(S[e].v);
+  }
+  if (a_k_out) memcpy(a_k_out, ak, (size_t)M);
+  free(S);
+  free(Yc);
+  free(Ys);
+  free(sv);
+  free(ak);
+  return nS;
+}

@@ -74,3 +74,54 @@ int64_t orc_exact(const double* x, const orc_exact_params* p, int64_t cap,
 }
 #endif
 #endif
+
+#ifndef SFFT_ORACLE_GENERAL_H
+#define SFFT_ORACLE_GENERAL_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- generally K-sparse signals (Sec. III, Algorithm 2) ---------------- */
+
+/* SplitMix64 (Steele, Lea, Flood 2014): output i of the stream seeded with
+ * `seed` (counter-based: state = seed + (i+1) * 0x9E3779B97F4A7C15). */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t i);
+
+/* r distinct shifts uniform in [0, d) (reading of Sec. III-A: "uniformly
+ * drawn", without replacement so no measurement repeats): partial
+ * Fisher-Yates on 0..d-1 driven by the SplitMix64 stream of `seed`,
+ * draw i swapping position i with i + (u_i mod (d - i)).  Returns 0 / -1. */
+int orc_cs_shifts(uint64_t seed, int64_t d, int r, int64_t* out);
+
+/* Singular values (descending) of the n x n complex Hankel matrix
+ * H_ij = m_{i+j} (Eq. (26)), by one-sided Jacobi in FP64. */
+int orc_hankel_svals(int n, const double* m, double* sv);
+
+/* Subspace Pursuit (Dai and Dai 2009) for y = Phi b with sparsity ks:
+ * Phi is rows x cols (row-major, complex), at most `iters` iterations.
+ * Writes b (cols complex values, ks of them non-zero) and returns the
+ * number of non-zeros (or -1). */
+int orc_subspace_pursuit(int rows, int cols, const double* Phi, const double* y, int ks,
+                         int iters, double* b);
+
+typedef struct {
+  int64_t N;        /* signal length                                        */
+  int64_t K;        /* number of significant frequencies kept               */
+  int64_t M;        /* bins, d = N / M                                      */
+  int32_t a_max;    /* a_m: syndromes 0..2a_m-1, Hankel a_m x a_m           */
+  int32_t r;        /* random shifts for the CS measurements (3 a_m)        */
+  uint64_t seed;    /* draws the random shifts                              */
+  int32_t keep;     /* candidates kept per significant term (2: O(a) = 2a)  */
+  int32_t sp_iters; /* Subspace Pursuit iteration cap                       */
+} orc_general_params;
+
+/* Algorithm 2.  Writes the recovered (s, X[s]) in ascending s (at most cap)
+ * and, if a_k is not NULL, the vote a_k of every bin (M bytes).  Returns the
+ * number of entries or -1. */
+int64_t orc_general(const double* x, const orc_general_params* p, int64_t cap, int64_t* idx,
+                    double* val, unsigned char* a_k);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
