@@ -22,6 +22,17 @@
  *   SFT_EXACT_FIXED  the non-iterative method (Fig. 1(b)): all 2 a_max shifts
  *                    at d, each active bin decoded once with the smallest
  *                    a <= a_max that validates.
+ *   SFT_GENERAL      generally K-sparse signals, Algorithm 2 (Sec. III): the
+ *                    2 a_max consecutive shifts and r = n_cs_shifts random
+ *                    shifts n_l (drawn from `seed`); per bin the singular
+ *                    values of the a_max x a_max Hankel matrix of
+ *                    m_0..m_{2a_max-2} (Eq. (26)); the K largest over all
+ *                    bins give each bin its count a_k; per bin with a_k > 0
+ *                    the a_k-term locator is evaluated at all d candidates,
+ *                    the 2 a_k smallest |P~| are kept (pruning Steps 2-3)
+ *                    and Subspace Pursuit on the pruned sensing matrix
+ *                    Phi_p[j][t] = omega^{(k + tM) n_j} (Eq. (22)) returns
+ *                    a_k values.
  *
  * Precision.
  *   SFT_FP64   input complex128 (interleaved re, im doubles); FFTs, folds,
@@ -71,12 +82,12 @@ typedef struct {
   int64_t K;           /* sparsity; the result capacity must be >= K         */
   int64_t d;           /* (initial) downsampling factor; d | N, M = N/d a     */
                        /* power of two, M <= 2^26 (M > 8192: four-step FFT)  */
-  int32_t a_max;       /* largest alias count decoded, 1..4 (paper: a_m = 4)  */
+  int32_t a_max;       /* largest alias count, 1..4 (0 -> 4 exact, 3 general) */
   int32_t max_iters;   /* ITER: number of levels, 1..a_max (0 -> a_max);     */
                        /* M / 2^(max_iters-1) must be >= 1                   */
   int32_t mode;        /* sft_mode                                           */
   int32_t precision;   /* sft_precision                                      */
-  int32_t n_cs_shifts; /* SFT_GENERAL only (random shifts r); 0 -> 3 a_max    */
+  int32_t n_cs_shifts; /* SFT_GENERAL: random shifts r, 1..16, r <= d (0 -> 3 a_max) */
   int32_t reserved_;   /* must be 0                                          */
   uint64_t seed;       /* SFT_GENERAL only: draws the random shifts          */
   double zero_tol;     /* bin active iff |m| > zero_tol * max_k |Y_{d,0}[k]| */
@@ -85,7 +96,8 @@ typedef struct {
 } sft_params;
 
 /* Fills *p with the paper's defaults for (N, K, d, mode, precision):
- * a_max = 4, max_iters = 4, and tolerances keyed to the input precision
+ * a_max = 4 (3 for SFT_GENERAL, with r = 9 random shifts), max_iters =
+ * a_max, seed 0, and tolerances keyed to the input precision
  * (FP64: zero 1e-10, root 0.1, residual 1e-9; MIXED: 1e-6, 0.1, 1e-6).
  * Returns SFT_EINVAL for a NULL pointer, SFT_OK otherwise (validation of
  * the sizes happens in sft_plan_create). */
@@ -147,6 +159,24 @@ sft_status sft_exact(sft_plan_t plan, int64_t n_signals, const void* x, int64_t 
  *     place; otherwise they are staged on the device and copied back. */
 sft_status sft_exact_host(sft_plan_t plan, int64_t n_signals, const void* x_host,
                           int64_t x_stride, const sft_result* r_host, void* stream);
+
+/* Generally K-sparse transform (Algorithm 2) of n_signals signals; the plan
+ * must have mode SFT_GENERAL.  Arguments, layout and behaviour as for
+ * sft_exact; at most K entries per signal (sum of the votes a_k); the
+ * `unresolved` count is 0 (the method has no unsolved-bin notion). */
+sft_status sft_general(sft_plan_t plan, int64_t n_signals, const void* x, int64_t x_stride,
+                       const sft_result* r, void* stream);
+
+/* Host-memory variant of sft_general (as sft_exact_host). */
+sft_status sft_general_host(sft_plan_t plan, int64_t n_signals, const void* x_host,
+                            int64_t x_stride, const sft_result* r_host, void* stream);
+
+/* The random shifts n_l of an SFT_GENERAL plan: r distinct values in
+ * [0, d), a partial Fisher-Yates shuffle of 0..d-1 whose draw i exchanges
+ * positions i and i + (u_i mod (d - i)), u_i the i-th output of SplitMix64
+ * (Steele, Lea, Flood 2014) seeded with params.seed.  Writes up to `cap`
+ * into out (host) and returns r (0 for exact plans, -1 for a NULL plan). */
+int32_t sft_plan_cs_shifts(sft_plan_t plan, int64_t* out, int32_t cap);
 
 /* Allocation-free variant of sft_exact (the paper has no counterpart: this
  * is a deployment interface).  Some callers cannot allocate device memory

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -27,7 +28,8 @@ int ilog2(int64_t v) {
 constexpr int64_t kMaxM = int64_t(1) << 26;  // largest M = N/d (four-step FFT of 2^13 x 2^13)
 
 sft_status fill_defaults(sft_params* p) {
-  if (p->a_max == 0) p->a_max = 4;
+  if (p->a_max == 0) p->a_max = p->mode == SFT_GENERAL ? 3 : 4;
+  if (p->mode == SFT_GENERAL && p->n_cs_shifts == 0) p->n_cs_shifts = 3 * p->a_max;
   if (p->max_iters == 0) p->max_iters = p->a_max;
   const bool fp64 = p->precision == SFT_FP64;
   if (!(p->zero_tol > 0)) p->zero_tol = fp64 ? 1e-10 : 1e-6;
@@ -36,21 +38,31 @@ sft_status fill_defaults(sft_params* p) {
   return SFT_OK;
 }
 
+sft_status why(sft_status st, const char* msg) {
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s", msg);
+  return st;
+}
+
 sft_status validate(const sft_params& p) {
-  if (!is_pow2(p.N) || p.N < 8 || p.N > (int64_t(1) << 30)) return SFT_EINVAL;
-  if (p.K < 0 || p.K > p.N) return SFT_EINVAL;
-  if (!is_pow2(p.d) || p.d > p.N) return SFT_EINVAL;
-  if (p.a_max < 1 || p.a_max > 4) return SFT_EINVAL;
-  if (p.precision != SFT_FP64 && p.precision != SFT_MIXED) return SFT_EINVAL;
-  if (p.mode == SFT_GENERAL) return SFT_EUNSUPPORTED;
-  if (p.mode != SFT_EXACT_ITER && p.mode != SFT_EXACT_FIXED) return SFT_EINVAL;
-  if (p.reserved_ != 0) return SFT_EINVAL;
+  if (!is_pow2(p.N) || p.N < 8 || p.N > (int64_t(1) << 30))
+    return why(SFT_EINVAL, "N must be a power of two in [2^3, 2^30]");
+  if (p.K < 0 || p.K > p.N) return why(SFT_EINVAL, "K must lie in [0, N]");
+  if (!is_pow2(p.d) || p.d > p.N) return why(SFT_EINVAL, "d must be a power of two <= N");
+  if (p.a_max < 1 || p.a_max > 4) return why(SFT_EINVAL, "a_max must lie in [1, 4]");
+  if (p.precision != SFT_FP64 && p.precision != SFT_MIXED)
+    return why(SFT_EINVAL, "unknown precision");
+  if (p.mode != SFT_EXACT_ITER && p.mode != SFT_EXACT_FIXED && p.mode != SFT_GENERAL)
+    return why(SFT_EINVAL, "unknown mode");
+  if (p.mode == SFT_GENERAL && (p.n_cs_shifts < 1 || p.n_cs_shifts > 16 || p.n_cs_shifts > p.d))
+    return why(SFT_EINVAL, "n_cs_shifts must lie in [1, min(16, d)]");
+  if (p.reserved_ != 0) return why(SFT_EINVAL, "reserved_ must be 0");
   const int64_t M0 = p.N / p.d;
   if (p.mode == SFT_EXACT_ITER) {
-    if (p.max_iters < 1 || p.max_iters > p.a_max) return SFT_EINVAL;
-    if ((M0 >> (p.max_iters - 1)) < 1) return SFT_EINVAL;
+    if (p.max_iters < 1 || p.max_iters > p.a_max)
+      return why(SFT_EINVAL, "max_iters must lie in [1, a_max]");
+    if ((M0 >> (p.max_iters - 1)) < 1) return why(SFT_EINVAL, "N/d too small for max_iters");
   }
-  if (M0 > kMaxM) return SFT_EUNSUPPORTED;
+  if (M0 > kMaxM) return why(SFT_EUNSUPPORTED, "N/d above 2^26");
   return SFT_OK;
 }
 
@@ -61,10 +73,32 @@ cudaError_t dalloc(T** ptr, size_t count, size_t* total) {
 }
 
 void free_plan_memory(sft_plan_s* P) {
-  void* ptrs[] = {P->tab.om_hi,    P->tab.om_lo,    P->tab.tw,  P->tab.om_hi_ff,
-                  P->tab.om_lo_ff, P->ws_base,      P->x_stage, P->r_stage};
+  void* ptrs[] = {P->tab.om_hi, P->tab.om_lo,    P->tab.tw,  P->tab.om_hi_ff, P->tab.om_lo_ff,
+                  P->tab.cs_shifts, P->ws_base, P->x_stage, P->r_stage};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014), output i of the stream of `seed`
+uint64_t splitmix64(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// The r random shifts of the general path: r distinct values in [0, d) by
+// a partial Fisher-Yates shuffle of 0..d-1, draw i exchanging positions i
+// and i + (u_i mod (d - i)).
+std::vector<int64_t> draw_cs_shifts(uint64_t seed, int64_t d, int r) {
+  std::vector<int64_t> a((size_t)d), out((size_t)r);
+  for (int64_t i = 0; i < d; ++i) a[(size_t)i] = i;
+  for (int i = 0; i < r; ++i) {
+    const int64_t j = i + (int64_t)(splitmix64(seed, (uint64_t)i) % (uint64_t)(d - i));
+    std::swap(a[(size_t)i], a[(size_t)j]);
+    out[(size_t)i] = a[(size_t)i];
+  }
+  return out;
 }
 
 // omega^e = e^{2 pi i e / N} and e^{-2 pi i q / M0}, rounded from long double
@@ -83,6 +117,13 @@ cudaError_t upload_tables(sft_plan_s* P, size_t* total) {
     hi[i] = make_double2((double)cosl(t), (double)sinl(t));
   }
   cudaError_t e;
+  if (P->p.mode == SFT_GENERAL) {
+    P->cs_host = draw_cs_shifts(P->p.seed, P->p.d, P->p.n_cs_shifts);
+    if ((e = dalloc(&P->tab.cs_shifts, P->cs_host.size(), total)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(P->tab.cs_shifts, P->cs_host.data(), P->cs_host.size() * sizeof(int64_t),
+                        cudaMemcpyHostToDevice)))
+      return e;
+  }
   if ((e = dalloc(&P->tab.om_lo, n_lo, total)) != cudaSuccess) return e;
   if ((e = dalloc(&P->tab.om_hi, n_hi, total)) != cudaSuccess) return e;
   P->tab.om_lo_bits = lo_bits;
@@ -131,13 +172,14 @@ cudaError_t upload_tables(sft_plan_s* P, size_t* total) {
 }
 
 cudaError_t alloc_workspace(sft_plan_s* P, size_t* total) {
-  const size_t bytes =
-      sft::layout_workspace(nullptr, nullptr, P->max_signals, P->M0, P->p.mode, P->p.a_max);
+  const size_t bytes = sft::layout_workspace(nullptr, nullptr, P->max_signals, P->M0, P->p.mode,
+                                             P->p.a_max, P->p.n_cs_shifts);
   char* base = nullptr;
   cudaError_t e = dalloc(&base, bytes, total);
   if (e != cudaSuccess) return e;
   P->ws_base = base;
-  sft::layout_workspace(&P->ws, base, P->max_signals, P->M0, P->p.mode, P->p.a_max);
+  sft::layout_workspace(&P->ws, base, P->max_signals, P->M0, P->p.mode, P->p.a_max,
+                        P->p.n_cs_shifts);
   return cudaSuccess;
 }
 
@@ -162,6 +204,8 @@ sft_status sft_params_default(sft_params* p, int64_t N, int64_t K, int64_t d, in
   p->max_iters = 4;
   p->mode = mode;
   p->precision = precision;
+  p->a_max = 0;
+  p->max_iters = 0;
   fill_defaults(p);
   return SFT_OK;
 }
@@ -229,8 +273,8 @@ static sft_status check_call(sft_plan_t P, int64_t n, const void* x, int64_t x_s
   return SFT_OK;
 }
 
-sft_status sft_exact(sft_plan_t P, int64_t n, const void* x, int64_t x_stride,
-                     const sft_result* r, void* stream) {
+static sft_status run_device(sft_plan_t P, int64_t n, const void* x, int64_t x_stride,
+                             const sft_result* r, void* stream) {
   sft_status st = check_call(P, n, x, x_stride, r);
   if (st != SFT_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -253,8 +297,8 @@ static void* mapped(const void* h) {
   return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
-sft_status sft_exact_host(sft_plan_t P, int64_t n, const void* x_host, int64_t x_stride,
-                          const sft_result* rh, void* stream) {
+static sft_status run_host(sft_plan_t P, int64_t n, const void* x_host, int64_t x_stride,
+                           const sft_result* rh, void* stream) {
   sft_status st = check_call(P, n, x_host, x_stride, rh);
   if (st != SFT_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -337,6 +381,46 @@ sft_status sft_exact_host(sft_plan_t P, int64_t n, const void* x_host, int64_t x
     return SFT_ECUDA;
   }
   return SFT_OK;
+}
+
+static sft_status want_mode(sft_plan_t P, bool general) {
+  if (!P) return reject("NULL plan (%lld %lld)", 0, 0);
+  if ((P->p.mode == SFT_GENERAL) != general)
+    return reject(general ? "plan mode %lld is not SFT_GENERAL (%lld)"
+                          : "plan mode %lld is SFT_GENERAL (%lld): use sft_general",
+                  P->p.mode, 0);
+  return SFT_OK;
+}
+
+sft_status sft_exact(sft_plan_t P, int64_t n, const void* x, int64_t x_stride,
+                     const sft_result* r, void* stream) {
+  sft_status st = want_mode(P, false);
+  return st != SFT_OK ? st : run_device(P, n, x, x_stride, r, stream);
+}
+
+sft_status sft_exact_host(sft_plan_t P, int64_t n, const void* x_host, int64_t x_stride,
+                          const sft_result* rh, void* stream) {
+  sft_status st = want_mode(P, false);
+  return st != SFT_OK ? st : run_host(P, n, x_host, x_stride, rh, stream);
+}
+
+sft_status sft_general(sft_plan_t P, int64_t n, const void* x, int64_t x_stride,
+                       const sft_result* r, void* stream) {
+  sft_status st = want_mode(P, true);
+  return st != SFT_OK ? st : run_device(P, n, x, x_stride, r, stream);
+}
+
+sft_status sft_general_host(sft_plan_t P, int64_t n, const void* x_host, int64_t x_stride,
+                            const sft_result* rh, void* stream) {
+  sft_status st = want_mode(P, true);
+  return st != SFT_OK ? st : run_host(P, n, x_host, x_stride, rh, stream);
+}
+
+int32_t sft_plan_cs_shifts(sft_plan_t P, int64_t* out, int32_t cap) {
+  if (!P) return -1;
+  const int32_t n = (int32_t)P->cs_host.size();
+  for (int32_t i = 0; i < n && i < cap && out; ++i) out[i] = P->cs_host[(size_t)i];
+  return n;
 }
 
 static void drop_stage_recs(sft_plan_s* P) {

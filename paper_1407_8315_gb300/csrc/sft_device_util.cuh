@@ -1,0 +1,61 @@
+// sft_device_util.cuh -- device helpers shared by the kernel files: filing
+// recovered frequencies under their level-0 bins and warp-aggregated queue
+// appends.
+#pragma once
+
+#include "sft_common.cuh"
+
+namespace sft {
+
+// File the a recovered frequencies of one decode event under their level-0
+// bins (the calling thread owns every level-0 bin congruent to its bin).
+template <class F, int A>
+__device__ __forceinline__ void file_solution(const int64_t* s, const cdbl* p, int64_t M0,
+                                              uint8_t* cnt, int64_t* ss,
+                                              typename Store<F>::T* sp, int32_t* flag) {
+#pragma unroll
+  for (int j = 0; j < A; ++j) {
+    const int64_t k0 = s[j] & (M0 - 1);
+    const int c = cnt[k0];
+    if (c < 4) {
+      ss[k0 * 4 + c] = s[j];
+      sp[k0 * 4 + c] = Store<F>::from_d(p[j]);
+      cnt[k0] = (uint8_t)(c + 1);
+    } else {
+      atomicOr(flag, 1);
+    }
+  }
+}
+
+// Append (b, k) to a device queue when `pred`; one atomic per warp.  Every
+// lane of the warp must call this (inactive lanes with pred = false).
+__device__ __forceinline__ void queue_push(bool pred, int b, int k, int2* q, int* count) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned mask = __ballot_sync(0xffffffffu, pred);
+  if (mask == 0u) return;
+  const int leader = __ffs(mask) - 1;
+  int base = 0;
+  if ((int)lane == leader) base = atomicAdd(count, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (pred) q[base + __popc(mask & ((1u << lane) - 1u))] = make_int2(b, k);
+}
+
+// File n recovered frequencies (n known only at run time).
+template <class F>
+__device__ __forceinline__ void file_n(int n, const int64_t* s, const cdbl* p, int64_t M0,
+                                       uint8_t* cnt, int64_t* ss, typename Store<F>::T* sp,
+                                       int32_t* flag) {
+  for (int j = 0; j < n; ++j) {
+    const int64_t k0 = s[j] & (M0 - 1);
+    const int c = cnt[k0];
+    if (c < 4) {
+      ss[k0 * 4 + c] = s[j];
+      sp[k0 * 4 + c] = Store<F>::from_d(p[j]);
+      cnt[k0] = (uint8_t)(c + 1);
+    } else {
+      atomicOr(flag, 1);
+    }
+  }
+}
+
+}  // namespace sft

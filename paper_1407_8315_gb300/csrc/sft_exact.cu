@@ -26,6 +26,7 @@
 #include <type_traits>
 
 #include "sft_decode.cuh"
+#include "sft_device_util.cuh"
 #include "sft_fft.cuh"
 #include "sft_internal.h"
 
@@ -36,12 +37,14 @@ template <class F>
 __global__ void __launch_bounds__(512) k_gather_fft(
     const typename F::In* __restrict__ x, int64_t x_stride, int64_t N, int64_t d, int log2M,
     int shift0, int log2Mt, const typename F::Tw* __restrict__ tw, void* __restrict__ out_v,
-    int64_t out_sig, int64_t out_row, int row0, unsigned long long* __restrict__ ymax2) {
+    int64_t out_sig, int64_t out_row, int row0, unsigned long long* __restrict__ ymax2,
+    const int64_t* __restrict__ shift_list) {
   extern __shared__ __align__(16) char smem[];
   typedef typename F::Out Out;
   const int b = blockIdx.y;
   const int js = blockIdx.x;
-  const int64_t shift = shift0 + js;
+  // consecutive shifts shift0 + js, or an explicit list (random CS shifts)
+  const int64_t shift = shift_list != nullptr ? shift_list[js] : shift0 + js;
   const int M = 1 << log2M;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const typename F::In* xs = x + (int64_t)b * x_stride;
@@ -107,10 +110,11 @@ template <class F>
 __global__ void __launch_bounds__(512) k_fft4_cols(
     const typename F::In* __restrict__ x, int64_t x_stride, int64_t N, int64_t d, int log2M1,
     int log2M2, int shift0, int log2Mt, const typename F::Tw* __restrict__ tw,
-    typename F::Out* __restrict__ W, int64_t w_sig, int nshift) {
+    typename F::Out* __restrict__ W, int64_t w_sig, int nshift,
+    const int64_t* __restrict__ shift_list) {
   extern __shared__ __align__(16) char smem[];
   const int b = blockIdx.z, js = blockIdx.y;
-  const int64_t shift = shift0 + js;
+  const int64_t shift = shift_list != nullptr ? shift_list[js] : shift0 + js;
   const int M1 = 1 << log2M1, M2 = 1 << log2M2;
   const int log2M = log2M1 + log2M2;
   const int CB = kFft4Points >> log2M1;  // columns per CTA
@@ -176,7 +180,7 @@ __global__ void __launch_bounds__(512) k_fft4_rows(
     o[(int64_t)(r0 + gg) + (int64_t)M1 * k2] = w;
     lmax = fmax(lmax, F::out_norm(w));
   }
-  if (ymax2 != nullptr && shift0 + js == 0) {
+  if (ymax2 != nullptr && js == 0 && shift0 == 0) {
     __shared__ double wmax[32];
 #pragma unroll
     for (int o2 = 16; o2 > 0; o2 >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o2));
@@ -208,39 +212,6 @@ struct LevelArgs {
   OmegaTab om;
   OmegaTabFF omff;
 };
-
-// File the a recovered frequencies of one decode event under their level-0
-// bins (the calling thread owns every level-0 bin congruent to its bin).
-template <class F, int A>
-__device__ __forceinline__ void file_solution(const int64_t* s, const cdbl* p, int64_t M0,
-                                              uint8_t* cnt, int64_t* ss,
-                                              typename Store<F>::T* sp, int32_t* flag) {
-#pragma unroll
-  for (int j = 0; j < A; ++j) {
-    const int64_t k0 = s[j] & (M0 - 1);
-    const int c = cnt[k0];
-    if (c < 4) {
-      ss[k0 * 4 + c] = s[j];
-      sp[k0 * 4 + c] = Store<F>::from_d(p[j]);
-      cnt[k0] = (uint8_t)(c + 1);
-    } else {
-      atomicOr(flag, 1);
-    }
-  }
-}
-
-// Append (b, k) to a device queue when `pred`; one atomic per warp.  Every
-// lane of the warp must call this (inactive lanes with pred = false).
-__device__ __forceinline__ void queue_push(bool pred, int b, int k, int2* q, int* count) {
-  const unsigned lane = threadIdx.x & 31u;
-  const unsigned mask = __ballot_sync(0xffffffffu, pred);
-  if (mask == 0u) return;
-  const int leader = __ffs(mask) - 1;
-  int base = 0;
-  if ((int)lane == leader) base = atomicAdd(count, __popc(mask));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (pred) q[base + __popc(mask & ((1u << lane) - 1u))] = make_int2(b, k);
-}
 
 // |m|^2 > theta^2 decided from the float-float hi parts when they are
 // clearly on one side (relative error of the hi-part norm < 1e-6), in FP64
@@ -550,6 +521,7 @@ cudaError_t prepare_kernels(sft_plan_s* P) {
 }
 
 int launches_per_call(const sft_plan_s* P) {
+  if (P->p.mode == SFT_GENERAL) return 2 * (P->M0 > kFft4Points ? 2 : 1) + 3 + 1;
   if (P->p.mode == SFT_EXACT_FIXED) return (P->M0 > kFft4Points ? 2 : 1) + 1 + P->p.a_max + 1;
   int fft = 0;
   for (int l = 0; l < P->levels; ++l) fft += (P->M0 >> l) > kFft4Points ? 2 : 1;
@@ -578,9 +550,10 @@ void stage_end(sft_plan_s* P, cudaStream_t st) {
 }
 
 template <class F>
-static void launch_gather_fft(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride,
-                              int64_t d, int log2M, int shift0, int nshift, void* out,
-                              int64_t out_row, int row0, bool want_ymax, cudaStream_t st) {
+void launch_gather_fft(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int64_t d,
+                       int log2M, int shift0, int nshift, void* out, int64_t out_row, int row0,
+                       bool want_ymax, cudaStream_t st, const int64_t* shift_list,
+                       const char* stage) {
   static const char* names[] = {"gather_fft_l0", "gather_fft_l1", "gather_fft_l2", "gather_fft_l3"};
   static const char* cnames[] = {"gather_cols_l0", "gather_cols_l1", "gather_cols_l2",
                                  "gather_cols_l3"};
@@ -592,10 +565,10 @@ static void launch_gather_fft(sft_plan_s* P, int64_t B, const void* x, int64_t x
     dim3 grid(nshift, (unsigned)B);
     const int nthr = fft_threads(log2M);
     const size_t smem = (size_t)padded(1 << log2M) * F::kBytesPerPoint;
-    stage_begin(P, nshift > 2 ? "gather_fft_fixed" : names[lvl], st);
+    stage_begin(P, stage ? stage : (nshift > 2 ? "gather_fft_fixed" : names[lvl]), st);
     k_gather_fft<F><<<grid, nthr, smem, st>>>(xin, x_stride, P->p.N, d, log2M, shift0, P->log2M0,
                                               tw, out, P->ws.held_elems, out_row, row0,
-                                              want_ymax ? P->ws.ymax2 : nullptr);
+                                              want_ymax ? P->ws.ymax2 : nullptr, shift_list);
     stage_end(P, st);
     return;
   }
@@ -606,15 +579,28 @@ static void launch_gather_fft(sft_plan_s* P, int64_t B, const void* x, int64_t x
   const size_t smem = (size_t)padded(kFft4Points) * F::kBytesPerPoint;
   auto* W = reinterpret_cast<typename F::Out*>(P->ws.fft4);
   const int64_t w_sig = (int64_t)nshift * Mlev;
-  stage_begin(P, cnames[lvl], st);
+  stage_begin(P, stage ? stage : cnames[lvl], st);
   k_fft4_cols<F><<<dim3(ctas, nshift, (unsigned)B), 512, smem, st>>>(
-      xin, x_stride, P->p.N, d, log2M1, log2M2, shift0, P->log2M0, tw, W, w_sig, nshift);
+      xin, x_stride, P->p.N, d, log2M1, log2M2, shift0, P->log2M0, tw, W, w_sig, nshift,
+      shift_list);
   stage_end(P, st);
-  stage_begin(P, rnames[lvl], st);
+  stage_begin(P, stage ? "fft_rows" : rnames[lvl], st);
   k_fft4_rows<F><<<dim3(ctas, nshift, (unsigned)B), 512, smem, st>>>(
       W, w_sig, log2M1, log2M2, d, P->log2M0, tw, out, P->ws.held_elems, out_row, row0,
       want_ymax ? P->ws.ymax2 : nullptr, shift0);
   stage_end(P, st);
+}
+
+void launch_gather_fft_any(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int64_t d,
+                           int log2M, int shift0, int nshift, void* out, int64_t out_row, int row0,
+                           bool want_ymax, cudaStream_t st, const int64_t* shift_list,
+                           const char* stage) {
+  if (P->p.precision == SFT_FP64)
+    launch_gather_fft<F64>(P, B, x, x_stride, d, log2M, shift0, nshift, out, out_row, row0,
+                           want_ymax, st, shift_list, stage);
+  else
+    launch_gather_fft<FF>(P, B, x, x_stride, d, log2M, shift0, nshift, out, out_row, row0,
+                          want_ymax, st, shift_list, stage);
 }
 
 template <class F>
@@ -622,7 +608,8 @@ static void launch_fixed(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
                          const OmegaTab& om, int nsm, cudaStream_t st) {
   const Workspace& W = P->ws;
   const int nsh = 2 * P->p.a_max;
-  launch_gather_fft<F>(P, B, x, x_stride, P->p.d, P->log2M0, 0, nsh, W.held[0], P->M0, 0, true, st);
+  launch_gather_fft<F>(P, B, x, x_stride, P->p.d, P->log2M0, 0, nsh, W.held[0], P->M0, 0, true, st,
+                       nullptr, nullptr);
   FixedArgs g{P->p.N, P->M0, P->p.d, P->p.a_max, W.held[0], W.held_elems, W.T[0], W.slot_cnt,
               W.slot_s, W.slot_p, W.ymax2, W.flags, P->p.zero_tol, P->p.root_tol,
               P->p.res_tol, om};
@@ -692,7 +679,8 @@ static void launch_iter(sft_plan_s* P, int64_t B, const void* x, int64_t x_strid
     const int log2M = P->log2M0 - l;
     void* cur = W.held[l & 1];
     const void* prev = W.held[(l + 1) & 1];
-    launch_gather_fft<F>(P, B, x, x_stride, d, log2M, 2 * l, 2, cur, M, 2 * l, l == 0, st);
+    launch_gather_fft<F>(P, B, x, x_stride, d, log2M, 2 * l, 2, cur, M, 2 * l, l == 0, st, nullptr,
+                         nullptr);
     LevelArgs g{P->p.N, M, d, P->M0, prev, cur, W.held_elems, W.T[(l + 1) & 1], W.T[l & 1],
                 W.slot_cnt, W.slot_s, W.slot_p, W.ymax2, W.flags, P->p.zero_tol,
                 P->p.root_tol, P->p.res_tol, om, omff};
@@ -735,7 +723,10 @@ cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int64_t M_last = P->M0;
   const uint8_t* T_last = W.T[0];
-  if (P->p.mode == SFT_EXACT_FIXED) {
+  if (P->p.mode == SFT_GENERAL) {
+    launch_general(P, B, x, x_stride, nsm, st);
+    M_last = 0;  // no unsolved-bin flags on the general path
+  } else if (P->p.mode == SFT_EXACT_FIXED) {
     if (fp64)
       launch_fixed<F64>(P, B, x, x_stride, om, nsm, st);
     else

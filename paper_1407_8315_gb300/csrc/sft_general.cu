@@ -1,0 +1,489 @@
+// sft_general.cu -- generally K-sparse signals (Sec. III, Algorithm 2) for
+// sm_103a.
+//
+// Per call, batched over B signals of one plan (M bins, d = N / M):
+//   gather + FFT   the 2 a_m consecutive shifts 0 .. 2a_m-1 and the r random
+//                  shifts n_l (Part 1, lines 02-10)
+//   k_gen_svals    one thread per bin: the a_m singular values of the
+//                  a_m x a_m Hankel matrix of m_0 .. m_{2a_m-2} (Eq. (26)) by
+//                  one-sided Jacobi in FP64 (Part 2, lines 11-15)
+//   k_gen_vote     one CTA per signal: the K largest singular values (radix
+//                  select on their FP64 bit patterns, ties to the lower
+//                  index) vote a_k per bin (lines 16-21); bins with a_k > 0
+//                  are queued
+//   k_gen_solve    per queued bin: the a_k x a_k Hankel locator, |P~| at all
+//                  d candidates of U_k with the 2 a_k smallest kept (pruning
+//                  Steps 2-3), Subspace Pursuit on the pruned sensing matrix
+//                  Phi_p (Parts 3-4, lines 22-29)
+//   k_finalize     as for the exact transform
+#include <algorithm>
+#include <cstdio>
+#include <type_traits>
+
+#include "sft_decode.cuh"
+#include "sft_device_util.cuh"
+#include "sft_internal.h"
+
+namespace sft {
+
+struct GenArgs {
+  int64_t N, M, d, K;
+  int a_max, r, keep, sp_iters;
+  const void* Y;  // rows 0..2a_m-1: consecutive shifts; 2a_m..2a_m+r-1: random
+  int64_t held_elems;
+  double* sv;   // [B][M a_m]
+  uint8_t* ak;  // [B][M0] votes
+  int2* queue;
+  int* qcount;
+  const int64_t* cs;  // the r random shifts n_l
+  uint8_t* slot_cnt;
+  int64_t* slot_s;
+  void* slot_p;
+  int32_t* flags;
+  OmegaTab om;
+};
+
+// One-sided Jacobi on the n x n Hankel H_ij = m_{i+j}: rotate column pairs
+// until orthogonal (phase-align the inner product, then a real rotation with
+// cot 2theta = (beta - alpha) / (2|gamma|)); singular values = column norms,
+// returned descending.
+template <int n>
+__device__ void hankel_svals(const cdbl* m, double* sv) {
+  cdbl A[n * n];
+#pragma unroll
+  for (int i = 0; i < n; ++i)
+#pragma unroll
+    for (int j = 0; j < n; ++j) A[i * n + j] = m[i + j];
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0;
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+#pragma unroll
+      for (int q = p + 1; q < n; ++q) {
+        double alpha = 0.0, beta = 0.0;
+        cdbl gamma = mk(0.0, 0.0);
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+          alpha += norm2(A[i * n + p]);
+          beta += norm2(A[i * n + q]);
+          gamma = gamma + conjd(A[i * n + p]) * A[i * n + q];
+        }
+        const double g2 = norm2(gamma), ab = alpha * beta;
+        if (!(g2 > 0.0) || !(ab > 0.0)) continue;
+        const double g = sqrt(g2), sab = sqrt(ab);
+        off = fmax(off, g / sab);
+        if (!(g > 1e-15 * sab)) continue;
+        const double ig = 1.0 / g;
+        const cdbl phc = mk(gamma.x * ig, -gamma.y * ig);  // conj(gamma / |gamma|)
+        const double zeta = (beta - alpha) * (0.5 * ig);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+          const cdbl ap = A[i * n + p], aq = A[i * n + q] * phc;
+          A[i * n + p] = ap * c - aq * s;
+          A[i * n + q] = ap * s + aq * c;
+        }
+      }
+    }
+    if (off <= 1e-15) break;
+  }
+#pragma unroll
+  for (int j = 0; j < n; ++j) {
+    double s2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < n; ++i) s2 += norm2(A[i * n + j]);
+    sv[j] = sqrt(s2);
+  }
+#pragma unroll
+  for (int i = 1; i < n; ++i)
+#pragma unroll
+    for (int j = n - 1; j >= 1; --j)
+      if (j <= i && sv[j - 1] < sv[j]) {
+        const double t = sv[j];
+        sv[j] = sv[j - 1];
+        sv[j - 1] = t;
+      }
+}
+
+template <class F, int AM>
+__global__ void __launch_bounds__(256) k_gen_svals(GenArgs g) {
+  typedef typename Store<F>::T T;
+  const int b = blockIdx.y;
+  const int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (k >= g.M) return;
+  const T* Y = reinterpret_cast<const T*>(g.Y) + (int64_t)b * g.held_elems;
+  cdbl m[2 * AM - 1];
+#pragma unroll
+  for (int j = 0; j < 2 * AM - 1; ++j) m[j] = Store<F>::to_d(Y[j * g.M + k]);
+  double sv[AM];
+  hankel_svals<AM>(m, sv);
+  double* o = g.sv + ((int64_t)b * g.M + k) * AM;
+#pragma unroll
+  for (int i = 0; i < AM; ++i) o[i] = sv[i];
+}
+
+// Block-wide exclusive scan of one int per thread.
+__device__ __forceinline__ int gen_block_scan(int v, int* total) {
+  __shared__ int wsum[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    wsum[lane] = s;
+  }
+  __syncthreads();
+  const int before = (w > 0 ? wsum[w - 1] : 0) + x - v;
+  *total = wsum[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before;
+}
+
+// Lines 16-21: the K largest of the M a_m singular values of one signal.
+// MSB-first radix select (8 passes of 8 bits) on the bit patterns of the
+// non-negative doubles finds the K-th largest value tau and how many of the
+// values equal to tau are selected; those are the ones of lowest index.
+__global__ void __launch_bounds__(1024) k_gen_vote(GenArgs g) {
+  __shared__ unsigned hist[256];
+  __shared__ unsigned long long s_prefix;
+  __shared__ long long s_rem;
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int am = g.a_max;
+  const int64_t n = g.M * am;
+  const unsigned long long* keys =
+      reinterpret_cast<const unsigned long long*>(g.sv + (int64_t)b * n);
+  uint8_t* ak = g.ak + (int64_t)b * g.M;
+  const int64_t K = g.K < n ? g.K : n;
+  unsigned long long prefix = 0ull, mask = 0ull;
+  long long rem = K;  // rank (from the top) still to find among keys matching prefix
+  if (K > 0) {
+    for (int pass = 0; pass < 8; ++pass) {
+      const int shift = 56 - 8 * pass;
+      for (int i = tid; i < 256; i += nthr) hist[i] = 0u;
+      __syncthreads();
+      for (int64_t i = tid; i < n; i += nthr) {
+        const unsigned long long key = keys[i];
+        if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        long long cum = 0;
+        int sel = 0;
+        for (int dg = 255; dg >= 0; --dg) {
+          if (cum + (long long)hist[dg] >= rem) {
+            sel = dg;
+            break;
+          }
+          cum += hist[dg];
+        }
+        s_prefix = prefix | ((unsigned long long)sel << shift);
+        s_rem = rem - cum;
+      }
+      __syncthreads();
+      prefix = s_prefix;
+      rem = s_rem;
+      mask |= 255ull << shift;
+      __syncthreads();
+    }
+  }
+  const unsigned long long tau = prefix;  // K-th largest key
+  // per-thread chunk of whole bins, in index order
+  const int64_t chunk = (g.M + nthr - 1) / nthr;
+  const int64_t k_lo = min((int64_t)tid * chunk, g.M), k_hi = min(k_lo + chunk, g.M);
+  int ties = 0;
+  if (K > 0)
+    for (int64_t i = k_lo * am; i < k_hi * am; ++i) ties += keys[i] == tau;
+  int tie_total = 0;
+  int tie_before = gen_block_scan(ties, &tie_total);
+  for (int64_t k = k_lo; k < k_hi; ++k) {
+    int a = 0;
+    if (K > 0) {
+      for (int j = 0; j < am; ++j) {
+        const unsigned long long key = keys[k * am + j];
+        if (key > tau) {
+          ++a;
+        } else if (key == tau) {
+          if (tie_before < rem) ++a;
+          ++tie_before;
+        }
+      }
+    }
+    ak[k] = (uint8_t)a;
+    if (a > 0) g.queue[atomicAdd(g.qcount, 1)] = make_int2(b, (int)k);
+  }
+}
+
+// least squares on the columns T (ascending) of Phi (rows x cols, row-major
+// in phi), normal equations by Gaussian elimination with partial pivoting;
+// returns |y - Phi_T x|^2 or -1 when singular
+__device__ double ls_cols(int rows, int cols, const cdbl* phi, const cdbl* y, const int* T, int nT,
+                          cdbl* x, cdbl* res) {
+  cdbl G[64], gv[8];
+  for (int u = 0; u < nT; ++u) {
+    gv[u] = mk(0.0, 0.0);
+    for (int v = 0; v < nT; ++v) G[u * 8 + v] = mk(0.0, 0.0);
+    for (int i = 0; i < rows; ++i) {
+      const cdbl cu = conjd(phi[i * cols + T[u]]);
+      gv[u] = gv[u] + cu * y[i];
+      for (int v = 0; v < nT; ++v) G[u * 8 + v] = G[u * 8 + v] + cu * phi[i * cols + T[v]];
+    }
+  }
+  double amax2 = 0.0;
+  for (int u = 0; u < nT; ++u)
+    for (int v = 0; v < nT; ++v) amax2 = fmax(amax2, norm2(G[u * 8 + v]));
+  if (!(amax2 > 0.0)) return -1.0;
+  cdbl inv[8];
+  for (int c = 0; c < nT; ++c) {
+    int piv = c;
+    double best = norm2(G[c * 8 + c]);
+    for (int rr = c + 1; rr < nT; ++rr) {
+      const double v = norm2(G[rr * 8 + c]);
+      if (v > best) {
+        best = v;
+        piv = rr;
+      }
+    }
+    if (!(best > 1e-28 * amax2)) return -1.0;
+    if (piv != c) {
+      for (int q = 0; q < nT; ++q) {
+        const cdbl t = G[c * 8 + q];
+        G[c * 8 + q] = G[piv * 8 + q];
+        G[piv * 8 + q] = t;
+      }
+      const cdbl t = gv[c];
+      gv[c] = gv[piv];
+      gv[piv] = t;
+    }
+    inv[c] = crcp(G[c * 8 + c]);
+    for (int rr = c + 1; rr < nT; ++rr) {
+      const cdbl f = G[rr * 8 + c] * inv[c];
+      for (int q = c + 1; q < nT; ++q) G[rr * 8 + q] = G[rr * 8 + q] - f * G[c * 8 + q];
+      gv[rr] = gv[rr] - f * gv[c];
+    }
+  }
+  for (int rr = nT - 1; rr >= 0; --rr) {
+    cdbl acc = gv[rr];
+    for (int q = rr + 1; q < nT; ++q) acc = acc - G[rr * 8 + q] * x[q];
+    x[rr] = acc * inv[rr];
+  }
+  double rn = 0.0;
+  for (int i = 0; i < rows; ++i) {
+    cdbl f = mk(0.0, 0.0);
+    for (int u = 0; u < nT; ++u) f = f + phi[i * cols + T[u]] * x[u];
+    res[i] = y[i] - f;
+    rn += norm2(res[i]);
+  }
+  return rn;
+}
+
+// indices (ascending) of the ks largest v[i] among allowed i (ties: lower i)
+__device__ int top_ks(int n, const double* v, unsigned allowed, int ks, int* out) {
+  unsigned taken = 0u;
+  int cnt = 0;
+  for (int r = 0; r < ks; ++r) {
+    int best = -1;
+    for (int i = 0; i < n; ++i)
+      if (((allowed >> i) & 1u) && !((taken >> i) & 1u) && (best < 0 || v[i] > v[best])) best = i;
+    if (best < 0) break;
+    taken |= 1u << best;
+    ++cnt;
+  }
+  int w = 0;
+  for (int i = 0; i < n; ++i)
+    if ((taken >> i) & 1u) out[w++] = i;
+  return cnt;
+}
+
+// Subspace Pursuit (Dai and Dai 2009) on Phi (rows x cols), sparsity ks:
+// T = ks columns most correlated with y; repeat: T' = T + the ks columns
+// most correlated with the residual, least squares on T', keep its ks
+// largest coefficients, least squares again; stop when the residual does
+// not shrink.  Writes the support and the coefficients; returns |T|.
+__device__ int subspace_pursuit(int rows, int cols, const cdbl* phi, const cdbl* y, int ks,
+                                int iters, int* T, cdbl* x) {
+  const unsigned all = (cols >= 32) ? 0xffffffffu : ((1u << cols) - 1u);
+  double corr[16];
+  cdbl res[16], xn[8], resn[16];
+  if (ks > cols) ks = cols;
+  for (int j = 0; j < cols; ++j) {
+    cdbl c = mk(0.0, 0.0);
+    for (int i = 0; i < rows; ++i) c = c + conjd(phi[i * cols + j]) * y[i];
+    corr[j] = norm2(c);
+  }
+  int nT = top_ks(cols, corr, all, ks, T);
+  double rn = ls_cols(rows, cols, phi, y, T, nT, x, res);
+  if (rn < 0.0) return 0;
+  for (int it = 0; it < iters; ++it) {
+    for (int j = 0; j < cols; ++j) {
+      cdbl c = mk(0.0, 0.0);
+      for (int i = 0; i < rows; ++i) c = c + conjd(phi[i * cols + j]) * res[i];
+      corr[j] = norm2(c);
+    }
+    int add[8];
+    const int na = top_ks(cols, corr, all, ks, add);
+    unsigned in2 = 0u;
+    for (int u = 0; u < nT; ++u) in2 |= 1u << T[u];
+    for (int u = 0; u < na; ++u) in2 |= 1u << add[u];
+    int T2[16], n2 = 0;
+    for (int j = 0; j < cols; ++j)
+      if ((in2 >> j) & 1u) T2[n2++] = j;
+    cdbl x2[16], r2[16];
+    if (ls_cols(rows, cols, phi, y, T2, n2, x2, r2) < 0.0) break;
+    double mag[16];
+    for (int j = 0; j < cols; ++j) mag[j] = 0.0;
+    for (int u = 0; u < n2; ++u) mag[T2[u]] = norm2(x2[u]);
+    int Tn[8];
+    const int nn = top_ks(cols, mag, in2, ks, Tn);
+    const double rnn = ls_cols(rows, cols, phi, y, Tn, nn, xn, resn);
+    if (rnn < 0.0 || rnn >= rn) break;
+    nT = nn;
+    for (int u = 0; u < nT; ++u) {
+      T[u] = Tn[u];
+      x[u] = xn[u];
+    }
+    for (int i = 0; i < rows; ++i) res[i] = resn[i];
+    rn = rnn;
+  }
+  return nT;
+}
+
+template <class F, int A>
+__device__ void solve_bin(const GenArgs& g, int b, int64_t k) {
+  typedef typename Store<F>::T T;
+  const int64_t M = g.M, d = g.d;
+  const T* Y = reinterpret_cast<const T*>(g.Y) + (int64_t)b * g.held_elems;
+  cdbl m[2 * A];
+#pragma unroll
+  for (int j = 0; j < 2 * A; ++j) m[j] = Store<F>::to_d(Y[j * M + k]);
+  // Step 2 (a): the a x a Hankel system with the observed syndromes
+  cdbl H[A * A], rhs[A], c[A];
+#pragma unroll
+  for (int i = 0; i < A; ++i) {
+#pragma unroll
+    for (int j = 0; j < A; ++j) H[i * A + j] = m[i + j];
+    rhs[i] = -m[A + i];
+  }
+  if (!solve_small<A>(H, rhs, c)) return;
+  // (b)-(c): |P~(z)| at every z = omega^{k + tM} of U_k; keep the smallest
+  const int nk = (int)min((int64_t)min(g.keep * A, 8), d);
+  double bv[8];
+  int bt[8];
+  int have = 0;
+  for (int64_t t = 0; t < d; ++t) {
+    const cdbl z = omega_pow(g.om, k + t * M);
+    cdbl P = mk(1.0, 0.0);
+#pragma unroll
+    for (int j = A - 1; j >= 0; --j) P = P * z + c[j];
+    const double v = norm2(P);
+    if (have < nk || v < bv[nk - 1]) {
+      int pos = have < nk ? have : nk - 1;
+      while (pos > 0 && bv[pos - 1] > v) {  // stable: equal values keep lower t first
+        bv[pos] = bv[pos - 1];
+        bt[pos] = bt[pos - 1];
+        --pos;
+      }
+      bv[pos] = v;
+      bt[pos] = (int)t;
+      if (have < nk) ++have;
+    }
+  }
+  // Step 3: kept candidates in ascending t; Phi_p[j][u] = omega^{(k + t_u M) n_j}
+  for (int i = 1; i < have; ++i)
+    for (int j = i; j > 0 && bt[j - 1] > bt[j]; --j) {
+      const int tt = bt[j];
+      bt[j] = bt[j - 1];
+      bt[j - 1] = tt;
+    }
+  const int r = g.r;
+  cdbl phi[16 * 8], y[16];
+  for (int j = 0; j < r; ++j) {
+    y[j] = Store<F>::to_d(Y[(2 * g.a_max + j) * M + k]);
+    for (int u = 0; u < have; ++u) phi[j * have + u] = omega_pow(g.om, (k + (int64_t)bt[u] * M) * g.cs[j]);
+  }
+  int Tsup[8];
+  cdbl xs[8];
+  const int nz = subspace_pursuit(r, have, phi, y, A, g.sp_iters, Tsup, xs);
+  int64_t s_out[8];
+  cdbl p_out[8];
+  int nout = 0;
+  for (int u = 0; u < nz; ++u) {
+    if (xs[u].x == 0.0 && xs[u].y == 0.0) continue;
+    s_out[nout] = k + (int64_t)bt[Tsup[u]] * M;
+    p_out[nout] = xs[u];
+    ++nout;
+  }
+  file_n<F>(nout, s_out, p_out, g.M, g.slot_cnt + (int64_t)b * g.M, g.slot_s + (int64_t)b * g.M * 4,
+            reinterpret_cast<T*>(g.slot_p) + (int64_t)b * g.M * 4, g.flags + b);
+}
+
+template <class F>
+__global__ void __launch_bounds__(128) k_gen_solve(GenArgs g) {
+  const int n = *g.qcount;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 q = g.queue[e];
+    const int a = g.ak[(int64_t)q.x * g.M + q.y];
+    switch (a) {
+      case 1: solve_bin<F, 1>(g, q.x, q.y); break;
+      case 2: solve_bin<F, 2>(g, q.x, q.y); break;
+      case 3: solve_bin<F, 3>(g, q.x, q.y); break;
+      case 4: solve_bin<F, 4>(g, q.x, q.y); break;
+      default: break;
+    }
+  }
+}
+
+template <class F>
+static void launch_general_t(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int nsm,
+                             cudaStream_t st) {
+  const Workspace& W = P->ws;
+  const int am = P->p.a_max, r = P->p.n_cs_shifts;
+  // Part 1: 2 a_m consecutive shifts (rows 0..2a_m-1), r random shifts after
+  launch_gather_fft_any(P, B, x, x_stride, P->p.d, P->log2M0, 0, 2 * am, W.held[0], P->M0, 0,
+                        true, st, nullptr, "gather_fft_consecutive");
+  launch_gather_fft_any(P, B, x, x_stride, P->p.d, P->log2M0, 0, r, W.held[0], P->M0, 2 * am,
+                        false, st, P->tab.cs_shifts, "gather_fft_random");
+  GenArgs g{P->p.N, P->M0, P->p.d, P->p.K, am, r, 2, 8, W.held[0], W.held_elems, W.sv, W.T[0],
+            W.queue[0], W.qcount, P->tab.cs_shifts, W.slot_cnt, W.slot_s, W.slot_p, W.flags,
+            OmegaTab{P->tab.om_hi, P->tab.om_lo, P->tab.om_lo_bits, P->p.N - 1}};
+  dim3 sgrid((unsigned)((P->M0 + 255) / 256), (unsigned)B);
+  stage_begin(P, "gen_svals", st);
+  switch (am) {
+    case 1: k_gen_svals<F, 1><<<sgrid, 256, 0, st>>>(g); break;
+    case 2: k_gen_svals<F, 2><<<sgrid, 256, 0, st>>>(g); break;
+    case 3: k_gen_svals<F, 3><<<sgrid, 256, 0, st>>>(g); break;
+    default: k_gen_svals<F, 4><<<sgrid, 256, 0, st>>>(g); break;
+  }
+  stage_end(P, st);
+  stage_begin(P, "gen_vote", st);
+  k_gen_vote<<<(unsigned)B, 1024, 0, st>>>(g);
+  stage_end(P, st);
+  const int64_t maxq = B * std::min<int64_t>(P->M0, std::max<int64_t>(P->p.K, 1));
+  const unsigned dgrid =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>((maxq + 127) / 128, 8 * (int64_t)nsm));
+  stage_begin(P, "gen_solve", st);
+  k_gen_solve<F><<<dgrid, 128, 0, st>>>(g);
+  stage_end(P, st);
+}
+
+void launch_general(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int nsm,
+                    cudaStream_t st) {
+  if (P->p.precision == SFT_FP64)
+    launch_general_t<F64>(P, B, x, x_stride, nsm, st);
+  else
+    launch_general_t<FF>(P, B, x, x_stride, nsm, st);
+}
+
+}  // namespace sft

@@ -37,15 +37,18 @@ struct Workspace {
   void* zero_base = nullptr;  // ymax2 | flags | qcount | slot_cnt
   size_t zero_bytes = 0;
   void* fft4 = nullptr;  // four-step FFT intermediate (only when N/d > 8192)
+  double* sv = nullptr;  // general path: a_m singular values per bin
 };
 
 // Lays the workspace of B signals out from `base` (or only sizes it when
 // base is null) and returns its byte size; every array is 256-byte aligned.
 inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, int mode,
-                               int a_max) {
+                               int a_max, int n_cs = 0) {
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
-  const int64_t held_elems = mode == SFT_EXACT_FIXED ? 2 * a_max * M0 : 2 * M0;
-  const int nbuf = mode == SFT_EXACT_FIXED ? 1 : 2;  // FIXED keeps one level
+  const int64_t held_elems = mode == SFT_EXACT_FIXED ? 2 * a_max * M0
+                             : mode == SFT_GENERAL   ? (2 * a_max + n_cs) * M0
+                                                     : 2 * M0;
+  const int nbuf = mode == SFT_EXACT_ITER ? 2 : 1;  // only ITER keeps two levels
   size_t off = 0;
   size_t o_held[2] = {0, 0}, o_T[2] = {0, 0}, o_q[2];
   for (int i = 0; i < 2; ++i) {
@@ -65,8 +68,13 @@ inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, 
   off = al(off + (size_t)(B * M0 * 4) * 8);
   const size_t o_sp = off;
   off = al(off + (size_t)(B * M0 * 4) * 16);
+  // singular values of every bin (general path)
+  const size_t o_sv = off;
+  if (mode == SFT_GENERAL) off = al(off + (size_t)(B * M0 * a_max) * 8);
   // four-step FFT intermediate: one M0-point plane per shift of a launch
-  const int nsh = mode == SFT_EXACT_FIXED ? 2 * a_max : 2;
+  const int nsh = mode == SFT_EXACT_FIXED ? 2 * a_max
+                  : mode == SFT_GENERAL   ? (2 * a_max > n_cs ? 2 * a_max : n_cs)
+                                          : 2;
   const size_t o_f4 = off;
   if (M0 > 8192) off = al(off + (size_t)(B * nsh * M0) * 16);
   if (W != nullptr && base != nullptr) {
@@ -86,6 +94,7 @@ inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, 
     W->slot_s = reinterpret_cast<int64_t*>(base + o_ss);
     W->slot_p = base + o_sp;
     W->fft4 = M0 > 8192 ? base + o_f4 : nullptr;
+    W->sv = mode == SFT_GENERAL ? reinterpret_cast<double*>(base + o_sv) : nullptr;
   }
   return off;
 }
@@ -97,6 +106,7 @@ struct Tables {
   void* tw = nullptr;        // e^{-2 pi i q / M0}: double2 (FP64) or float4 (FF)
   float4* om_hi_ff = nullptr;  // the omega tables as float-float (mixed path only)
   float4* om_lo_ff = nullptr;
+  int64_t* cs_shifts = nullptr;  // general path: the r random shifts n_l (device)
 };
 
 }  // namespace sft
@@ -124,6 +134,7 @@ struct sft_plan_s {
   size_t x_stage_bytes = 0;
   void* r_stage = nullptr;
   size_t r_stage_bytes = 0;
+  std::vector<int64_t> cs_host;  // general path: the random shifts (host copy)
   // profiling
   bool profiling = false;
   std::vector<sft::StageRec> stage_recs;   // records since the last read
@@ -138,6 +149,16 @@ cudaError_t launch_exact(sft_plan_s* plan, int64_t n_signals, const void* x, int
 // One-time per-plan kernel attributes (dynamic shared memory limits).
 cudaError_t prepare_kernels(sft_plan_s* plan);
 int launches_per_call(const sft_plan_s* plan);
+// Gather + FFT of `nshift` shifts (consecutive from shift0, or shift_list)
+// into rows row0.. of `out`, either precision; `stage` names the profiling
+// stage (nullptr: the level's default name).
+void launch_gather_fft_any(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int64_t d,
+                           int log2M, int shift0, int nshift, void* out, int64_t out_row, int row0,
+                           bool want_ymax, cudaStream_t st, const int64_t* shift_list,
+                           const char* stage);
+// The general path (Algorithm 2) of one call, before k_finalize.
+void launch_general(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int nsm,
+                    cudaStream_t st);
 // Sets the calling thread's error detail returned by sft_last_cuda_error.
 void set_error_detail(const char* msg);
 // Profiling brackets around one launch (no-ops unless plan->profiling).

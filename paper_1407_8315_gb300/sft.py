@@ -40,7 +40,7 @@ class sft_result(C.Structure):
 EXPORTS = ["sft_params_default", "sft_plan_create", "sft_plan_destroy", "sft_plan_workspace_bytes",
            "sft_exact", "sft_exact_host", "sft_plan_launches_per_call", "sft_strerror",
            "sft_last_cuda_error", "sft_plan_set_profiling", "sft_plan_stage_times",
-           "sft_exact_noalloc"]
+           "sft_exact_noalloc", "sft_general", "sft_general_host", "sft_plan_cs_shifts"]
 
 _lib = None
 
@@ -91,6 +91,10 @@ def load(build_if_missing: bool = False):
                                          P(C.c_int64), P(C.c_int32)]
     lib.sft_exact_noalloc.argtypes = [P(sft_params), C.c_int64, C.c_void_p, C.c_int64,
                                       P(sft_result), C.c_void_p]
+    lib.sft_general.argtypes = lib.sft_exact.argtypes
+    lib.sft_general_host.argtypes = lib.sft_exact_host.argtypes
+    lib.sft_plan_cs_shifts.argtypes = [C.c_void_p, P(C.c_int64), C.c_int32]
+    lib.sft_plan_cs_shifts.restype = C.c_int32
     lib.sft_strerror.argtypes = [C.c_int]
     lib.sft_strerror.restype = C.c_char_p
     lib.sft_last_cuda_error.argtypes = []
@@ -132,7 +136,8 @@ def _stream_ptr(stream) -> int:
 Result = namedtuple("Result", "idx val count unresolved overflow")
 
 
-def sft_exact(handle: int, x, cap: int, out: Result | None = None, stream=None) -> Result:
+def sft_exact(handle: int, x, cap: int, out: Result | None = None, stream=None,
+              _entry: str = "sft_exact") -> Result:
     """x: torch tensor [B, N] (complex128 for fp64 plans, complex64 for mixed)
     on the current CUDA device.  Returns device tensors (idx int64 [B, cap],
     val complex128 [B, cap], count int64 [B], unresolved int32 [B],
@@ -156,13 +161,19 @@ def sft_exact(handle: int, x, cap: int, out: Result | None = None, stream=None) 
                    out.unresolved.data_ptr(), out.overflow.data_ptr())
     # a single row has no meaningful pitch (numpy/torch may report 0 for it)
     pitch = x.stride(0) if B > 1 else x.shape[1]
-    _check(load().sft_exact(C.c_void_p(handle), B, C.c_void_p(x.data_ptr()), pitch,
-                            C.byref(r), C.c_void_p(_stream_ptr(stream))), "sft_exact")
+    _check(getattr(load(), _entry)(C.c_void_p(handle), B, C.c_void_p(x.data_ptr()), pitch,
+                                   C.byref(r), C.c_void_p(_stream_ptr(stream))), _entry)
     return out
 
 
+def sft_general(handle: int, x, cap: int, out: Result | None = None, stream=None) -> Result:
+    """Generally K-sparse transform (Algorithm 2) through the C entry point
+    sft_general; arguments as sft_exact."""
+    return sft_exact(handle, x, cap, out, stream, _entry="sft_general")
+
+
 def sft_exact_host(handle: int, x: np.ndarray, cap: int, out: Result | None = None,
-                   stream=None) -> Result:
+                   stream=None, _entry: str = "sft_exact_host") -> Result:
     """Host-memory variant: x is a numpy array [B, N]; results come back as
     numpy arrays.  The library copies in, computes and copies out."""
     if x.ndim == 1:
@@ -176,9 +187,22 @@ def sft_exact_host(handle: int, x: np.ndarray, cap: int, out: Result | None = No
     r = sft_result(cap, out.idx.ctypes.data, out.val.ctypes.data, out.count.ctypes.data,
                    out.unresolved.ctypes.data, out.overflow.ctypes.data)
     pitch = x.strides[0] // x.itemsize if B > 1 else x.shape[1]
-    _check(load().sft_exact_host(C.c_void_p(handle), B, C.c_void_p(x.ctypes.data),
-                                 pitch, C.byref(r),
-                                 C.c_void_p(_stream_ptr(stream))), "sft_exact_host")
+    _check(getattr(load(), _entry)(C.c_void_p(handle), B, C.c_void_p(x.ctypes.data),
+                                   pitch, C.byref(r), C.c_void_p(_stream_ptr(stream))), _entry)
+    return out
+
+
+def sft_general_host(handle: int, x: np.ndarray, cap: int, out: Result | None = None,
+                     stream=None) -> Result:
+    return sft_exact_host(handle, x, cap, out, stream, _entry="sft_general_host")
+
+
+def sft_plan_cs_shifts(handle: int) -> np.ndarray:
+    lib = load()
+    n = lib.sft_plan_cs_shifts(C.c_void_p(handle), None, 0)
+    out = np.zeros(max(n, 0), dtype=np.int64)
+    if n > 0:
+        lib.sft_plan_cs_shifts(C.c_void_p(handle), out.ctypes.data_as(C.POINTER(C.c_int64)), n)
     return out
 
 
@@ -232,11 +256,17 @@ def sft_plan_stage_times(handle: int) -> dict:
 class Plan:
     """Convenience owner of one sft plan."""
 
-    def __init__(self, N, K, d, mode="iter", precision="mixed", max_signals=1, a_max=4,
-                 max_iters=0, zero_tol=0.0, root_tol=0.0, res_tol=0.0):
+    def __init__(self, N, K, d, mode="iter", precision="mixed", max_signals=1, a_max=0,
+                 max_iters=0, zero_tol=0.0, root_tol=0.0, res_tol=0.0, seed=0, n_cs_shifts=0):
         p = sft_params_default(N, K, d, mode, precision)
-        p.a_max = int(a_max)
-        p.max_iters = int(max_iters) if max_iters else int(a_max)
+        if a_max:
+            p.a_max = int(a_max)
+            if mode == "general" and not n_cs_shifts:
+                p.n_cs_shifts = 3 * int(a_max)
+        p.max_iters = int(max_iters) if max_iters else int(p.a_max)
+        p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        if n_cs_shifts:
+            p.n_cs_shifts = int(n_cs_shifts)
         if zero_tol:
             p.zero_tol = float(zero_tol)
         if root_tol:
@@ -268,6 +298,16 @@ class Plan:
 
     def exact_host(self, x, cap=None, out=None, stream=None) -> Result:
         return sft_exact_host(self.handle, x, cap or max(self.K, 1), out, stream)
+
+    def general(self, x, cap=None, out=None, stream=None) -> Result:
+        return sft_general(self.handle, x, cap or max(self.K, 1), out, stream)
+
+    def general_host(self, x, cap=None, out=None, stream=None) -> Result:
+        return sft_general_host(self.handle, x, cap or max(self.K, 1), out, stream)
+
+    @property
+    def cs_shifts(self) -> np.ndarray:
+        return sft_plan_cs_shifts(self.handle)
 
     def set_profiling(self, enable: bool = True):
         sft_plan_set_profiling(self.handle, enable)

@@ -58,7 +58,6 @@ def test_params_default(lib):
 @pytest.mark.parametrize("field,value,status", [
     ("N", 1000, 1), ("N", 4, 1), ("d", 3, 1), ("d", 1 << 23, 1), ("a_max", 5, 1),
     ("max_iters", 5, 1), ("mode", 7, 1), ("precision", 9, 1), ("reserved_", 1, 1),
-    ("mode", 2, 5),          # SFT_GENERAL: not in this build
 ])
 def test_plan_create_rejects_before_touching_the_gpu(lib, field, value, status):
     from paper_1407_8315_gb300 import sft
@@ -67,6 +66,17 @@ def test_plan_create_rejects_before_touching_the_gpu(lib, field, value, status):
     h = C.c_void_p()
     assert lib.sft_plan_create(C.byref(p), 1, C.byref(h)) == status
     assert h.value is None
+
+
+@pytest.mark.parametrize("r,d", [(17, 32), (9, 8), (-1, 32)])
+def test_general_plan_rejects_bad_shift_counts(lib, r, d):
+    """r random shifts must be 1..16 and no more than d (they are distinct)."""
+    from paper_1407_8315_gb300 import sft
+    p = sft.sft_params_default(1 << 20, 1024, d, "general", "mixed")
+    assert p.a_max == 3 and p.n_cs_shifts == 9
+    p.n_cs_shifts = r
+    h = C.c_void_p()
+    assert lib.sft_plan_create(C.byref(p), 1, C.byref(h)) == sft.SFT_EINVAL
 
 
 def test_plan_create_rejects_too_many_bins(lib):

@@ -1,0 +1,105 @@
+"""GPU parity of the generally K-sparse transform (Algorithm 2) against the
+FP64 oracle, through the C ABI: the random shifts, the votes (supports) and
+the Subspace Pursuit values."""
+import numpy as np
+import pytest
+
+import siggen
+
+pytestmark = pytest.mark.gpu
+
+MIXED_VAL_TOL = 1e-4
+FP64_VAL_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1407_8315_gb300 as pkg
+    pkg.build()
+    return torch
+
+
+def _run(torch, plan, xs, cap):
+    x = torch.from_numpy(np.ascontiguousarray(xs)).cuda()
+    out = plan.general(x, cap)
+    torch.cuda.synchronize()
+    return [t.cpu().numpy() for t in out]
+
+
+def _compare(orc, plan, xs, seed, val_tol, a_max=3):
+    import torch
+    cap = 2 * plan.K + 16
+    idx, val, cnt, unres, ovf = _run(torch, plan, xs, cap)
+    worst = 0.0
+    for b in range(xs.shape[0]):
+        oi, ov, _ = orc.general(xs[b], plan.M, plan.K, a_max=a_max, seed=seed, cap=cap)
+        n = int(cnt[b])
+        gi, gv = idx[b, :n], val[b, :n]
+        o = np.argsort(gi, kind="stable")
+        gi, gv = gi[o], gv[o]
+        assert ovf[b] == 0 and unres[b] == 0
+        np.testing.assert_array_equal(gi, oi, err_msg=f"signal {b}: supports differ")
+        if n:
+            worst = max(worst, float((np.abs(gv - ov) / np.abs(ov)).max()))
+    assert worst <= val_tol, worst
+    return worst
+
+
+def test_cs_shifts_match_the_oracle(gpu, orc):
+    from paper_1407_8315_gb300 import Plan
+    for seed in (0, 1, 12345, 2**63 + 7):
+        plan = Plan(1 << 20, 1024, 32, "general", "mixed", seed=seed)
+        np.testing.assert_array_equal(plan.cs_shifts, orc.cs_shifts(seed, 32, 9))
+
+
+@pytest.mark.parametrize("snr", [20, 30, 40])
+def test_noisy_full_size(gpu, orc, snr):
+    """N = 2^20 complex64, K = 1024, |X| ~ U[1,10], white noise at 20/30/40 dB;
+    the paper's setting d = N/(32K) = 32 (M = 2^15, four-step FFT), a_m = 3,
+    r = 9.  Three signals per batch."""
+    from paper_1407_8315_gb300 import Plan
+    N, K = 1 << 20, 1024
+    d = N // (32 * K)
+    plan = Plan(N, K, d, "general", "mixed", max_signals=3, seed=snr)
+    xs = np.stack([siggen.noisy_signal(N, K, 300 + 10 * snr + i, snr, mag=(1, 10))[0]
+                   for i in range(3)])
+    _compare(orc, plan, xs, snr, MIXED_VAL_TOL)
+
+
+def test_noiseless_equals_planted(gpu, orc):
+    from paper_1407_8315_gb300 import Plan
+    N, K = 1 << 16, 128
+    M = N // 16
+    plan = Plan(N, K, 16, "general", "fp64", max_signals=2, seed=3)
+    xs = np.stack([siggen.exact_signal(N, K, s, mag=(1, 10))[0] for s in (0, 5)])
+    _compare(orc, plan, xs, 3, FP64_VAL_TOL)
+    idx, val, cnt, _, _ = _run(gpu, plan, xs, 2 * K)
+    for b, s in enumerate((0, 5)):
+        _, supp, vals = siggen.exact_signal(N, K, s, mag=(1, 10))
+        if np.bincount(supp % M).max() <= 3:
+            np.testing.assert_array_equal(np.sort(idx[b, :cnt[b]]), supp)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("N,K,d,a_max", [(1 << 14, 64, 8, 2), (1 << 16, 300, 16, 2),
+                                         (1 << 17, 700, 16, 4), (1 << 18, 1 << 9, 16, 3)])
+def test_sizes(gpu, orc, prec, N, K, d, a_max):
+    from paper_1407_8315_gb300 import Plan
+    dt = np.complex128 if prec == "fp64" else np.complex64
+    plan = Plan(N, K, d, "general", prec, max_signals=2, seed=N + K, a_max=a_max)
+    xs = np.stack([siggen.noisy_signal(N, K, 7 * N + i, 25, mag=(1, 10), dtype=dt)[0]
+                   for i in range(2)])
+    _compare(orc, plan, xs, N + K, FP64_VAL_TOL if prec == "fp64" else MIXED_VAL_TOL,
+             a_max=a_max)
+
+
+def test_exact_entry_rejects_general_plan(gpu):
+    from paper_1407_8315_gb300 import Plan, SftError
+    import torch
+    plan = Plan(1 << 14, 64, 16, "general", "mixed")
+    x = torch.zeros((1, 1 << 14), dtype=torch.complex64, device="cuda")
+    with pytest.raises(SftError):
+        plan.exact(x, 64)
