@@ -178,6 +178,40 @@ sft_status sft_general_host(sft_plan_t plan, int64_t n_signals, const void* x_ho
  * into out (host) and returns r (0 for exact plans, -1 for a NULL plan). */
 int32_t sft_plan_cs_shifts(sft_plan_t plan, int64_t* out, int32_t cap);
 
+/* ---- heterogeneous batches ---------------------------------------------
+ * Many signals of uneven N, K and kind (exactly or generally sparse) in one
+ * call.  A batch context groups the signals by shape (everything except K
+ * that fixes the launch sequence), keeps one internal plan per shape, reads
+ * every signal's input pointer, result buffers and K from device tables
+ * (no copies of the signals), captures the launches of the whole call into
+ * one CUDA graph and replays it while the composition of the batch (the
+ * shapes and how many signals of each) stays the same.  On the first call
+ * of a shape an autotuner times the bin decoders at 2, 4, 8 and 16 CTAs
+ * per SM on that call's data and keeps the fastest.  Not thread-safe; calls
+ * on one context must not overlap on the GPU. */
+typedef struct sft_batch_s* sft_batch_t;
+
+sft_status sft_batch_create(sft_batch_t* out);
+/* Frees the context, its plans and its graph (synchronises the device). */
+void sft_batch_destroy(sft_batch_t ctx);
+/* use_graph: capture and replay (default 1); autotune: tune new shapes
+ * (default 1). */
+sft_status sft_batch_set_options(sft_batch_t ctx, int32_t use_graph, int32_t autotune);
+/* Transforms n_signals signals.  Host arrays of n_signals entries:
+ *   params   the parameters of each signal (mode SFT_EXACT_ITER,
+ *            SFT_EXACT_FIXED or SFT_GENERAL; as for sft_plan_create)
+ *   x        the device address of each signal (complex64 for SFT_MIXED,
+ *            complex128 for SFT_FP64)
+ *   results  each signal's own result buffers (device pointers; count,
+ *            unresolved and overflow point at one value each; cap >= K)
+ * Asynchronous on `stream`; the first call of a new composition builds
+ * plans (allocates) and captures the graph. */
+sft_status sft_batch(sft_batch_t ctx, int64_t n_signals, const sft_params* params,
+                     const void* const* x, const sft_result* results, void* stream);
+/* Groups of the last call, nodes of the current graph, shapes tuned so far. */
+int32_t sft_batch_info(sft_batch_t ctx, int32_t* n_groups, int64_t* n_graph_nodes,
+                       int32_t* n_tuned);
+
 /* Allocation-free variant of sft_exact (the paper has no counterpart: this
  * is a deployment interface).  Some callers cannot allocate device memory
  * when they need a transform -- code inside another framework's memory

@@ -186,6 +186,8 @@ cudaError_t alloc_workspace(sft_plan_s* P, size_t* total) {
 }  // namespace
 
 namespace sft {
+sft_status normalize_params(sft_params* p) { return fill_defaults(p); }
+sft_status validate_params(const sft_params& p) { return validate(p); }
 // Records `msg` as the calling thread's error detail (read back through
 // sft_last_cuda_error).
 void set_error_detail(const char* msg) { std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s", msg); }

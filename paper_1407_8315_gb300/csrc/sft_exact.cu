@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(512) k_gather_fft(
     const typename F::In* __restrict__ x, int64_t x_stride, int64_t N, int64_t d, int log2M,
     int shift0, int log2Mt, const typename F::Tw* __restrict__ tw, void* __restrict__ out_v,
     int64_t out_sig, int64_t out_row, int row0, unsigned long long* __restrict__ ymax2,
-    const int64_t* __restrict__ shift_list) {
+    const int64_t* __restrict__ shift_list, const void* const* __restrict__ x_table) {
   extern __shared__ __align__(16) char smem[];
   typedef typename F::Out Out;
   const int b = blockIdx.y;
@@ -47,7 +47,10 @@ __global__ void __launch_bounds__(512) k_gather_fft(
   const int64_t shift = shift_list != nullptr ? shift_list[js] : shift0 + js;
   const int M = 1 << log2M;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const typename F::In* xs = x + (int64_t)b * x_stride;
+  // signal b: base + b * stride, or its own pointer (heterogeneous batches)
+  const typename F::In* xs = x_table != nullptr
+                                 ? reinterpret_cast<const typename F::In*>(x_table[b])
+                                 : x + (int64_t)b * x_stride;
   // x_{d,shift}[n] = x[(n d + shift) mod N]: every load of the thread is
   // issued before the first store (at most 16 per thread)
   typename F::In v[16];
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(512) k_fft4_cols(
     const typename F::In* __restrict__ x, int64_t x_stride, int64_t N, int64_t d, int log2M1,
     int log2M2, int shift0, int log2Mt, const typename F::Tw* __restrict__ tw,
     typename F::Out* __restrict__ W, int64_t w_sig, int nshift,
-    const int64_t* __restrict__ shift_list) {
+    const int64_t* __restrict__ shift_list, const void* const* __restrict__ x_table) {
   extern __shared__ __align__(16) char smem[];
   const int b = blockIdx.z, js = blockIdx.y;
   const int64_t shift = shift_list != nullptr ? shift_list[js] : shift0 + js;
@@ -121,7 +124,9 @@ __global__ void __launch_bounds__(512) k_fft4_cols(
   const int tpg = M1 / 16;               // threads per column
   const int tid = threadIdx.x, g = tid / tpg, t = tid % tpg;
   const int c0 = blockIdx.x * CB;
-  const typename F::In* xs = x + (int64_t)b * x_stride;
+  const typename F::In* xs = x_table != nullptr
+                                 ? reinterpret_cast<const typename F::In*>(x_table[b])
+                                 : x + (int64_t)b * x_stride;
   char* buf = smem + (size_t)g * padded(M1) * F::kBytesPerPoint;
   typename F::In v[16];
 #pragma unroll
@@ -428,6 +433,7 @@ struct FinArgs {
   int64_t* count;
   int32_t* unresolved;
   int32_t* overflow;
+  const sft_result* r_table;  // per-signal result buffers (heterogeneous batches)
 };
 
 // Block-wide exclusive scan of one int per thread (blockDim = 1024).
@@ -472,12 +478,25 @@ __global__ void __launch_bounds__(1024) k_finalize(FinArgs g) {
   for (int64_t k0 = lo; k0 < hi; ++k0) mine += cnt[k0];
   int total = 0;
   int pos = block_excl_scan(mine, &total);
+  int64_t cap = g.cap;
   int64_t* idx = g.idx + (int64_t)b * g.cap;
   double2* val = g.val + (int64_t)b * g.cap;
+  int64_t* count = g.count + b;
+  int32_t* unresolved = g.unresolved + b;
+  int32_t* overflow = g.overflow + b;
+  if (g.r_table != nullptr) {
+    const sft_result& rt = g.r_table[b];
+    cap = rt.cap;
+    idx = rt.idx;
+    val = reinterpret_cast<double2*>(rt.val);
+    count = rt.count;
+    unresolved = rt.unresolved;
+    overflow = rt.overflow;
+  }
   for (int64_t k0 = lo; k0 < hi; ++k0) {
     const int c = cnt[k0];
     for (int e = 0; e < c; ++e, ++pos) {
-      if (pos < g.cap) {
+      if (pos < cap) {
         idx[pos] = g.slot_s[((int64_t)b * M0 + k0) * 4 + e];
         const cdbl v = Store<F>::to_d(sp[((int64_t)b * M0 + k0) * 4 + e]);
         val[pos] = make_double2(v.x, v.y);
@@ -491,9 +510,9 @@ __global__ void __launch_bounds__(1024) k_finalize(FinArgs g) {
   int un_total = 0;
   (void)block_excl_scan(un, &un_total);
   if (tid == 0) {
-    g.count[b] = total < g.cap ? total : g.cap;
-    g.unresolved[b] = un_total;
-    g.overflow[b] = (total > g.cap || (g.flags[b] & 1)) ? 1 : 0;
+    *count = total < cap ? total : cap;
+    *unresolved = un_total;
+    *overflow = (total > cap || (g.flags[b] & 1)) ? 1 : 0;
   }
 }
 
@@ -503,21 +522,24 @@ static int fft_threads(int log2M) {
   return M / 16 > 32 ? M / 16 : 32;
 }
 
+// The opt-in shared-memory limit is a property of the kernel, shared by every
+// plan alive: it is raised once to the largest tile any plan launches
+// (kFft4Points points), never lowered to one plan's size.  Occupancy follows
+// the shared memory each launch actually requests.
 template <class F>
-static cudaError_t prepare_kernels_t(int64_t M0) {
-  const int smem = padded((int)std::min<int64_t>(M0, kFft4Points)) * 16;
-  const int smem4 = padded(kFft4Points) * 16;
+static cudaError_t prepare_kernels_t() {
+  const int smem = padded(kFft4Points) * 16;
   cudaError_t e = cudaFuncSetAttribute(k_gather_fft<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        smem);
-  if (e == cudaSuccess && M0 > kFft4Points)
-    e = cudaFuncSetAttribute(k_fft4_cols<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem4);
-  if (e == cudaSuccess && M0 > kFft4Points)
-    e = cudaFuncSetAttribute(k_fft4_rows<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem4);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fft4_cols<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fft4_rows<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return e;
 }
 
 cudaError_t prepare_kernels(sft_plan_s* P) {
-  return P->p.precision == SFT_FP64 ? prepare_kernels_t<F64>(P->M0) : prepare_kernels_t<FF>(P->M0);
+  return P->p.precision == SFT_FP64 ? prepare_kernels_t<F64>() : prepare_kernels_t<FF>();
 }
 
 int launches_per_call(const sft_plan_s* P) {
@@ -568,7 +590,8 @@ void launch_gather_fft(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride
     stage_begin(P, stage ? stage : (nshift > 2 ? "gather_fft_fixed" : names[lvl]), st);
     k_gather_fft<F><<<grid, nthr, smem, st>>>(xin, x_stride, P->p.N, d, log2M, shift0, P->log2M0,
                                               tw, out, P->ws.held_elems, out_row, row0,
-                                              want_ymax ? P->ws.ymax2 : nullptr, shift_list);
+                                              want_ymax ? P->ws.ymax2 : nullptr, shift_list,
+                                              P->x_table);
     stage_end(P, st);
     return;
   }
@@ -582,7 +605,7 @@ void launch_gather_fft(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride
   stage_begin(P, stage ? stage : cnames[lvl], st);
   k_fft4_cols<F><<<dim3(ctas, nshift, (unsigned)B), 512, smem, st>>>(
       xin, x_stride, P->p.N, d, log2M1, log2M2, shift0, P->log2M0, tw, W, w_sig, nshift,
-      shift_list);
+      shift_list, P->x_table);
   stage_end(P, st);
   stage_begin(P, stage ? "fft_rows" : rnames[lvl], st);
   k_fft4_rows<F><<<dim3(ctas, nshift, (unsigned)B), 512, smem, st>>>(
@@ -616,7 +639,7 @@ static void launch_fixed(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
   dim3 sgrid((unsigned)((P->M0 + kFoldThreads - 1) / kFoldThreads), (unsigned)B);
   const int64_t maxq = B * P->M0;
   const unsigned dgrid = (unsigned)std::max<int64_t>(
-      1, std::min<int64_t>((maxq + kDecThreads - 1) / kDecThreads, 8 * (int64_t)nsm));
+      1, std::min<int64_t>((maxq + kDecThreads - 1) / kDecThreads, (int64_t)P->dec_ctas_per_sm * nsm));
   int2* q0 = W.queue[0];
   int2* q1 = W.queue[1];
   int* c = W.qcount;
@@ -689,7 +712,7 @@ static void launch_iter(sft_plan_s* P, int64_t B, const void* x, int64_t x_strid
     dim3 fgrid((unsigned)((M + kFoldThreads - 1) / kFoldThreads), (unsigned)B);
     const int64_t maxq = B * M;
     const unsigned dgrid = (unsigned)std::max<int64_t>(
-        1, std::min<int64_t>((maxq + kDecThreads - 1) / kDecThreads, 8 * (int64_t)nsm));
+        1, std::min<int64_t>((maxq + kDecThreads - 1) / kDecThreads, (int64_t)P->dec_ctas_per_sm * nsm));
     static const char* fnames[] = {"fold_l0", "fold_l1", "fold_l2", "fold_l3"};
     static const char* dnames[] = {"decode_l0", "decode_l1", "decode_l2", "decode_l3"};
     stage_begin(P, fnames[l], st);
@@ -738,7 +761,7 @@ cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
       launch_iter<FF>(P, B, x, x_stride, om, nsm, st, &M_last, &T_last);
   }
   FinArgs f{P->M0, M_last, W.slot_cnt, W.slot_s, W.slot_p, T_last, W.flags, r->cap, r->idx,
-            reinterpret_cast<double2*>(r->val), r->count, r->unresolved, r->overflow};
+            reinterpret_cast<double2*>(r->val), r->count, r->unresolved, r->overflow, P->r_table};
   stage_begin(P, "finalize", st);
   if (fp64)
     k_finalize<F64><<<(unsigned)B, 1024, 0, st>>>(f);

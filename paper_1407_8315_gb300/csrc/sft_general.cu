@@ -36,6 +36,7 @@ struct GenArgs {
   int2* queue;
   int* qcount;
   const int64_t* cs;  // the r random shifts n_l
+  const int64_t* K_table;  // per-signal K (heterogeneous batches) or null
   uint8_t* slot_cnt;
   int64_t* slot_s;
   void* slot_p;
@@ -166,7 +167,8 @@ __global__ void __launch_bounds__(1024) k_gen_vote(GenArgs g) {
   const unsigned long long* keys =
       reinterpret_cast<const unsigned long long*>(g.sv + (int64_t)b * n);
   uint8_t* ak = g.ak + (int64_t)b * g.M;
-  const int64_t K = g.K < n ? g.K : n;
+  const int64_t Kb = g.K_table != nullptr ? g.K_table[b] : g.K;
+  const int64_t K = Kb < n ? Kb : n;
   unsigned long long prefix = 0ull, mask = 0ull;
   long long rem = K;  // rank (from the top) still to find among keys matching prefix
   if (K > 0) {
@@ -456,8 +458,8 @@ static void launch_general_t(sft_plan_s* P, int64_t B, const void* x, int64_t x_
   launch_gather_fft_any(P, B, x, x_stride, P->p.d, P->log2M0, 0, r, W.held[0], P->M0, 2 * am,
                         false, st, P->tab.cs_shifts, "gather_fft_random");
   GenArgs g{P->p.N, P->M0, P->p.d, P->p.K, am, r, 2, 8, W.held[0], W.held_elems, W.sv, W.T[0],
-            W.queue[0], W.qcount, P->tab.cs_shifts, W.slot_cnt, W.slot_s, W.slot_p, W.flags,
-            OmegaTab{P->tab.om_hi, P->tab.om_lo, P->tab.om_lo_bits, P->p.N - 1}};
+            W.queue[0], W.qcount, P->tab.cs_shifts, P->K_table, W.slot_cnt, W.slot_s, W.slot_p,
+            W.flags, OmegaTab{P->tab.om_hi, P->tab.om_lo, P->tab.om_lo_bits, P->p.N - 1}};
   dim3 sgrid((unsigned)((P->M0 + 255) / 256), (unsigned)B);
   stage_begin(P, "gen_svals", st);
   switch (am) {
@@ -470,9 +472,10 @@ static void launch_general_t(sft_plan_s* P, int64_t B, const void* x, int64_t x_
   stage_begin(P, "gen_vote", st);
   k_gen_vote<<<(unsigned)B, 1024, 0, st>>>(g);
   stage_end(P, st);
-  const int64_t maxq = B * std::min<int64_t>(P->M0, std::max<int64_t>(P->p.K, 1));
+  const int64_t maxq =
+      B * (P->K_table != nullptr ? P->M0 : std::min<int64_t>(P->M0, std::max<int64_t>(P->p.K, 1)));
   const unsigned dgrid =
-      (unsigned)std::max<int64_t>(1, std::min<int64_t>((maxq + 127) / 128, 8 * (int64_t)nsm));
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>((maxq + 127) / 128, (int64_t)P->dec_ctas_per_sm * nsm));
   stage_begin(P, "gen_solve", st);
   k_gen_solve<F><<<dgrid, 128, 0, st>>>(g);
   stage_end(P, st);

@@ -135,6 +135,13 @@ struct sft_plan_s {
   void* r_stage = nullptr;
   size_t r_stage_bytes = 0;
   std::vector<int64_t> cs_host;  // general path: the random shifts (host copy)
+  // heterogeneous batches: per-signal input pointers and result buffers
+  // (device tables; null for the strided single-shape entry points)
+  const void* const* x_table = nullptr;
+  const sft_result* r_table = nullptr;
+  const int64_t* K_table = nullptr;  // per-signal K for the general vote
+  // launch shape chosen by the batch autotuner
+  int dec_ctas_per_sm = 8;
   // profiling
   bool profiling = false;
   std::vector<sft::StageRec> stage_recs;   // records since the last read
@@ -161,6 +168,9 @@ void launch_general(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, i
                     cudaStream_t st);
 // Sets the calling thread's error detail returned by sft_last_cuda_error.
 void set_error_detail(const char* msg);
+// Defaults of zero fields (as sft_plan_create applies them) and validation.
+sft_status normalize_params(sft_params* p);
+sft_status validate_params(const sft_params& p);
 // Profiling brackets around one launch (no-ops unless plan->profiling).
 void stage_begin(sft_plan_s* plan, const char* name, cudaStream_t st);
 void stage_end(sft_plan_s* plan, cudaStream_t st);

@@ -40,7 +40,9 @@ class sft_result(C.Structure):
 EXPORTS = ["sft_params_default", "sft_plan_create", "sft_plan_destroy", "sft_plan_workspace_bytes",
            "sft_exact", "sft_exact_host", "sft_plan_launches_per_call", "sft_strerror",
            "sft_last_cuda_error", "sft_plan_set_profiling", "sft_plan_stage_times",
-           "sft_exact_noalloc", "sft_general", "sft_general_host", "sft_plan_cs_shifts"]
+           "sft_exact_noalloc", "sft_general", "sft_general_host", "sft_plan_cs_shifts",
+           "sft_batch_create", "sft_batch_destroy", "sft_batch_set_options", "sft_batch",
+           "sft_batch_info"]
 
 _lib = None
 
@@ -95,6 +97,14 @@ def load(build_if_missing: bool = False):
     lib.sft_general_host.argtypes = lib.sft_exact_host.argtypes
     lib.sft_plan_cs_shifts.argtypes = [C.c_void_p, P(C.c_int64), C.c_int32]
     lib.sft_plan_cs_shifts.restype = C.c_int32
+    lib.sft_batch_create.argtypes = [P(C.c_void_p)]
+    lib.sft_batch_destroy.argtypes = [C.c_void_p]
+    lib.sft_batch_destroy.restype = None
+    lib.sft_batch_set_options.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
+    lib.sft_batch.argtypes = [C.c_void_p, C.c_int64, P(sft_params), P(C.c_void_p), P(sft_result),
+                              C.c_void_p]
+    lib.sft_batch_info.argtypes = [C.c_void_p, P(C.c_int32), P(C.c_int64), P(C.c_int32)]
+    lib.sft_batch_info.restype = C.c_int32
     lib.sft_strerror.argtypes = [C.c_int]
     lib.sft_strerror.restype = C.c_char_p
     lib.sft_last_cuda_error.argtypes = []
@@ -318,6 +328,48 @@ class Plan:
     def close(self):
         if self.handle:
             sft_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A heterogeneous batch context (sft_batch_create / sft_batch)."""
+
+    def __init__(self, use_graph: bool = True, autotune: bool = True):
+        h = C.c_void_p()
+        _check(load().sft_batch_create(C.byref(h)), "sft_batch_create")
+        self.handle = h.value
+        _check(load().sft_batch_set_options(C.c_void_p(self.handle), int(use_graph), int(autotune)),
+               "sft_batch_set_options")
+        self._keep = None
+
+    def run(self, params, xs, outs, stream=None):
+        """params: list of sft_params; xs: list of CUDA tensors (one signal
+        each); outs: list of Result with per-signal device tensors."""
+        n = len(params)
+        pa = (sft_params * n)(*params)
+        xa = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+        ra = (sft_result * n)(*[sft_result(o.idx.numel(), o.idx.data_ptr(), o.val.data_ptr(),
+                                           o.count.data_ptr(), o.unresolved.data_ptr(),
+                                           o.overflow.data_ptr()) for o in outs])
+        self._keep = (pa, xa, ra)
+        _check(load().sft_batch(C.c_void_p(self.handle), n, pa, xa, ra,
+                                C.c_void_p(_stream_ptr(stream))), "sft_batch")
+
+    def info(self):
+        g, t = C.c_int32(), C.c_int32()
+        nodes = C.c_int64()
+        load().sft_batch_info(C.c_void_p(self.handle), C.byref(g), C.byref(nodes), C.byref(t))
+        return {"groups": g.value, "graph_nodes": nodes.value, "tuned": t.value}
+
+    def close(self):
+        if self.handle:
+            load().sft_batch_destroy(C.c_void_p(self.handle))
             self.handle = None
 
     def __del__(self):

@@ -122,10 +122,17 @@ def batch_exact(N: int, K: int, seeds, mag=(1.0, 10.0), dtype=np.complex64, out=
     return out, supps, valss
 
 
+def _next_pow2(v: int) -> int:
+    return 1 << max(0, int(v - 1).bit_length())
+
+
 def hetero_batch_spec(n_signals: int, seed: int):
     """Sizes for a heterogeneous batch: N = 2^u, u ~ U{12..20};
     K = round(2^v), v ~ U[3, 10], capped at N/64; even entries exactly sparse,
-    odd entries noisy at 30 dB.  Returns a list of dicts (N, K, kind, seed)."""
+    odd entries noisy at 30 dB.  Bins: exact entries M = min(N, pow2 >= 4K);
+    noisy entries M = min(N/16, pow2 >= 32K), so that d = N/M >= 16 leaves room
+    for the 2a_m = 6 consecutive and r = 9 random shifts of the general path.
+    Returns a list of dicts (N, K, M, kind, seed)."""
     rng = _rng(seed ^ 0xBA7C4)
     out = []
     for i in range(n_signals):
@@ -133,6 +140,11 @@ def hetero_batch_spec(n_signals: int, seed: int):
         N = 1 << u
         K = int(round(2.0 ** rng.uniform(3.0, 10.0)))
         K = max(1, min(K, N // 64))
-        out.append({"N": N, "K": K, "kind": "exact" if i % 2 == 0 else "noisy",
+        kind = "exact" if i % 2 == 0 else "noisy"
+        if kind == "exact":
+            M = min(N, _next_pow2(4 * K))
+        else:
+            M = min(N // 16, _next_pow2(32 * K))
+        out.append({"N": N, "K": K, "M": M, "kind": kind,
                     "seed": int(seed) * 100003 + i})
     return out

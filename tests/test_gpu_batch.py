@@ -1,0 +1,118 @@
+"""Heterogeneous batches (sft_batch): signals of uneven N, K and kind in one
+graph-captured call give exactly the results of transforming each signal on
+its own (same kernels, same per-signal arithmetic), on the first call
+(capture), on a replay with new data, and without the graph."""
+import numpy as np
+import pytest
+
+import siggen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1407_8315_gb300 as pkg
+    pkg.build()
+    return torch
+
+
+def _make(n_signals, seed):
+    """The heterogeneous workload's signal kinds and bin counts, with N capped
+    at 2^16 (K and M scaled with it) to keep the test short."""
+    from paper_1407_8315_gb300 import sft
+    specs = siggen.hetero_batch_spec(n_signals, seed)
+    params, xs = [], []
+    for sp in specs:
+        scale = max(1, sp["N"] >> 16)
+        N, K = sp["N"] // scale, max(1, sp["K"] // scale)
+        M = max(32, sp["M"] // scale)
+        if sp["kind"] == "exact":
+            p = sft.sft_params_default(N, K, N // M, "iter", "mixed")
+            x = siggen.exact_signal(N, K, sp["seed"], mag=(1, 10), dtype=np.complex64)[0]
+        else:
+            p = sft.sft_params_default(N, K, N // M, "general", "mixed")
+            p.seed = 77
+            x = siggen.noisy_signal(N, K, sp["seed"], 30, mag=(1, 10))[0]
+        params.append(p)
+        xs.append(x)
+    return params, xs
+
+
+def _single(torch, p, x, cap):
+    from paper_1407_8315_gb300 import sft
+    h = sft.sft_plan_create(p, 1)
+    try:
+        xt = torch.from_numpy(x).cuda()[None, :]
+        fn = sft.sft_general if p.mode == sft.SFT_GENERAL else sft.sft_exact
+        out = fn(h, xt, cap)
+        torch.cuda.synchronize()
+        return [t.cpu().numpy()[0] for t in out]
+    finally:
+        sft.sft_plan_destroy(h)
+
+
+def _outs(torch, n, cap):
+    from paper_1407_8315_gb300 import sft
+    return [sft.Result(torch.empty(cap, dtype=torch.int64, device="cuda"),
+                       torch.empty(cap, dtype=torch.complex128, device="cuda"),
+                       torch.empty(1, dtype=torch.int64, device="cuda"),
+                       torch.empty(1, dtype=torch.int32, device="cuda"),
+                       torch.empty(1, dtype=torch.int32, device="cuda")) for _ in range(n)]
+
+
+def _check(torch, params, xs, outs, cap):
+    for i, (p, x) in enumerate(zip(params, xs)):
+        ri, rv, rc, ru, ro = _single(torch, p, x, cap)
+        o = outs[i]
+        n = int(o.count.item())
+        assert n == int(rc), i
+        assert int(o.unresolved.item()) == int(ru) and int(o.overflow.item()) == int(ro)
+        np.testing.assert_array_equal(o.idx[:n].cpu().numpy(), ri[:n])
+        np.testing.assert_array_equal(o.val[:n].cpu().numpy(), rv[:n])
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_equals_single_signal_calls(gpu, use_graph):
+    torch = gpu
+    from paper_1407_8315_gb300 import sft
+    cap = 2048
+    params, xs = _make(24, 5)
+    batch = sft.Batch(use_graph=use_graph, autotune=True)
+    xt = [torch.from_numpy(x).cuda() for x in xs]
+    outs = _outs(torch, len(xs), cap)
+    batch.run(params, xt, outs)
+    torch.cuda.synchronize()
+    info = batch.info()
+    assert info["groups"] >= 4 and info["tuned"] == info["groups"]
+    if use_graph:
+        assert info["graph_nodes"] > info["groups"]
+    _check(torch, params, xs, outs, cap)
+    # same composition, new data: the graph is replayed with fresh tables
+    params2, xs2 = _make(24, 5)
+    rng = np.random.default_rng(1)
+    xs2 = [(x * np.complex64(np.exp(1j * rng.uniform(0, 6.28)))).astype(np.complex64) for x in xs2]
+    for t, x in zip(xt, xs2):
+        t.copy_(torch.from_numpy(x))
+    outs2 = _outs(torch, len(xs), cap)
+    batch.run(params2, xt, outs2)
+    torch.cuda.synchronize()
+    assert batch.info()["graph_nodes"] == info["graph_nodes"]
+    _check(torch, params2, xs2, outs2, cap)
+    batch.close()
+
+
+def test_batch_rejects_bad_signal(gpu):
+    torch = gpu
+    from paper_1407_8315_gb300 import sft
+    params, xs = _make(4, 9)
+    params[2].a_max = 7
+    batch = sft.Batch()
+    xt = [torch.from_numpy(x).cuda() for x in xs]
+    with pytest.raises(sft.SftError) as ei:
+        batch.run(params, xt, _outs(torch, 4, 2048))
+    assert "signal 2" in str(ei.value)
+    batch.close()

@@ -231,3 +231,16 @@ def test_strided_batch(gpu, orc):
         oi, _, _ = orc.exact(xs[b], M, 4, orc.ITER, **_tol_of(plan), cap=4 * M)
         gi = np.sort(out.idx[b, :int(out.count[b])].cpu().numpy())
         np.testing.assert_array_equal(gi, oi)
+
+
+def test_plans_of_different_sizes_coexist(gpu, orc):
+    """A plan created after a larger one must not shrink the larger plan's
+    FFT tile: both run correctly in either order."""
+    from paper_1407_8315_gb300 import Plan
+    big = Plan(1 << 16, 512, (1 << 16) // 4096, "iter", "mixed", max_signals=1)
+    small = Plan(1 << 12, 16, (1 << 12) // 64, "iter", "mixed", max_signals=1)
+    xb = siggen.exact_signal(1 << 16, 512, 3, mag=(1, 10), dtype=np.complex64)[0][None, :]
+    xs = siggen.exact_signal(1 << 12, 16, 4, mag=(1, 10), dtype=np.complex64)[0][None, :]
+    for _ in range(2):
+        _compare(orc, big, xb, "iter", 2048, MIXED_VAL_TOL)
+        _compare(orc, small, xs, "iter", 256, MIXED_VAL_TOL)
