@@ -1,19 +1,32 @@
 #!/usr/bin/env python
-"""Throughput of the exactly K-sparse sFFT-DT hot path on GB300.
+"""Throughput of the sFFT-DT hot path on GB300, through the C ABI.
 
-Workload (one "step"): one batch of B independent seeded synthetic signals,
-N = 2^22 complex64, K = 4096 non-zero frequencies at uniform positions with
-|X| ~ U[1, 10] and uniform phase, transformed by iterative sFFT-DT
-(Algorithm 1) with d = 512 (M = 2^13 bins), a_m = 4 levels, FP32
-(compensated) FFTs and FP64 solves -- through the C ABI (sft_exact).
+Default workload (one "step"): one batch of B = 152 independent seeded
+synthetic signals, N = 2^22 complex64, K = 4096 non-zero frequencies at
+uniform positions with |X| ~ U[1, 10] and uniform phase, transformed by
+iterative sFFT-DT (Algorithm 1) with d = 512 (M = 2^13 bins), a_m = 4 levels,
+compensated-FP32 FFTs and FP64 solves (sft_exact).
 
-Printed: one JSON line (rank 0) with signals/s, the end-to-end rate through
-the host entry point (sft_exact_host, pinned buffers, copies timed), the
-roofline of the dominant kernel, sampled SM clocks, recovered fraction and
-the error against the FP64 oracle on a sample, and the oracle's own rate on
-the host cores as a CPU baseline.
+Other workloads (--workload):
+  exact-2^22-fp64   the same signals through the plain FP64 form (complex128)
+  exact-2^22-fixed  the same signals, non-iterative FIXED mode
+  general-2^20      N = 2^20, K = 1024 plus white noise at 20/30/40 dB,
+                    d = N/(32K) = 32, a_m = 3, r = 9 (Algorithm 2, sft_general)
+  hetero-4096       4096 signals, N = 2^12..2^20, K = 8..1024 capped at N/64,
+                    half exact (ITER) and half noisy at 30 dB (general), in
+                    one graph-replayed sft_batch call; against launching
+                    every signal separately
+  exact-2^27        N = 2^27 (1 GiB per signal), K = 2^16, M = 2^18
+  general-2^27      the same at 30 dB, a_m = 4, r = 12
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
+Printed: one JSON line (rank 0) with signals/s over the timed steps (CUDA
+events, L2 flushed between steps), the end-to-end rate through the host entry
+point (page-locked inputs and results, copies inside the timed region), the
+roofline of the dominant kernel from live stage events, SM clocks sampled
+during the timed steps, recovery quality, the error against the FP64 oracle,
+and the oracle's own rate on the host cores as a CPU baseline.
+
+  python bench.py [--workload W] [--gpus N] [--steps K] [--warmup W]
   python bench.py --impl reference ...   # the FP64 CPU oracle as reference arm
 Multi-GPU (torchrun, one process per GPU): every rank transforms its own
 batch (replicas, no data-path collective); value = all signals / max time.
@@ -23,6 +36,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -38,64 +52,153 @@ sys.path.insert(0, ROOT)
 
 import siggen  # noqa: E402
 
-N, K, M = 1 << 22, 4096, 1 << 13
-D = N // M
-METRIC = "SFT signals/sec at N=2^22,K=4096; recovered fraction; max err vs FP64 oracle"
-WORKLOAD = "exact-iter N=2^22 K=4096 d=512 (M=2^13) a_m=4 c64 |X|~U[1,10]"
-THROTTLE = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+HEADLINE_METRIC = "SFT signals/sec at N=2^22,K=4096; recovered fraction; max err vs FP64 oracle"
+HETERO_METRIC = "SFT signals/sec, 4096 heterogeneous signals in one graph-replayed batch"
+FLUSH_BYTES = 512 << 20  # > 129 MB of L2
+
+
+# ------------------------------------------------------------------ workloads
+class W:
+    """A single-shape workload: B signals of one (N, K, M, mode, precision)."""
+
+    def __init__(self, name, metric, desc, N, K, M, mode, precision, batch, a_max,
+                 snrs=None, r=0, plan_seed=0, c64_input=False):
+        self.name, self.metric, self.desc = name, metric, desc
+        self.N, self.K, self.M, self.d = N, K, M, N // M
+        self.mode, self.precision, self.batch, self.a_max = mode, precision, batch, a_max
+        self.snrs, self.r, self.plan_seed = snrs, (r or 3 * a_max), plan_seed
+        self.general = mode == "general"
+        self.dtype = np.complex128 if precision == "fp64" else np.complex64
+        self.esize = 16 if precision == "fp64" else 8
+        self.cap = 2 * K + 16
+        # c64_input: the signals are generated as complex64 (as for the mixed
+        # form) and upcast, and the plan keeps the mixed form's tolerances,
+        # so that both forms see one input and recover the same set
+        self.c64_input = c64_input
+
+    def snr_of(self, b):
+        return self.snrs[b % len(self.snrs)] if self.snrs else None
+
+    def gen_one(self, seed, b):
+        if self.general:
+            x, s, _, _ = siggen.noisy_signal(self.N, self.K, seed, self.snr_of(b), mag=(1, 10),
+                                             dtype=self.dtype)
+        elif self.c64_input:
+            x, s, _ = siggen.exact_signal(self.N, self.K, seed, mag=(1, 10), dtype=np.complex64)
+            x = x.astype(self.dtype)
+        else:
+            x, s, _ = siggen.exact_signal(self.N, self.K, seed, mag=(1, 10), dtype=self.dtype)
+        return x, s
+
+    def h2d_per_signal(self):
+        """Bytes of samples each transform must read."""
+        if self.general:
+            return (2 * self.a_max + self.r) * self.M * self.esize
+        if self.mode == "fixed":
+            return 2 * self.a_max * self.M * self.esize
+        return sum(2 * (self.M >> l) * self.esize for l in range(self.a_max))
+
+    def stage_model(self, stage):
+        """Algorithmic work of one launch of a gather/FFT stage, per signal:
+        the input bytes it must read, and the FFT's radix-2 butterflies at
+        their float-float cost in FP32 instructions (68 each: one complex
+        float-float multiply, 36, and two complex float-float additions, 16
+        each).  None for other stages."""
+        if stage.startswith("gather_fft_l") or stage.startswith("gather_cols_l"):
+            Ml, ns = self.M >> int(stage[-1]), 2
+        elif stage in ("gather_fft_fixed", "gather_fft_consecutive"):
+            Ml, ns = self.M, 2 * self.a_max
+        elif stage == "gather_fft_random":
+            Ml, ns = self.M, self.r
+        else:
+            return None
+        bfly = ns * (Ml // 2) * int(math.log2(Ml))
+        return {"bytes": ns * Ml * self.esize, "fft_ops": bfly * 68}
+
+
+WORKLOADS = {
+    "exact-2^22": W("exact-2^22", HEADLINE_METRIC,
+                    "exact-iter N=2^22 K=4096 d=512 (M=2^13) a_m=4 c64 |X|~U[1,10]",
+                    1 << 22, 4096, 1 << 13, "iter", "mixed", 152, 4),
+    "exact-2^22-fp64": W("exact-2^22-fp64",
+                         "SFT signals/sec at N=2^22,K=4096, plain FP64 form",
+                         "exact-iter N=2^22 K=4096 d=512 (M=2^13) a_m=4, the headline's c64 "
+                         "signals upcast to c128, plain FP64 form, the mixed form's tolerances",
+                         1 << 22, 4096, 1 << 13, "iter", "fp64", 152, 4, c64_input=True),
+    "exact-2^22-fixed": W("exact-2^22-fixed",
+                          "SFT signals/sec at N=2^22,K=4096, non-iterative (FIXED)",
+                          "exact-fixed N=2^22 K=4096 d=512 (M=2^13) a_m=4 c64",
+                          1 << 22, 4096, 1 << 13, "fixed", "mixed", 152, 4),
+    "general-2^20": W("general-2^20",
+                      "SFT signals/sec at N=2^20,K=1024 noisy 20/30/40 dB; SNR_out",
+                      "general N=2^20 K=1024 d=32 (M=2^15) a_m=3 r=9 c64 SNR 20/30/40 dB",
+                      1 << 20, 1024, 1 << 15, "general", "mixed", 150, 3, snrs=(20, 30, 40),
+                      plan_seed=2024),
+    "exact-2^27": W("exact-2^27", "SFT signals/sec at N=2^27,K=2^16 (exact)",
+                    "exact-iter N=2^27 K=2^16 d=512 (M=2^18) a_m=4 c64",
+                    1 << 27, 1 << 16, 1 << 18, "iter", "mixed", 2, 4),
+    "general-2^27": W("general-2^27", "SFT signals/sec at N=2^27,K=2^16 noisy 30 dB; SNR_out",
+                      "general N=2^27 K=2^16 d=512 (M=2^18) a_m=4 r=12 c64 SNR 30 dB",
+                      1 << 27, 1 << 16, 1 << 18, "general", "mixed", 1, 4, snrs=(30,), r=12,
+                      plan_seed=2027),
+}
+HETERO = "hetero-4096"
 
 
 def parse():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="exact-2^22", choices=list(WORKLOADS) + [HETERO])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--batch", type=int, default=152)
+    ap.add_argument("--batch", type=int, default=0, help="signals per step (0: the workload's)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------ utilities
-def dist_setup(args):
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+def dist_setup():
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def gen_batch(B, seed0, threads):
-    out = np.empty((B, N), np.complex64)
+def host_threads():
+    return max(1, min(16, os.cpu_count() or 1))
+
+
+def gen_batch(wl, B, seed0):
+    out = np.empty((B, wl.N), wl.dtype)
     supps = [None] * B
 
     def one(i):
-        x, s, _ = siggen.exact_signal(N, K, seed0 + i, mag=(1, 10), dtype=np.complex64)
+        x, s = wl.gen_one(seed0 + i, i)
         out[i] = x
         supps[i] = s
 
-    with ThreadPoolExecutor(max_workers=threads) as ex:
+    with ThreadPoolExecutor(max_workers=min(host_threads(), 4 if wl.N > 1 << 24 else 16)) as ex:
         list(ex.map(one, range(B)))
     return out, supps
 
 
 class ClockSampler:
-    """nvidia-smi SM clocks and throttle reasons, sampled every 200 ms."""
+    """nvidia-smi SM clocks and throttle reasons every 50 ms; the summary
+    covers the samples read between mark_start() and mark_end()."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
-        self.index = index
-        self.proc = None
-        self.lines = []
+        self.index, self.proc, self.lines = index, None, []
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -104,34 +207,52 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.12)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=5)
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [t.strip() for t in ln.split(",")]
-            if len(f) < 8:
-                continue
-            try:
-                sm.append(float(f[0]))
-                smax.append(float(f[1]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[4:8]):
-                if v.lower() == "active":
-                    reasons.add(nm)
+
+        def summarise(lines):
+            sm, smax, reasons = [], [], set()
+            for _, ln in lines:
+                f = [t.strip() for t in ln.split(",")]
+                if len(f) < 8:
+                    continue
+                try:
+                    sm.append(float(f[0]))
+                    smax.append(float(f[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            return sm, smax, reasons
+
+        inside = [x for x in self.lines
+                  if self.t0 is not None and self.t0 <= x[0] <= self.t1 + 0.06]
+        sm, smax, reasons = summarise(inside)
+        window = "timed region"
+        if not sm:
+            sm, smax, reasons = summarise(self.lines)
+            window = "whole run (timed region shorter than one sample)"
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "window": window, "reasons": sorted(reasons)}
 
 
 def measured_peaks():
@@ -151,39 +272,28 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """dram bytes per launch of `kernel` from the committed ncu summary, or
-    None if the summary is missing or was taken on other kernel sources."""
+def ncu_traffic(workload: str, kernel: str):
+    """DRAM bytes per launch of `kernel` in `workload` from the committed ncu
+    summary, or None when it is missing or was taken on other sources."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
-    ent = t.get(kernel)
+    ent = t.get(workload, {}).get(kernel)
     if not ent or ent.get("source_sha") != source_hash():
         return None
     return ent.get("dram_bytes_per_launch")
 
 
-# Algorithmic work per launch of each stage, per signal.  The gather/FFT
-# stages must read 2 shifts x M_l samples of 8 B (complex64) and produce
-# 2 x M_l syndromes; bytes below count the samples (the input the method has
-# to touch).  FP32 work of the compensated FFT: 5 M log2 M flop per shift
-# counted as real flops of a radix-2 FFT.
-def stage_model(name):
-    if name.startswith("gather_fft_l"):
-        l = int(name[-1])
-        Ml = M >> l
-        return {"bytes": 2 * Ml * 8, "flops": 2 * 5 * Ml * int(np.log2(Ml))}
-    return None
-
-
 def kernel_of(stage: str) -> str:
-    """The __global__ function (template instance) that runs a stage: one
-    gather/FFT kernel serves every level, the fold and decode kernels are
-    instantiated per level (a = l + 1)."""
+    """The __global__ function (template instance) that runs a stage."""
     if stage.startswith("gather_fft"):
         return "k_gather_fft"
+    if stage.startswith("gather_cols"):
+        return "k_fft4_cols"
+    if stage.startswith("fft_rows"):
+        return "k_fft4_rows"
     if stage.startswith("fold_l"):
         return f"k_iter_fold<a={int(stage[-1]) + 1}>"
     if stage.startswith("decode_l"):
@@ -191,76 +301,232 @@ def kernel_of(stage: str) -> str:
     return "k_" + stage
 
 
+def roofline(wl, stages, B, clk):
+    """Dominant kernel (largest share of the step) and its roofline.  The
+    gather/FFT kernels of the mixed form are bound by the FP32 pipes (the
+    float-float FFT), so 'achieved' counts the FFT's radix-2 butterflies at
+    their float-float cost in FP32 instructions against 152 SMs x 128 FP32
+    lanes x the sampled SM clock; the HBM view (input bytes / time against
+    the measured copy bandwidth) is given beside it."""
+    peaks, src = measured_peaks()
+    groups = {}
+    for name, (ms_tot, nl) in stages.items():
+        g = groups.setdefault(kernel_of(name), {"ms": 0.0, "launches": 0, "bytes": 0, "ops": 0})
+        g["ms"] += ms_tot
+        g["launches"] += nl
+        m = wl.stage_model(name)
+        if m is not None:
+            g["bytes"] += m["bytes"] * B * nl
+            g["ops"] += m["fft_ops"] * B * nl
+    dom_name = max(groups, key=lambda k: groups[k]["ms"])
+    dom = groups[dom_name]
+    step_ms = sum(g["ms"] for g in groups.values())
+    sec = dom["ms"] / 1e3
+    roof = {"kernel": dom_name, "share": dom["ms"] / step_ms,
+            "ms_per_launch": dom["ms"] / dom["launches"], "peak_source": src,
+            "traffic": ncu_traffic(wl.name, dom_name)}
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    if dom["ops"] and wl.precision != "fp64":
+        peak = 152 * 128 * mhz * 1e6 / 1e12
+        ach = dom["ops"] / sec / 1e12
+        roof.update({"bound": "alu", "achieved": ach, "peak": peak,
+                     "unit": "T FP32-instr/s", "frac": ach / peak,
+                     "peak_note": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz (sampled)",
+                     "hbm_view": {"achieved_gbs": dom["bytes"] / sec / 1e9,
+                                  "peak_gbs": peaks["hbm_gbs"],
+                                  "frac": dom["bytes"] / sec / 1e9 / peaks["hbm_gbs"]}})
+    elif dom["bytes"]:
+        ach = dom["bytes"] / sec / 1e9
+        roof.update({"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": ach / peaks["hbm_gbs"]})
+    else:
+        # the solve kernels are FP64-pipe bound; no algorithmic flop model
+        # is claimed for them
+        roof.update({"bound": "alu", "achieved": None, "peak": None, "unit": None,
+                     "frac": None})
+    return roof
+
+
+def l2_flusher(torch):
+    buf = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    return lambda: buf.zero_()
+
+
+def timed_steps(torch, step, steps, flush, stream, clocks=None):
+    """Time `steps` calls of step() with CUDA events on `stream`, flushing L2
+    before each (the flush is outside the events).  Returns total ms."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.mark_start()
+    for a, b in ev:
+        flush()
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.mark_end()
+    return sum(a.elapsed_time(b) for a, b in ev)
+
+
+def max_over_ranks(torch, dist, ws, v):
+    if ws == 1:
+        return v
+    t = torch.tensor([v], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def snr_out(x, idx, val):
+    """SNR(x_out) = 10 log10(||X_out||^2 / ||X - X_out||^2) (Eq. (37))."""
+    X = np.fft.fft(x.astype(np.complex128))
+    Xo = np.zeros_like(X)
+    Xo[idx] = val
+    return float(10 * np.log10(np.vdot(Xo, Xo).real / max(np.vdot(X - Xo, X - Xo).real, 1e-300)))
+
+
+# ------------------------------------------------------------ oracle helpers
+def oracle_call(oracle, cfg, x, cap):
+    """The oracle's transform of one signal; cfg holds mode, precision, M,
+    K, a_max (and r, plan_seed for the general path)."""
+    if cfg["mode"] == "general":
+        idx, val, _ = oracle.general(x, cfg["M"], cfg["K"], a_max=cfg["a_max"], r=cfg["r"],
+                                     seed=cfg["plan_seed"], cap=cap)
+        return idx, val
+    tol = cfg.get("tol") or (oracle.TOL_FP64 if cfg["precision"] == "fp64" else oracle.TOL_MIXED)
+    mode = oracle.FIXED if cfg["mode"] == "fixed" else oracle.ITER
+    idx, val, _ = oracle.exact(x, cfg["M"], cfg["a_max"], mode, max_iters=cfg["a_max"], cap=cap,
+                               **tol)
+    return idx, val
+
+
+def cfg_of(wl):
+    return {"mode": wl.mode, "precision": wl.precision, "M": wl.M, "K": wl.K,
+            "a_max": wl.a_max, "r": wl.r, "plan_seed": wl.plan_seed}
+
+
+def compare_sorted(gi, gv, oi, ov):
+    o = np.argsort(gi, kind="stable")
+    gi, gv = gi[o], gv[o]
+    if not np.array_equal(gi, oi):
+        return False, 0.0
+    if len(oi) == 0:
+        return True, 0.0
+    return True, float((np.abs(gv - ov) / np.maximum(np.abs(ov), 1e-300)).max())
+
+
+def cpu_baseline(items, seconds, repeat=True):
+    """Time the oracle (as it stands) on the host cores, one transform per
+    thread, over `items` (callables) -- cycling through them until `seconds`
+    have passed when `repeat`, else once in order until then.  Returns the
+    rate, cores, transforms, seconds and the first result of each item."""
+    cores = os.cpu_count() or 1
+    results = {}
+    done = 0
+    t0 = time.perf_counter()
+    i = 0
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        while time.perf_counter() - t0 < seconds:
+            if i >= len(items):
+                if not repeat:
+                    break
+                i = 0
+            chunk = list(range(i, min(len(items), i + cores)))
+            for j, r in zip(chunk, ex.map(lambda j: items[j](), chunk)):
+                results.setdefault(j, r)
+                done += 1
+            i += len(chunk)
+    el = time.perf_counter() - t0
+    return done / el, cores, done, el, results
+
+
+def oracle_errors(res, get_gpu):
+    worst, mism = 0.0, 0
+    for i, (oi, ov) in res.items():
+        gi, gv = get_gpu(i)
+        same, e = compare_sorted(gi, gv, oi, ov)
+        mism += 0 if same else 1
+        worst = max(worst, e)
+    return {"max_rel_err": worst, "support_mismatch_signals": mism, "sample_signals": len(res)}
+
+
 # ------------------------------------------------------------------ our arm
-def run_ours(args):
+def run_plan_workload(args, wl):
     import torch
     import torch.distributed as dist
 
+    import paper_1407_8315_gb300.sft as S
     from paper_1407_8315_gb300 import Plan, build
 
-    ws, rank, local = dist_setup(args)
+    ws, rank, local = dist_setup()
     if ws > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     build()
-    B = args.batch
-    threads = max(1, min(16, os.cpu_count() or 1))
-    x_host_np, supps = gen_batch(B, 1_000_000 * (rank + 1), threads)
-    # pinned host copy for the end-to-end leg
-    pinned = torch.empty((B, N), dtype=torch.complex64, pin_memory=True)
-    pinned.numpy()[:] = x_host_np
-    x_dev = pinned.to("cuda", non_blocking=False)
-    plan = Plan(N, K, D, "iter", "mixed", max_signals=B)
-    cap = 2 * K
-    out = plan.exact(x_dev, cap)
+    B = args.batch or wl.batch
+    x_np, supps = gen_batch(wl, B, 1_000_000 * (rank + 1))
+    tdt = torch.complex128 if wl.precision == "fp64" else torch.complex64
+    pinned = torch.empty((B, wl.N), dtype=tdt, pin_memory=True)
+    pinned.numpy()[:] = x_np
+    x_dev = pinned.to("cuda")
+    tol = {}
+    if wl.c64_input:
+        mixed = S.sft_params_default(wl.N, wl.K, wl.d, wl.mode, "mixed")
+        tol = dict(zero_tol=mixed.zero_tol, root_tol=mixed.root_tol, res_tol=mixed.res_tol)
+    plan = Plan(wl.N, wl.K, wl.d, wl.mode, wl.precision, max_signals=B, a_max=wl.a_max,
+                seed=wl.plan_seed, n_cs_shifts=wl.r if wl.general else 0, **tol)
+    fn = plan.general if wl.general else plan.exact
+    fn_host = plan.general_host if wl.general else plan.exact_host
+    cap = wl.cap
+    out = fn(x_dev, cap)
     stream = torch.cuda.current_stream()
+    flush = l2_flusher(torch)
     for _ in range(args.warmup):
-        plan.exact(x_dev, cap, out)
+        flush()
+        fn(x_dev, cap, out)
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps, device time by CUDA events, stage events live
+    # ---- timed region: CUDA events per step, L2 flushed between steps
     plan.set_profiling(True)
-    _ = plan.stage_times()  # reset
+    plan.stage_times()  # reset
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(0.4)
+    time.sleep(0.3)
     if ws > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        plan.exact(x_dev, cap, out)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms = timed_steps(torch, lambda: fn(x_dev, cap, out), args.steps, flush, stream, clocks)
     if ws > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
     stages = plan.stage_times()
     plan.set_profiling(False)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    ms_per_step = ms / args.steps
+    ms = max_over_ranks(torch, dist, ws, ms)
     value = ws * B * args.steps / (ms / 1e3)
     launches = plan.launches_per_call * args.steps
 
-    # ---- quality on this rank's batch: recovered fraction vs planted support
     cnt = out.count.cpu().numpy()
     idx = out.idx.cpu().numpy()
-    found = sum(int(np.isin(idx[b, :cnt[b]], supps[b]).sum()) for b in range(B))
-    false_pos = sum(int(cnt[b]) for b in range(B)) - found
-    recovered = found / (B * K)
+    val = out.val.cpu().numpy()
+    quality = {}
+    if wl.general:
+        per = {}
+        for b in range(min(B, 24)):
+            per.setdefault(wl.snr_of(b), []).append(
+                snr_out(x_np[b], idx[b, :cnt[b]], val[b, :cnt[b]]))
+        quality["snr_out_db"] = {str(k): float(np.mean(v)) for k, v in sorted(per.items())}
+        quality["snr_out_sample"] = min(B, 24)
+    else:
+        found = sum(int(np.isin(idx[b, :cnt[b]], supps[b]).sum()) for b in range(B))
+        quality["recovered_fraction"] = found / (B * wl.K)
+        quality["false_positives"] = int(cnt.sum()) - found
 
-    # ---- end to end through the host entry point.  Two page-locked copies
-    # of the batch alternate so that no line of one step's input can still
-    # sit in L2 at the next step; the kernels read the samples in place over
-    # NVLink-C2C and write the results into page-locked host arrays.
-    import paper_1407_8315_gb300.sft as S
-    pinned2 = torch.empty((B, N), dtype=torch.complex64, pin_memory=True)
-    pinned2.numpy()[:] = x_host_np
+    # ---- end to end through the host entry point: page-locked inputs read
+    # in place over NVLink-C2C, results written in place into page-locked
+    # host arrays; two alternating input copies, L2 flushed before each step
+    pinned2 = torch.empty((B, wl.N), dtype=tdt, pin_memory=True)
+    pinned2.numpy()[:] = x_np
     srcs = [pinned.numpy(), pinned2.numpy()]
     h_out = S.Result(torch.empty((B, cap), dtype=torch.int64, pin_memory=True).numpy(),
                      torch.empty((B, cap), dtype=torch.complex128, pin_memory=True).numpy(),
@@ -268,80 +534,58 @@ def run_ours(args):
                      torch.empty(B, dtype=torch.int32, pin_memory=True).numpy(),
                      torch.empty(B, dtype=torch.int32, pin_memory=True).numpy())
     for i in range(3):
-        plan.exact_host(srcs[i & 1], cap, h_out)  # warm
+        flush()
+        fn_host(srcs[i & 1], cap, h_out)
     if ws > 1:
         dist.barrier()
     t0 = time.perf_counter()
     for i in range(args.e2e_steps):
-        plan.exact_host(srcs[i & 1], cap, h_out)
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    # bytes crossing the host link per step: the samples of the shifts the
-    # transform reads (2 shifts x M_l samples of 8 B at each level) in, the
-    # recovered entries and per-signal counters out
-    levels = 4
-    h2d = int(B * sum(2 * (M >> l) * 8 for l in range(levels)))
-    d2h = int(int(h_out.count.sum()) * 24 + B * 16)
+        flush()
+        fn_host(srcs[i & 1], cap, h_out)
+    e2e_s = max_over_ranks(torch, dist, ws, time.perf_counter() - t0)
     e2e = {"value": ws * B * args.e2e_steps / e2e_s, "unit": "signals/s",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "path": "sft_exact_host, page-locked host input read in place (zero-copy gather "
-                   "over NVLink-C2C), results written in place; two alternating input copies"}
-
+           "h2d_bytes_per_step": int(B * wl.h2d_per_signal()),
+           "d2h_bytes_per_step": int(int(h_out.count.sum()) * 24 + B * 16),
+           "path": ("sft_general_host" if wl.general else "sft_exact_host") +
+                   ", page-locked input read in place (zero-copy gather over NVLink-C2C), "
+                   "results written in place; two alternating input copies, L2 flushed "
+                   "before each step (flush time included)"}
     if ws > 1:
         dist.barrier()
     if rank != 0:
         dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel (live stage events).  Stages are
-    # grouped by the kernel that runs them (k_gather_fft serves every level);
-    # the dominant kernel is the one with the largest share of step time.
-    peaks, peak_src = measured_peaks()
-    groups = {}
-    for name, (ms_tot, nl) in stages.items():
-        kern = kernel_of(name)
-        g = groups.setdefault(kern, {"ms": 0.0, "launches": 0, "bytes": 0, "stages": []})
-        g["ms"] += ms_tot
-        g["launches"] += nl
-        g["stages"].append(name)
-        model = stage_model(name)
-        if model is not None:
-            g["bytes"] += model["bytes"] * B * nl
-    dom_name = max(groups, key=lambda k: groups[k]["ms"])
-    dom = groups[dom_name]
-    step_ms = sum(g["ms"] for g in groups.values())
-    if dom["bytes"]:
-        ach = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
-        roof = {"kernel": dom_name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "peak_source": peak_src,
-                "traffic": ncu_traffic(dom_name), "share": dom["ms"] / step_ms,
-                "ms_per_launch": dom["ms"] / dom["launches"]}
-    else:
-        roof = {"kernel": dom_name, "bound": "alu", "achieved": None, "peak": None,
-                "unit": None, "frac": None, "peak_source": peak_src, "traffic": None,
-                "share": dom["ms"] / step_ms, "ms_per_launch": dom["ms"] / dom["launches"]}
+    roof = roofline(wl, stages, B, clk)
     stage_ms = {k: round(v[0] / v[1], 5) for k, v in stages.items()}
 
-    # ---- CPU baseline and error vs the FP64 oracle on a sample
-    cpu = None
-    err = {"max_rel_err": None, "support_mismatch_signals": None, "sample_signals": 0}
+    # ---- CPU baseline (the oracle on the host cores) and error vs the oracle
+    cpu, err = None, {"max_rel_err": None, "support_mismatch_signals": None, "sample_signals": 0}
     if not args.no_cpu:
-        cpu, err = cpu_baseline(x_host_np, idx, out.val.cpu().numpy(), cnt, plan, args.cpu_seconds)
+        import oracle
+        oracle.build()
+        cfg = cfg_of(wl)
+        p = plan.params  # the tolerances the plan runs with
+        cfg["tol"] = dict(zero_tol=p.zero_tol, root_tol=p.root_tol, res_tol=p.res_tol)
+        items = [lambda b=b: oracle_call(oracle, cfg, x_np[b], cap) for b in range(B)]
+        rate, cores, done, el, res = cpu_baseline(items, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "signals/s", "cores": cores, "kind": "oracle",
+               "sample": f"{done} transforms of this step's {B} signals ({len(res)} distinct), "
+                         f"one signal per thread, {cores} threads, {el:.1f} s"}
+        err = oracle_errors(res, lambda b: (idx[b, :cnt[b]], val[b, :cnt[b]]))
 
     line = {
-        "metric": METRIC, "value": value, "unit": "signals/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "metric": wl.metric, "value": value, "unit": "signals/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "ff32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "batch_per_gpu": B, "mode": "iter",
-                   "precision": "mixed (compensated-FP32 FFT, FP64 solves)",
+        "dtype": "f64" if wl.precision == "fp64" else "ff32+f64", "data": "synthetic",
+        "config": {"workload": wl.desc, "batch_per_gpu": B, "mode": wl.mode,
+                   "precision": "plain FP64" if wl.precision == "fp64"
+                   else "mixed (compensated-FP32 FFT, FP64 solves)",
                    "parallelism": f"replicas x{ws}",
-                   "l2": f"inputs larger than L2 ({B} x 32 MiB per GPU), no flush"},
-        "recovered_fraction": recovered, "false_positives": false_pos,
-        "vs_oracle": err,
+                   "l2": f"flushed between timed steps ({FLUSH_BYTES >> 20} MiB write, outside "
+                         f"the step events)"},
+        **quality, "vs_oracle": err,
         "e2e": e2e, "gpu_launches": launches, "stage_ms_per_launch": stage_ms,
         "roofline": roof, "clocks": clk, "cpu_baseline": cpu,
     }
@@ -350,80 +594,252 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def cpu_baseline(xs, idx, val, cnt, plan, seconds):
-    """Time the FP64 oracle (as it stands) on the host cores over signals of
-    the benchmark batch, and compare its output with the GPU's."""
-    import oracle
-    oracle.build()
-    p = plan.params
-    tol = dict(zero_tol=p.zero_tol, root_tol=p.root_tol, res_tol=p.res_tol)
-    cores = os.cpu_count() or 1
-    B = xs.shape[0]
+# ------------------------------------------------------ heterogeneous batch
+def hetero_cfg(sp):
+    if sp["kind"] == "exact":
+        return {"mode": "iter", "precision": "mixed", "M": sp["M"], "K": sp["K"], "a_max": 4}
+    return {"mode": "general", "precision": "mixed", "M": sp["M"], "K": sp["K"], "a_max": 3,
+            "r": 9, "plan_seed": 77}
 
-    def one(b):
-        return b, oracle.exact(xs[b], M, 4, oracle.ITER, max_iters=4, cap=2 * K, **tol)
 
-    results = {}
-    done = 0
-    t0 = time.perf_counter()
-    with ThreadPoolExecutor(max_workers=cores) as ex:
-        while True:
-            for b, r in ex.map(one, range(B)):
-                results[b] = r
-                done += 1
-            if time.perf_counter() - t0 >= seconds or done >= 8 * B:
+def hetero_params(S, sp):
+    cfg = hetero_cfg(sp)
+    p = S.sft_params_default(sp["N"], sp["K"], sp["N"] // sp["M"], cfg["mode"], "mixed")
+    if cfg["mode"] == "general":
+        p.seed = cfg["plan_seed"]
+    else:
+        cfg["tol"] = dict(zero_tol=p.zero_tol, root_tol=p.root_tol, res_tol=p.res_tol)
+    return p, cfg
+
+
+def hetero_gen(specs):
+    xs = [None] * len(specs)
+    truth = [None] * len(specs)
+
+    def one(i):
+        sp = specs[i]
+        if sp["kind"] == "exact":
+            x, s, _ = siggen.exact_signal(sp["N"], sp["K"], sp["seed"], mag=(1, 10),
+                                          dtype=np.complex64)
+        else:
+            x, s, _, _ = siggen.noisy_signal(sp["N"], sp["K"], sp["seed"], 30, mag=(1, 10))
+        xs[i] = x
+        truth[i] = s
+
+    with ThreadPoolExecutor(max_workers=host_threads()) as ex:
+        list(ex.map(one, range(len(specs))))
+    return xs, truth
+
+
+def run_hetero(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1407_8315_gb300.sft as S
+    from paper_1407_8315_gb300 import Plan, build
+
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build()
+    n = args.batch or 4096
+    specs = siggen.hetero_batch_spec(n, 4096 + rank)
+    xs, truth = hetero_gen(specs)
+    pc = [hetero_params(S, sp) for sp in specs]
+    params = [p for p, _ in pc]
+    caps = [2 * sp["K"] + 16 for sp in specs]
+    offs = np.concatenate([[0], np.cumsum([sp["N"] for sp in specs])]).astype(np.int64)
+    coffs = np.concatenate([[0], np.cumsum(caps)]).astype(np.int64)
+    total, ctotal = int(offs[-1]), int(coffs[-1])
+    flat_h = torch.empty(total, dtype=torch.complex64, pin_memory=True)
+    fh = flat_h.numpy()
+    for i, x in enumerate(xs):
+        fh[offs[i]:offs[i + 1]] = x
+    flat_d = flat_h.to("cuda")
+
+    def results(dev):
+        if dev:
+            mk = lambda k, dt: torch.empty(k, dtype=dt, device="cuda")  # noqa: E731
+        else:
+            mk = lambda k, dt: torch.empty(k, dtype=dt, pin_memory=True)  # noqa: E731
+        idx, val = mk(ctotal, torch.int64), mk(ctotal, torch.complex128)
+        cnt, unr, ovf = mk(n, torch.int64), mk(n, torch.int32), mk(n, torch.int32)
+        per = [S.Result(idx[coffs[i]:coffs[i + 1]], val[coffs[i]:coffs[i + 1]], cnt[i:i + 1],
+                        unr[i:i + 1], ovf[i:i + 1]) for i in range(n)]
+        return (idx, val, cnt), per
+
+    (b_idx, b_val, b_cnt), b_res = results(True)
+    base = flat_d.data_ptr()
+    batch = S.Batch(use_graph=True, autotune=True)
+    prep = batch.prepare(params, [base + int(offs[i]) * 8 for i in range(n)], b_res)
+    stream = torch.cuda.current_stream()
+    flush = l2_flusher(torch)
+    batch.launch(prep)  # first call: plans, autotune, capture
+    for _ in range(args.warmup):
+        flush()
+        batch.launch(prep)
+    torch.cuda.synchronize()
+    info = batch.info()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    steps = max(3, args.steps // 20)
+    ms = timed_steps(torch, lambda: batch.launch(prep), steps, flush, stream, clocks)
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(torch, dist, ws, ms)
+    value = ws * n * steps / (ms / 1e3)
+    kernels_per_call = info["graph_nodes"] - info["groups"]  # one memset node per group
+
+    # ---- the same signals launched one by one (one plan per signal)
+    plans = [Plan(sp["N"], sp["K"], sp["N"] // sp["M"], cfg["mode"], "mixed", max_signals=1,
+                  seed=cfg.get("plan_seed", 0)) for (_, cfg), sp in zip(pc, specs)]
+    (s_idx, s_val, s_cnt), s_res = results(True)
+    xviews = [flat_d[offs[i]:offs[i + 1]].view(1, -1) for i in range(n)]
+    fns = [pl.general if cfg["mode"] == "general" else pl.exact for pl, (_, cfg) in zip(plans, pc)]
+
+    def per_signal():
+        for i in range(n):
+            fns[i](xviews[i], caps[i], s_res[i])
+
+    per_signal()
+    torch.cuda.synchronize()
+    ps_steps = 2
+    ps_ms = timed_steps(torch, per_signal, ps_steps, flush, stream)
+    ps_value = n * ps_steps / (ps_ms / 1e3)
+    identical = bool(torch.equal(b_cnt, s_cnt))
+    if identical:
+        for i in range(n):
+            c = int(b_cnt[i])
+            if not (torch.equal(b_idx[coffs[i]:coffs[i] + c], s_idx[coffs[i]:coffs[i] + c]) and
+                    torch.equal(b_val[coffs[i]:coffs[i] + c], s_val[coffs[i]:coffs[i] + c])):
+                identical = False
                 break
-    el = time.perf_counter() - t0
-    worst, mism = 0.0, 0
-    for b, (oi, ov, ou) in results.items():
-        gi, gv = idx[b, :cnt[b]], val[b, :cnt[b]]
-        o = np.argsort(gi, kind="stable")
-        gi, gv = gi[o], gv[o]
-        if not np.array_equal(gi, oi):
-            mism += 1
-            continue
-        if len(oi):
-            worst = max(worst, float((np.abs(gv - ov) / np.abs(ov)).max()))
-    cpu = {"value": done / el, "unit": "signals/s", "cores": cores, "kind": "oracle",
-           "sample": f"{done} transforms of the {B} benchmark signals ({len(results)} distinct), "
-                     f"one per thread, {cores} threads, {el:.1f} s"}
-    err = {"max_rel_err": worst, "support_mismatch_signals": mism, "sample_signals": len(results)}
-    return cpu, err
+    for pl in plans:
+        pl.close()
+
+    # ---- end to end: page-locked inputs and results, read/written in place
+    (h_idx, h_val, h_cnt), h_res = results(False)
+    hbase = flat_h.data_ptr()
+    hprep = batch.prepare(params, [hbase + int(offs[i]) * 8 for i in range(n)], h_res)
+    for _ in range(2):
+        batch.launch(hprep)
+        torch.cuda.synchronize()
+    e2e_steps = max(3, args.e2e_steps // 10)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        flush()
+        batch.launch(hprep)
+        torch.cuda.synchronize()
+    e2e_s = max_over_ranks(torch, dist, ws, time.perf_counter() - t0)
+    h2d = sum((sum(2 * (sp["M"] >> l) * 8 for l in range(4)) if sp["kind"] == "exact"
+               else 15 * sp["M"] * 8) for sp in specs)
+    e2e = {"value": ws * n * e2e_steps / e2e_s, "unit": "signals/s",
+           "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(int(h_cnt.numpy().sum()) * 24 + n * 16),
+           "path": "sft_batch with page-locked host inputs and results (zero-copy), L2 flushed "
+                   "before each step (flush time included)"}
+    if ws > 1:
+        dist.barrier()
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    cnt = b_cnt.cpu().numpy()
+    idx = b_idx.cpu().numpy()
+    val = b_val.cpu().numpy()
+    ex_found = ex_k = 0
+    snrs = []
+    for i, sp in enumerate(specs):
+        gi = idx[coffs[i]:coffs[i] + cnt[i]]
+        if sp["kind"] == "exact":
+            ex_found += int(np.isin(gi, truth[i]).sum())
+            ex_k += sp["K"]
+        elif len(snrs) < 48 and sp["N"] <= 1 << 18:
+            snrs.append(snr_out(xs[i], gi, val[coffs[i]:coffs[i] + cnt[i]]))
+
+    cpu, err = None, {"max_rel_err": None, "support_mismatch_signals": None, "sample_signals": 0}
+    if not args.no_cpu:
+        import oracle
+        oracle.build()
+        items = [lambda i=i: oracle_call(oracle, pc[i][1], xs[i], caps[i]) for i in range(n)]
+        rate, cores, done, el, res = cpu_baseline(items, args.cpu_seconds, repeat=False)
+        cpu = {"value": rate, "unit": "signals/s", "cores": cores, "kind": "oracle",
+               "sample": f"the first {done} signals of the batch in order, one per thread, "
+                         f"{cores} threads, {el:.1f} s"}
+        err = oracle_errors(res, lambda i: (idx[coffs[i]:coffs[i] + cnt[i]],
+                                            val[coffs[i]:coffs[i] + cnt[i]]))
+
+    line = {
+        "metric": HETERO_METRIC,
+        "value": value, "unit": "signals/s", "n_gpus": ws, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "ff32+f64", "data": "synthetic",
+        "config": {"workload": f"hetero {n} signals: N=2^12..2^20, K=8..1024 capped N/64, even "
+                               "exact-iter M=min(N,pow2>=4K), odd general 30 dB "
+                               "M=min(N/16,pow2>=32K)", "batch_per_gpu": n,
+                   "parallelism": f"replicas x{ws}",
+                   "l2": f"flushed between timed steps ({FLUSH_BYTES >> 20} MiB)"},
+        "groups": info["groups"], "graph_nodes": info["graph_nodes"],
+        "tuned_shapes": info["tuned"],
+        "per_signal_launches": {"value": ps_value, "unit": "signals/s",
+                                "speedup_of_batch": value / ps_value,
+                                "identical_results": identical},
+        "recovered_fraction_exact": ex_found / max(ex_k, 1),
+        "snr_out_db_noisy_mean": float(np.mean(snrs)) if snrs else None,
+        "vs_oracle": err, "e2e": e2e, "gpu_launches": kernels_per_call * steps,
+        "roofline": None, "clocks": clk, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+    if ws > 1:
+        dist.destroy_process_group()
 
 
 # ------------------------------------------------------------ reference arm
 def run_reference(args):
     """The FP64 CPU oracle on the host cores: each step transforms one signal
-    per core (a bounded sample of the same workload)."""
-    ws, rank, _ = dist_setup(args)
+    of the workload per core (a bounded sample of the same workload)."""
+    ws, rank, _ = dist_setup()
     if rank != 0:
         return
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
-    xs, _ = gen_batch(cores, 7_000_000, max(1, min(16, cores)))
-    tol = oracle.TOL_MIXED
-
-    def one(b):
-        return oracle.exact(xs[b], M, 4, oracle.ITER, max_iters=4, cap=2 * K, **tol)
-
+    if args.workload == HETERO:
+        specs = siggen.hetero_batch_spec(cores, 4096)
+        xs, _ = hetero_gen(specs)
+        items = [lambda i=i: oracle_call(oracle, hetero_cfg(specs[i]), xs[i],
+                                         2 * specs[i]["K"] + 16) for i in range(cores)]
+        metric, desc = HETERO_METRIC, "hetero sample: the first signals of the batch, one per core"
+    else:
+        wl = WORKLOADS[args.workload]
+        xs, _ = gen_batch(wl, cores, 7_000_000)
+        cfg = cfg_of(wl)
+        items = [lambda i=i: oracle_call(oracle, cfg, xs[i], wl.cap) for i in range(cores)]
+        metric, desc = wl.metric, wl.desc
     with ThreadPoolExecutor(max_workers=cores) as ex:
         for _ in range(args.warmup):
-            list(ex.map(one, range(cores)))
+            list(ex.map(lambda f: f(), items))
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            list(ex.map(one, range(cores)))
+            list(ex.map(lambda f: f(), items))
         el = time.perf_counter() - t0
     value = cores * args.steps / el
     line = {
-        "metric": METRIC, "value": value, "unit": "signals/s", "n_gpus": ws,
+        "metric": metric, "value": value, "unit": "signals/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD, "batch_per_step": cores, "mode": "iter",
-                   "precision": "FP64 CPU oracle"},
+        "config": {"workload": desc, "batch_per_step": cores, "precision": "FP64 CPU oracle"},
         "cpu_baseline": {"value": value, "unit": "signals/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{cores} signals per step, one per thread"},
+                         "sample": f"{cores} signals per step, one per thread, "
+                                   f"{args.steps} steps, {el:.1f} s"},
         "e2e": {"value": value, "unit": "signals/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -436,8 +852,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == HETERO:
+        run_hetero(args)
     else:
-        run_ours(args)
+        run_plan_workload(args, WORKLOADS[args.workload])
 
 
 if __name__ == "__main__":

@@ -200,10 +200,12 @@ sft_status sft_batch_set_options(sft_batch_t ctx, int32_t use_graph, int32_t aut
 /* Transforms n_signals signals.  Host arrays of n_signals entries:
  *   params   the parameters of each signal (mode SFT_EXACT_ITER,
  *            SFT_EXACT_FIXED or SFT_GENERAL; as for sft_plan_create)
- *   x        the device address of each signal (complex64 for SFT_MIXED,
- *            complex128 for SFT_FP64)
- *   results  each signal's own result buffers (device pointers; count,
- *            unresolved and overflow point at one value each; cap >= K)
+ *   x        the address of each signal as the GPU sees it (complex64 for
+ *            SFT_MIXED, complex128 for SFT_FP64): device memory, or
+ *            page-locked host memory, which the kernels read in place
+ *   results  each signal's own result buffers (device or page-locked host
+ *            memory; count, unresolved and overflow point at one value
+ *            each; cap >= K)
  * Asynchronous on `stream`; the first call of a new composition builds
  * plans (allocates) and captures the graph. */
 sft_status sft_batch(sft_batch_t ctx, int64_t n_signals, const sft_params* params,

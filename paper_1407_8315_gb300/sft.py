@@ -348,18 +348,42 @@ class Batch:
                "sft_batch_set_options")
         self._keep = None
 
-    def run(self, params, xs, outs, stream=None):
-        """params: list of sft_params; xs: list of CUDA tensors (one signal
-        each); outs: list of Result with per-signal device tensors."""
+    @staticmethod
+    def _ptr(a) -> int:
+        if hasattr(a, "data_ptr"):
+            return int(a.data_ptr())
+        if isinstance(a, np.ndarray):
+            return int(a.ctypes.data)
+        return int(a)
+
+    @staticmethod
+    def _size(a) -> int:
+        return int(a.numel()) if hasattr(a, "numel") else int(np.size(a))
+
+    def prepare(self, params, xs, outs):
+        """Marshal one call: params (sft_params list), xs (device tensors,
+        page-locked host arrays or raw addresses, one signal each), outs
+        (Result of per-signal buffers).  Returns the argument arrays for
+        launch(), reusable while the buffers stay alive."""
         n = len(params)
         pa = (sft_params * n)(*params)
-        xa = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
-        ra = (sft_result * n)(*[sft_result(o.idx.numel(), o.idx.data_ptr(), o.val.data_ptr(),
-                                           o.count.data_ptr(), o.unresolved.data_ptr(),
-                                           o.overflow.data_ptr()) for o in outs])
-        self._keep = (pa, xa, ra)
+        xa = (C.c_void_p * n)(*[self._ptr(x) for x in xs])
+        ra = (sft_result * n)(*[sft_result(self._size(o.idx), self._ptr(o.idx), self._ptr(o.val),
+                                           self._ptr(o.count), self._ptr(o.unresolved),
+                                           self._ptr(o.overflow)) for o in outs])
+        return n, pa, xa, ra
+
+    def launch(self, prepared, stream=None):
+        n, pa, xa, ra = prepared
         _check(load().sft_batch(C.c_void_p(self.handle), n, pa, xa, ra,
                                 C.c_void_p(_stream_ptr(stream))), "sft_batch")
+
+    def run(self, params, xs, outs, stream=None):
+        """params: list of sft_params; xs: one signal each (device tensors or
+        page-locked host memory); outs: list of Result with per-signal
+        buffers."""
+        self._keep = self.prepare(params, xs, outs)
+        self.launch(self._keep, stream)
 
     def info(self):
         g, t = C.c_int32(), C.c_int32()
