@@ -39,8 +39,9 @@
  *              peels and solves in FP64.
  *   SFT_MIXED  input complex64 (interleaved re, im floats); the FFTs run on
  *              the FP32 pipes in compensated (float-float) arithmetic, which
- *              keeps FP64-grade syndromes; folds, peels and the per-bin
- *              Hankel / root / value solves run in FP64.
+ *              keeps FP64-grade syndromes; the held syndromes, folds, peels
+ *              and activity tests stay in float-float on the FP32 pipes, and
+ *              the per-bin Hankel / root / value solves run in FP64.
  *
  * Conventions of every entry point.
  *   - Pointers marked "device" must be CUDA device (or managed) memory on
@@ -241,6 +242,89 @@ int32_t sft_batch_info(sft_batch_t ctx, int32_t* n_groups, int64_t* n_graph_node
 #define SFT_NOALLOC_SCRATCH_BYTES (16u << 20)
 sft_status sft_exact_noalloc(const sft_params* p, int64_t n_signals, const void* x,
                              int64_t x_stride, const sft_result* r, void* stream);
+
+/* ---- learned support proposal (generally K-sparse path) ----------------
+ *
+ * Not in the paper: a small network proposes, for every bin that Algorithm 2
+ * votes a_k > 0 aliases, the candidates t of S_k = {k + tM} that pruning
+ * Step 2 would otherwise take from the a_k-term locator; Subspace Pursuit
+ * runs on them as in Step 3, and the paper's own residual judges the
+ * result: over all 2a_m + r equations of Eq. (3) the network's solution
+ * replaces the plain one only when its squared residual is below
+ * (1 - 1e-6) times the plain solution's.  The plain decoder is therefore
+ * the fallback and the judge of every prediction.
+ *
+ * Features of a voted bin k (2 (2a_m + r) floats): the syndromes of its
+ * 2a_m consecutive and r random shifts sh_l, de-rotated by omega^{-k sh_l}
+ * (which leaves sum_j p_j e^{2 pi i t_j sh_l / d}), rotated so that the
+ * first is real and non-negative, scaled to unit 2-norm, interleaved
+ * (re, im).  Network: n_in -> 128 -> 128 -> n_sup + n_cls, ReLU, FP16
+ * weights with FP32 accumulation (FP32 master copy, Adam).  Outputs:
+ * support logits over t = 0..d-1 and count logits over 0..a_m+1 aliases.
+ * Loss per row: count cross-entropy + mean support binary cross-entropy.
+ *
+ * Parameters are one FP32 vector, in order: W1 [n_in][128], b1 [128],
+ * W2 [128][128], b2 [128], W3 [128][n_out], b3 [n_out], n_out = n_sup +
+ * n_cls (support logits first).  Not thread-safe; calls that share an
+ * sft_mlp_t must not overlap on the GPU. */
+typedef struct sft_mlp_s* sft_mlp_t;
+typedef struct {
+  int32_t n_in;      /* 2 (2 a_max + n_cs_shifts), at most 48             */
+  int32_t n_hidden;  /* 128 (the only width built)                        */
+  int32_t n_sup;     /* support logits: d, at most 128                    */
+  int32_t n_cls;     /* count classes: a_max + 2                          */
+  uint64_t seed;     /* initial weights: He-uniform from SplitMix64(seed) */
+  float lr, beta1, beta2, eps;  /* Adam                                    */
+} sft_mlp_config;
+
+/* Dimensions matching a SFT_GENERAL parameter set (and the default Adam
+ * settings lr 2e-3, 0.9, 0.999, 1e-8).  SFT_EUNSUPPORTED when d > 128 or
+ * the feature count exceeds 48. */
+sft_status sft_mlp_config_for(const sft_params* p, sft_mlp_config* out);
+sft_status sft_mlp_create(const sft_mlp_config* c, sft_mlp_t* out);
+void sft_mlp_destroy(sft_mlp_t mlp);
+int64_t sft_mlp_param_count(sft_mlp_t mlp);
+/* Host copies of the FP32 parameters (layout above).  Setting them resets
+ * the Adam moments and step count. */
+sft_status sft_mlp_get_params(sft_mlp_t mlp, float* host_out);
+sft_status sft_mlp_set_params(sft_mlp_t mlp, const float* host_in);
+
+/* Features of the bins a SFT_GENERAL plan votes, for training data: runs
+ * the gather/FFT, singular-value and vote stages of sft_general on
+ * n_signals signals (x as for sft_general) and writes, for up to cap_rows
+ * voted bins, feat (device, [cap_rows][n_in] floats) and rows (device,
+ * [cap_rows][3] int32: signal, bin, a_k).  Row order is unspecified.
+ * Synchronises `stream`; *n_rows (host) receives the number of voted bins
+ * (rows beyond cap_rows are not written). */
+sft_status sft_mlp_features(sft_plan_t plan, int64_t n_signals, const void* x, int64_t x_stride,
+                            float* feat, int32_t* rows, int64_t cap_rows, int64_t* n_rows,
+                            void* stream);
+/* Logits of n_rows feature rows (device [n_rows][n_in] -> device
+ * [n_rows][n_out] floats).  Asynchronous. */
+sft_status sft_mlp_forward(sft_mlp_t mlp, const float* feat, int64_t n_rows, float* logits,
+                           void* stream);
+/* Mean loss and its gradient over n_rows labelled rows, without updating
+ * the parameters: feat (device [n_rows][n_in]), cls (device int32
+ * [n_rows], 0..n_cls-1), sup (device uint32 [n_rows][4], bit t of word
+ * t/32 set when t is in the bin's support); grad (device, param_count
+ * floats, overwritten), loss (device, one float, overwritten).
+ * Asynchronous. */
+sft_status sft_mlp_grad(sft_mlp_t mlp, const float* feat, const int32_t* cls, const uint32_t* sup,
+                        int64_t n_rows, float* grad, float* loss, void* stream);
+/* Trains in place with Adam for `epochs` passes over the rows in
+ * minibatches of `batch` (a fresh SplitMix64-driven shuffle per epoch from
+ * shuffle_seed); the forward and backward passes and the update run in
+ * this library's kernels.  loss_out (host, `epochs` floats, may be NULL)
+ * receives each epoch's mean loss.  Synchronises `stream`. */
+sft_status sft_mlp_train(sft_mlp_t mlp, const float* feat, const int32_t* cls, const uint32_t* sup,
+                         int64_t n_rows, int32_t epochs, int32_t batch, uint64_t shuffle_seed,
+                         float* loss_out, void* stream);
+/* Attach the network to a SFT_GENERAL plan (its dimensions must match the
+ * plan: n_in = 2 (2 a_max + n_cs_shifts), n_sup = d, n_cls = a_max + 2);
+ * sft_general on that plan then proposes and judges as described above.
+ * NULL detaches.  The plan does not own the network; keep it alive while
+ * attached. */
+sft_status sft_plan_attach_mlp(sft_plan_t plan, sft_mlp_t mlp);
 
 /* Number of kernel launches one sft_exact call of this plan issues. */
 int32_t sft_plan_launches_per_call(sft_plan_t plan);

@@ -12,6 +12,6 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 from . import sft  # noqa: E402
-from .sft import Plan, Result, SftError  # noqa: E402
+from .sft import Batch, Mlp, Plan, Result, SftError  # noqa: E402
 
-__all__ = ["build", "sft", "Plan", "Result", "SftError"]
+__all__ = ["build", "sft", "Batch", "Mlp", "Plan", "Result", "SftError"]

@@ -74,7 +74,7 @@ cudaError_t dalloc(T** ptr, size_t count, size_t* total) {
 
 void free_plan_memory(sft_plan_s* P) {
   void* ptrs[] = {P->tab.om_hi, P->tab.om_lo,    P->tab.tw,  P->tab.om_hi_ff, P->tab.om_lo_ff,
-                  P->tab.cs_shifts, P->ws_base, P->x_stage, P->r_stage};
+                  P->tab.cs_shifts, P->ws_base, P->x_stage, P->r_stage, P->mlp_prop};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }

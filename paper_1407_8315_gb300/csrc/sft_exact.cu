@@ -543,7 +543,8 @@ cudaError_t prepare_kernels(sft_plan_s* P) {
 }
 
 int launches_per_call(const sft_plan_s* P) {
-  if (P->p.mode == SFT_GENERAL) return 2 * (P->M0 > kFft4Points ? 2 : 1) + 3 + 1;
+  if (P->p.mode == SFT_GENERAL)
+    return 2 * (P->M0 > kFft4Points ? 2 : 1) + 3 + (P->mlp != nullptr ? 1 : 0) + 1;
   if (P->p.mode == SFT_EXACT_FIXED) return (P->M0 > kFft4Points ? 2 : 1) + 1 + P->p.a_max + 1;
   int fft = 0;
   for (int l = 0; l < P->levels; ++l) fft += (P->M0 >> l) > kFft4Points ? 2 : 1;

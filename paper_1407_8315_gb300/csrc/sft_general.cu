@@ -42,6 +42,7 @@ struct GenArgs {
   void* slot_p;
   int32_t* flags;
   OmegaTab om;
+  const int16_t* prop;  // learned proposal: 8 candidates t per queue entry, or null
 };
 
 // One-sided Jacobi on the n x n Hankel H_ij = m_{i+j}: rotate column pairs
@@ -362,11 +363,33 @@ __device__ int subspace_pursuit(int rows, int cols, const cdbl* phi, const cdbl*
   return nT;
 }
 
+// squared residual of a bin's solution {(s_u, p_u)} over all its equations:
+// the 2a_m consecutive syndromes and the r random-shift syndromes (Eq. (3))
+template <class F>
+__device__ double judge_res2(const GenArgs& g, const typename Store<F>::T* Y, int64_t k,
+                             const int64_t* s, const cdbl* p, int n) {
+  double acc = 0.0;
+  const int nsyn = 2 * g.a_max + g.r;
+  for (int l = 0; l < nsyn; ++l) {
+    const int64_t sh = l < 2 * g.a_max ? (int64_t)l : g.cs[l - 2 * g.a_max];
+    cdbl res = Store<F>::to_d(Y[(int64_t)l * g.M + k]);
+    for (int u = 0; u < n; ++u) res = res - p[u] * omega_pow(g.om, s[u] * sh);
+    acc += norm2(res);
+  }
+  return acc;
+}
+
 template <class F, int A>
-__device__ void solve_bin(const GenArgs& g, int b, int64_t k) {
+__device__ void solve_bin(const GenArgs& g, int b, int64_t k, int e) {
   typedef typename Store<F>::T T;
   const int64_t M = g.M, d = g.d;
   const T* Y = reinterpret_cast<const T*>(g.Y) + (int64_t)b * g.held_elems;
+  const int r = g.r;
+  cdbl y[16];
+  for (int j = 0; j < r; ++j) y[j] = Store<F>::to_d(Y[(2 * g.a_max + j) * M + k]);
+  int64_t s_out[8];
+  cdbl p_out[8];
+  int nout = 0;
   cdbl m[2 * A];
 #pragma unroll
   for (int j = 0; j < 2 * A; ++j) m[j] = Store<F>::to_d(Y[j * M + k]);
@@ -378,55 +401,91 @@ __device__ void solve_bin(const GenArgs& g, int b, int64_t k) {
     for (int j = 0; j < A; ++j) H[i * A + j] = m[i + j];
     rhs[i] = -m[A + i];
   }
-  if (!solve_small<A>(H, rhs, c)) return;
-  // (b)-(c): |P~(z)| at every z = omega^{k + tM} of U_k; keep the smallest
-  const int nk = (int)min((int64_t)min(g.keep * A, 8), d);
-  double bv[8];
-  int bt[8];
-  int have = 0;
-  for (int64_t t = 0; t < d; ++t) {
-    const cdbl z = omega_pow(g.om, k + t * M);
-    cdbl P = mk(1.0, 0.0);
+  if (solve_small<A>(H, rhs, c)) {
+    // (b)-(c): |P~(z)| at every z = omega^{k + tM} of U_k; keep the smallest
+    const int nk = (int)min((int64_t)min(g.keep * A, 8), d);
+    double bv[8];
+    int bt[8];
+    int have = 0;
+    for (int64_t t = 0; t < d; ++t) {
+      const cdbl z = omega_pow(g.om, k + t * M);
+      cdbl P = mk(1.0, 0.0);
 #pragma unroll
-    for (int j = A - 1; j >= 0; --j) P = P * z + c[j];
-    const double v = norm2(P);
-    if (have < nk || v < bv[nk - 1]) {
-      int pos = have < nk ? have : nk - 1;
-      while (pos > 0 && bv[pos - 1] > v) {  // stable: equal values keep lower t first
-        bv[pos] = bv[pos - 1];
-        bt[pos] = bt[pos - 1];
-        --pos;
+      for (int j = A - 1; j >= 0; --j) P = P * z + c[j];
+      const double v = norm2(P);
+      if (have < nk || v < bv[nk - 1]) {
+        int pos = have < nk ? have : nk - 1;
+        while (pos > 0 && bv[pos - 1] > v) {  // stable: equal values keep lower t first
+          bv[pos] = bv[pos - 1];
+          bt[pos] = bt[pos - 1];
+          --pos;
+        }
+        bv[pos] = v;
+        bt[pos] = (int)t;
+        if (have < nk) ++have;
       }
-      bv[pos] = v;
-      bt[pos] = (int)t;
-      if (have < nk) ++have;
+    }
+    // Step 3: kept candidates in ascending t; Phi_p[j][u] = omega^{(k + t_u M) n_j}
+    for (int i = 1; i < have; ++i)
+      for (int j = i; j > 0 && bt[j - 1] > bt[j]; --j) {
+        const int tt = bt[j];
+        bt[j] = bt[j - 1];
+        bt[j - 1] = tt;
+      }
+    cdbl phi[16 * 8];
+    for (int j = 0; j < r; ++j)
+      for (int u = 0; u < have; ++u)
+        phi[j * have + u] = omega_pow(g.om, (k + (int64_t)bt[u] * M) * g.cs[j]);
+    int Tsup[8];
+    cdbl xs[8];
+    const int nz = subspace_pursuit(r, have, phi, y, A, g.sp_iters, Tsup, xs);
+    for (int u = 0; u < nz; ++u) {
+      if (xs[u].x == 0.0 && xs[u].y == 0.0) continue;
+      s_out[nout] = k + (int64_t)bt[Tsup[u]] * M;
+      p_out[nout] = xs[u];
+      ++nout;
     }
   }
-  // Step 3: kept candidates in ascending t; Phi_p[j][u] = omega^{(k + t_u M) n_j}
-  for (int i = 1; i < have; ++i)
-    for (int j = i; j > 0 && bt[j - 1] > bt[j]; --j) {
-      const int tt = bt[j];
-      bt[j] = bt[j - 1];
-      bt[j - 1] = tt;
+  // learned proposal: Subspace Pursuit on the network's candidates, kept
+  // only when its residual over all equations is below (1 - 1e-6) times
+  // the plain solution's
+  if (g.prop != nullptr) {
+    const int16_t* pr = g.prop + (int64_t)e * 8;
+    int ct[8];
+    int nc = 0;
+    for (int u = 0; u < 8; ++u)
+      if (pr[u] >= 0) ct[nc++] = pr[u];
+    if (nc > 0) {
+      cdbl phi2[16 * 8];
+      for (int j = 0; j < r; ++j)
+        for (int u = 0; u < nc; ++u)
+          phi2[j * nc + u] = omega_pow(g.om, (k + (int64_t)ct[u] * M) * g.cs[j]);
+      int T2[8];
+      cdbl x2[8];
+      const int nz2 = subspace_pursuit(r, nc, phi2, y, A, g.sp_iters, T2, x2);
+      int64_t s2[8];
+      cdbl p2[8];
+      int n2 = 0;
+      for (int u = 0; u < nz2; ++u) {
+        if (x2[u].x == 0.0 && x2[u].y == 0.0) continue;
+        s2[n2] = k + (int64_t)ct[T2[u]] * M;
+        p2[n2] = x2[u];
+        ++n2;
+      }
+      if (n2 > 0) {
+        const double rp = judge_res2<F>(g, Y, k, s_out, p_out, nout);
+        const double rm = judge_res2<F>(g, Y, k, s2, p2, n2);
+        if (rm < (1.0 - 1e-6) * rp) {
+          for (int u = 0; u < n2; ++u) {
+            s_out[u] = s2[u];
+            p_out[u] = p2[u];
+          }
+          nout = n2;
+        }
+      }
     }
-  const int r = g.r;
-  cdbl phi[16 * 8], y[16];
-  for (int j = 0; j < r; ++j) {
-    y[j] = Store<F>::to_d(Y[(2 * g.a_max + j) * M + k]);
-    for (int u = 0; u < have; ++u) phi[j * have + u] = omega_pow(g.om, (k + (int64_t)bt[u] * M) * g.cs[j]);
   }
-  int Tsup[8];
-  cdbl xs[8];
-  const int nz = subspace_pursuit(r, have, phi, y, A, g.sp_iters, Tsup, xs);
-  int64_t s_out[8];
-  cdbl p_out[8];
-  int nout = 0;
-  for (int u = 0; u < nz; ++u) {
-    if (xs[u].x == 0.0 && xs[u].y == 0.0) continue;
-    s_out[nout] = k + (int64_t)bt[Tsup[u]] * M;
-    p_out[nout] = xs[u];
-    ++nout;
-  }
+  if (nout == 0) return;
   file_n<F>(nout, s_out, p_out, g.M, g.slot_cnt + (int64_t)b * g.M, g.slot_s + (int64_t)b * g.M * 4,
             reinterpret_cast<T*>(g.slot_p) + (int64_t)b * g.M * 4, g.flags + b);
 }
@@ -438,17 +497,19 @@ __global__ void __launch_bounds__(128) k_gen_solve(GenArgs g) {
     const int2 q = g.queue[e];
     const int a = g.ak[(int64_t)q.x * g.M + q.y];
     switch (a) {
-      case 1: solve_bin<F, 1>(g, q.x, q.y); break;
-      case 2: solve_bin<F, 2>(g, q.x, q.y); break;
-      case 3: solve_bin<F, 3>(g, q.x, q.y); break;
-      case 4: solve_bin<F, 4>(g, q.x, q.y); break;
+      case 1: solve_bin<F, 1>(g, q.x, q.y, e); break;
+      case 2: solve_bin<F, 2>(g, q.x, q.y, e); break;
+      case 3: solve_bin<F, 3>(g, q.x, q.y, e); break;
+      case 4: solve_bin<F, 4>(g, q.x, q.y, e); break;
       default: break;
     }
   }
 }
 
+// Part 1 and Part 2 (gather/FFT of every shift, singular values, vote);
+// returns the arguments of the later stages
 template <class F>
-static void launch_general_t(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int nsm,
+static GenArgs general_front(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride,
                              cudaStream_t st) {
   const Workspace& W = P->ws;
   const int am = P->p.a_max, r = P->p.n_cs_shifts;
@@ -459,7 +520,8 @@ static void launch_general_t(sft_plan_s* P, int64_t B, const void* x, int64_t x_
                         false, st, P->tab.cs_shifts, "gather_fft_random");
   GenArgs g{P->p.N, P->M0, P->p.d, P->p.K, am, r, 2, 8, W.held[0], W.held_elems, W.sv, W.T[0],
             W.queue[0], W.qcount, P->tab.cs_shifts, P->K_table, W.slot_cnt, W.slot_s, W.slot_p,
-            W.flags, OmegaTab{P->tab.om_hi, P->tab.om_lo, P->tab.om_lo_bits, P->p.N - 1}};
+            W.flags, OmegaTab{P->tab.om_hi, P->tab.om_lo, P->tab.om_lo_bits, P->p.N - 1},
+            nullptr};
   dim3 sgrid((unsigned)((P->M0 + 255) / 256), (unsigned)B);
   stage_begin(P, "gen_svals", st);
   switch (am) {
@@ -472,6 +534,12 @@ static void launch_general_t(sft_plan_s* P, int64_t B, const void* x, int64_t x_
   stage_begin(P, "gen_vote", st);
   k_gen_vote<<<(unsigned)B, 1024, 0, st>>>(g);
   stage_end(P, st);
+  return g;
+}
+
+// Parts 3-4: pruning and Subspace Pursuit per voted bin
+template <class F>
+static void general_solve(sft_plan_s* P, int64_t B, int nsm, cudaStream_t st, const GenArgs& g) {
   const int64_t maxq =
       B * (P->K_table != nullptr ? P->M0 : std::min<int64_t>(P->M0, std::max<int64_t>(P->p.K, 1)));
   const unsigned dgrid =
@@ -481,12 +549,32 @@ static void launch_general_t(sft_plan_s* P, int64_t B, const void* x, int64_t x_
   stage_end(P, st);
 }
 
+template <class F>
+static void launch_general_t(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int nsm,
+                             cudaStream_t st) {
+  GenArgs g = general_front<F>(P, B, x, x_stride, st);
+  if (P->mlp != nullptr && P->mlp_prop != nullptr) {
+    mlp_propose(P, B, nsm, st);
+    g.prop = P->mlp_prop;
+  }
+  general_solve<F>(P, B, nsm, st, g);
+}
+
 void launch_general(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int nsm,
                     cudaStream_t st) {
   if (P->p.precision == SFT_FP64)
     launch_general_t<F64>(P, B, x, x_stride, nsm, st);
   else
     launch_general_t<FF>(P, B, x, x_stride, nsm, st);
+}
+
+void launch_general_features(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int nsm,
+                             float* feat, int32_t* rows, int64_t cap_rows, cudaStream_t st) {
+  if (P->p.precision == SFT_FP64)
+    general_front<F64>(P, B, x, x_stride, st);
+  else
+    general_front<FF>(P, B, x, x_stride, st);
+  mlp_features(P, B, nsm, feat, rows, cap_rows, st);
 }
 
 }  // namespace sft

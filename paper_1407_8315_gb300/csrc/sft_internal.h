@@ -142,6 +142,10 @@ struct sft_plan_s {
   const int64_t* K_table = nullptr;  // per-signal K for the general vote
   // launch shape chosen by the batch autotuner
   int dec_ctas_per_sm = 8;
+  // learned proposal (general plans): the attached network (not owned) and
+  // 8 proposed candidates t per queued bin (int16, -1 = none)
+  struct sft_mlp_s* mlp = nullptr;
+  int16_t* mlp_prop = nullptr;
   // profiling
   bool profiling = false;
   std::vector<sft::StageRec> stage_recs;   // records since the last read
@@ -163,9 +167,20 @@ void launch_gather_fft_any(sft_plan_s* P, int64_t B, const void* x, int64_t x_st
                            int log2M, int shift0, int nshift, void* out, int64_t out_row, int row0,
                            bool want_ymax, cudaStream_t st, const int64_t* shift_list,
                            const char* stage);
-// The general path (Algorithm 2) of one call, before k_finalize.
+// The general path (Algorithm 2) of one call, before k_finalize (with the
+// learned proposal when a network is attached).
 void launch_general(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int nsm,
                     cudaStream_t st);
+// The general path up to the vote, then the features of every voted bin
+// (training data for the learned proposal).
+void launch_general_features(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int nsm,
+                             float* feat, int32_t* rows, int64_t cap_rows, cudaStream_t st);
+// Learned proposal kernels (sft_mlp.cu): features + forward + the 2 a_k
+// largest support logits of every queued voted bin into P->mlp_prop; and
+// the features alone, written out.
+void mlp_propose(sft_plan_s* P, int64_t B, int nsm, cudaStream_t st);
+void mlp_features(sft_plan_s* P, int64_t B, int nsm, float* feat, int32_t* rows, int64_t cap_rows,
+                  cudaStream_t st);
 // Sets the calling thread's error detail returned by sft_last_cuda_error.
 void set_error_detail(const char* msg);
 // Defaults of zero fields (as sft_plan_create applies them) and validation.

@@ -32,6 +32,12 @@ class sft_params(C.Structure):
                 ("zero_tol", C.c_double), ("root_tol", C.c_double), ("res_tol", C.c_double)]
 
 
+class sft_mlp_config(C.Structure):
+    _fields_ = [("n_in", C.c_int32), ("n_hidden", C.c_int32), ("n_sup", C.c_int32),
+                ("n_cls", C.c_int32), ("seed", C.c_uint64), ("lr", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
+
+
 class sft_result(C.Structure):
     _fields_ = [("cap", C.c_int64), ("idx", C.c_void_p), ("val", C.c_void_p),
                 ("count", C.c_void_p), ("unresolved", C.c_void_p), ("overflow", C.c_void_p)]
@@ -42,7 +48,9 @@ EXPORTS = ["sft_params_default", "sft_plan_create", "sft_plan_destroy", "sft_pla
            "sft_last_cuda_error", "sft_plan_set_profiling", "sft_plan_stage_times",
            "sft_exact_noalloc", "sft_general", "sft_general_host", "sft_plan_cs_shifts",
            "sft_batch_create", "sft_batch_destroy", "sft_batch_set_options", "sft_batch",
-           "sft_batch_info"]
+           "sft_batch_info", "sft_mlp_config_for", "sft_mlp_create", "sft_mlp_destroy",
+           "sft_mlp_param_count", "sft_mlp_get_params", "sft_mlp_set_params", "sft_mlp_features",
+           "sft_mlp_forward", "sft_mlp_grad", "sft_mlp_train", "sft_plan_attach_mlp"]
 
 _lib = None
 
@@ -105,6 +113,22 @@ def load(build_if_missing: bool = False):
                               C.c_void_p]
     lib.sft_batch_info.argtypes = [C.c_void_p, P(C.c_int32), P(C.c_int64), P(C.c_int32)]
     lib.sft_batch_info.restype = C.c_int32
+    lib.sft_mlp_config_for.argtypes = [P(sft_params), P(sft_mlp_config)]
+    lib.sft_mlp_create.argtypes = [P(sft_mlp_config), P(C.c_void_p)]
+    lib.sft_mlp_destroy.argtypes = [C.c_void_p]
+    lib.sft_mlp_destroy.restype = None
+    lib.sft_mlp_param_count.argtypes = [C.c_void_p]
+    lib.sft_mlp_param_count.restype = C.c_int64
+    lib.sft_mlp_get_params.argtypes = [C.c_void_p, C.c_void_p]
+    lib.sft_mlp_set_params.argtypes = [C.c_void_p, C.c_void_p]
+    lib.sft_mlp_features.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                                     C.c_void_p, C.c_int64, P(C.c_int64), C.c_void_p]
+    lib.sft_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+    lib.sft_mlp_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                 C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.sft_mlp_train.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                  C.c_int32, C.c_int32, C.c_uint64, C.c_void_p, C.c_void_p]
+    lib.sft_plan_attach_mlp.argtypes = [C.c_void_p, C.c_void_p]
     lib.sft_strerror.argtypes = [C.c_int]
     lib.sft_strerror.restype = C.c_char_p
     lib.sft_last_cuda_error.argtypes = []
@@ -322,6 +346,13 @@ class Plan:
     def set_profiling(self, enable: bool = True):
         sft_plan_set_profiling(self.handle, enable)
 
+    def attach_mlp(self, mlp):
+        """Attach a learned proposal (Mlp) to this SFT_GENERAL plan; None detaches."""
+        _check(load().sft_plan_attach_mlp(C.c_void_p(self.handle),
+                                          C.c_void_p(mlp.handle if mlp is not None else None)),
+               "sft_plan_attach_mlp")
+        self._mlp = mlp
+
     def stage_times(self) -> dict:
         return sft_plan_stage_times(self.handle)
 
@@ -394,6 +425,118 @@ class Batch:
     def close(self):
         if self.handle:
             load().sft_batch_destroy(C.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------- learned proposal
+def support_bits(supports, d: int) -> np.ndarray:
+    """Support labels as the C ABI takes them: uint32 [rows][4], bit t of
+    word t // 32 set for every t in the row's support (t < d <= 128)."""
+    out = np.zeros((len(supports), 4), np.uint32)
+    for i, ts in enumerate(supports):
+        for t in ts:
+            if not 0 <= t < d:
+                raise ValueError("support index outside [0, d)")
+            out[i, t >> 5] |= np.uint32(1) << np.uint32(t & 31)
+    return out
+
+
+class Mlp:
+    """The learned support proposal (sft_mlp_*): a network sized for a
+    SFT_GENERAL plan's (a_max, n_cs_shifts, d)."""
+
+    def __init__(self, plan: "Plan" = None, seed: int = 0, lr: float = 0.0, config=None):
+        cfg = sft_mlp_config()
+        if config is not None:
+            cfg = config
+        else:
+            _check(load().sft_mlp_config_for(C.byref(plan.params), C.byref(cfg)),
+                   "sft_mlp_config_for")
+            cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+            if lr:
+                cfg.lr = float(lr)
+        self.config = cfg
+        self.n_in, self.n_sup, self.n_cls = cfg.n_in, cfg.n_sup, cfg.n_cls
+        self.n_out = cfg.n_sup + cfg.n_cls
+        h = C.c_void_p()
+        _check(load().sft_mlp_create(C.byref(cfg), C.byref(h)), "sft_mlp_create")
+        self.handle = h.value
+
+    @property
+    def param_count(self) -> int:
+        return int(load().sft_mlp_param_count(C.c_void_p(self.handle)))
+
+    @property
+    def params(self) -> np.ndarray:
+        out = np.empty(self.param_count, np.float32)
+        _check(load().sft_mlp_get_params(C.c_void_p(self.handle), out.ctypes.data),
+               "sft_mlp_get_params")
+        return out
+
+    @params.setter
+    def params(self, v):
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        if v.size != self.param_count:
+            raise ValueError("wrong parameter count")
+        _check(load().sft_mlp_set_params(C.c_void_p(self.handle), v.ctypes.data),
+               "sft_mlp_set_params")
+
+    def features(self, plan: "Plan", x, cap_rows: int):
+        """Features of the bins the plan votes on x [B, N] (CUDA tensor):
+        (feat [rows, n_in] float32, rows [rows, 3] int32: signal, bin, a_k)."""
+        import torch
+        if x.dim() == 1:
+            x = x.unsqueeze(0)
+        B = x.shape[0]
+        feat = torch.empty((cap_rows, self.n_in), dtype=torch.float32, device=x.device)
+        rows = torch.empty((cap_rows, 3), dtype=torch.int32, device=x.device)
+        n = C.c_int64()
+        pitch = x.stride(0) if B > 1 else x.shape[1]
+        _check(load().sft_mlp_features(C.c_void_p(plan.handle), B, C.c_void_p(x.data_ptr()), pitch,
+                                       C.c_void_p(feat.data_ptr()), C.c_void_p(rows.data_ptr()),
+                                       cap_rows, C.byref(n), C.c_void_p(_stream_ptr(None))),
+               "sft_mlp_features")
+        k = min(int(n.value), cap_rows)
+        return feat[:k], rows[:k], int(n.value)
+
+    def forward(self, feat):
+        import torch
+        logits = torch.empty((feat.shape[0], self.n_out), dtype=torch.float32, device=feat.device)
+        _check(load().sft_mlp_forward(C.c_void_p(self.handle), C.c_void_p(feat.data_ptr()),
+                                      feat.shape[0], C.c_void_p(logits.data_ptr()),
+                                      C.c_void_p(_stream_ptr(None))), "sft_mlp_forward")
+        return logits
+
+    def grad(self, feat, cls, sup):
+        """(gradient [param_count] float32 tensor, mean loss tensor [1])."""
+        import torch
+        g = torch.empty(self.param_count, dtype=torch.float32, device=feat.device)
+        loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+        _check(load().sft_mlp_grad(C.c_void_p(self.handle), C.c_void_p(feat.data_ptr()),
+                                   C.c_void_p(cls.data_ptr()), C.c_void_p(sup.data_ptr()),
+                                   feat.shape[0], C.c_void_p(g.data_ptr()),
+                                   C.c_void_p(loss.data_ptr()), C.c_void_p(_stream_ptr(None))),
+               "sft_mlp_grad")
+        return g, loss
+
+    def train(self, feat, cls, sup, epochs: int, batch: int = 4096, seed: int = 0) -> np.ndarray:
+        losses = np.zeros(epochs, np.float32)
+        _check(load().sft_mlp_train(C.c_void_p(self.handle), C.c_void_p(feat.data_ptr()),
+                                    C.c_void_p(cls.data_ptr()), C.c_void_p(sup.data_ptr()),
+                                    feat.shape[0], int(epochs), int(batch),
+                                    int(seed) & 0xFFFFFFFFFFFFFFFF, losses.ctypes.data,
+                                    C.c_void_p(_stream_ptr(None))), "sft_mlp_train")
+        return losses
+
+    def close(self):
+        if self.handle:
+            load().sft_mlp_destroy(C.c_void_p(self.handle))
             self.handle = None
 
     def __del__(self):

@@ -93,3 +93,29 @@ def test_null_arguments(lib):
     assert lib.sft_params_default(None, 8, 1, 1, 0, 0) == 1
     assert lib.sft_exact(None, 1, None, 0, None, None) == 1
     assert lib.sft_plan_workspace_bytes(None) == 0
+
+
+def test_mlp_config_and_create_validation(lib):
+    """The learned proposal's dimensions follow the general plan; bad shapes
+    are rejected before any device memory is touched."""
+    import ctypes as C
+    from paper_1407_8315_gb300 import sft
+    c = sft.sft_mlp_config()
+    p = sft.sft_params_default(1 << 20, 1024, 32, "general", "mixed")
+    assert lib.sft_mlp_config_for(C.byref(p), C.byref(c)) == sft.SFT_OK
+    assert (c.n_in, c.n_hidden, c.n_sup, c.n_cls) == (30, 128, 32, 5)
+    p.a_max, p.n_cs_shifts = 4, 12
+    assert lib.sft_mlp_config_for(C.byref(p), C.byref(c)) == sft.SFT_OK
+    assert (c.n_in, c.n_cls) == (40, 6)
+    big = sft.sft_params_default(1 << 27, 1 << 16, 512, "general", "mixed")
+    assert lib.sft_mlp_config_for(C.byref(big), C.byref(c)) == sft.SFT_EUNSUPPORTED
+    ex = sft.sft_params_default(1 << 16, 64, 256, "iter", "mixed")
+    assert lib.sft_mlp_config_for(C.byref(ex), C.byref(c)) == sft.SFT_EINVAL
+    h = C.c_void_p()
+    bad = sft.sft_mlp_config(30, 64, 32, 5, 0, 1e-3, 0.9, 0.999, 1e-8)
+    assert lib.sft_mlp_create(C.byref(bad), C.byref(h)) == sft.SFT_EUNSUPPORTED
+    bad = sft.sft_mlp_config(30, 128, 200, 5, 0, 1e-3, 0.9, 0.999, 1e-8)
+    assert lib.sft_mlp_create(C.byref(bad), C.byref(h)) == sft.SFT_EINVAL
+    bad = sft.sft_mlp_config(30, 128, 32, 5, 0, -1.0, 0.9, 0.999, 1e-8)
+    assert lib.sft_mlp_create(C.byref(bad), C.byref(h)) == sft.SFT_EINVAL
+    assert lib.sft_plan_attach_mlp(None, None) == sft.SFT_EINVAL
