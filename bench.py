@@ -62,7 +62,7 @@ class W:
     """A single-shape workload: B signals of one (N, K, M, mode, precision)."""
 
     def __init__(self, name, metric, desc, N, K, M, mode, precision, batch, a_max,
-                 snrs=None, r=0, plan_seed=0, c64_input=False):
+                 snrs=None, r=0, plan_seed=0, c64_input=False, mlp_rows=0, mlp_snrs=None):
         self.name, self.metric, self.desc = name, metric, desc
         self.N, self.K, self.M, self.d = N, K, M, N // M
         self.mode, self.precision, self.batch, self.a_max = mode, precision, batch, a_max
@@ -75,6 +75,9 @@ class W:
         # form) and upcast, and the plan keeps the mixed form's tolerances,
         # so that both forms see one input and recover the same set
         self.c64_input = c64_input
+        # learned proposal: train on about mlp_rows voted bins of fresh
+        # signals at mlp_snrs, then attach it for the timed steps
+        self.mlp_rows, self.mlp_snrs = mlp_rows, mlp_snrs
 
     def snr_of(self, b):
         return self.snrs[b % len(self.snrs)] if self.snrs else None
@@ -134,6 +137,19 @@ WORKLOADS = {
                       "general N=2^20 K=1024 d=32 (M=2^15) a_m=3 r=9 c64 SNR 20/30/40 dB",
                       1 << 20, 1024, 1 << 15, "general", "mixed", 150, 3, snrs=(20, 30, 40),
                       plan_seed=2024),
+    "general-2^20-mlp": W("general-2^20-mlp",
+                          "SFT signals/sec at N=2^20,K=1024 noisy, learned proposal; SNR_out",
+                          "general N=2^20 K=1024 d=32 (M=2^15) a_m=3 r=9 c64 SNR 20/30/40 dB, "
+                          "learned proposal trained on ~10^6 voted bins (10-40 dB)",
+                          1 << 20, 1024, 1 << 15, "general", "mixed", 150, 3, snrs=(20, 30, 40),
+                          plan_seed=2024, mlp_rows=1_000_000, mlp_snrs=(10, 20, 30, 40)),
+    "general-2^18-d128-mlp": W("general-2^18-d128-mlp",
+                               "SFT signals/sec at N=2^18,K=64 d=128 noisy, learned proposal; "
+                               "SNR_out",
+                               "general N=2^18 K=64 d=128 (M=2^11, N/K=2^12) a_m=3 r=9 c64 SNR "
+                               "10/20/30 dB, learned proposal trained on ~1.5*10^5 voted bins",
+                               1 << 18, 64, 1 << 11, "general", "mixed", 150, 3, snrs=(10, 20, 30),
+                               plan_seed=11, mlp_rows=150_000, mlp_snrs=(10, 15, 20, 30)),
     "exact-2^27": W("exact-2^27", "SFT signals/sec at N=2^27,K=2^16 (exact)",
                     "exact-iter N=2^27 K=2^16 d=512 (M=2^18) a_m=4 c64",
                     1 << 27, 1 << 16, 1 << 18, "iter", "mixed", 2, 4),
@@ -452,6 +468,58 @@ def oracle_errors(res, get_gpu):
     return {"max_rel_err": worst, "support_mismatch_signals": mism, "sample_signals": len(res)}
 
 
+# ------------------------------------------------------- learned proposal
+def train_proposal(torch, S, plan, wl, B):
+    """Train the learned proposal for `plan` on fresh seeded signals: the
+    GPU path computes the features of every voted bin, labels come from the
+    planted spectra, the library's kernels train.  Returns (net, record)."""
+    from paper_1407_8315_gb300 import Mlp
+    t0 = time.perf_counter()
+    net = Mlp(plan, seed=7)
+    feats, cls, sup_words = [], [], []
+    rows_done, chunk, seed0 = 0, 0, 50_000_000
+    snrs = wl.mlp_snrs
+    while rows_done < wl.mlp_rows:
+        seeds = [seed0 + chunk * B + i for i in range(B)]
+        out = [None] * B
+
+        def one(i):
+            x, s, _, _ = siggen.noisy_signal(wl.N, wl.K, seeds[i], snrs[i % len(snrs)], mag=(1, 10))
+            out[i] = (x, s)
+
+        with ThreadPoolExecutor(max_workers=host_threads()) as ex:
+            list(ex.map(one, range(B)))
+        x = torch.from_numpy(np.stack([o[0] for o in out])).cuda()
+        f, rows, _ = net.features(plan, x, B * wl.M)
+        rows = rows.cpu().numpy()
+        # labels: per signal, bin -> aliases t of the planted support
+        lab = []
+        for b in range(B):
+            s = out[b][1]
+            lab.append({})
+            for k, t in zip((s % wl.M).tolist(), (s // wl.M).tolist()):
+                lab[b].setdefault(k, []).append(t)
+        ts = [lab[b].get(k, []) for b, k in zip(rows[:, 0].tolist(), rows[:, 1].tolist())]
+        cls.append(np.array([min(len(t), wl.a_max + 1) for t in ts], np.int32))
+        sup_words.append(S.support_bits(ts, wl.d))
+        feats.append(f)
+        rows_done += f.shape[0]
+        chunk += 1
+    F = torch.cat(feats)
+    t1 = time.perf_counter()
+    epochs = 8 if F.shape[0] > 500_000 else 25
+    losses = net.train(F, torch.from_numpy(np.concatenate(cls)).cuda(),
+                       torch.from_numpy(np.concatenate(sup_words)).cuda(), epochs=epochs,
+                       batch=4096 if F.shape[0] > 500_000 else 1024, seed=3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    rec = {"train_rows": int(F.shape[0]), "train_signals": chunk * B, "epochs": epochs,
+           "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1]),
+           "data_seconds": round(t1 - t0, 2), "train_seconds_gpu": round(t2 - t1, 2),
+           "train_snrs_db": list(snrs)}
+    return net, rec
+
+
 # ------------------------------------------------------------------ our arm
 def run_plan_workload(args, wl):
     import torch
@@ -480,6 +548,10 @@ def run_plan_workload(args, wl):
     fn = plan.general if wl.general else plan.exact
     fn_host = plan.general_host if wl.general else plan.exact_host
     cap = wl.cap
+    mlp_rec = None
+    if wl.mlp_rows:
+        net, mlp_rec = train_proposal(torch, S, plan, wl, B)
+        plan.attach_mlp(net)
     out = fn(x_dev, cap)
     stream = torch.cuda.current_stream()
     flush = l2_flusher(torch)
@@ -510,6 +582,25 @@ def run_plan_workload(args, wl):
     idx = out.idx.cpu().numpy()
     val = out.val.cpu().numpy()
     quality = {}
+    if mlp_rec is not None:
+        # the same signals without the network: rate and SNR_out
+        plan.attach_mlp(None)
+        out_p = fn(x_dev, cap)
+        for _ in range(3):
+            fn(x_dev, cap, out_p)
+        ms_p = timed_steps(torch, lambda: fn(x_dev, cap, out_p), max(3, args.steps // 4), flush,
+                           stream)
+        pc, pi, pv = out_p.count.cpu().numpy(), out_p.idx.cpu().numpy(), out_p.val.cpu().numpy()
+        plan.attach_mlp(net)
+        per_p, per_m = {}, {}
+        for b in range(min(B, 30)):
+            per_p.setdefault(wl.snr_of(b), []).append(snr_out(x_np[b], pi[b, :pc[b]], pv[b, :pc[b]]))
+            per_m.setdefault(wl.snr_of(b), []).append(snr_out(x_np[b], idx[b, :cnt[b]], val[b, :cnt[b]]))
+        mlp_rec["plain_value"] = B * max(3, args.steps // 4) / (ms_p / 1e3)
+        mlp_rec["snr_out_db_plain"] = {str(k): float(np.mean(v)) for k, v in sorted(per_p.items())}
+        mlp_rec["snr_out_db_mlp"] = {str(k): float(np.mean(v)) for k, v in sorted(per_m.items())}
+        mlp_rec["snr_sample_signals"] = min(B, 30)
+        quality["learned_proposal"] = mlp_rec
     if wl.general:
         per = {}
         for b in range(min(B, 24)):
@@ -561,6 +652,10 @@ def run_plan_workload(args, wl):
 
     # ---- CPU baseline (the oracle on the host cores) and error vs the oracle
     cpu, err = None, {"max_rel_err": None, "support_mismatch_signals": None, "sample_signals": 0}
+    if mlp_rec is not None:
+        err["note"] = ("the judged path runs GPU-trained weights; its parity with the FP64 "
+                       "reference is tested with CPU-trained weights (tests/test_gpu_mlp.py); "
+                       "cpu_baseline times the oracle's plain Algorithm 2")
     if not args.no_cpu:
         import oracle
         oracle.build()
@@ -572,7 +667,8 @@ def run_plan_workload(args, wl):
         cpu = {"value": rate, "unit": "signals/s", "cores": cores, "kind": "oracle",
                "sample": f"{done} transforms of this step's {B} signals ({len(res)} distinct), "
                          f"one signal per thread, {cores} threads, {el:.1f} s"}
-        err = oracle_errors(res, lambda b: (idx[b, :cnt[b]], val[b, :cnt[b]]))
+        if mlp_rec is None:
+            err = oracle_errors(res, lambda b: (idx[b, :cnt[b]], val[b, :cnt[b]]))
 
     line = {
         "metric": wl.metric, "value": value, "unit": "signals/s", "n_gpus": ws,

@@ -326,7 +326,25 @@ sft_status sft_mlp_train(sft_mlp_t mlp, const float* feat, const int32_t* cls, c
  * attached. */
 sft_status sft_plan_attach_mlp(sft_plan_t plan, sft_mlp_t mlp);
 
-/* Number of kernel launches one sft_exact call of this plan issues. */
+/* Unknown K (Sec. II-E, the bottom-up strategy): each signal is transformed
+ * with d = N / M_start, then with d halved (M doubled) while its run leaves
+ * a bin unsolved or a level-0 bin overflowed, up to M_max (0: N).
+ *   p        N, a_max, mode (SFT_EXACT_ITER or SFT_EXACT_FIXED), precision,
+ *            tolerances; K, d and max_iters are ignored (ITER runs
+ *            min(a_max, log2(M) + 1) levels at each M)
+ *   x        device, n_signals rows of N complex values, row pitch x_stride
+ *   r        device result arrays laid out as for sft_exact (cap per
+ *            signal); each signal's row holds its last run
+ *   m_out    host, n_signals entries (may be NULL): the M each signal
+ *            stopped at (its last M when it never solved every bin)
+ * Creates and destroys one plan per M tried (synchronous; allocates).
+ * SFT_EINVAL on bad arguments, SFT_EUNSUPPORTED when M_max > 2^26. */
+sft_status sft_exact_auto(const sft_params* p, int64_t n_signals, const void* x, int64_t x_stride,
+                          int64_t M_start, int64_t M_max, const sft_result* r, int64_t* m_out,
+                          void* stream);
+
+/* Number of kernel launches one call of this plan on max_signals signals
+ * issues (sft_exact / sft_general). */
 int32_t sft_plan_launches_per_call(sft_plan_t plan);
 
 /* Per-stage timing.  With profiling enabled, every launch of an sft_exact

@@ -173,6 +173,27 @@ def exact(x, M0: int, a_max: int = 4, mode: int = ITER, max_iters: int | None = 
     return idx[:n].copy(), val[:n].copy(), int(unres.value)
 
 
+def exact_auto(x, a_max: int = 4, mode: int = ITER, M_start: int = 1, M_max: int | None = None,
+               zero_tol: float | None = None, root_tol: float | None = None,
+               res_tol: float | None = None):
+    """Unknown K (Sec. II-E, the bottom-up strategy): run the exact transform
+    with d = N / M_start and halve d (double M) until a run leaves no bin
+    unsolved, or M reaches M_max (default N).  ITER runs
+    min(a_max, log2(M) + 1) levels.  Returns (idx, val, unresolved, M) of the
+    last run."""
+    x = np.asarray(x)
+    N = x.size
+    M_max = N if M_max is None else int(M_max)
+    M = int(M_start)
+    while True:
+        iters = min(int(a_max), int(np.log2(M)) + 1) if mode == ITER else int(a_max)
+        idx, val, un = exact(x, M, a_max, mode, max_iters=iters, zero_tol=zero_tol,
+                             root_tol=root_tol, res_tol=res_tol, cap=4 * M * int(a_max))
+        if un == 0 or M >= M_max:
+            return idx, val, un, M
+        M *= 2
+
+
 # --------------------------------------------- generally K-sparse (Alg. 2)
 def splitmix64(seed: int, i: int) -> int:
     """Output i of the SplitMix64 stream of `seed`."""

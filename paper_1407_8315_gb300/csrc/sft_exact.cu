@@ -14,7 +14,8 @@
 //   FIXED: k_gather_fft for the 2 a_max shifts at d0, k_fixed_scan (queue
 //          the active bins), k_fixed_round for a = 1 .. a_max (the bins no
 //          smaller a decoded).
-//   k_finalize       compacts the recovered frequencies into the result.
+//   k_fin_count,     compact the recovered frequencies into the result in
+//   k_finalize       two tiled passes (tile sums, then offsets + writes).
 //
 // Two arithmetic flavours F (sft_common.cuh): F64 everywhere on the plain
 // path; on the mixed path (FF) the FFT, the folds, the peels and the
@@ -434,7 +435,14 @@ struct FinArgs {
   int32_t* unresolved;
   int32_t* overflow;
   const sft_result* r_table;  // per-signal result buffers (heterogeneous batches)
+  int* tile_sum;              // [B][n_tiles]: entries filed in each tile of bins
+  int* tile_un;               // [B][n_tiles]: unresolved bins of the last level per tile
+  int n_tiles;
+  int64_t tile_bins;          // bins per tile (kFinTile, or M0 for one tile per signal)
 };
+
+// bins per finalize tile (1024 threads x 4 bins)
+constexpr int kFinTile = 4096;
 
 // Block-wide exclusive scan of one int per thread (blockDim = 1024).
 __device__ __forceinline__ int block_excl_scan(int v, int* total) {
@@ -464,20 +472,65 @@ __device__ __forceinline__ int block_excl_scan(int v, int* total) {
   return before;
 }
 
+// Finalize pass 1: per tile of kFinTile level-0 bins, the number of filed
+// frequencies and of unresolved bins of the last level (coalesced reads).
+__global__ void __launch_bounds__(256) k_fin_count(FinArgs g) {
+  const int b = blockIdx.y, tile = blockIdx.x, tid = threadIdx.x;
+  const int64_t k_lo = (int64_t)tile * g.tile_bins;
+  const uint8_t* cnt = g.slot_cnt + (int64_t)b * g.M0;
+  const uint8_t* T_ = g.T_last + (int64_t)b * g.M0;
+  int c = 0, u = 0;
+  for (int64_t k = k_lo + tid; k < min(k_lo + g.tile_bins, g.M0); k += 256) {
+    c += cnt[k];
+    if (k < g.M_last) u += T_[k];
+  }
+  __shared__ int sc[8], su[8];
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    u += __shfl_xor_sync(0xffffffffu, u, o);
+  }
+  if ((tid & 31) == 0) {
+    sc[tid >> 5] = c;
+    su[tid >> 5] = u;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int tc = 0, tu = 0;
+    for (int w = 0; w < 8; ++w) {
+      tc += sc[w];
+      tu += su[w];
+    }
+    g.tile_sum[(int64_t)b * g.n_tiles + tile] = tc;
+    g.tile_un[(int64_t)b * g.n_tiles + tile] = tu;
+  }
+}
+
+// Finalize pass 2: each tile's entries go to its offset (sum of the earlier
+// tiles) plus the block scan of its bins, in bin order; tile 0 writes the
+// counters.
 template <class F>
 __global__ void __launch_bounds__(1024) k_finalize(FinArgs g) {
   typedef typename Store<F>::T T;
-  const int b = blockIdx.x;
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int b = blockIdx.y, tile = blockIdx.x;
+  const int tid = threadIdx.x;
   const int64_t M0 = g.M0;
   const uint8_t* cnt = g.slot_cnt + (int64_t)b * M0;
   const T* sp = reinterpret_cast<const T*>(g.slot_p);
-  const int64_t chunk = (M0 + nthr - 1) / nthr;
-  const int64_t lo = min((int64_t)tid * chunk, M0), hi = min(lo + chunk, M0);
+  __shared__ int s_base;
+  if (tid < 32) {
+    int acc = 0;
+    for (int j = tid; j < tile; j += 32) acc += g.tile_sum[(int64_t)b * g.n_tiles + j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (tid == 0) s_base = acc;
+  }
+  const int64_t per = (g.tile_bins + blockDim.x - 1) / blockDim.x;
+  const int64_t t_hi = min((int64_t)(tile + 1) * g.tile_bins, M0);
+  const int64_t lo = min((int64_t)tile * g.tile_bins + per * tid, t_hi), hi = min(lo + per, t_hi);
   int mine = 0;
   for (int64_t k0 = lo; k0 < hi; ++k0) mine += cnt[k0];
-  int total = 0;
-  int pos = block_excl_scan(mine, &total);
+  int total_tile = 0;
+  int pos = block_excl_scan(mine, &total_tile);  // synchronises: s_base visible
+  pos += s_base;
   int64_t cap = g.cap;
   int64_t* idx = g.idx + (int64_t)b * g.cap;
   double2* val = g.val + (int64_t)b * g.cap;
@@ -503,15 +556,26 @@ __global__ void __launch_bounds__(1024) k_finalize(FinArgs g) {
       }
     }
   }
-  // unresolved bins at the last level
-  int un = 0;
-  const uint8_t* T_ = g.T_last + (int64_t)b * M0;
-  for (int64_t k = tid; k < g.M_last; k += nthr) un += T_[k];
-  int un_total = 0;
-  (void)block_excl_scan(un, &un_total);
-  if (tid == 0) {
+  if (g.n_tiles == 1) {
+    // one tile per signal (no count pass): the unresolved bins here
+    int un = 0;
+    const uint8_t* T_ = g.T_last + (int64_t)b * M0;
+    for (int64_t k = tid; k < g.M_last; k += blockDim.x) un += T_[k];
+    int un_total = 0;
+    (void)block_excl_scan(un, &un_total);
+    if (tid == 0) {
+      *count = total_tile < cap ? total_tile : cap;
+      *unresolved = un_total;
+      *overflow = (total_tile > cap || (g.flags[b] & 1)) ? 1 : 0;
+    }
+  } else if (tile == 0 && tid == 0) {
+    int64_t total = 0, un = 0;
+    for (int j = 0; j < g.n_tiles; ++j) {
+      total += g.tile_sum[(int64_t)b * g.n_tiles + j];
+      un += g.tile_un[(int64_t)b * g.n_tiles + j];
+    }
     *count = total < cap ? total : cap;
-    *unresolved = un_total;
+    *unresolved = (int32_t)un;
     *overflow = (total > cap || (g.flags[b] & 1)) ? 1 : 0;
   }
 }
@@ -542,13 +606,22 @@ cudaError_t prepare_kernels(sft_plan_s* P) {
   return P->p.precision == SFT_FP64 ? prepare_kernels_t<F64>() : prepare_kernels_t<FF>();
 }
 
+// one finalize tile per signal when the signals alone fill the GPU
+static bool fin_single(const sft_plan_s* P, int64_t B, int nsm) {
+  return B >= nsm && P->M0 <= 65536;
+}
+
 int launches_per_call(const sft_plan_s* P) {
+  int dev = 0, nsm = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int fin = fin_single(P, P->max_signals, nsm) ? 1 : 2;
   if (P->p.mode == SFT_GENERAL)
-    return 2 * (P->M0 > kFft4Points ? 2 : 1) + 3 + (P->mlp != nullptr ? 1 : 0) + 1;
-  if (P->p.mode == SFT_EXACT_FIXED) return (P->M0 > kFft4Points ? 2 : 1) + 1 + P->p.a_max + 1;
+    return 2 * (P->M0 > kFft4Points ? 2 : 1) + 6 + (P->mlp != nullptr ? 1 : 0) + fin;
+  if (P->p.mode == SFT_EXACT_FIXED) return (P->M0 > kFft4Points ? 2 : 1) + 1 + P->p.a_max + fin;
   int fft = 0;
   for (int l = 0; l < P->levels; ++l) fft += (P->M0 >> l) > kFft4Points ? 2 : 1;
-  return fft + 2 * P->levels + 1;
+  return fft + 2 * P->levels + fin;
 }
 
 static cudaEvent_t pool_event(sft_plan_s* P) {
@@ -761,13 +834,22 @@ cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
     else
       launch_iter<FF>(P, B, x, x_stride, om, nsm, st, &M_last, &T_last);
   }
-  FinArgs f{P->M0, M_last, W.slot_cnt, W.slot_s, W.slot_p, T_last, W.flags, r->cap, r->idx,
-            reinterpret_cast<double2*>(r->val), r->count, r->unresolved, r->overflow, P->r_table};
+  // One tile per signal when the signals alone fill the GPU (and a thread
+  // walks at most 64 bins); else tiles of kFinTile bins, whose sums live in
+  // the second queue (free once the decoders are done).
+  const bool single = fin_single(P, B, nsm);
+  const int n_tiles = single ? 1 : (int)((P->M0 + kFinTile - 1) / kFinTile);
+  int* tiles = reinterpret_cast<int*>(W.queue[1]);
+  FinArgs f{P->M0,    M_last,   W.slot_cnt, W.slot_s, W.slot_p, T_last, W.flags, r->cap, r->idx,
+            reinterpret_cast<double2*>(r->val), r->count, r->unresolved, r->overflow, P->r_table,
+            tiles,    tiles + B * n_tiles, n_tiles, single ? P->M0 : (int64_t)kFinTile};
+  const dim3 fgrid((unsigned)n_tiles, (unsigned)B);
   stage_begin(P, "finalize", st);
+  if (!single) k_fin_count<<<fgrid, 256, 0, st>>>(f);
   if (fp64)
-    k_finalize<F64><<<(unsigned)B, 1024, 0, st>>>(f);
+    k_finalize<F64><<<fgrid, 1024, 0, st>>>(f);
   else
-    k_finalize<FF><<<(unsigned)B, 1024, 0, st>>>(f);
+    k_finalize<FF><<<fgrid, 1024, 0, st>>>(f);
   stage_end(P, st);
   return cudaGetLastError();
 }

@@ -4,9 +4,13 @@
 // Per call, batched over B signals of one plan (M bins, d = N / M):
 //   gather + FFT   the 2 a_m consecutive shifts 0 .. 2a_m-1 and the r random
 //                  shifts n_l (Part 1, lines 02-10)
-//   k_gen_svals    one thread per bin: the a_m singular values of the
-//                  a_m x a_m Hankel matrix of m_0 .. m_{2a_m-2} (Eq. (26)) by
-//                  one-sided Jacobi in FP64 (Part 2, lines 11-15)
+//   k_gen_bound,   per bin a lower bound ||H||_F / sqrt(a_m) of the largest
+//   k_gen_tau,     singular value, its K-th largest tau_L per signal, and
+//   k_gen_prune    the bins whose upper bound ||H||_F reaches tau_L (the
+//                  others cannot hold a vote) queued for
+//   k_gen_svals    the a_m singular values of the a_m x a_m Hankel matrix of
+//                  m_0 .. m_{2a_m-2} (Eq. (26)) by one-sided Jacobi in FP64
+//                  (Part 2, lines 11-15), grid-stride over the queue
 //   k_gen_vote     one CTA per signal: the K largest singular values (radix
 //                  select on their FP64 bit patterns, ties to the lower
 //                  index) vote a_k per bin (lines 16-21); bins with a_k > 0
@@ -43,6 +47,10 @@ struct GenArgs {
   int32_t* flags;
   OmegaTab om;
   const int16_t* prop;  // learned proposal: 8 candidates t per queue entry, or null
+  double* tau_lo;       // per signal: pruning threshold tau_L
+  double* lbound;       // [B][M]: per-bin lower bound of sigma_1
+  int2* svq;            // bins whose singular values are computed
+  int* svq_count;
 };
 
 // One-sided Jacobi on the n x n Hankel H_ij = m_{i+j}: rotate column pairs
@@ -108,8 +116,22 @@ __device__ void hankel_svals(const cdbl* m, double* sv) {
       }
 }
 
+// ||H||_F^2 of the a_m x a_m Hankel matrix of m_0..m_{2a_m-2}: m_l appears
+// min(l + 1, 2a_m - 1 - l) times
+template <int AM>
+__device__ __forceinline__ double hankel_frob2(const cdbl* m) {
+  double f2 = 0.0;
+#pragma unroll
+  for (int l = 0; l < 2 * AM - 1; ++l) f2 += (double)min(l + 1, 2 * AM - 1 - l) * norm2(m[l]);
+  return f2;
+}
+
+// Pruning bound, per bin: sigma_1 >= L_k = ||H v|| / ||v|| for any v; with
+// v = conj of the first row of H (one power step) this is exact for a bin
+// holding one alias (H = p z z^T is rank one).  Written to lbound[b M + k]
+// for k_gen_tau.
 template <class F, int AM>
-__global__ void __launch_bounds__(256) k_gen_svals(GenArgs g) {
+__global__ void __launch_bounds__(256) k_gen_bound(GenArgs g) {
   typedef typename Store<F>::T T;
   const int b = blockIdx.y;
   const int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x;
@@ -118,11 +140,66 @@ __global__ void __launch_bounds__(256) k_gen_svals(GenArgs g) {
   cdbl m[2 * AM - 1];
 #pragma unroll
   for (int j = 0; j < 2 * AM - 1; ++j) m[j] = Store<F>::to_d(Y[j * g.M + k]);
-  double sv[AM];
-  hankel_svals<AM>(m, sv);
-  double* o = g.sv + ((int64_t)b * g.M + k) * AM;
+  double v2 = 0.0, hv2 = 0.0;
 #pragma unroll
-  for (int i = 0; i < AM; ++i) o[i] = sv[i];
+  for (int j = 0; j < AM; ++j) v2 += norm2(m[j]);
+#pragma unroll
+  for (int i = 0; i < AM; ++i) {
+    cdbl acc = mk(0.0, 0.0);
+#pragma unroll
+    for (int j = 0; j < AM; ++j) acc = acc + m[i + j] * conjd(m[j]);
+    hv2 += norm2(acc);
+  }
+  g.lbound[(int64_t)b * g.M + k] = v2 > 0.0 ? sqrt(hv2 / v2) : 0.0;
+}
+
+// Bins that cannot hold a vote: ||H||_F bounds every singular value of the
+// bin; if it is below tau_L, the K-th largest of the bins' lower bounds of
+// sigma_1 (so tau_L <= the K-th largest singular value of the signal), the
+// vote gives the bin nothing.  Every bin's singular values are cleared
+// here; the others are queued for k_gen_svals (warp-aggregated).
+template <class F, int AM>
+__global__ void __launch_bounds__(256) k_gen_prune(GenArgs g) {
+  typedef typename Store<F>::T T;
+  const int b = blockIdx.y;
+  const int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  bool keep = false;
+  if (k < g.M) {
+    double* o = g.sv + ((int64_t)b * g.M + k) * AM;
+#pragma unroll
+    for (int i = 0; i < AM; ++i) o[i] = 0.0;
+    const double tau = g.tau_lo[b];
+    // a bin whose lower bound already reaches tau_L needs no more reading
+    keep = g.lbound[(int64_t)b * g.M + k] >= tau;
+    if (!keep) {
+      const T* Y = reinterpret_cast<const T*>(g.Y) + (int64_t)b * g.held_elems;
+      cdbl m[2 * AM - 1];
+#pragma unroll
+      for (int j = 0; j < 2 * AM - 1; ++j) m[j] = Store<F>::to_d(Y[j * g.M + k]);
+      const double u = sqrt(hankel_frob2<AM>(m));
+      keep = u * (1.0 + 1e-12) >= tau && u > 0.0;
+    }
+  }
+  queue_push(keep, b, (int)k, g.svq, g.svq_count);
+}
+
+// Singular values of the queued bins (grid-stride over the queue).
+template <class F, int AM>
+__global__ void __launch_bounds__(128) k_gen_svals(GenArgs g) {
+  typedef typename Store<F>::T T;
+  const int n = *g.svq_count;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 q = g.svq[e];
+    const T* Y = reinterpret_cast<const T*>(g.Y) + (int64_t)q.x * g.held_elems;
+    cdbl m[2 * AM - 1];
+#pragma unroll
+    for (int j = 0; j < 2 * AM - 1; ++j) m[j] = Store<F>::to_d(Y[j * g.M + q.y]);
+    double sv[AM];
+    hankel_svals<AM>(m, sv);
+    double* o = g.sv + ((int64_t)q.x * g.M + q.y) * AM;
+#pragma unroll
+    for (int i = 0; i < AM; ++i) o[i] = sv[i];
+  }
 }
 
 // Block-wide exclusive scan of one int per thread.
@@ -153,14 +230,69 @@ __device__ __forceinline__ int gen_block_scan(int v, int* total) {
   return before;
 }
 
-// Lines 16-21: the K largest of the M a_m singular values of one signal.
-// MSB-first radix select (8 passes of 8 bits) on the bit patterns of the
-// non-negative doubles finds the K-th largest value tau and how many of the
-// values equal to tau are selected; those are the ones of lowest index.
-__global__ void __launch_bounds__(1024) k_gen_vote(GenArgs g) {
+// K-th largest of the n non-negative doubles `keys` (as bit patterns) of
+// one CTA's signal: MSB-first radix select, 8 passes of 8 bits.  Returns the
+// K-th largest key and, in *rem_out, how many of the keys equal to it are
+// among the K largest (0 < K <= n).
+__device__ unsigned long long radix_select_desc(const unsigned long long* keys, int64_t n,
+                                                long long K, long long* rem_out) {
   __shared__ unsigned hist[256];
   __shared__ unsigned long long s_prefix;
   __shared__ long long s_rem;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  unsigned long long prefix = 0ull, mask = 0ull;
+  long long rem = K;  // rank (from the top) still to find among keys matching prefix
+  for (int pass = 0; pass < 8; ++pass) {
+    const int shift = 56 - 8 * pass;
+    for (int i = tid; i < 256; i += nthr) hist[i] = 0u;
+    __syncthreads();
+    for (int64_t i = tid; i < n; i += nthr) {
+      const unsigned long long key = keys[i];
+      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      long long cum = 0;
+      int sel = 0;
+      for (int dg = 255; dg >= 0; --dg) {
+        if (cum + (long long)hist[dg] >= rem) {
+          sel = dg;
+          break;
+        }
+        cum += hist[dg];
+      }
+      s_prefix = prefix | ((unsigned long long)sel << shift);
+      s_rem = rem - cum;
+    }
+    __syncthreads();
+    prefix = s_prefix;
+    rem = s_rem;
+    mask |= 255ull << shift;
+    __syncthreads();
+  }
+  *rem_out = rem;
+  return prefix;
+}
+
+// tau_L per signal: the K-th largest of the M bins' lower bounds (0 when K
+// is 0 or not below M, which disables pruning)
+__global__ void __launch_bounds__(1024) k_gen_tau(GenArgs g) {
+  const int b = blockIdx.x;
+  const int64_t Kb = g.K_table != nullptr ? g.K_table[b] : g.K;
+  double tau = 0.0;
+  if (Kb > 0 && Kb < g.M) {
+    long long rem = 0;
+    const unsigned long long key = radix_select_desc(
+        reinterpret_cast<const unsigned long long*>(g.lbound + (int64_t)b * g.M), g.M, Kb, &rem);
+    tau = __longlong_as_double((long long)key);
+  }
+  if (threadIdx.x == 0) g.tau_lo[b] = tau;
+}
+
+// Lines 16-21: the K largest of the M a_m singular values of one signal
+// (radix select on their bit patterns); of the values equal to the K-th
+// largest tau, those of lowest index are selected.
+__global__ void __launch_bounds__(1024) k_gen_vote(GenArgs g) {
   const int b = blockIdx.x;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int am = g.a_max;
@@ -170,38 +302,9 @@ __global__ void __launch_bounds__(1024) k_gen_vote(GenArgs g) {
   uint8_t* ak = g.ak + (int64_t)b * g.M;
   const int64_t Kb = g.K_table != nullptr ? g.K_table[b] : g.K;
   const int64_t K = Kb < n ? Kb : n;
-  unsigned long long prefix = 0ull, mask = 0ull;
-  long long rem = K;  // rank (from the top) still to find among keys matching prefix
-  if (K > 0) {
-    for (int pass = 0; pass < 8; ++pass) {
-      const int shift = 56 - 8 * pass;
-      for (int i = tid; i < 256; i += nthr) hist[i] = 0u;
-      __syncthreads();
-      for (int64_t i = tid; i < n; i += nthr) {
-        const unsigned long long key = keys[i];
-        if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
-      }
-      __syncthreads();
-      if (tid == 0) {
-        long long cum = 0;
-        int sel = 0;
-        for (int dg = 255; dg >= 0; --dg) {
-          if (cum + (long long)hist[dg] >= rem) {
-            sel = dg;
-            break;
-          }
-          cum += hist[dg];
-        }
-        s_prefix = prefix | ((unsigned long long)sel << shift);
-        s_rem = rem - cum;
-      }
-      __syncthreads();
-      prefix = s_prefix;
-      rem = s_rem;
-      mask |= 255ull << shift;
-      __syncthreads();
-    }
-  }
+  unsigned long long prefix = 0ull;
+  long long rem = 0;
+  if (K > 0) prefix = radix_select_desc(keys, n, K, &rem);
   const unsigned long long tau = prefix;  // K-th largest key
   // per-thread chunk of whole bins, in index order
   const int64_t chunk = (g.M + nthr - 1) / nthr;
@@ -515,20 +618,47 @@ static GenArgs general_front(sft_plan_s* P, int64_t B, const void* x, int64_t x_
   const int am = P->p.a_max, r = P->p.n_cs_shifts;
   // Part 1: 2 a_m consecutive shifts (rows 0..2a_m-1), r random shifts after
   launch_gather_fft_any(P, B, x, x_stride, P->p.d, P->log2M0, 0, 2 * am, W.held[0], P->M0, 0,
-                        true, st, nullptr, "gather_fft_consecutive");
+                        false, st, nullptr, "gather_fft_consecutive");
   launch_gather_fft_any(P, B, x, x_stride, P->p.d, P->log2M0, 0, r, W.held[0], P->M0, 2 * am,
                         false, st, P->tab.cs_shifts, "gather_fft_random");
+  // the bounds use the solution slots (filled only by k_gen_solve), the
+  // pruned-bin queue the second queue and counter
   GenArgs g{P->p.N, P->M0, P->p.d, P->p.K, am, r, 2, 8, W.held[0], W.held_elems, W.sv, W.T[0],
             W.queue[0], W.qcount, P->tab.cs_shifts, P->K_table, W.slot_cnt, W.slot_s, W.slot_p,
             W.flags, OmegaTab{P->tab.om_hi, P->tab.om_lo, P->tab.om_lo_bits, P->p.N - 1},
-            nullptr};
+            nullptr, reinterpret_cast<double*>(W.ymax2), reinterpret_cast<double*>(W.slot_s),
+            W.queue[1], W.qcount + 1};
   dim3 sgrid((unsigned)((P->M0 + 255) / 256), (unsigned)B);
+  stage_begin(P, "gen_bound", st);
+  switch (am) {
+    case 1: k_gen_bound<F, 1><<<sgrid, 256, 0, st>>>(g); break;
+    case 2: k_gen_bound<F, 2><<<sgrid, 256, 0, st>>>(g); break;
+    case 3: k_gen_bound<F, 3><<<sgrid, 256, 0, st>>>(g); break;
+    default: k_gen_bound<F, 4><<<sgrid, 256, 0, st>>>(g); break;
+  }
+  stage_end(P, st);
+  stage_begin(P, "gen_tau", st);
+  k_gen_tau<<<(unsigned)B, 1024, 0, st>>>(g);
+  stage_end(P, st);
+  stage_begin(P, "gen_prune", st);
+  switch (am) {
+    case 1: k_gen_prune<F, 1><<<sgrid, 256, 0, st>>>(g); break;
+    case 2: k_gen_prune<F, 2><<<sgrid, 256, 0, st>>>(g); break;
+    case 3: k_gen_prune<F, 3><<<sgrid, 256, 0, st>>>(g); break;
+    default: k_gen_prune<F, 4><<<sgrid, 256, 0, st>>>(g); break;
+  }
+  stage_end(P, st);
+  int dev = 0, nsm = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned vgrid = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((B * P->M0 + 127) / 128, (int64_t)P->dec_ctas_per_sm * nsm));
   stage_begin(P, "gen_svals", st);
   switch (am) {
-    case 1: k_gen_svals<F, 1><<<sgrid, 256, 0, st>>>(g); break;
-    case 2: k_gen_svals<F, 2><<<sgrid, 256, 0, st>>>(g); break;
-    case 3: k_gen_svals<F, 3><<<sgrid, 256, 0, st>>>(g); break;
-    default: k_gen_svals<F, 4><<<sgrid, 256, 0, st>>>(g); break;
+    case 1: k_gen_svals<F, 1><<<vgrid, 128, 0, st>>>(g); break;
+    case 2: k_gen_svals<F, 2><<<vgrid, 128, 0, st>>>(g); break;
+    case 3: k_gen_svals<F, 3><<<vgrid, 128, 0, st>>>(g); break;
+    default: k_gen_svals<F, 4><<<vgrid, 128, 0, st>>>(g); break;
   }
   stage_end(P, st);
   stage_begin(P, "gen_vote", st);

@@ -50,7 +50,8 @@ EXPORTS = ["sft_params_default", "sft_plan_create", "sft_plan_destroy", "sft_pla
            "sft_batch_create", "sft_batch_destroy", "sft_batch_set_options", "sft_batch",
            "sft_batch_info", "sft_mlp_config_for", "sft_mlp_create", "sft_mlp_destroy",
            "sft_mlp_param_count", "sft_mlp_get_params", "sft_mlp_set_params", "sft_mlp_features",
-           "sft_mlp_forward", "sft_mlp_grad", "sft_mlp_train", "sft_plan_attach_mlp"]
+           "sft_mlp_forward", "sft_mlp_grad", "sft_mlp_train", "sft_plan_attach_mlp",
+           "sft_exact_auto"]
 
 _lib = None
 
@@ -129,6 +130,8 @@ def load(build_if_missing: bool = False):
     lib.sft_mlp_train.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                   C.c_int32, C.c_int32, C.c_uint64, C.c_void_p, C.c_void_p]
     lib.sft_plan_attach_mlp.argtypes = [C.c_void_p, C.c_void_p]
+    lib.sft_exact_auto.argtypes = [P(sft_params), C.c_int64, C.c_void_p, C.c_int64, C.c_int64,
+                                   C.c_int64, P(sft_result), C.c_void_p, C.c_void_p]
     lib.sft_strerror.argtypes = [C.c_int]
     lib.sft_strerror.restype = C.c_char_p
     lib.sft_last_cuda_error.argtypes = []
@@ -432,6 +435,25 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def sft_exact_auto(params: sft_params, x, cap: int, M_start: int = 1, M_max: int = 0,
+                   stream=None):
+    """Unknown K (Sec. II-E): x torch CUDA tensor [B, N].  Returns (Result of
+    device tensors, numpy int64 [B] of the M each signal stopped at)."""
+    import torch
+    if x.dim() == 1:
+        x = x.unsqueeze(0)
+    B = x.shape[0]
+    out = _device_result(B, cap, x.device)
+    r = sft_result(cap, out.idx.data_ptr(), out.val.data_ptr(), out.count.data_ptr(),
+                   out.unresolved.data_ptr(), out.overflow.data_ptr())
+    m = np.zeros(B, np.int64)
+    pitch = x.stride(0) if B > 1 else x.shape[1]
+    _check(load().sft_exact_auto(C.byref(params), B, C.c_void_p(x.data_ptr()), pitch, int(M_start),
+                                 int(M_max), C.byref(r), m.ctypes.data,
+                                 C.c_void_p(_stream_ptr(stream))), "sft_exact_auto")
+    return out, m
 
 
 # ------------------------------------------------------- learned proposal

@@ -173,3 +173,39 @@ def test_empty_signal(orc):
     x = np.zeros(1 << 12, complex)
     idx, val, un = orc.exact(x, 64)
     assert idx.size == 0 and un == 0
+
+
+@pytest.mark.parametrize("mode", ["iter", "fixed"])
+def test_unknown_k_stops_where_the_decision_rule_first_solves_every_bin(orc, mode):
+    """Sec. II-E: starting at d = N (M = 1) and halving d, the bottom-up
+    strategy stops at the first M whose run leaves no bin unsolved.  The
+    support-only simulation of the decision rule predicts that M and the
+    recovered set exactly; at that M the whole planted spectrum is
+    returned."""
+    for N, K, seeds in [(1 << 12, 5, range(8)), (1 << 14, 40, range(6)), (1 << 16, 300, range(3))]:
+        for seed in seeds:
+            x, supp, vals = siggen.exact_signal(N, K, seed, mag=(1, 10))
+            M = 1
+            while True:
+                iters = min(4, int(np.log2(M)) + 1)
+                want, un = (simulate_iter(supp, M, iters) if mode == "iter"
+                            else simulate_fixed(supp, M, 4))
+                if un == 0:
+                    break
+                M *= 2
+            idx, val, un, M_got = orc.exact_auto(x, 4, orc.ITER if mode == "iter" else orc.FIXED)
+            assert M_got == M and un == 0, (N, K, seed, M_got, M)
+            assert idx.tolist() == sorted(supp.tolist())
+            assert np.abs(val - vals[np.argsort(supp)]).max() < 1e-8 * np.abs(vals).max()
+            # no earlier M solves every bin
+            assert M == 1 or (simulate_iter(supp, M // 2, min(4, int(np.log2(M // 2)) + 1))[1]
+                              if mode == "iter" else simulate_fixed(supp, M // 2, 4)[1]) > 0
+
+
+def test_unknown_k_costs_at_most_twice_the_known_k_run(orc):
+    """Sec. II-E's cost claim in transform sizes: the runs at M = 1, 2, ...,
+    M* sum to sum_j 2^j log 2^j <= 2 M* log M* (FFT work of the final run)."""
+    x, supp, _ = siggen.exact_signal(1 << 16, 300, 1, mag=(1, 10))
+    _, _, _, Ms = orc.exact_auto(x, 4, orc.FIXED)
+    total = sum((1 << j) * max(j, 1) for j in range(int(np.log2(Ms)) + 1))
+    assert total <= 2 * Ms * max(int(np.log2(Ms)), 1)
