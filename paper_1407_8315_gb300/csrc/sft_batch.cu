@@ -10,10 +10,12 @@
 // tables are refreshed per call.  On the first call of a shape an
 // autotuner times the queue decoders at 2, 4, 8 and 16 CTAs per SM on that
 // call's own data and keeps the fastest.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "sft_internal.h"
@@ -58,6 +60,12 @@ struct sft_batch_s {
   int64_t* hk = nullptr;
   cudaEvent_t staged = nullptr;  // last table upload done
   cudaStream_t cap_stream = nullptr;
+  // independent groups run concurrently inside the graph: forked onto
+  // kLanes capture streams, joined back at the end
+  static constexpr int kLanes = 8;
+  cudaStream_t lane[kLanes] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kLanes] = {};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<int64_t> comp;  // composition the graph was captured for
@@ -163,8 +171,13 @@ sft_status sft_batch_create(sft_batch_t* out) {
   if (!out) return SFT_EINVAL;
   sft_batch_s* B = new (std::nothrow) sft_batch_s();
   if (!B) return SFT_ENOMEM;
-  if (cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&B->staged, cudaEventDisableTiming) != cudaSuccess) {
+  bool ok = cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&B->staged, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&B->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; ok && i < sft_batch_s::kLanes; ++i)
+    ok = cudaStreamCreateWithFlags(&B->lane[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&B->join_ev[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
     sft::set_error_detail("sft_batch_create: stream or event creation failed");
     delete B;
     return SFT_ECUDA;
@@ -181,6 +194,11 @@ void sft_batch_destroy(sft_batch_t B) {
     if (kv.second.plan) sft_plan_destroy(kv.second.plan);
   free_tables(B);
   if (B->staged) cudaEventDestroy(B->staged);
+  if (B->fork_ev) cudaEventDestroy(B->fork_ev);
+  for (int i = 0; i < sft_batch_s::kLanes; ++i) {
+    if (B->lane[i]) cudaStreamDestroy(B->lane[i]);
+    if (B->join_ev[i]) cudaEventDestroy(B->join_ev[i]);
+  }
   if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
   delete B;
 }
@@ -302,11 +320,36 @@ sft_status sft_batch(sft_batch_t B, int64_t n, const sft_params* ps, const void*
   if (e == cudaSuccess && B->use_graph) {
     if (!B->exec || comp != B->comp) {
       drop_graph(B);
-      // the graph is captured on a private stream and launched on `st`
+      // the graph is captured on a private stream and launched on `st`; the
+      // groups (independent plans and workspaces) are spread over the lanes,
+      // largest first onto the least-loaded lane, so that small groups run
+      // side by side
       e = cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) e = cudaEventRecord(B->fork_ev, B->cap_stream);
+      for (int i = 0; e == cudaSuccess && i < sft_batch_s::kLanes; ++i)
+        e = cudaStreamWaitEvent(B->lane[i], B->fork_ev, 0);
+      std::vector<std::pair<double, Group*>> order;
       for (auto& kv : B->groups)
-        if (e == cudaSuccess && !kv.second.members.empty())
-          e = enqueue_group(B, kv.second, B->cap_stream);
+        if (!kv.second.members.empty())
+          order.push_back({(double)kv.second.members.size() * (double)kv.second.plan->p.N,
+                           &kv.second});
+      std::sort(order.begin(), order.end(),
+                [](const std::pair<double, Group*>& a, const std::pair<double, Group*>& b) {
+                  return a.first > b.first;
+                });
+      double load[sft_batch_s::kLanes] = {};
+      for (auto& og : order) {
+        if (e != cudaSuccess) break;
+        int li = 0;
+        for (int i = 1; i < sft_batch_s::kLanes; ++i)
+          if (load[i] < load[li]) li = i;
+        load[li] += og.first;
+        e = enqueue_group(B, *og.second, B->lane[li]);
+      }
+      for (int i = 0; e == cudaSuccess && i < sft_batch_s::kLanes; ++i) {
+        e = cudaEventRecord(B->join_ev[i], B->lane[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(B->cap_stream, B->join_ev[i], 0);
+      }
       cudaGraph_t gph = nullptr;
       cudaError_t e2 = cudaStreamEndCapture(B->cap_stream, &gph);
       if (e == cudaSuccess) e = e2;

@@ -223,6 +223,22 @@ __device__ __forceinline__ int64_t snap_root(cdbl z, int64_t k, const BinGeom& g
   return k + t * g.M;
 }
 
+// snap_root for a root given in FP32 (z = m1 / m0 rounded): the FP64 root
+// is formed only when the FP32 angle lies near a candidate midpoint.
+__device__ __forceinline__ int64_t snap_root_f(float zx, float zy, int64_t k, const BinGeom& g,
+                                               cdbl m0, cdbl m1) {
+  const float inv2pi = 0.15915494309189533577f;
+  const float ang = atan2f(zy, zx);
+  const float df = (float)g.d;
+  const float q = fmaf(ang, df * inv2pi, -(float)k / (float)g.M);
+  const float fr = q - rintf(q);
+  const float margin = fmaxf(1e-3f, 8e-7f * df);
+  if (fabsf(fabsf(fr) - 0.5f) < margin) return snap_root(m1 * crcp(m0), k, g);
+  int64_t t = ((int64_t)rintf(q)) % g.d;
+  if (t < 0) t += g.d;
+  return k + t * g.M;
+}
+
 // Decode bin k with `a` aliases from m[0..nm).  On success fills s[0..a)
 // (ascending), p[0..a), replaces m[0..nm) by the residual m - Z p and
 // returns true; on failure m is unchanged.
@@ -231,13 +247,37 @@ __device__ __forceinline__ bool decode_bin(cdbl* m, int64_t k, const BinGeom& g,
                                            int64_t* s, cdbl* p) {
   static_assert(nm >= 2 * a && nm <= 8, "need 2a <= nm <= 8 syndromes");
   if constexpr (a == 1) {
-    // c_0 = -m_1 / m_0, the single root z = m_1 / m_0 (Sec. II-A)
+    // c_0 = -m_1 / m_0, the single root z = m_1 / m_0 (Sec. II-A).  Only
+    // the root's angle (to pick the candidate) and its distance to that
+    // candidate (against root_tol) are used, so z is formed in FP32; FP64
+    // decides where the FP32 values lie near a candidate midpoint or near
+    // the root_tol bound, and when the FP32 quotient leaves the float range.
     if (m[0].x == 0.0 && m[0].y == 0.0) return false;
-    const cdbl z = m[1] * crcp(m[0]);
-    if (!(isfinite(z.x) && isfinite(z.y)) || (z.x == 0.0 && z.y == 0.0)) return false;
-    s[0] = snap_root(z, k, g);
-    const cdbl w = omega_pow(g.om, s[0]);
-    if (!(norm2(z - w) <= tol.root2)) return false;
+    const float m0x = (float)m[0].x, m0y = (float)m[0].y;
+    const float m1x = (float)m[1].x, m1y = (float)m[1].y;
+    const float den = m0x * m0x + m0y * m0y;
+    cdbl w;
+    if (den > 1e-30f && den < 1e30f) {
+      const float inv = __frcp_rn(den);
+      const float zx = (m1x * m0x + m1y * m0y) * inv, zy = (m1y * m0x - m1x * m0y) * inv;
+      if (zx == 0.0f && zy == 0.0f) return false;
+      s[0] = snap_root_f(zx, zy, k, g, m[0], m[1]);
+      w = omega_pow(g.om, s[0]);
+      const float dx = zx - (float)w.x, dy = zy - (float)w.y;
+      const float dz = dx * dx + dy * dy, r2 = (float)tol.root2;
+      if (fabsf(dz - r2) <= 1e-4f * r2) {
+        const cdbl z = m[1] * crcp(m[0]);
+        if (!(norm2(z - w) <= tol.root2)) return false;
+      } else if (!(dz <= r2)) {
+        return false;
+      }
+    } else {
+      const cdbl z = m[1] * crcp(m[0]);
+      if (!(isfinite(z.x) && isfinite(z.y)) || (z.x == 0.0 && z.y == 0.0)) return false;
+      s[0] = snap_root(z, k, g);
+      w = omega_pow(g.om, s[0]);
+      if (!(norm2(z - w) <= tol.root2)) return false;
+    }
     // least squares over all equations: Z^H Z = nm, p = (1/nm) sum conj(w^i) m_i
     if constexpr (nm == 2) {
       // p = (m0 + conj(w) m1) / 2; the residuals are r0 = (m0 - conj(w) m1)/2
@@ -329,25 +369,38 @@ __device__ __forceinline__ bool decode_bin(cdbl* m, int64_t k, const BinGeom& g,
     for (int j = 1; j < a; ++j)
       if (s[j] == s[j - 1]) return false;
 
-    // normal equations (Z^H Z) p = Z^H m over all nm equations, Z_ij = w_j^i
+    // normal equations (Z^H Z) p = Z^H m over all nm equations, Z_ij = w_j^i.
+    // Z^H Z is Hermitian with diagonal nm, and its (u, v) entry is the
+    // geometric sum sum_i q^i of q = conj(w_u) w_v: a(a-1)/2 sums.
     cdbl G[a * a], gr[a], wp[a];
 #pragma unroll
     for (int u = 0; u < a; ++u) {
-      gr[u] = mk(0.0, 0.0);
-      wp[u] = mk(1.0, 0.0);
+      G[u * a + u] = mk((double)nm, 0.0);
 #pragma unroll
-      for (int v = 0; v < a; ++v) G[u * a + v] = mk(0.0, 0.0);
+      for (int v = u + 1; v < a; ++v) {
+        const cdbl q = conjd(w[u]) * w[v];
+        cdbl acc = mk(1.0, 0.0), qp = q;
+#pragma unroll
+        for (int i = 1; i < nm; ++i) {
+          acc = acc + qp;
+          if (i + 1 < nm) qp = qp * q;
+        }
+        G[u * a + v] = acc;
+        G[v * a + u] = conjd(acc);
+      }
     }
 #pragma unroll
-    for (int i = 0; i < nm; ++i) {
+    for (int u = 0; u < a; ++u) {
+      gr[u] = m[0];
+      wp[u] = w[u];
+    }
+#pragma unroll
+    for (int i = 1; i < nm; ++i) {
 #pragma unroll
       for (int u = 0; u < a; ++u) {
         gr[u] = gr[u] + conjd(wp[u]) * m[i];
-#pragma unroll
-        for (int v = 0; v < a; ++v) G[u * a + v] = G[u * a + v] + conjd(wp[u]) * wp[v];
+        if (i + 1 < nm) wp[u] = wp[u] * w[u];
       }
-#pragma unroll
-      for (int u = 0; u < a; ++u) wp[u] = wp[u] * w[u];
     }
     if (!solve_small<a>(G, gr, p)) return false;
 #pragma unroll

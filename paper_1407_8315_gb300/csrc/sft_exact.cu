@@ -34,8 +34,8 @@
 namespace sft {
 
 // ----------------------------------------------------------- gather + FFT
-template <class F>
-__global__ void __launch_bounds__(512) k_gather_fft(
+template <class F, int PTS>
+__global__ void __launch_bounds__(8192 / PTS) k_gather_fft(
     const typename F::In* __restrict__ x, int64_t x_stride, int64_t N, int64_t d, int log2M,
     int shift0, int log2Mt, const typename F::Tw* __restrict__ tw, void* __restrict__ out_v,
     int64_t out_sig, int64_t out_row, int row0, unsigned long long* __restrict__ ymax2,
@@ -53,20 +53,20 @@ __global__ void __launch_bounds__(512) k_gather_fft(
                                  ? reinterpret_cast<const typename F::In*>(x_table[b])
                                  : x + (int64_t)b * x_stride;
   // x_{d,shift}[n] = x[(n d + shift) mod N]: every load of the thread is
-  // issued before the first store (at most 16 per thread)
-  typename F::In v[16];
+  // issued before the first store (at most PTS per thread)
+  typename F::In v[PTS];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
+  for (int i = 0; i < PTS; ++i) {
     const int n = tid + i * nthr;
     if (n < M) v[i] = __ldg(xs + (((int64_t)n * d + shift) & (N - 1)));
   }
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
+  for (int i = 0; i < PTS; ++i) {
     const int n = tid + i * nthr;
     if (n < M) F::st(smem, M, n, F::from_in(v[i]));
   }
   __syncthreads();
-  cta_fft<F>(smem, log2M, log2Mt, tw, tid, nthr);
+  cta_fft<F, PTS>(smem, log2M, log2Mt, tw, tid, nthr);
   Out* o = reinterpret_cast<Out*>(out_v) + (int64_t)b * out_sig + (int64_t)(row0 + js) * out_row;
   double lmax = 0.0;
   if constexpr (std::is_same<F, F64>::value) {
@@ -581,9 +581,9 @@ __global__ void __launch_bounds__(1024) k_finalize(FinArgs g) {
 }
 
 // ------------------------------------------------------------ launchers
-static int fft_threads(int log2M) {
+static int fft_threads(int log2M, int pts) {
   const int M = 1 << log2M;
-  return M / 16 > 32 ? M / 16 : 32;
+  return M / pts > 32 ? M / pts : 32;
 }
 
 // The opt-in shared-memory limit is a property of the kernel, shared by every
@@ -593,8 +593,10 @@ static int fft_threads(int log2M) {
 template <class F>
 static cudaError_t prepare_kernels_t() {
   const int smem = padded(kFft4Points) * 16;
-  cudaError_t e = cudaFuncSetAttribute(k_gather_fft<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem);
+  cudaError_t e = cudaFuncSetAttribute(k_gather_fft<F, 16>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gather_fft<F, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fft4_cols<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
@@ -617,7 +619,7 @@ int launches_per_call(const sft_plan_s* P) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int fin = fin_single(P, P->max_signals, nsm) ? 1 : 2;
   if (P->p.mode == SFT_GENERAL)
-    return 2 * (P->M0 > kFft4Points ? 2 : 1) + 6 + (P->mlp != nullptr ? 1 : 0) + fin;
+    return 2 * (P->M0 > kFft4Points ? 2 : 1) + 5 + P->p.a_max + (P->mlp != nullptr ? 1 : 0) + fin;
   if (P->p.mode == SFT_EXACT_FIXED) return (P->M0 > kFft4Points ? 2 : 1) + 1 + P->p.a_max + fin;
   int fft = 0;
   for (int l = 0; l < P->levels; ++l) fft += (P->M0 >> l) > kFft4Points ? 2 : 1;
@@ -659,13 +661,20 @@ void launch_gather_fft(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride
   const auto* tw = reinterpret_cast<const typename F::Tw*>(P->tab.tw);
   if ((1 << log2M) <= kFft4Points) {
     dim3 grid(nshift, (unsigned)B);
-    const int nthr = fft_threads(log2M);
+    const int pts = P->fft_pts;
+    const int nthr = fft_threads(log2M, pts);
     const size_t smem = (size_t)padded(1 << log2M) * F::kBytesPerPoint;
     stage_begin(P, stage ? stage : (nshift > 2 ? "gather_fft_fixed" : names[lvl]), st);
-    k_gather_fft<F><<<grid, nthr, smem, st>>>(xin, x_stride, P->p.N, d, log2M, shift0, P->log2M0,
-                                              tw, out, P->ws.held_elems, out_row, row0,
-                                              want_ymax ? P->ws.ymax2 : nullptr, shift_list,
-                                              P->x_table);
+    if (pts == 8)
+      k_gather_fft<F, 8><<<grid, nthr, smem, st>>>(xin, x_stride, P->p.N, d, log2M, shift0,
+                                                   P->log2M0, tw, out, P->ws.held_elems, out_row,
+                                                   row0, want_ymax ? P->ws.ymax2 : nullptr,
+                                                   shift_list, P->x_table);
+    else
+      k_gather_fft<F, 16><<<grid, nthr, smem, st>>>(xin, x_stride, P->p.N, d, log2M, shift0,
+                                                    P->log2M0, tw, out, P->ws.held_elems, out_row,
+                                                    row0, want_ymax ? P->ws.ymax2 : nullptr,
+                                                    shift_list, P->x_table);
     stage_end(P, st);
     return;
   }

@@ -61,12 +61,12 @@ __device__ __forceinline__ void dft_reg(typename F::V* v) {
 }
 
 // One Stockham pass of radix R over buf[0..M).  Each thread owns up to
-// G = 16 / R groups (group j = tid + g * nthr).
-template <class F, int R>
+// G = PTS / R groups (group j = tid + g * nthr): PTS points per thread.
+template <class F, int R, int PTS = 16>
 __device__ __forceinline__ void stockham_pass(char* buf, int M, int Ns, int log2Mt,
                                               const typename F::Tw* __restrict__ tw, int tid,
                                               int nthr) {
-  constexpr int G = 16 / R;
+  constexpr int G = PTS / R;
   const int groups = M / R;
   typename F::V v[G][R];
   const int twstep_log = log2Mt - (31 - __clz(Ns * R));  // log2(Mt / (Ns R))
@@ -98,21 +98,27 @@ __device__ __forceinline__ void stockham_pass(char* buf, int M, int Ns, int log2
 }
 
 // Forward FFT of buf[0..M), M = 2^log2M (1 <= log2M <= 13 here), executed by
-// nthr threads (nthr * 16 >= M).  Caller synchronises before the call.
-template <class F>
+// nthr threads holding PTS = 16 or 8 points each (nthr * PTS >= M): radix-PTS
+// passes and one radix-2/4/8 pass for the remaining factor.  Caller
+// synchronises before the call.
+template <class F, int PTS = 16>
 __device__ void cta_fft(char* buf, int log2M, int log2Mt, const typename F::Tw* __restrict__ tw,
                         int tid, int nthr) {
+  static_assert(PTS == 16 || PTS == 8, "16 or 8 points per thread");
+  constexpr int LP = PTS == 16 ? 4 : 3;
   const int M = 1 << log2M;
   int Ns = 1;
   int rem = log2M;
-  while (rem >= 4) {
-    stockham_pass<F, 16>(buf, M, Ns, log2Mt, tw, tid, nthr);
-    Ns <<= 4;
-    rem -= 4;
+  while (rem >= LP) {
+    stockham_pass<F, PTS, PTS>(buf, M, Ns, log2Mt, tw, tid, nthr);
+    Ns <<= LP;
+    rem -= LP;
   }
-  if (rem == 3) stockham_pass<F, 8>(buf, M, Ns, log2Mt, tw, tid, nthr);
-  if (rem == 2) stockham_pass<F, 4>(buf, M, Ns, log2Mt, tw, tid, nthr);
-  if (rem == 1) stockham_pass<F, 2>(buf, M, Ns, log2Mt, tw, tid, nthr);
+  if constexpr (PTS == 16) {
+    if (rem == 3) stockham_pass<F, 8, PTS>(buf, M, Ns, log2Mt, tw, tid, nthr);
+  }
+  if (rem == 2) stockham_pass<F, 4, PTS>(buf, M, Ns, log2Mt, tw, tid, nthr);
+  if (rem == 1) stockham_pass<F, 2, PTS>(buf, M, Ns, log2Mt, tw, tid, nthr);
 }
 
 }  // namespace sft

@@ -15,7 +15,7 @@
 //                  select on their FP64 bit patterns, ties to the lower
 //                  index) vote a_k per bin (lines 16-21); bins with a_k > 0
 //                  are queued
-//   k_gen_solve    per queued bin: the a_k x a_k Hankel locator, |P~| at all
+//   k_gen_solve    per queued bin (one kernel per a_k): the a_k x a_k Hankel locator, |P~| at all
 //                  d candidates of U_k with the 2 a_k smallest kept (pruning
 //                  Steps 2-3), Subspace Pursuit on the pruned sensing matrix
 //                  Phi_p (Parts 3-4, lines 22-29)
@@ -129,7 +129,76 @@ __device__ __forceinline__ double hankel_frob2(const cdbl* m) {
 // Pruning bound, per bin: sigma_1 >= L_k = ||H v|| / ||v|| for any v; with
 // v = conj of the first row of H (one power step) this is exact for a bin
 // holding one alias (H = p z z^T is rank one).  Written to lbound[b M + k]
-// for k_gen_tau.
+// for k_gen_tau.  The mixed path forms the bounds in FP32 from the
+// float-float hi parts (relative error far below the pruning margin);
+// FP64 serves the plain path and values outside the float range.
+template <int AM, class C>
+__device__ __forceinline__ void power_bound(const C* m, decltype(m[0].x)& v2, decltype(m[0].x)& hv2) {
+  typedef decltype(m[0].x) R;
+  v2 = R(0);
+  hv2 = R(0);
+#pragma unroll
+  for (int j = 0; j < AM; ++j) v2 += m[j].x * m[j].x + m[j].y * m[j].y;
+#pragma unroll
+  for (int i = 0; i < AM; ++i) {
+    R ax = R(0), ay = R(0);
+#pragma unroll
+    for (int j = 0; j < AM; ++j) {  // m_{i+j} conj(m_j)
+      ax += m[i + j].x * m[j].x + m[i + j].y * m[j].y;
+      ay += m[i + j].y * m[j].x - m[i + j].x * m[j].y;
+    }
+    hv2 += ax * ax + ay * ay;
+  }
+}
+
+template <class F, int AM>
+__device__ __forceinline__ double bin_lower_bound(const typename Store<F>::T* Y, int64_t M,
+                                                  int64_t k) {
+  if constexpr (std::is_same<F, FF>::value) {
+    float2 mf[2 * AM - 1];
+#pragma unroll
+    for (int j = 0; j < 2 * AM - 1; ++j) {
+      const float4 v = Y[j * M + k];
+      mf[j] = make_float2(v.x, v.z);
+    }
+    float v2, hv2;
+    power_bound<AM>(mf, v2, hv2);
+    if (v2 > 1e-30f && hv2 < 1e37f) return (double)sqrtf(hv2 / v2);
+  }
+  cdbl m[2 * AM - 1];
+#pragma unroll
+  for (int j = 0; j < 2 * AM - 1; ++j) m[j] = Store<F>::to_d(Y[j * M + k]);
+  double v2, hv2;
+  power_bound<AM>(m, v2, hv2);
+  return v2 > 0.0 ? sqrt(hv2 / v2) : 0.0;
+}
+
+// ||H||_F, the upper bound of every singular value of the bin: FP32 on the
+// mixed path, FP64 on the plain path and outside the float range
+template <class F, int AM>
+__device__ __forceinline__ double bin_upper_bound(const typename Store<F>::T* Y, int64_t M,
+                                                  int64_t k) {
+  if constexpr (std::is_same<F, FF>::value) {
+    float f2 = 0.0f;
+#pragma unroll
+    for (int l = 0; l < 2 * AM - 1; ++l) {
+      const float4 v = Y[l * M + k];
+      f2 += (float)min(l + 1, 2 * AM - 1 - l) * (v.x * v.x + v.z * v.z);
+    }
+    if (f2 < 1e37f) return (double)sqrtf(f2);
+  }
+  cdbl m[2 * AM - 1];
+#pragma unroll
+  for (int j = 0; j < 2 * AM - 1; ++j) m[j] = Store<F>::to_d(Y[j * M + k]);
+  return sqrt(hankel_frob2<AM>(m));
+}
+
+// relative margin of the pruning test: FP32 bounds on the mixed path
+template <class F>
+__device__ __forceinline__ double prune_margin() {
+  return std::is_same<F, FF>::value ? 4e-5 : 1e-12;
+}
+
 template <class F, int AM>
 __global__ void __launch_bounds__(256) k_gen_bound(GenArgs g) {
   typedef typename Store<F>::T T;
@@ -137,27 +206,15 @@ __global__ void __launch_bounds__(256) k_gen_bound(GenArgs g) {
   const int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (k >= g.M) return;
   const T* Y = reinterpret_cast<const T*>(g.Y) + (int64_t)b * g.held_elems;
-  cdbl m[2 * AM - 1];
-#pragma unroll
-  for (int j = 0; j < 2 * AM - 1; ++j) m[j] = Store<F>::to_d(Y[j * g.M + k]);
-  double v2 = 0.0, hv2 = 0.0;
-#pragma unroll
-  for (int j = 0; j < AM; ++j) v2 += norm2(m[j]);
-#pragma unroll
-  for (int i = 0; i < AM; ++i) {
-    cdbl acc = mk(0.0, 0.0);
-#pragma unroll
-    for (int j = 0; j < AM; ++j) acc = acc + m[i + j] * conjd(m[j]);
-    hv2 += norm2(acc);
-  }
-  g.lbound[(int64_t)b * g.M + k] = v2 > 0.0 ? sqrt(hv2 / v2) : 0.0;
+  g.lbound[(int64_t)b * g.M + k] = bin_lower_bound<F, AM>(Y, g.M, k);
 }
 
 // Bins that cannot hold a vote: ||H||_F bounds every singular value of the
 // bin; if it is below tau_L, the K-th largest of the bins' lower bounds of
-// sigma_1 (so tau_L <= the K-th largest singular value of the signal), the
-// vote gives the bin nothing.  Every bin's singular values are cleared
-// here; the others are queued for k_gen_svals (warp-aggregated).
+// sigma_1 (so tau_L <= the K-th largest singular value of the signal, up to
+// the rounding the margin covers), the vote gives the bin nothing.  Every
+// bin's singular values are cleared here; the others are queued for
+// k_gen_svals (warp-aggregated).
 template <class F, int AM>
 __global__ void __launch_bounds__(256) k_gen_prune(GenArgs g) {
   typedef typename Store<F>::T T;
@@ -173,11 +230,8 @@ __global__ void __launch_bounds__(256) k_gen_prune(GenArgs g) {
     keep = g.lbound[(int64_t)b * g.M + k] >= tau;
     if (!keep) {
       const T* Y = reinterpret_cast<const T*>(g.Y) + (int64_t)b * g.held_elems;
-      cdbl m[2 * AM - 1];
-#pragma unroll
-      for (int j = 0; j < 2 * AM - 1; ++j) m[j] = Store<F>::to_d(Y[j * g.M + k]);
-      const double u = sqrt(hankel_frob2<AM>(m));
-      keep = u * (1.0 + 1e-12) >= tau && u > 0.0;
+      const double u = bin_upper_bound<F, AM>(Y, g.M, k);
+      keep = u * (1.0 + prune_margin<F>()) >= tau && u > 0.0;
     }
   }
   queue_push(keep, b, (int)k, g.svq, g.svq_count);
@@ -332,31 +386,35 @@ __global__ void __launch_bounds__(1024) k_gen_vote(GenArgs g) {
   }
 }
 
+// Subspace Pursuit on at most C = 2 a_k candidate columns and 16 rows; the
+// arrays are sized by C so that a one-alias bin keeps a small frame.
+//
 // least squares on the columns T (ascending) of Phi (rows x cols, row-major
 // in phi), normal equations by Gaussian elimination with partial pivoting;
 // returns |y - Phi_T x|^2 or -1 when singular
+template <int C>
 __device__ double ls_cols(int rows, int cols, const cdbl* phi, const cdbl* y, const int* T, int nT,
                           cdbl* x, cdbl* res) {
-  cdbl G[64], gv[8];
+  cdbl G[C * C], gv[C];
   for (int u = 0; u < nT; ++u) {
     gv[u] = mk(0.0, 0.0);
-    for (int v = 0; v < nT; ++v) G[u * 8 + v] = mk(0.0, 0.0);
+    for (int v = 0; v < nT; ++v) G[u * C + v] = mk(0.0, 0.0);
     for (int i = 0; i < rows; ++i) {
       const cdbl cu = conjd(phi[i * cols + T[u]]);
       gv[u] = gv[u] + cu * y[i];
-      for (int v = 0; v < nT; ++v) G[u * 8 + v] = G[u * 8 + v] + cu * phi[i * cols + T[v]];
+      for (int v = 0; v < nT; ++v) G[u * C + v] = G[u * C + v] + cu * phi[i * cols + T[v]];
     }
   }
   double amax2 = 0.0;
   for (int u = 0; u < nT; ++u)
-    for (int v = 0; v < nT; ++v) amax2 = fmax(amax2, norm2(G[u * 8 + v]));
+    for (int v = 0; v < nT; ++v) amax2 = fmax(amax2, norm2(G[u * C + v]));
   if (!(amax2 > 0.0)) return -1.0;
-  cdbl inv[8];
+  cdbl inv[C];
   for (int c = 0; c < nT; ++c) {
     int piv = c;
-    double best = norm2(G[c * 8 + c]);
+    double best = norm2(G[c * C + c]);
     for (int rr = c + 1; rr < nT; ++rr) {
-      const double v = norm2(G[rr * 8 + c]);
+      const double v = norm2(G[rr * C + c]);
       if (v > best) {
         best = v;
         piv = rr;
@@ -365,24 +423,24 @@ __device__ double ls_cols(int rows, int cols, const cdbl* phi, const cdbl* y, co
     if (!(best > 1e-28 * amax2)) return -1.0;
     if (piv != c) {
       for (int q = 0; q < nT; ++q) {
-        const cdbl t = G[c * 8 + q];
-        G[c * 8 + q] = G[piv * 8 + q];
-        G[piv * 8 + q] = t;
+        const cdbl t = G[c * C + q];
+        G[c * C + q] = G[piv * C + q];
+        G[piv * C + q] = t;
       }
       const cdbl t = gv[c];
       gv[c] = gv[piv];
       gv[piv] = t;
     }
-    inv[c] = crcp(G[c * 8 + c]);
+    inv[c] = crcp(G[c * C + c]);
     for (int rr = c + 1; rr < nT; ++rr) {
-      const cdbl f = G[rr * 8 + c] * inv[c];
-      for (int q = c + 1; q < nT; ++q) G[rr * 8 + q] = G[rr * 8 + q] - f * G[c * 8 + q];
+      const cdbl f = G[rr * C + c] * inv[c];
+      for (int q = c + 1; q < nT; ++q) G[rr * C + q] = G[rr * C + q] - f * G[c * C + q];
       gv[rr] = gv[rr] - f * gv[c];
     }
   }
   for (int rr = nT - 1; rr >= 0; --rr) {
     cdbl acc = gv[rr];
-    for (int q = rr + 1; q < nT; ++q) acc = acc - G[rr * 8 + q] * x[q];
+    for (int q = rr + 1; q < nT; ++q) acc = acc - G[rr * C + q] * x[q];
     x[rr] = acc * inv[rr];
   }
   double rn = 0.0;
@@ -413,16 +471,17 @@ __device__ int top_ks(int n, const double* v, unsigned allowed, int ks, int* out
   return cnt;
 }
 
-// Subspace Pursuit (Dai and Dai 2009) on Phi (rows x cols), sparsity ks:
-// T = ks columns most correlated with y; repeat: T' = T + the ks columns
-// most correlated with the residual, least squares on T', keep its ks
-// largest coefficients, least squares again; stop when the residual does
-// not shrink.  Writes the support and the coefficients; returns |T|.
+// Subspace Pursuit (Dai and Dai 2009) on Phi (rows x cols, cols <= C),
+// sparsity ks: T = ks columns most correlated with y; repeat: T' = T + the
+// ks columns most correlated with the residual, least squares on T', keep
+// its ks largest coefficients, least squares again; stop when the residual
+// does not shrink.  Writes the support and the coefficients; returns |T|.
+template <int C>
 __device__ int subspace_pursuit(int rows, int cols, const cdbl* phi, const cdbl* y, int ks,
                                 int iters, int* T, cdbl* x) {
   const unsigned all = (cols >= 32) ? 0xffffffffu : ((1u << cols) - 1u);
-  double corr[16];
-  cdbl res[16], xn[8], resn[16];
+  double corr[C];
+  cdbl res[16], xn[C], resn[16];
   if (ks > cols) ks = cols;
   for (int j = 0; j < cols; ++j) {
     cdbl c = mk(0.0, 0.0);
@@ -430,7 +489,7 @@ __device__ int subspace_pursuit(int rows, int cols, const cdbl* phi, const cdbl*
     corr[j] = norm2(c);
   }
   int nT = top_ks(cols, corr, all, ks, T);
-  double rn = ls_cols(rows, cols, phi, y, T, nT, x, res);
+  double rn = ls_cols<C>(rows, cols, phi, y, T, nT, x, res);
   if (rn < 0.0) return 0;
   for (int it = 0; it < iters; ++it) {
     for (int j = 0; j < cols; ++j) {
@@ -438,22 +497,22 @@ __device__ int subspace_pursuit(int rows, int cols, const cdbl* phi, const cdbl*
       for (int i = 0; i < rows; ++i) c = c + conjd(phi[i * cols + j]) * res[i];
       corr[j] = norm2(c);
     }
-    int add[8];
+    int add[C];
     const int na = top_ks(cols, corr, all, ks, add);
     unsigned in2 = 0u;
     for (int u = 0; u < nT; ++u) in2 |= 1u << T[u];
     for (int u = 0; u < na; ++u) in2 |= 1u << add[u];
-    int T2[16], n2 = 0;
+    int T2[C], n2 = 0;
     for (int j = 0; j < cols; ++j)
       if ((in2 >> j) & 1u) T2[n2++] = j;
-    cdbl x2[16], r2[16];
-    if (ls_cols(rows, cols, phi, y, T2, n2, x2, r2) < 0.0) break;
-    double mag[16];
+    cdbl x2[C], r2[16];
+    if (ls_cols<C>(rows, cols, phi, y, T2, n2, x2, r2) < 0.0) break;
+    double mag[C];
     for (int j = 0; j < cols; ++j) mag[j] = 0.0;
     for (int u = 0; u < n2; ++u) mag[T2[u]] = norm2(x2[u]);
-    int Tn[8];
+    int Tn[C];
     const int nn = top_ks(cols, mag, in2, ks, Tn);
-    const double rnn = ls_cols(rows, cols, phi, y, Tn, nn, xn, resn);
+    const double rnn = ls_cols<C>(rows, cols, phi, y, Tn, nn, xn, resn);
     if (rnn < 0.0 || rnn >= rn) break;
     nT = nn;
     for (int u = 0; u < nT; ++u) {
@@ -490,8 +549,8 @@ __device__ void solve_bin(const GenArgs& g, int b, int64_t k, int e) {
   const int r = g.r;
   cdbl y[16];
   for (int j = 0; j < r; ++j) y[j] = Store<F>::to_d(Y[(2 * g.a_max + j) * M + k]);
-  int64_t s_out[8];
-  cdbl p_out[8];
+  int64_t s_out[2 * A];
+  cdbl p_out[2 * A];
   int nout = 0;
   cdbl m[2 * A];
 #pragma unroll
@@ -506,9 +565,9 @@ __device__ void solve_bin(const GenArgs& g, int b, int64_t k, int e) {
   }
   if (solve_small<A>(H, rhs, c)) {
     // (b)-(c): |P~(z)| at every z = omega^{k + tM} of U_k; keep the smallest
-    const int nk = (int)min((int64_t)min(g.keep * A, 8), d);
-    double bv[8];
-    int bt[8];
+    const int nk = (int)min((int64_t)min(g.keep * A, 2 * A), d);
+    double bv[2 * A];
+    int bt[2 * A];
     int have = 0;
     for (int64_t t = 0; t < d; ++t) {
       const cdbl z = omega_pow(g.om, k + t * M);
@@ -535,13 +594,13 @@ __device__ void solve_bin(const GenArgs& g, int b, int64_t k, int e) {
         bt[j] = bt[j - 1];
         bt[j - 1] = tt;
       }
-    cdbl phi[16 * 8];
+    cdbl phi[16 * 2 * A];
     for (int j = 0; j < r; ++j)
       for (int u = 0; u < have; ++u)
         phi[j * have + u] = omega_pow(g.om, (k + (int64_t)bt[u] * M) * g.cs[j]);
-    int Tsup[8];
-    cdbl xs[8];
-    const int nz = subspace_pursuit(r, have, phi, y, A, g.sp_iters, Tsup, xs);
+    int Tsup[2 * A];
+    cdbl xs[2 * A];
+    const int nz = subspace_pursuit<2 * A>(r, have, phi, y, A, g.sp_iters, Tsup, xs);
     for (int u = 0; u < nz; ++u) {
       if (xs[u].x == 0.0 && xs[u].y == 0.0) continue;
       s_out[nout] = k + (int64_t)bt[Tsup[u]] * M;
@@ -554,20 +613,20 @@ __device__ void solve_bin(const GenArgs& g, int b, int64_t k, int e) {
   // the plain solution's
   if (g.prop != nullptr) {
     const int16_t* pr = g.prop + (int64_t)e * 8;
-    int ct[8];
+    int ct[2 * A];
     int nc = 0;
-    for (int u = 0; u < 8; ++u)
+    for (int u = 0; u < 8 && nc < 2 * A; ++u)
       if (pr[u] >= 0) ct[nc++] = pr[u];
     if (nc > 0) {
-      cdbl phi2[16 * 8];
+      cdbl phi2[16 * 2 * A];
       for (int j = 0; j < r; ++j)
         for (int u = 0; u < nc; ++u)
           phi2[j * nc + u] = omega_pow(g.om, (k + (int64_t)ct[u] * M) * g.cs[j]);
-      int T2[8];
-      cdbl x2[8];
-      const int nz2 = subspace_pursuit(r, nc, phi2, y, A, g.sp_iters, T2, x2);
-      int64_t s2[8];
-      cdbl p2[8];
+      int T2[2 * A];
+      cdbl x2[2 * A];
+      const int nz2 = subspace_pursuit<2 * A>(r, nc, phi2, y, A, g.sp_iters, T2, x2);
+      int64_t s2[2 * A];
+      cdbl p2[2 * A];
       int n2 = 0;
       for (int u = 0; u < nz2; ++u) {
         if (x2[u].x == 0.0 && x2[u].y == 0.0) continue;
@@ -593,19 +652,15 @@ __device__ void solve_bin(const GenArgs& g, int b, int64_t k, int e) {
             reinterpret_cast<T*>(g.slot_p) + (int64_t)b * g.M * 4, g.flags + b);
 }
 
-template <class F>
+// One kernel per alias count A, each taking the queued bins with a_k = A
+// (grid-stride over the queue), so that every A has its own frame and
+// register budget.
+template <class F, int A>
 __global__ void __launch_bounds__(128) k_gen_solve(GenArgs g) {
   const int n = *g.qcount;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     const int2 q = g.queue[e];
-    const int a = g.ak[(int64_t)q.x * g.M + q.y];
-    switch (a) {
-      case 1: solve_bin<F, 1>(g, q.x, q.y, e); break;
-      case 2: solve_bin<F, 2>(g, q.x, q.y, e); break;
-      case 3: solve_bin<F, 3>(g, q.x, q.y, e); break;
-      case 4: solve_bin<F, 4>(g, q.x, q.y, e); break;
-      default: break;
-    }
+    if (g.ak[(int64_t)q.x * g.M + q.y] == A) solve_bin<F, A>(g, q.x, q.y, e);
   }
 }
 
@@ -675,7 +730,10 @@ static void general_solve(sft_plan_s* P, int64_t B, int nsm, cudaStream_t st, co
   const unsigned dgrid =
       (unsigned)std::max<int64_t>(1, std::min<int64_t>((maxq + 127) / 128, (int64_t)P->dec_ctas_per_sm * nsm));
   stage_begin(P, "gen_solve", st);
-  k_gen_solve<F><<<dgrid, 128, 0, st>>>(g);
+  k_gen_solve<F, 1><<<dgrid, 128, 0, st>>>(g);
+  if (P->p.a_max >= 2) k_gen_solve<F, 2><<<dgrid, 128, 0, st>>>(g);
+  if (P->p.a_max >= 3) k_gen_solve<F, 3><<<dgrid, 128, 0, st>>>(g);
+  if (P->p.a_max >= 4) k_gen_solve<F, 4><<<dgrid, 128, 0, st>>>(g);
   stage_end(P, st);
 }
 
