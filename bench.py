@@ -388,11 +388,25 @@ def timed_steps(torch, step, steps, flush, stream, clocks=None):
 
 
 def max_over_ranks(torch, dist, ws, v):
+    """The largest of every rank's v (the job's time is its slowest rank's);
+    on the process group's own device (CUDA for NCCL, host for gloo)."""
     if ws == 1:
         return v
-    t = torch.tensor([v], device="cuda", dtype=torch.float64)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], device=dev, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_seed0(rank: int) -> int:
+    """First signal seed of a rank's batch: replicas transform disjoint
+    seeded signals (at most 10^6 per rank)."""
+    return 1_000_000 * (rank + 1)
+
+
+def job_value(ws: int, per_rank_signals: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank's signals over the slowest rank's time."""
+    return ws * per_rank_signals * steps / (max_ms / 1e3)
 
 
 def snr_out(x, idx, val):
@@ -534,7 +548,7 @@ def run_plan_workload(args, wl):
     torch.cuda.set_device(local)
     build()
     B = args.batch or wl.batch
-    x_np, supps = gen_batch(wl, B, 1_000_000 * (rank + 1))
+    x_np, supps = gen_batch(wl, B, rank_seed0(rank))
     tdt = torch.complex128 if wl.precision == "fp64" else torch.complex64
     pinned = torch.empty((B, wl.N), dtype=tdt, pin_memory=True)
     pinned.numpy()[:] = x_np
@@ -575,7 +589,7 @@ def run_plan_workload(args, wl):
     stages = plan.stage_times()
     plan.set_profiling(False)
     ms = max_over_ranks(torch, dist, ws, ms)
-    value = ws * B * args.steps / (ms / 1e3)
+    value = job_value(ws, B, args.steps, ms)
     launches = plan.launches_per_call * args.steps
 
     cnt = out.count.cpu().numpy()

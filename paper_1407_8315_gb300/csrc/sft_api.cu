@@ -221,10 +221,6 @@ sft_status sft_plan_create(const sft_params* pin, int64_t max_signals, sft_plan_
   sft_status st = validate(p);
   if (st != SFT_OK) return st;
   sft_plan_s* P = new (std::nothrow) sft_plan_s();
-  if (P) {
-    const char* pts = std::getenv("SFT_FFT_POINTS");  // FFT shape under evaluation
-    if (pts && std::atoi(pts) == 8) P->fft_pts = 8;
-  }
   if (!P) return SFT_ENOMEM;
   P->p = p;
   P->max_signals = max_signals;

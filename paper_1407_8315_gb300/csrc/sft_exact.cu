@@ -619,7 +619,8 @@ int launches_per_call(const sft_plan_s* P) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int fin = fin_single(P, P->max_signals, nsm) ? 1 : 2;
   if (P->p.mode == SFT_GENERAL)
-    return 2 * (P->M0 > kFft4Points ? 2 : 1) + 5 + P->p.a_max + (P->mlp != nullptr ? 1 : 0) + fin;
+    return 2 * (P->M0 > kFft4Points ? 2 : 1) + 5 + (P->p.a_max >= 2 ? 2 : 1) +
+           (P->mlp != nullptr ? 1 : 0) + fin;
   if (P->p.mode == SFT_EXACT_FIXED) return (P->M0 > kFft4Points ? 2 : 1) + 1 + P->p.a_max + fin;
   int fft = 0;
   for (int l = 0; l < P->levels; ++l) fft += (P->M0 >> l) > kFft4Points ? 2 : 1;

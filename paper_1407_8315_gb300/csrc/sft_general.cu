@@ -15,7 +15,8 @@
 //                  select on their FP64 bit patterns, ties to the lower
 //                  index) vote a_k per bin (lines 16-21); bins with a_k > 0
 //                  are queued
-//   k_gen_solve    per queued bin (one kernel per a_k): the a_k x a_k Hankel locator, |P~| at all
+//   k_gen_solve1,  per voted bin (one-alias bins, then the others): the a_k x a_k
+//   _multi         Hankel locator, |P~| at all
 //                  d candidates of U_k with the 2 a_k smallest kept (pruning
 //                  Steps 2-3), Subspace Pursuit on the pruned sensing matrix
 //                  Phi_p (Parts 3-4, lines 22-29)
@@ -51,6 +52,10 @@ struct GenArgs {
   double* lbound;       // [B][M]: per-bin lower bound of sigma_1
   int2* svq;            // bins whose singular values are computed
   int* svq_count;
+  // voted bins: a_k = 1 filed from the front of `queue` (count *qcount),
+  // a_k >= 2 from the back (count *qcount_hi, entry i at qcap - 1 - i)
+  int* qcount_hi;
+  int64_t qcap;
 };
 
 // One-sided Jacobi on the n x n Hankel H_ij = m_{i+j}: rotate column pairs
@@ -382,7 +387,10 @@ __global__ void __launch_bounds__(1024) k_gen_vote(GenArgs g) {
       }
     }
     ak[k] = (uint8_t)a;
-    if (a > 0) g.queue[atomicAdd(g.qcount, 1)] = make_int2(b, (int)k);
+    if (a == 1)
+      g.queue[atomicAdd(g.qcount, 1)] = make_int2(b, (int)k);
+    else if (a > 1)
+      g.queue[g.qcap - 1 - atomicAdd(g.qcount_hi, 1)] = make_int2(b, (int)k);
   }
 }
 
@@ -652,15 +660,29 @@ __device__ void solve_bin(const GenArgs& g, int b, int64_t k, int e) {
             reinterpret_cast<T*>(g.slot_p) + (int64_t)b * g.M * 4, g.flags + b);
 }
 
-// One kernel per alias count A, each taking the queued bins with a_k = A
-// (grid-stride over the queue), so that every A has its own frame and
-// register budget.
-template <class F, int A>
-__global__ void __launch_bounds__(128) k_gen_solve(GenArgs g) {
+// The one-alias bins (the front of the queue; every warp full and of one
+// kind) and the bins with a_k >= 2 (the back of the queue), grid-stride.
+template <class F>
+__global__ void __launch_bounds__(128) k_gen_solve1(GenArgs g) {
   const int n = *g.qcount;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     const int2 q = g.queue[e];
-    if (g.ak[(int64_t)q.x * g.M + q.y] == A) solve_bin<F, A>(g, q.x, q.y, e);
+    solve_bin<F, 1>(g, q.x, q.y, e);
+  }
+}
+
+template <class F>
+__global__ void __launch_bounds__(128) k_gen_solve_multi(GenArgs g) {
+  const int n = *g.qcount_hi;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int e = (int)(g.qcap - 1 - i);
+    const int2 q = g.queue[e];
+    switch (g.ak[(int64_t)q.x * g.M + q.y]) {
+      case 2: solve_bin<F, 2>(g, q.x, q.y, e); break;
+      case 3: solve_bin<F, 3>(g, q.x, q.y, e); break;
+      case 4: solve_bin<F, 4>(g, q.x, q.y, e); break;
+      default: break;
+    }
   }
 }
 
@@ -682,7 +704,7 @@ static GenArgs general_front(sft_plan_s* P, int64_t B, const void* x, int64_t x_
             W.queue[0], W.qcount, P->tab.cs_shifts, P->K_table, W.slot_cnt, W.slot_s, W.slot_p,
             W.flags, OmegaTab{P->tab.om_hi, P->tab.om_lo, P->tab.om_lo_bits, P->p.N - 1},
             nullptr, reinterpret_cast<double*>(W.ymax2), reinterpret_cast<double*>(W.slot_s),
-            W.queue[1], W.qcount + 1};
+            W.queue[1], W.qcount + 1, W.qcount + 2, B * P->M0};
   dim3 sgrid((unsigned)((P->M0 + 255) / 256), (unsigned)B);
   stage_begin(P, "gen_bound", st);
   switch (am) {
@@ -730,10 +752,8 @@ static void general_solve(sft_plan_s* P, int64_t B, int nsm, cudaStream_t st, co
   const unsigned dgrid =
       (unsigned)std::max<int64_t>(1, std::min<int64_t>((maxq + 127) / 128, (int64_t)P->dec_ctas_per_sm * nsm));
   stage_begin(P, "gen_solve", st);
-  k_gen_solve<F, 1><<<dgrid, 128, 0, st>>>(g);
-  if (P->p.a_max >= 2) k_gen_solve<F, 2><<<dgrid, 128, 0, st>>>(g);
-  if (P->p.a_max >= 3) k_gen_solve<F, 3><<<dgrid, 128, 0, st>>>(g);
-  if (P->p.a_max >= 4) k_gen_solve<F, 4><<<dgrid, 128, 0, st>>>(g);
+  k_gen_solve1<F><<<dgrid, 128, 0, st>>>(g);
+  if (P->p.a_max >= 2) k_gen_solve_multi<F><<<dgrid, 128, 0, st>>>(g);
   stage_end(P, st);
 }
 

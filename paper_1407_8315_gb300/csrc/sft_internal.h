@@ -142,9 +142,10 @@ struct sft_plan_s {
   const int64_t* K_table = nullptr;  // per-signal K for the general vote
   // launch shape chosen by the batch autotuner
   int dec_ctas_per_sm = 8;
-  // points per thread of the one-CTA FFT (16: M/16 threads, radix-16
-  // passes; 8: M/8 threads, radix-8 passes)
-  int fft_pts = 16;
+  // points per thread of the one-CTA FFT (8: M/8 threads, radix-8 passes,
+  // at most 64 registers, twice the resident warps of 16 points per thread;
+  // measured faster on every level of the exact transforms)
+  int fft_pts = 8;
   // learned proposal (general plans): the attached network (not owned) and
   // 8 proposed candidates t per queued bin (int16, -1 = none)
   struct sft_mlp_s* mlp = nullptr;

@@ -160,10 +160,18 @@ struct FeatArgs {
   int64_t held_elems;
   const uint8_t* ak;
   const int2* queue;
-  const int* qcount;
+  const int* qcount;     // entries filed from the front of the queue
+  const int* qcount_hi;  // entries filed from the back (entry i at qcap - 1 - i)
+  int64_t qcap;
   const int64_t* cs;
   OmegaTab om;
 };
+
+// queue position of the i-th voted bin (front entries first, then back)
+__device__ __forceinline__ int queue_pos(const FeatArgs& g, int i) {
+  const int n1 = *g.qcount;
+  return i < n1 ? i : (int)(g.qcap - 1 - (i - n1));
+}
 
 // Features of queue entries e0 .. e0+nt-1 into X (rows beyond nt zero):
 // m~_l = Y_l[k] omega^{-k sh_l} in FP64, rotated by conj(m~_0)/|m~_0| and
@@ -176,7 +184,7 @@ __device__ void tile_features(const FeatArgs& g, int e0, int nt, FwdSmem& s, int
     const int rr = it / nsyn, l = it - rr * nsyn;
     cdbl v = mk(0.0, 0.0);
     if (rr < nt) {
-      const int2 q = g.queue[e0 + rr];
+      const int2 q = g.queue[queue_pos(g, e0 + rr)];
       const T* Y = reinterpret_cast<const T*>(g.Y) + (int64_t)q.x * g.held_elems;
       const cdbl y = Store<F>::to_d(Y[(int64_t)l * g.M + q.y]);
       const int64_t sh = l < 2 * g.a_max ? (int64_t)l : g.cs[l - 2 * g.a_max];
@@ -218,13 +226,14 @@ __global__ void __launch_bounds__(kThr) k_mlp_propose(FeatArgs g, MlpDims D, Mlp
   const int tid = threadIdx.x;
   load_weights(s.w, D, w, tid);
   __syncthreads();
-  const int n = *g.qcount;
+  const int n = *g.qcount + *g.qcount_hi;
   for (int e0 = blockIdx.x * kRows; e0 < n; e0 += gridDim.x * kRows) {
     const int nt = min(kRows, n - e0);
     tile_features<F>(g, e0, nt, s, tid);
     forward_tile(s.w, D, s.X, s.A1, s.A2, s.Z, tid);
     if (tid < nt) {
-      const int2 q = g.queue[e0 + tid];
+      const int pos = queue_pos(g, e0 + tid);
+      const int2 q = g.queue[pos];
       const int a = g.ak[(int64_t)q.x * g.M + q.y];
       const int nk = (int)min((int64_t)min(2 * a, 8), g.d);
       float bv[8];
@@ -251,7 +260,7 @@ __global__ void __launch_bounds__(kThr) k_mlp_propose(FeatArgs g, MlpDims D, Mlp
           bt[j] = bt[j - 1];
           bt[j - 1] = tt;
         }
-      int16_t* o = prop + (int64_t)(e0 + tid) * 8;
+      int16_t* o = prop + (int64_t)pos * 8;
       for (int u = 0; u < 8; ++u) o[u] = u < have ? (int16_t)bt[u] : (int16_t)-1;
     }
     __syncthreads();
@@ -265,7 +274,7 @@ __global__ void __launch_bounds__(kThr) k_mlp_features(FeatArgs g, int n_in, int
   extern __shared__ __align__(16) char smem_raw[];
   FwdSmem& s = *reinterpret_cast<FwdSmem*>(smem_raw);
   const int tid = threadIdx.x;
-  const int n = (int)min((int64_t)*g.qcount, cap);
+  const int n = (int)min((int64_t)*g.qcount + *g.qcount_hi, cap);
   for (int e0 = blockIdx.x * kRows; e0 < n; e0 += gridDim.x * kRows) {
     const int nt = min(kRows, n - e0);
     tile_features<F>(g, e0, nt, s, tid);
@@ -274,7 +283,7 @@ __global__ void __launch_bounds__(kThr) k_mlp_features(FeatArgs g, int n_in, int
       feat[(int64_t)(e0 + rr) * n_in + c] = s.X[rr * kMaxIn + c];
     }
     if (tid < nt) {
-      const int2 q = g.queue[e0 + tid];
+      const int2 q = g.queue[queue_pos(g, e0 + tid)];
       int32_t* o = rows + (int64_t)(e0 + tid) * 3;
       o[0] = q.x;
       o[1] = q.y;
@@ -568,11 +577,11 @@ void refresh_half(sft_mlp_s* m, cudaStream_t st) {
   sft::k_mlp_to_half<<<64, 256, 0, st>>>(m->D, m->master, m->w16);
 }
 
-sft::FeatArgs feat_args(const sft_plan_s* P) {
+sft::FeatArgs feat_args(const sft_plan_s* P, int64_t B) {
   const sft::Workspace& W = P->ws;
   return sft::FeatArgs{P->p.N,        P->M0,     P->p.d,      P->p.a_max,
                        P->p.n_cs_shifts, W.held[0], W.held_elems, W.T[0],
-                       W.queue[0],    W.qcount,  P->tab.cs_shifts,
+                       W.queue[0],    W.qcount,  W.qcount + 2, B * P->M0, P->tab.cs_shifts,
                        sft::OmegaTab{P->tab.om_hi, P->tab.om_lo, P->tab.om_lo_bits, P->p.N - 1}};
 }
 
@@ -586,10 +595,10 @@ void mlp_propose(sft_plan_s* P, int64_t B, int nsm, cudaStream_t st) {
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((maxq + kRows - 1) / kRows, nsm));
   stage_begin(P, "mlp_propose", st);
   if (P->p.precision == SFT_FP64)
-    k_mlp_propose<F64><<<grid, kThr, sizeof(FwdSmem), st>>>(feat_args(P), m->D, weights_of(m),
+    k_mlp_propose<F64><<<grid, kThr, sizeof(FwdSmem), st>>>(feat_args(P, B), m->D, weights_of(m),
                                                              P->mlp_prop);
   else
-    k_mlp_propose<FF><<<grid, kThr, sizeof(FwdSmem), st>>>(feat_args(P), m->D, weights_of(m),
+    k_mlp_propose<FF><<<grid, kThr, sizeof(FwdSmem), st>>>(feat_args(P, B), m->D, weights_of(m),
                                                             P->mlp_prop);
   stage_end(P, st);
 }
@@ -601,9 +610,9 @@ void mlp_features(sft_plan_s* P, int64_t B, int nsm, float* feat, int32_t* rows,
   if (maxq <= 0) return;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((maxq + kRows - 1) / kRows, nsm));
   if (P->p.precision == SFT_FP64)
-    k_mlp_features<F64><<<grid, kThr, sizeof(FwdSmem), st>>>(feat_args(P), n_in, cap_rows, feat, rows);
+    k_mlp_features<F64><<<grid, kThr, sizeof(FwdSmem), st>>>(feat_args(P, B), n_in, cap_rows, feat, rows);
   else
-    k_mlp_features<FF><<<grid, kThr, sizeof(FwdSmem), st>>>(feat_args(P), n_in, cap_rows, feat, rows);
+    k_mlp_features<FF><<<grid, kThr, sizeof(FwdSmem), st>>>(feat_args(P, B), n_in, cap_rows, feat, rows);
 }
 
 }  // namespace sft
@@ -855,11 +864,11 @@ sft_status sft_mlp_features(sft_plan_t P, int64_t n, const void* x, int64_t x_st
     sft::launch_general_features(P, n, x, x_stride, num_sms(), feat, rows, cap_rows, st);
     e = cudaGetLastError();
   }
-  int q = 0;
-  if (!e) e = cudaMemcpyAsync(&q, P->ws.qcount, sizeof(int), cudaMemcpyDeviceToHost, st);
+  int q[3] = {0, 0, 0};  // voted bins: front (one alias), -, back (several)
+  if (!e) e = cudaMemcpyAsync(q, P->ws.qcount, sizeof(q), cudaMemcpyDeviceToHost, st);
   if (!e) e = cudaStreamSynchronize(st);
   if (e) return cuda_fail(e);
-  *n_rows = q;
+  *n_rows = (int64_t)q[0] + q[2];
   return SFT_OK;
 }
 
