@@ -75,7 +75,8 @@ cudaError_t dalloc(T** ptr, size_t count, size_t* total) {
 
 void free_plan_memory(sft_plan_s* P) {
   void* ptrs[] = {P->tab.om_hi, P->tab.om_lo,    P->tab.tw,  P->tab.om_hi_ff, P->tab.om_lo_ff,
-                  P->tab.cs_shifts, P->ws_base, P->x_stage, P->r_stage, P->mlp_prop};
+                  P->tab.cs_shifts, P->tab.xc_shifts, P->ws_base, P->x_stage, P->r_stage,
+                  P->mlp_prop};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -122,6 +123,23 @@ cudaError_t upload_tables(sft_plan_s* P, size_t* total) {
     P->cs_host = draw_cs_shifts(P->p.seed, P->p.d, P->p.n_cs_shifts);
     if ((e = dalloc(&P->tab.cs_shifts, P->cs_host.size(), total)) != cudaSuccess) return e;
     if ((e = cudaMemcpy(P->tab.cs_shifts, P->cs_host.data(), P->cs_host.size() * sizeof(int64_t),
+                        cudaMemcpyHostToDevice)))
+      return e;
+  }
+  if (P->p.mode != SFT_GENERAL) {
+    // the shifts' row offsets in the compact samples: ITER level l reads
+    // rows 0 and M0 / 2^l of its block; FIXED shift j is row j M0
+    std::vector<int64_t> xs;
+    if (P->p.mode == SFT_EXACT_FIXED) {
+      for (int j = 0; j < 2 * P->p.a_max; ++j) xs.push_back((int64_t)j * P->M0);
+    } else {
+      for (int l = 0; l < P->levels; ++l) {
+        xs.push_back(0);
+        xs.push_back(P->M0 >> l);
+      }
+    }
+    if ((e = dalloc(&P->tab.xc_shifts, xs.size(), total)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(P->tab.xc_shifts, xs.data(), xs.size() * sizeof(int64_t),
                         cudaMemcpyHostToDevice)))
       return e;
   }
@@ -173,14 +191,15 @@ cudaError_t upload_tables(sft_plan_s* P, size_t* total) {
 }
 
 cudaError_t alloc_workspace(sft_plan_s* P, size_t* total) {
+  const int esize = P->p.precision == SFT_FP64 ? 16 : 8;
   const size_t bytes = sft::layout_workspace(nullptr, nullptr, P->max_signals, P->M0, P->p.mode,
-                                             P->p.a_max, P->p.n_cs_shifts);
+                                             P->p.a_max, P->p.n_cs_shifts, P->levels, esize);
   char* base = nullptr;
   cudaError_t e = dalloc(&base, bytes, total);
   if (e != cudaSuccess) return e;
   P->ws_base = base;
   sft::layout_workspace(&P->ws, base, P->max_signals, P->M0, P->p.mode, P->p.a_max,
-                        P->p.n_cs_shifts);
+                        P->p.n_cs_shifts, P->levels, esize);
   return cudaSuccess;
 }
 

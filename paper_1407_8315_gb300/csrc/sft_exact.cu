@@ -36,8 +36,8 @@ namespace sft {
 // ----------------------------------------------------------- gather + FFT
 template <class F, int PTS>
 __global__ void __launch_bounds__(8192 / PTS) k_gather_fft(
-    const typename F::In* __restrict__ x, int64_t x_stride, int64_t N, int64_t d, int log2M,
-    int shift0, int log2Mt, const typename F::Tw* __restrict__ tw, void* __restrict__ out_v,
+    const typename F::In* __restrict__ x, int64_t x_stride, int64_t N, int64_t d, int64_t dscale,
+    int log2M, int shift0, int log2Mt, const typename F::Tw* __restrict__ tw, void* __restrict__ out_v,
     int64_t out_sig, int64_t out_row, int row0, unsigned long long* __restrict__ ymax2,
     const int64_t* __restrict__ shift_list, const void* const* __restrict__ x_table) {
   extern __shared__ __align__(16) char smem[];
@@ -71,14 +71,14 @@ __global__ void __launch_bounds__(8192 / PTS) k_gather_fft(
   double lmax = 0.0;
   if constexpr (std::is_same<F, F64>::value) {
     for (int k = tid; k < M; k += nthr) {
-      const double2 w = F::out(F::ld(smem, M, k), (double)d);
+      const double2 w = F::out(F::ld(smem, M, k), (double)dscale);
       o[k] = w;
       lmax = fmax(lmax, w.x * w.x + w.y * w.y);
     }
   } else {
     float fmax_hi = 0.0f;
     for (int k = tid; k < M; k += nthr) {
-      const float4 w = F::out(F::ld(smem, M, k), (float)d);
+      const float4 w = F::out(F::ld(smem, M, k), (float)dscale);
       o[k] = w;
       fmax_hi = fmaxf(fmax_hi, F::out_norm_hi(w));
     }
@@ -98,6 +98,50 @@ __global__ void __launch_bounds__(8192 / PTS) k_gather_fft(
       for (int o2 = 16; o2 > 0; o2 >>= 1) w = fmax(w, __shfl_xor_sync(0xffffffffu, w, o2));
       if (tid == 0) atomicMax(ymax2 + b, (unsigned long long)__double_as_longlong(w));
     }
+  }
+}
+
+// --------------------------------------------------- input extraction
+// The samples every FFT of one call reads, copied once into shift-major
+// contiguous arrays: each row n of the level-0 grid (x[n d .. n d + 2a_m))
+// is read by one thread, so its 64-byte run of shifts 0..7 (complex64)
+// crosses the memory system once instead of once per level; the FFTs then
+// read coalesced.  ITER: level l keeps [2][M_l] at offset
+// sum_{l' < l} 2 M_l', rows n = 2^l n'; FIXED: [2 a_m][M0].
+template <class In>
+__global__ void __launch_bounds__(256) k_extract(const In* __restrict__ x, int64_t x_stride,
+                                                 const void* const* __restrict__ x_table,
+                                                 int64_t N, int64_t d, int64_t M0, int levels,
+                                                 int fixed_nsh, In* __restrict__ C, int64_t c_sig) {
+  const int b = blockIdx.y;
+  const int64_t n = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (n >= M0) return;
+  const In* xs = x_table != nullptr ? reinterpret_cast<const In*>(x_table[b]) : x + (int64_t)b * x_stride;
+  In* cb = C + (int64_t)b * c_sig;
+  In v[8];
+  if (fixed_nsh > 0) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j < fixed_nsh) v[j] = __ldg(xs + ((n * d + j) & (N - 1)));
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j < fixed_nsh) cb[(int64_t)j * M0 + n] = v[j];
+    return;
+  }
+  // rows n with n mod 2^l == 0 feed level l (shifts 2l, 2l+1)
+  const int lv = min(levels, (n == 0 ? 4 : __ffsll(n) - 1 + 1));
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    if (j < 2 * lv) v[j] = __ldg(xs + ((n * d + j) & (N - 1)));
+  int64_t off = 0, Ml = M0;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    if (l < lv) {
+      cb[off + (n >> l)] = v[2 * l];
+      cb[off + Ml + (n >> l)] = v[2 * l + 1];
+    }
+    off += 2 * Ml;
+    Ml >>= 1;
   }
 }
 
@@ -287,11 +331,17 @@ __global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* q
         m[j] = FF::add(FF::from4(prev[j * 2 * M + k]), FF::from4(prev[j * 2 * M + k + M]));
       m[2 * l] = FF::from4(cur[(2 * l) * M + k]);
       m[2 * l + 1] = FF::from4(cur[(2 * l + 1) * M + k]);
-      if (l > 0) {
-        for (int64_t u = 0; u < nsub; ++u) {
-          const int64_t k0 = k + u * M;
-          const int c = cnt[k0];
-          for (int e = 0; e < c; ++e) {
+      if constexpr (l > 0) {
+        // the 2^l level-0 bins folded into k: all counts are loaded before
+        // the first entry, so that the loads of different sub-bins overlap
+        constexpr int NS = 1 << l;
+        int c[NS];
+#pragma unroll
+        for (int u = 0; u < NS; ++u) c[u] = cnt[k + (int64_t)u * M];
+#pragma unroll
+        for (int u = 0; u < NS; ++u) {
+          const int64_t k0 = k + (int64_t)u * M;
+          for (int e = 0; e < c[u]; ++e) {
             const int64_t sl = ss[k0 * 4 + e];
             const FF::V p = FF::from4(sp[k0 * 4 + e]);
             m[2 * l] = FF::sub(m[2 * l], FF::mulv(p, omega_ff(g.omff, sl * (2 * l))));
@@ -621,10 +671,12 @@ int launches_per_call(const sft_plan_s* P) {
   if (P->p.mode == SFT_GENERAL)
     return 2 * (P->M0 > kFft4Points ? 2 : 1) + 5 + (P->p.a_max >= 2 ? 2 : 1) +
            (P->mlp != nullptr ? 1 : 0) + fin;
-  if (P->p.mode == SFT_EXACT_FIXED) return (P->M0 > kFft4Points ? 2 : 1) + 1 + P->p.a_max + fin;
+  const int ext = P->ws.xc != nullptr ? 1 : 0;
+  if (P->p.mode == SFT_EXACT_FIXED)
+    return ext + (P->M0 > kFft4Points ? 2 : 1) + 1 + P->p.a_max + fin;
   int fft = 0;
   for (int l = 0; l < P->levels; ++l) fft += (P->M0 >> l) > kFft4Points ? 2 : 1;
-  return fft + 2 * P->levels + fin;
+  return ext + fft + 2 * P->levels + fin;
 }
 
 static cudaEvent_t pool_event(sft_plan_s* P) {
@@ -648,9 +700,18 @@ void stage_end(sft_plan_s* P, cudaStream_t st) {
   cudaEventRecord(P->stage_recs.back().t1, st);
 }
 
+// Where the gather reads: sample n of shift s of signal b is
+// src.x[(n src.d + s) & (src.N - 1)] of that signal (src.table[b], or
+// src.x + b src.stride).
+struct GatherSrc {
+  const void* x;
+  int64_t stride, N, d;
+  const void* const* table;
+};
+
 template <class F>
-void launch_gather_fft(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int64_t d,
-                       int log2M, int shift0, int nshift, void* out, int64_t out_row, int row0,
+void launch_gather_fft(sft_plan_s* P, int64_t B, const GatherSrc& src, int64_t dscale, int log2M,
+                       int shift0, int nshift, void* out, int64_t out_row, int row0,
                        bool want_ymax, cudaStream_t st, const int64_t* shift_list,
                        const char* stage) {
   static const char* names[] = {"gather_fft_l0", "gather_fft_l1", "gather_fft_l2", "gather_fft_l3"};
@@ -658,7 +719,7 @@ void launch_gather_fft(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride
                                  "gather_cols_l3"};
   static const char* rnames[] = {"fft_rows_l0", "fft_rows_l1", "fft_rows_l2", "fft_rows_l3"};
   const int lvl = nshift > 2 ? 0 : shift0 / 2;
-  const auto* xin = reinterpret_cast<const typename F::In*>(x);
+  const auto* xin = reinterpret_cast<const typename F::In*>(src.x);
   const auto* tw = reinterpret_cast<const typename F::Tw*>(P->tab.tw);
   if ((1 << log2M) <= kFft4Points) {
     dim3 grid(nshift, (unsigned)B);
@@ -667,15 +728,17 @@ void launch_gather_fft(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride
     const size_t smem = (size_t)padded(1 << log2M) * F::kBytesPerPoint;
     stage_begin(P, stage ? stage : (nshift > 2 ? "gather_fft_fixed" : names[lvl]), st);
     if (pts == 8)
-      k_gather_fft<F, 8><<<grid, nthr, smem, st>>>(xin, x_stride, P->p.N, d, log2M, shift0,
-                                                   P->log2M0, tw, out, P->ws.held_elems, out_row,
-                                                   row0, want_ymax ? P->ws.ymax2 : nullptr,
-                                                   shift_list, P->x_table);
+      k_gather_fft<F, 8><<<grid, nthr, smem, st>>>(xin, src.stride, src.N, src.d, dscale, log2M,
+                                                   shift0, P->log2M0, tw, out, P->ws.held_elems,
+                                                   out_row, row0,
+                                                   want_ymax ? P->ws.ymax2 : nullptr, shift_list,
+                                                   src.table);
     else
-      k_gather_fft<F, 16><<<grid, nthr, smem, st>>>(xin, x_stride, P->p.N, d, log2M, shift0,
-                                                    P->log2M0, tw, out, P->ws.held_elems, out_row,
-                                                    row0, want_ymax ? P->ws.ymax2 : nullptr,
-                                                    shift_list, P->x_table);
+      k_gather_fft<F, 16><<<grid, nthr, smem, st>>>(xin, src.stride, src.N, src.d, dscale, log2M,
+                                                    shift0, P->log2M0, tw, out, P->ws.held_elems,
+                                                    out_row, row0,
+                                                    want_ymax ? P->ws.ymax2 : nullptr, shift_list,
+                                                    src.table);
     stage_end(P, st);
     return;
   }
@@ -688,12 +751,12 @@ void launch_gather_fft(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride
   const int64_t w_sig = (int64_t)nshift * Mlev;
   stage_begin(P, stage ? stage : cnames[lvl], st);
   k_fft4_cols<F><<<dim3(ctas, nshift, (unsigned)B), 512, smem, st>>>(
-      xin, x_stride, P->p.N, d, log2M1, log2M2, shift0, P->log2M0, tw, W, w_sig, nshift,
-      shift_list, P->x_table);
+      xin, src.stride, src.N, src.d, log2M1, log2M2, shift0, P->log2M0, tw, W, w_sig, nshift,
+      shift_list, src.table);
   stage_end(P, st);
   stage_begin(P, stage ? "fft_rows" : rnames[lvl], st);
   k_fft4_rows<F><<<dim3(ctas, nshift, (unsigned)B), 512, smem, st>>>(
-      W, w_sig, log2M1, log2M2, d, P->log2M0, tw, out, P->ws.held_elems, out_row, row0,
+      W, w_sig, log2M1, log2M2, dscale, P->log2M0, tw, out, P->ws.held_elems, out_row, row0,
       want_ymax ? P->ws.ymax2 : nullptr, shift0);
   stage_end(P, st);
 }
@@ -702,12 +765,25 @@ void launch_gather_fft_any(sft_plan_s* P, int64_t B, const void* x, int64_t x_st
                            int log2M, int shift0, int nshift, void* out, int64_t out_row, int row0,
                            bool want_ymax, cudaStream_t st, const int64_t* shift_list,
                            const char* stage) {
+  const GatherSrc src{x, x_stride, P->p.N, d, P->x_table};
   if (P->p.precision == SFT_FP64)
-    launch_gather_fft<F64>(P, B, x, x_stride, d, log2M, shift0, nshift, out, out_row, row0,
-                           want_ymax, st, shift_list, stage);
+    launch_gather_fft<F64>(P, B, src, d, log2M, shift0, nshift, out, out_row, row0, want_ymax, st,
+                           shift_list, stage);
   else
-    launch_gather_fft<FF>(P, B, x, x_stride, d, log2M, shift0, nshift, out, out_row, row0,
-                          want_ymax, st, shift_list, stage);
+    launch_gather_fft<FF>(P, B, src, d, log2M, shift0, nshift, out, out_row, row0, want_ymax, st,
+                          shift_list, stage);
+}
+
+// Copies the samples of the call into the compact arrays (P->ws.xc).
+template <class F>
+static void launch_extract(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int levels,
+                           int fixed_nsh, cudaStream_t st) {
+  const dim3 grid((unsigned)((P->M0 + 255) / 256), (unsigned)B);
+  stage_begin(P, "extract", st);
+  k_extract<typename F::In><<<grid, 256, 0, st>>>(
+      reinterpret_cast<const typename F::In*>(x), x_stride, P->x_table, P->p.N, P->p.d, P->M0,
+      levels, fixed_nsh, reinterpret_cast<typename F::In*>(P->ws.xc), P->ws.xc_sig);
+  stage_end(P, st);
 }
 
 template <class F>
@@ -715,8 +791,20 @@ static void launch_fixed(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
                          const OmegaTab& om, int nsm, cudaStream_t st) {
   const Workspace& W = P->ws;
   const int nsh = 2 * P->p.a_max;
-  launch_gather_fft<F>(P, B, x, x_stride, P->p.d, P->log2M0, 0, nsh, W.held[0], P->M0, 0, true, st,
-                       nullptr, nullptr);
+  if (W.xc != nullptr) {
+    // rows j M0 .. of the compact array hold shift j (index space rounded
+    // up to a power of two)
+    launch_extract<F>(P, B, x, x_stride, 0, nsh, st);
+    int64_t Nc = P->M0;
+    while (Nc < nsh * P->M0) Nc <<= 1;
+    const GatherSrc src{W.xc, W.xc_sig, Nc, 1, nullptr};
+    launch_gather_fft<F>(P, B, src, P->p.d, P->log2M0, 0, nsh, W.held[0], P->M0, 0, true, st,
+                         P->tab.xc_shifts, nullptr);
+  } else {
+    const GatherSrc src{x, x_stride, P->p.N, P->p.d, P->x_table};
+    launch_gather_fft<F>(P, B, src, P->p.d, P->log2M0, 0, nsh, W.held[0], P->M0, 0, true, st,
+                         nullptr, nullptr);
+  }
   FixedArgs g{P->p.N, P->M0, P->p.d, P->p.a_max, W.held[0], W.held_elems, W.T[0], W.slot_cnt,
               W.slot_s, W.slot_p, W.ymax2, W.flags, P->p.zero_tol, P->p.root_tol,
               P->p.res_tol, om};
@@ -777,17 +865,28 @@ static void launch_iter(sft_plan_s* P, int64_t B, const void* x, int64_t x_strid
                         const uint8_t** T_last) {
   const Workspace& W = P->ws;
   const OmegaTabFF omff{P->tab.om_hi_ff, P->tab.om_lo_ff, P->tab.om_lo_bits, P->p.N - 1};
-  int64_t M = P->M0, d = P->p.d;
+  int64_t M = P->M0, d = P->p.d, xc_off = 0;
+  if (W.xc != nullptr) launch_extract<F>(P, B, x, x_stride, P->levels, 0, st);
   for (int l = 0; l < P->levels; ++l) {
     if (l > 0) {
+      xc_off += 2 * M;
       M >>= 1;
       d <<= 1;
     }
     const int log2M = P->log2M0 - l;
     void* cur = W.held[l & 1];
     const void* prev = W.held[(l + 1) & 1];
-    launch_gather_fft<F>(P, B, x, x_stride, d, log2M, 2 * l, 2, cur, M, 2 * l, l == 0, st, nullptr,
-                         nullptr);
+    if (W.xc != nullptr) {
+      // level l's two shifts are rows 0 and M of its block
+      const GatherSrc src{reinterpret_cast<const typename F::In*>(W.xc) + xc_off, W.xc_sig, 2 * M,
+                          1, nullptr};
+      launch_gather_fft<F>(P, B, src, d, log2M, 2 * l, 2, cur, M, 2 * l, l == 0, st,
+                           P->tab.xc_shifts + 2 * l, nullptr);
+    } else {
+      const GatherSrc src{x, x_stride, P->p.N, d, P->x_table};
+      launch_gather_fft<F>(P, B, src, d, log2M, 2 * l, 2, cur, M, 2 * l, l == 0, st, nullptr,
+                           nullptr);
+    }
     LevelArgs g{P->p.N, M, d, P->M0, prev, cur, W.held_elems, W.T[(l + 1) & 1], W.T[l & 1],
                 W.slot_cnt, W.slot_s, W.slot_p, W.ymax2, W.flags, P->p.zero_tol,
                 P->p.root_tol, P->p.res_tol, om, omff};

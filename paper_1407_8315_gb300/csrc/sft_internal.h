@@ -38,12 +38,18 @@ struct Workspace {
   size_t zero_bytes = 0;
   void* fft4 = nullptr;  // four-step FFT intermediate (only when N/d > 8192)
   double* sv = nullptr;  // general path: a_m singular values per bin
+  void* xc = nullptr;    // exact paths: the call's samples, shift-major (input type)
+  int64_t xc_sig = 0;    // elements of xc per signal
 };
 
 // Lays the workspace of B signals out from `base` (or only sizes it when
 // base is null) and returns its byte size; every array is 256-byte aligned.
+//
+// With xc_esize > 0 (exact modes; the input element size) the workspace also
+// holds the compact copy of the samples each call reads: ITER, `levels`
+// blocks [2][M0 / 2^l]; FIXED, [2 a_max][M0].
 inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, int mode,
-                               int a_max, int n_cs = 0) {
+                               int a_max, int n_cs = 0, int levels = 0, int xc_esize = 0) {
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
   const int64_t held_elems = mode == SFT_EXACT_FIXED ? 2 * a_max * M0
                              : mode == SFT_GENERAL   ? (2 * a_max + n_cs) * M0
@@ -77,6 +83,13 @@ inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, 
                                           : 2;
   const size_t o_f4 = off;
   if (M0 > 8192) off = al(off + (size_t)(B * nsh * M0) * 16);
+  // compact samples of the exact modes
+  int64_t xc_sig = 0;
+  if (xc_esize > 0 && mode == SFT_EXACT_FIXED) xc_sig = 2 * a_max * M0;
+  if (xc_esize > 0 && mode == SFT_EXACT_ITER)
+    for (int l = 0; l < levels; ++l) xc_sig += 2 * (M0 >> l);
+  const size_t o_xc = off;
+  if (xc_sig > 0) off = al(off + (size_t)(B * xc_sig) * (size_t)xc_esize);
   if (W != nullptr && base != nullptr) {
     W->held_elems = held_elems;
     for (int i = 0; i < 2; ++i) {
@@ -95,6 +108,8 @@ inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, 
     W->slot_p = base + o_sp;
     W->fft4 = M0 > 8192 ? base + o_f4 : nullptr;
     W->sv = mode == SFT_GENERAL ? reinterpret_cast<double*>(base + o_sv) : nullptr;
+    W->xc = xc_sig > 0 ? base + o_xc : nullptr;
+    W->xc_sig = xc_sig;
   }
   return off;
 }
@@ -107,6 +122,7 @@ struct Tables {
   float4* om_hi_ff = nullptr;  // the omega tables as float-float (mixed path only)
   float4* om_lo_ff = nullptr;
   int64_t* cs_shifts = nullptr;  // general path: the r random shifts n_l (device)
+  int64_t* xc_shifts = nullptr;  // exact paths: row offsets of the shifts in the compact samples
 };
 
 }  // namespace sft
