@@ -106,17 +106,39 @@ class W:
         the input bytes it must read, and the FFT's radix-2 butterflies at
         their float-float cost in FP32 instructions (68 each: one complex
         float-float multiply, 36, and two complex float-float additions, 16
-        each).  None for other stages."""
-        if stage.startswith("gather_fft_l") or stage.startswith("gather_cols_l"):
+        each).  Above 8192 points the FFT runs as columns (log2 M1 stages,
+        reading the input) then rows (log2 M2 stages), M = M1 M2, M1 >= M2.
+        None for other stages."""
+        def split(Ml):
+            lg = int(math.log2(Ml))
+            return (lg, 0) if Ml <= 8192 else (lg - lg // 2, lg // 2)
+
+        fixed_ns = 2 * self.a_max
+        if stage.startswith("gather_fft_l"):
             Ml, ns = self.M >> int(stage[-1]), 2
-        elif stage in ("gather_fft_fixed", "gather_fft_consecutive"):
-            Ml, ns = self.M, 2 * self.a_max
-        elif stage == "gather_fft_random":
-            Ml, ns = self.M, self.r
+            stages, reads = split(Ml)[0], True
+        elif stage.startswith("gather_cols_l"):
+            Ml = self.M >> int(stage[-1])
+            ns = fixed_ns if self.mode == "fixed" else 2
+            stages, reads = split(Ml)[0], True
+        elif stage.startswith("fft_rows_l"):
+            Ml = self.M >> int(stage[-1])
+            ns = fixed_ns if self.mode == "fixed" else 2
+            stages, reads = split(Ml)[1], False
+        elif stage == "gather_fft_fixed":
+            Ml, ns = self.M, fixed_ns
+            stages, reads = split(Ml)[0], True
+        elif stage in ("gather_fft_consecutive", "gather_fft_random"):
+            Ml = self.M
+            ns = 2 * self.a_max if stage.endswith("consecutive") else self.r
+            stages, reads = split(Ml)[0], True
+        elif stage == "fft_rows":  # general path, one launch per shift group
+            Ml, ns = self.M, (2 * self.a_max + self.r) / 2
+            stages, reads = split(Ml)[1], False
         else:
             return None
-        bfly = ns * (Ml // 2) * int(math.log2(Ml))
-        return {"bytes": ns * Ml * self.esize, "fft_ops": bfly * 68}
+        bfly = ns * (Ml // 2) * stages
+        return {"bytes": ns * Ml * self.esize if reads else 0, "fft_ops": bfly * 68}
 
 
 WORKLOADS = {
@@ -288,22 +310,58 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+# headers every kernel includes (the FFT, value traits and decoders)
+KERNEL_HEADERS = ("sft_common.cuh", "sft_fft.cuh", "sft_decode.cuh", "sft_device_util.cuh")
+
+
+def kernel_source_hash(kernel: str):
+    """sha256 of the definition of the __global__ function `kernel` (from its
+    template line to its closing brace) and of the shared headers: the
+    counters of a kernel stay valid until one of these changes."""
+    import re
+    csrc = os.path.join(ROOT, "paper_1407_8315_gb300", "csrc")
+    name = kernel.split("<")[0]
+    h = hashlib.sha256()
+    found = False
+    for fn in sorted(os.listdir(csrc)):
+        if not fn.endswith(".cu"):
+            continue
+        text = open(os.path.join(csrc, fn)).read()
+        m = re.search(r"\n(template <[^\n]*>\n)?__global__[^\n]*\b" + re.escape(name) + r"\(", text)
+        if m is None:
+            continue
+        end = text.find("\n}\n", m.end())
+        h.update(text[m.start():end].encode())
+        found = True
+    if not found:
+        return None
+    for hdr in KERNEL_HEADERS:
+        with open(os.path.join(csrc, hdr), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic(workload: str, kernel: str):
     """DRAM bytes per launch of `kernel` in `workload` from the committed ncu
-    summary, or None when it is missing or was taken on other sources."""
+    summary, or None when it is missing or the kernel's source changed since
+    the counters were taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
     ent = t.get(workload, {}).get(kernel)
-    if not ent or ent.get("source_sha") != source_hash():
+    if not ent or ent.get("source_sha") != kernel_source_hash(kernel):
         return None
     return ent.get("dram_bytes_per_launch")
 
 
-def kernel_of(stage: str) -> str:
-    """The __global__ function (template instance) that runs a stage."""
+def kernel_of(stage: str, M: int = 0) -> str:
+    """The __global__ function (template instance) that runs a stage (the
+    general path's gather stages run the four-step column kernel above
+    8192 points)."""
+    if stage in ("gather_fft_consecutive", "gather_fft_random") and M > 8192:
+        return "k_fft4_cols"
     if stage.startswith("gather_fft"):
         return "k_gather_fft"
     if stage.startswith("gather_cols"):
@@ -327,7 +385,8 @@ def roofline(wl, stages, B, clk):
     peaks, src = measured_peaks()
     groups = {}
     for name, (ms_tot, nl) in stages.items():
-        g = groups.setdefault(kernel_of(name), {"ms": 0.0, "launches": 0, "bytes": 0, "ops": 0})
+        g = groups.setdefault(kernel_of(name, wl.M), {"ms": 0.0, "launches": 0, "bytes": 0,
+                                                      "ops": 0})
         g["ms"] += ms_tot
         g["launches"] += nl
         m = wl.stage_model(name)

@@ -384,7 +384,10 @@ static sft_status run_host(sft_plan_t P, int64_t n, const void* x_host, int64_t 
     rd.overflow = reinterpret_cast<int32_t*>(rs + (size_t)n * cap * 24 + (size_t)n * 12);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(P->ws.zero_base, 0, P->ws.zero_bytes, s);
+  // host-resident samples are read over NVLink-C2C, where wide requests pay
+  P->x_on_host = xd != P->x_stage;
   if (e == cudaSuccess) e = sft::launch_exact(P, n, xd, x_stride, &rd, s);
+  P->x_on_host = false;
   if (!in_place) {
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(rh->idx, rd.idx, (size_t)n * cap * 8, cudaMemcpyDeviceToHost, s);

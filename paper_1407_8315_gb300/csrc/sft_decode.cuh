@@ -239,12 +239,66 @@ __device__ __forceinline__ int64_t snap_root_f(float zx, float zy, int64_t k, co
   return k + t * g.M;
 }
 
+// Validation (iii) in float-float on the FP32 pipes (mixed path): the
+// residual r_i = m_i - sum_j p_j omega^{s_j i} over all nm equations from the
+// float-float syndromes `raw`, the values p rounded to float-float and the
+// float-float omega tables.  Its error (~1e-13 |m|) is far below res_tol, so
+// it accepts exactly the bins the FP64 residual accepts.  Returns -1 when the
+// squared magnitudes leave the float range (the caller then uses FP64),
+// else whether max |r_i|^2 <= res_tol^2 max |m_i|^2; on acceptance writes
+// the residual to res_out (if not null).
+template <int a, int nm>
+__device__ __forceinline__ int ff_residual_ok(const float4* raw, const int64_t* s, const cdbl* p,
+                                              const OmegaTabFF& omff, double res2, float4* res_out) {
+  FF::V pf[a], wf[a], wp[a];
+#pragma unroll
+  for (int j = 0; j < a; ++j) {
+    pf[j] = FF::from4(Store<FF>::from_d(p[j]));
+    wf[j] = omega_ff(omff, s[j]);
+    wp[j] = FF::V{1.0f, 0.0f, 0.0f, 0.0f};
+  }
+  float mmax2 = 0.0f, rmax2 = 0.0f;
+  FF::V r[nm];
+#pragma unroll
+  for (int i = 0; i < nm; ++i) {
+    const FF::V mi = FF::from4(raw[i]);
+    FF::V fit = FF::mulv(pf[0], wp[0]);
+#pragma unroll
+    for (int j = 1; j < a; ++j) fit = FF::add(fit, FF::mulv(pf[j], wp[j]));
+    r[i] = FF::sub(mi, fit);
+    if (i + 1 < nm) {
+#pragma unroll
+      for (int j = 0; j < a; ++j) wp[j] = FF::mulv(wp[j], wf[j]);
+    }
+    // magnitudes from hi + lo: after the cancellation in r the pair is not
+    // normalised (its hi part alone can overstate it by many ulps)
+    const float mx = __fadd_rn(mi.rh, mi.rl), my = __fadd_rn(mi.ih, mi.il);
+    const float rx = __fadd_rn(r[i].rh, r[i].rl), ry = __fadd_rn(r[i].ih, r[i].il);
+    mmax2 = fmaxf(mmax2, mx * mx + my * my);
+    rmax2 = fmaxf(rmax2, rx * rx + ry * ry);
+  }
+  if (!(mmax2 < 1e36f) || !(rmax2 < 1e36f)) return -1;
+  if (!((double)rmax2 <= res2 * (double)mmax2)) return 0;
+  if (res_out != nullptr) {
+#pragma unroll
+    for (int i = 0; i < nm; ++i) res_out[i] = FF::to4(r[i]);
+  }
+  return 1;
+}
+
 // Decode bin k with `a` aliases from m[0..nm).  On success fills s[0..a)
 // (ascending), p[0..a), replaces m[0..nm) by the residual m - Z p and
 // returns true; on failure m is unchanged.
+//
+// On the mixed path the caller passes the float-float syndromes `raw` and
+// the float-float omega tables: validation (iii) then runs in float-float
+// (ff_residual_ok) and, on success, the residual goes to res_out (float-
+// float) instead of m.  With raw == nullptr everything stays in FP64.
 template <int a, int nm>
 __device__ __forceinline__ bool decode_bin(cdbl* m, int64_t k, const BinGeom& g, const Tol2& tol,
-                                           int64_t* s, cdbl* p) {
+                                           int64_t* s, cdbl* p, const float4* raw = nullptr,
+                                           const OmegaTabFF* omff = nullptr,
+                                           float4* res_out = nullptr) {
   static_assert(nm >= 2 * a && nm <= 8, "need 2a <= nm <= 8 syndromes");
   if constexpr (a == 1) {
     // c_0 = -m_1 / m_0, the single root z = m_1 / m_0 (Sec. II-A).  Only
@@ -290,6 +344,10 @@ __device__ __forceinline__ bool decode_bin(cdbl* m, int64_t k, const BinGeom& g,
       if (!(norm2(r0) <= tol.res2 * mmax2)) return false;
       m[0] = r0;
       m[1] = -(w * r0);
+      if (res_out != nullptr) {
+        res_out[0] = Store<FF>::from_d_small(m[0]);
+        res_out[1] = Store<FF>::from_d_small(m[1]);
+      }
       return true;
     } else {
       cdbl acc = m[0], wp = w;
@@ -300,6 +358,10 @@ __device__ __forceinline__ bool decode_bin(cdbl* m, int64_t k, const BinGeom& g,
       }
       p[0] = acc * (1.0 / (double)nm);
       if (!(norm2(p[0]) > tol.theta2)) return false;
+      if (raw != nullptr) {
+        const int ok = ff_residual_ok<1, nm>(raw, s, p, *omff, tol.res2, res_out);
+        if (ok >= 0) return ok == 1;
+      }
       double mmax2 = 0.0, rmax2 = 0.0;
       cdbl r[nm];
       wp = mk(1.0, 0.0);
@@ -313,6 +375,10 @@ __device__ __forceinline__ bool decode_bin(cdbl* m, int64_t k, const BinGeom& g,
       if (!(rmax2 <= tol.res2 * mmax2)) return false;
 #pragma unroll
       for (int i = 0; i < nm; ++i) m[i] = r[i];
+      if (res_out != nullptr) {
+#pragma unroll
+        for (int i = 0; i < nm; ++i) res_out[i] = Store<FF>::from_d_small(m[i]);
+      }
       return true;
     }
   } else {
@@ -406,6 +472,10 @@ __device__ __forceinline__ bool decode_bin(cdbl* m, int64_t k, const BinGeom& g,
 #pragma unroll
     for (int j = 0; j < a; ++j)
       if (!(norm2(p[j]) > tol.theta2)) return false;
+    if (raw != nullptr) {
+      const int ok = ff_residual_ok<a, nm>(raw, s, p, *omff, tol.res2, res_out);
+      if (ok >= 0) return ok == 1;
+    }
     double mmax2 = 0.0, rmax2 = 0.0;
     cdbl r[nm];
 #pragma unroll
@@ -425,6 +495,10 @@ __device__ __forceinline__ bool decode_bin(cdbl* m, int64_t k, const BinGeom& g,
     if (!(rmax2 <= tol.res2 * mmax2)) return false;
 #pragma unroll
     for (int i = 0; i < nm; ++i) m[i] = r[i];
+    if (res_out != nullptr) {
+#pragma unroll
+      for (int i = 0; i < nm; ++i) res_out[i] = Store<FF>::from_d_small(m[i]);
+    }
     return true;
   }
 }

@@ -108,7 +108,25 @@ __global__ void __launch_bounds__(8192 / PTS) k_gather_fft(
 // crosses the memory system once instead of once per level; the FFTs then
 // read coalesced.  ITER: level l keeps [2][M_l] at offset
 // sum_{l' < l} 2 M_l', rows n = 2^l n'; FIXED: [2 a_m][M0].
+// Read-only load asking L2 for a 64-byte prefetch (a row's run of shifts
+// 0..7 of complex64 samples), not the default wider one.
+__device__ __forceinline__ float2 ld_row64(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.nc.L2::64B.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double2 ld_row64(const double2* p) {
+  double2 v;
+  asm volatile("ld.global.nc.L2::64B.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  return v;
+}
+
 template <class In>
+__device__ __forceinline__ In ld_row(const In* p, bool narrow) {
+  return narrow ? ld_row64(p) : __ldg(p);
+}
+
+template <class In, bool kNarrow>
 __global__ void __launch_bounds__(256) k_extract(const In* __restrict__ x, int64_t x_stride,
                                                  const void* const* __restrict__ x_table,
                                                  int64_t N, int64_t d, int64_t M0, int levels,
@@ -122,7 +140,7 @@ __global__ void __launch_bounds__(256) k_extract(const In* __restrict__ x, int64
   if (fixed_nsh > 0) {
 #pragma unroll
     for (int j = 0; j < 8; ++j)
-      if (j < fixed_nsh) v[j] = __ldg(xs + ((n * d + j) & (N - 1)));
+      if (j < fixed_nsh) v[j] = ld_row(xs + ((n * d + j) & (N - 1)), kNarrow);
 #pragma unroll
     for (int j = 0; j < 8; ++j)
       if (j < fixed_nsh) cb[(int64_t)j * M0 + n] = v[j];
@@ -132,7 +150,7 @@ __global__ void __launch_bounds__(256) k_extract(const In* __restrict__ x, int64
   const int lv = min(levels, (n == 0 ? 4 : __ffsll(n) - 1 + 1));
 #pragma unroll
   for (int j = 0; j < 8; ++j)
-    if (j < 2 * lv) v[j] = __ldg(xs + ((n * d + j) & (N - 1)));
+    if (j < 2 * lv) v[j] = ld_row(xs + ((n * d + j) & (N - 1)), kNarrow);
   int64_t off = 0, Ml = M0;
 #pragma unroll
   for (int l = 0; l < 4; ++l) {
@@ -374,18 +392,33 @@ __global__ void __launch_bounds__(kDecThreads) k_iter_decode(LevelArgs g, const 
     T* cur = reinterpret_cast<T*>(g.cur) + (int64_t)b * g.held_elems;
     const Tol2 tol{g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]),
                    g.root_tol * g.root_tol, g.res_tol * g.res_tol};
+    T raw[nm];
     cdbl m[nm];
 #pragma unroll
-    for (int j = 0; j < nm; ++j) m[j] = Store<F>::to_d(cur[j * M + k]);
+    for (int j = 0; j < nm; ++j) {
+      raw[j] = cur[j * M + k];
+      m[j] = Store<F>::to_d(raw[j]);
+    }
     int64_t s[4];
     cdbl p[4];
     uint8_t t = 1;
-    if (decode_bin<A, nm>(m, k, geom, tol, s, p)) {
+    bool ok;
+    float4 res[nm];
+    if constexpr (std::is_same<F, FF>::value)
+      ok = decode_bin<A, nm>(m, k, geom, tol, s, p, raw, &g.omff, res);
+    else
+      ok = decode_bin<A, nm>(m, k, geom, tol, s, p);
+    if (ok) {
       file_solution<F, A>(s, p, M0, g.slot_cnt + (int64_t)b * M0, g.slot_s + (int64_t)b * M0 * 4,
                           reinterpret_cast<T*>(g.slot_p) + (int64_t)b * M0 * 4, g.flags + b);
       // the recovered terms leave every syndrome held for this bin
+      if constexpr (std::is_same<F, FF>::value) {
 #pragma unroll
-      for (int j = 0; j < nm; ++j) cur[j * M + k] = Store<F>::from_d_small(m[j]);
+        for (int j = 0; j < nm; ++j) cur[j * M + k] = res[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < nm; ++j) cur[j * M + k] = Store<F>::from_d_small(m[j]);
+      }
       t = 0;
     }
     g.Tcur[(int64_t)b * M0 + k] = t;
@@ -406,6 +439,7 @@ struct FixedArgs {
   int32_t* flags;
   double zero_tol, root_tol, res_tol;
   OmegaTab om;
+  OmegaTabFF omff;  // float-float omega tables (mixed path)
 };
 
 // activity of every bin (any of the 2 a_max syndromes above theta)
@@ -452,12 +486,21 @@ __global__ void __launch_bounds__(kDecThreads) k_fixed_round(FixedArgs g, const 
       const T* Y = reinterpret_cast<const T*>(g.Y) + (int64_t)b * g.held_elems;
       const Tol2 tol{g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]),
                      g.root_tol * g.root_tol, g.res_tol * g.res_tol};
+      T raw[NM];
       cdbl m[NM];
 #pragma unroll
-      for (int j = 0; j < NM; ++j) m[j] = Store<F>::to_d(Y[j * M + k]);
+      for (int j = 0; j < NM; ++j) {
+        raw[j] = Y[j * M + k];
+        m[j] = Store<F>::to_d(raw[j]);
+      }
       int64_t s[4];
       cdbl p[4];
-      if (decode_bin<A, NM>(m, k, geom, tol, s, p)) {
+      bool ok;
+      if constexpr (std::is_same<F, FF>::value)
+        ok = decode_bin<A, NM>(m, k, geom, tol, s, p, raw, &g.omff, nullptr);
+      else
+        ok = decode_bin<A, NM>(m, k, geom, tol, s, p);
+      if (ok) {
         file_solution<F, A>(s, p, M, g.slot_cnt + (int64_t)b * M, g.slot_s + (int64_t)b * M * 4,
                             reinterpret_cast<T*>(g.slot_p) + (int64_t)b * M * 4, g.flags + b);
       } else if (qout == nullptr) {
@@ -780,9 +823,16 @@ static void launch_extract(sft_plan_s* P, int64_t B, const void* x, int64_t x_st
                            int fixed_nsh, cudaStream_t st) {
   const dim3 grid((unsigned)((P->M0 + 255) / 256), (unsigned)B);
   stage_begin(P, "extract", st);
-  k_extract<typename F::In><<<grid, 256, 0, st>>>(
-      reinterpret_cast<const typename F::In*>(x), x_stride, P->x_table, P->p.N, P->p.d, P->M0,
-      levels, fixed_nsh, reinterpret_cast<typename F::In*>(P->ws.xc), P->ws.xc_sig);
+  // device-resident samples: 64-byte L2 requests (one row's run of shifts);
+  // host-resident ones (read over NVLink-C2C): full-width requests
+  if (P->x_on_host)
+    k_extract<typename F::In, false><<<grid, 256, 0, st>>>(
+        reinterpret_cast<const typename F::In*>(x), x_stride, P->x_table, P->p.N, P->p.d, P->M0,
+        levels, fixed_nsh, reinterpret_cast<typename F::In*>(P->ws.xc), P->ws.xc_sig);
+  else
+    k_extract<typename F::In, true><<<grid, 256, 0, st>>>(
+        reinterpret_cast<const typename F::In*>(x), x_stride, P->x_table, P->p.N, P->p.d, P->M0,
+        levels, fixed_nsh, reinterpret_cast<typename F::In*>(P->ws.xc), P->ws.xc_sig);
   stage_end(P, st);
 }
 
@@ -807,7 +857,8 @@ static void launch_fixed(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
   }
   FixedArgs g{P->p.N, P->M0, P->p.d, P->p.a_max, W.held[0], W.held_elems, W.T[0], W.slot_cnt,
               W.slot_s, W.slot_p, W.ymax2, W.flags, P->p.zero_tol, P->p.root_tol,
-              P->p.res_tol, om};
+              P->p.res_tol, om,
+              OmegaTabFF{P->tab.om_hi_ff, P->tab.om_lo_ff, P->tab.om_lo_bits, P->p.N - 1}};
   dim3 sgrid((unsigned)((P->M0 + kFoldThreads - 1) / kFoldThreads), (unsigned)B);
   const int64_t maxq = B * P->M0;
   const unsigned dgrid = (unsigned)std::max<int64_t>(

@@ -162,6 +162,9 @@ struct sft_plan_s {
   // at most 64 registers, twice the resident warps of 16 points per thread;
   // measured faster on every level of the exact transforms)
   int fft_pts = 8;
+  // the current call reads page-locked host memory in place (the compact
+  // extraction then asks for full-width L2 lines)
+  bool x_on_host = false;
   // learned proposal (general plans): the attached network (not owned) and
   // 8 proposed candidates t per queued bin (int16, -1 = none)
   struct sft_mlp_s* mlp = nullptr;
