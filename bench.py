@@ -310,8 +310,14 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-# headers every kernel includes (the FFT, value traits and decoders)
+# headers each kernel's code draws on (default: all of them)
 KERNEL_HEADERS = ("sft_common.cuh", "sft_fft.cuh", "sft_decode.cuh", "sft_device_util.cuh")
+KERNEL_DEPS = {
+    "k_gather_fft": ("sft_common.cuh", "sft_fft.cuh"),
+    "k_fft4_cols": ("sft_common.cuh", "sft_fft.cuh"),
+    "k_fft4_rows": ("sft_common.cuh", "sft_fft.cuh"),
+    "k_extract": ("sft_common.cuh",),
+}
 
 
 def kernel_source_hash(kernel: str):
@@ -335,7 +341,7 @@ def kernel_source_hash(kernel: str):
         found = True
     if not found:
         return None
-    for hdr in KERNEL_HEADERS:
+    for hdr in KERNEL_DEPS.get(name, KERNEL_HEADERS):
         with open(os.path.join(csrc, hdr), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
