@@ -194,6 +194,18 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--crossover", action="store_true",
+                    help="dense-FFT crossover study: one JSON line per (N, K, path) against "
+                         "cuFFT on the same batch, then a summary line")
+    ap.add_argument("--crossover-n", default="20,22,24",
+                    help="log2 N of the crossover study, comma separated")
+    ap.add_argument("--pruning", action="store_true",
+                    help="Tables III-V at reduced N: the general path with and without the "
+                         "pruning strategy, time and SNR_out per (K, SNR); one JSON line each")
+    ap.add_argument("--pruning-n", type=int, default=20, help="log2 N of the pruning study")
+    ap.add_argument("--collisions", action="store_true",
+                    help="Fig. 2: probability that a bin holds a = 0..8 of K random locations "
+                         "at N+ = M/K from 1/4 to 8, counted on the GPU; one JSON line each")
     return ap.parse_args()
 
 
@@ -1021,11 +1033,178 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------- dense-FFT crossover study
+def _event_ms(torch, fn, steps, flush, stream):
+    """Mean ms of fn() over `steps` event-timed calls, L2 flushed before each."""
+    return timed_steps(torch, fn, steps, flush, stream) / steps
+
+
+def run_crossover(args):
+    """The paper's comparison with a dense FFT (Sec. V, the speed-up over
+    FFTW below K = N/2^4 for the exact path), on one GPU: for each N and
+    K = N/2^j, the batch's sparse transform (the exact ITER path, M = 2K,
+    a_m = 4; and the general path at 30 dB, d = N/(32K), a_m = 3, r = 9)
+    against cuFFT's dense transform of the same batch (torch.fft.fft, C2C
+    complex64, and complex128 for the FP64 accuracy class), inputs resident,
+    L2 flushed between steps.  cuFFT is a timing reference only.  Prints one
+    JSON line per point and a summary line with, per N, the largest K at
+    which the sparse transform is the faster."""
+    import torch
+
+    from paper_1407_8315_gb300 import Plan, build
+
+    torch.cuda.set_device(0)
+    build()
+    stream = torch.cuda.current_stream()
+    flush = l2_flusher(torch)
+    steps = max(3, min(args.steps, 20))
+    summary = {}
+    for lgN in (int(v) for v in args.crossover_n.split(",")):
+        N = 1 << lgN
+        B = max(4, min(128, (1 << 30) // (N * 8)))
+        dense = {}
+        points = [("exact", N >> j) for j in range(4, 13)] + \
+                 [("general", N >> j) for j in range(9, 13)]
+        for path, K in points:
+            if path == "exact":
+                wl = W("x", "", "", N, K, min(2 * K, N // 2), "iter", "mixed", B, 4)
+            else:
+                wl = W("x", "", "", N, K, 32 * K, "general", "mixed", B, 3, snrs=(30,),
+                       plan_seed=2024)
+            x_np, supps = gen_batch(wl, B, 9_000_000 + K)
+            x = torch.from_numpy(x_np).cuda()
+            if not dense:
+                y = torch.empty_like(x)
+                fn = lambda: torch.fft.fft(x, out=y)  # noqa: E731
+                for _ in range(args.warmup):
+                    fn()
+                dense["c64"] = _event_ms(torch, fn, steps, flush, stream)
+                x2 = x.to(torch.complex128)
+                y2 = torch.empty_like(x2)
+                fn = lambda: torch.fft.fft(x2, out=y2)  # noqa: E731
+                for _ in range(args.warmup):
+                    fn()
+                dense["c128"] = _event_ms(torch, fn, steps, flush, stream)
+                del x2, y2, y
+            plan = Plan(N, K, wl.d, wl.mode, "mixed", max_signals=B, a_max=wl.a_max,
+                        seed=wl.plan_seed, n_cs_shifts=wl.r if wl.general else 0)
+            call = plan.general if wl.general else plan.exact
+            out = call(x, wl.cap)
+            for _ in range(args.warmup):
+                call(x, wl.cap, out)
+            ms = _event_ms(torch, lambda: call(x, wl.cap, out), steps, flush, stream)
+            cnt, idx = out.count.cpu().numpy(), out.idx.cpu().numpy()
+            found = sum(int(np.isin(idx[b, :cnt[b]], supps[b]).sum()) for b in range(B))
+            line = {"study": "crossover", "path": path, "N": N, "K": K, "N_over_K": N // K,
+                    "M": wl.M, "batch": B, "sparse_ms": ms, "cufft_c64_ms": dense["c64"],
+                    "cufft_c128_ms": dense["c128"], "speedup_vs_c64": dense["c64"] / ms,
+                    "speedup_vs_c128": dense["c128"] / ms,
+                    "recovered_fraction": found / (B * K)}
+            print(json.dumps(line), flush=True)
+            if ms < dense["c64"]:
+                key = f"{path} N=2^{lgN}"
+                summary[key] = max(summary.get(key, 0), K)
+            plan.close()
+            del x, out
+            torch.cuda.empty_cache()
+    print(json.dumps({"study": "crossover", "largest_K_faster_than_cufft_c64": summary,
+                      "steps": steps, "warmup": args.warmup,
+                      "timing": "CUDA events, L2 flushed between steps, inputs resident"}),
+          flush=True)
+
+
+# ------------------------------------------------ pruning ablation study
+def run_pruning(args):
+    """Tables III-V at reduced N: Algorithm 2 with the pruning strategy
+    (SFT_GENERAL) and the CS model without it (SFT_GENERAL_UNPRUNED) on the
+    same batch, d = N/(32K), a_m = 3, r = 9, K = N/2^16 .. N/2^9 and input
+    SNR 30/20/10 dB: GPU time per signal (CUDA events, L2 flushed between
+    steps) and mean SNR_out (Eq. (37)) over the batch's first signals."""
+    import torch
+
+    from paper_1407_8315_gb300 import Plan, build
+
+    torch.cuda.set_device(0)
+    build()
+    stream = torch.cuda.current_stream()
+    flush = l2_flusher(torch)
+    steps = max(3, min(args.steps, 10))
+    N = 1 << args.pruning_n
+    B = max(4, min(64, (1 << 28) // (N * 8)))
+    n_snr = min(B, 8)
+    for snr in (30, 20, 10):
+        for j in range(16, 8, -1):
+            K = N >> j
+            if K < 1:
+                continue
+            d = N // (32 * K)
+            wl = W("x", "", "", N, K, N // d, "general", "mixed", B, 3, snrs=(snr,),
+                   plan_seed=snr)
+            x_np, _ = gen_batch(wl, B, 11_000_000 + 100 * j + snr)
+            x = torch.from_numpy(x_np).cuda()
+            line = {"study": "pruning", "N": N, "K": K, "N_over_K": N // K, "d": d,
+                    "snr_in_db": snr, "batch": B}
+            for mode, key in (("general", "pruned"), ("general-unpruned", "unpruned")):
+                plan = Plan(N, K, d, mode, "mixed", max_signals=B, seed=snr)
+                cap = 2 * K + 16 if mode == "general" else 3 * (N // d)
+                out = plan.general(x, cap)
+                for _ in range(args.warmup):
+                    plan.general(x, cap, out)
+                ms = _event_ms(torch, lambda: plan.general(x, cap, out), steps, flush, stream)
+                cnt, idx, val = out.count.cpu().numpy(), out.idx.cpu().numpy(), out.val.cpu().numpy()
+                snrs = [snr_out(x_np[b], idx[b, :cnt[b]], val[b, :cnt[b]]) for b in range(n_snr)]
+                line[f"{key}_ms_per_signal"] = ms / B
+                line[f"{key}_snr_out_db"] = float(np.mean(snrs))
+                line[f"{key}_entries_per_signal"] = float(cnt.mean())
+                plan.close()
+                del out
+            print(json.dumps(line), flush=True)
+            del x
+            torch.cuda.empty_cache()
+
+
+# ------------------------------------------------ collision-count study
+def run_collisions(args):
+    """Fig. 2 of Sec. II-C: for K = 2^12 locations drawn uniformly from
+    [0, 2^22) and M = N+ K bins (d = N/M), the probability that a bin holds
+    exactly a locations (and among the non-empty bins), from the GPU
+    histogram of 4000 sampled support sets per point."""
+    import torch
+
+    from paper_1407_8315_gb300 import build, sft
+
+    torch.cuda.set_device(0)
+    build()
+    N, K, sets, cells = 1 << 22, 1 << 12, 4000, 9
+    rng = np.random.default_rng(2014)
+    S = torch.from_numpy(np.stack([siggen.sparse_support(N, K, rng) for _ in range(sets)])).cuda()
+    for lg in range(-2, 4):
+        M = K << lg if lg >= 0 else K >> -lg
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record()
+        h = sft.alias_histogram(S, M, cells)
+        ev[1].record()
+        torch.cuda.synchronize()
+        h = h.cpu().numpy().astype(np.float64)
+        nonempty = h[1:].sum()
+        print(json.dumps({"study": "collisions", "N": N, "K": K, "M": M, "d": N // M,
+                          "N_plus": M / K, "sets": sets,
+                          "p_bin_holds_a": {str(a): h[a] / (sets * M) for a in range(cells)},
+                          "p_given_nonempty": {str(a): h[a] / nonempty for a in range(1, cells)},
+                          "gpu_ms": ev[0].elapsed_time(ev[1])}), flush=True)
+
+
 def main():
     args = parse()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.collisions:
+        run_collisions(args)
+    elif args.pruning:
+        run_pruning(args)
+    elif args.crossover:
+        run_crossover(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == HETERO:
         run_hetero(args)

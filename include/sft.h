@@ -33,6 +33,13 @@
  *                    and Subspace Pursuit on the pruned sensing matrix
  *                    Phi_p[j][t] = omega^{(k + tM) n_j} (Eq. (22)) returns
  *                    a_k values.
+ *   SFT_GENERAL_UNPRUNED  the CS model of Sec. III-B without the pruning
+ *                    strategy (the "without pruning" rows of Tables III-V):
+ *                    only the r random shifts; every bin solved by Subspace
+ *                    Pursuit at sparsity a_max on the full sensing matrix
+ *                    Phi[j][t] = omega^{(k + tM) n_j}, t < d (Eq. (18)),
+ *                    and every non-zero coefficient returned (up to
+ *                    a_max N/d entries per signal; K is not used).  d <= 4096.
  *
  * Precision.
  *   SFT_FP64   input complex128 (interleaved re, im doubles); FFTs, folds,
@@ -73,7 +80,12 @@ typedef enum {
   SFT_EUNSUPPORTED = 5  /* valid request this build does not implement    */
 } sft_status;
 
-typedef enum { SFT_EXACT_ITER = 0, SFT_EXACT_FIXED = 1, SFT_GENERAL = 2 } sft_mode;
+typedef enum {
+  SFT_EXACT_ITER = 0,
+  SFT_EXACT_FIXED = 1,
+  SFT_GENERAL = 2,
+  SFT_GENERAL_UNPRUNED = 3
+} sft_mode;
 typedef enum { SFT_FP64 = 0, SFT_MIXED = 1 } sft_precision;
 
 /* Parameters as the paper states the problem (Algorithm 1 inputs: x, K;
@@ -88,9 +100,9 @@ typedef struct {
                        /* M / 2^(max_iters-1) must be >= 1                   */
   int32_t mode;        /* sft_mode                                           */
   int32_t precision;   /* sft_precision                                      */
-  int32_t n_cs_shifts; /* SFT_GENERAL: random shifts r, 1..16, r <= d (0 -> 3 a_max) */
+  int32_t n_cs_shifts; /* general modes: random shifts r, 1..16, r <= d (0 -> 3 a_max) */
   int32_t reserved_;   /* must be 0                                          */
-  uint64_t seed;       /* SFT_GENERAL only: draws the random shifts          */
+  uint64_t seed;       /* general modes only: draws the random shifts        */
   double zero_tol;     /* bin active iff |m| > zero_tol * max_k |Y_{d,0}[k]| */
   double root_tol;     /* a root must lie within root_tol of its candidate    */
   double res_tol;      /* accept iff ||m - Z p||_inf <= res_tol ||m||_inf     */
@@ -162,8 +174,10 @@ sft_status sft_exact_host(sft_plan_t plan, int64_t n_signals, const void* x_host
                           int64_t x_stride, const sft_result* r_host, void* stream);
 
 /* Generally K-sparse transform (Algorithm 2) of n_signals signals; the plan
- * must have mode SFT_GENERAL.  Arguments, layout and behaviour as for
- * sft_exact; at most K entries per signal (sum of the votes a_k); the
+ * must have mode SFT_GENERAL (at most K entries per signal, the sum of the
+ * votes a_k) or SFT_GENERAL_UNPRUNED (at most a_max N/d entries; a result
+ * capacity below that count sets `overflow` and keeps the first cap
+ * entries in the documented order).  Arguments, layout and behaviour as for sft_exact; the
  * `unresolved` count is 0 (the method has no unsolved-bin notion). */
 sft_status sft_general(sft_plan_t plan, int64_t n_signals, const void* x, int64_t x_stride,
                        const sft_result* r, void* stream);
@@ -172,7 +186,7 @@ sft_status sft_general(sft_plan_t plan, int64_t n_signals, const void* x, int64_
 sft_status sft_general_host(sft_plan_t plan, int64_t n_signals, const void* x_host,
                             int64_t x_stride, const sft_result* r_host, void* stream);
 
-/* The random shifts n_l of an SFT_GENERAL plan: r distinct values in
+/* The random shifts n_l of a general-mode plan: r distinct values in
  * [0, d), a partial Fisher-Yates shuffle of 0..d-1 whose draw i exchanges
  * positions i and i + (u_i mod (d - i)), u_i the i-th output of SplitMix64
  * (Steele, Lea, Flood 2014) seeded with params.seed.  Writes up to `cap`
@@ -342,6 +356,19 @@ sft_status sft_plan_attach_mlp(sft_plan_t plan, sft_mlp_t mlp);
 sft_status sft_exact_auto(const sft_params* p, int64_t n_signals, const void* x, int64_t x_stride,
                           int64_t M_start, int64_t M_max, const sft_result* r, int64_t* m_out,
                           void* stream);
+
+/* Collision counts (Sec. II-C, Lemma 2 and Fig. 2): for n_sets support sets
+ * of K locations each, the number of bins k < M holding exactly a of a
+ * set's locations (k = s mod M), summed over the sets.
+ *   supports  device int64 [n_sets][K]; any values (only s mod M is used)
+ *   M         number of bins, a power of two <= 2^15
+ *   n_cells   2..33: hist[a] for a < n_cells - 1, hist[n_cells - 1] counts
+ *             the bins holding n_cells - 1 or more
+ *   hist      device int64 [n_cells], overwritten
+ * Asynchronous on `stream`.  SFT_EINVAL on NULL pointers or bad sizes,
+ * SFT_EUNSUPPORTED for M > 2^15. */
+sft_status sft_alias_histogram(const int64_t* supports, int64_t n_sets, int64_t K, int64_t M,
+                               int32_t n_cells, int64_t* hist, void* stream);
 
 /* Number of kernel launches one call of this plan on max_signals signals
  * issues (sft_exact / sft_general). */

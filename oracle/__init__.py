@@ -58,7 +58,7 @@ class _Params(C.Structure):
 class _GParams(C.Structure):
     _fields_ = [("N", C.c_int64), ("K", C.c_int64), ("M", C.c_int64), ("a_max", C.c_int32),
                 ("r", C.c_int32), ("seed", C.c_uint64), ("keep", C.c_int32),
-                ("sp_iters", C.c_int32)]
+                ("sp_iters", C.c_int32), ("prune", C.c_int32), ("pad_", C.c_int32)]
 
 
 def _load():
@@ -231,13 +231,16 @@ def subspace_pursuit(Phi, y, ks: int, iters: int = 8) -> np.ndarray:
 
 
 def general(x, M: int, K: int, a_max: int = 3, r: int | None = None, seed: int = 0,
-            keep: int = 2, sp_iters: int = 8, cap: int | None = None):
-    """Algorithm 2 on x (upcast to complex128).  Returns (idx, val, a_k)."""
+            keep: int = 2, sp_iters: int = 8, cap: int | None = None, prune: bool = True):
+    """Algorithm 2 on x (upcast to complex128).  Returns (idx, val, a_k).
+    prune=False: the CS model of Sec. III-B without the pruning strategy
+    (every bin by SP at sparsity a_m over all d candidates; K unused)."""
     x = _c128(x)
     N = x.size
     r = 3 * a_max if r is None else r
     prm = _GParams(N=N, K=int(K), M=int(M), a_max=int(a_max), r=int(r),
-                   seed=int(seed) & 0xFFFFFFFFFFFFFFFF, keep=int(keep), sp_iters=int(sp_iters))
+                   seed=int(seed) & 0xFFFFFFFFFFFFFFFF, keep=int(keep), sp_iters=int(sp_iters),
+                   prune=1 if prune else 0)
     cap = int(K) * 2 + 16 if cap is None else int(cap)
     idx = np.zeros(cap, dtype=np.int64)
     val = np.zeros(cap, dtype=np.complex128)
@@ -248,3 +251,29 @@ def general(x, M: int, K: int, a_max: int = 3, r: int | None = None, seed: int =
         raise ValueError("bad parameters")
     n = min(int(n), cap)
     return idx[:n].copy(), val[:n].copy(), ak
+
+
+def alias_histogram(supports, M: int, n_cells: int = 9) -> np.ndarray:
+    """Collision counts of Sec. II-C (Lemma 2, Fig. 2): for each support set
+    (a row of `supports`), the number of bins k < M that hold exactly a of
+    its locations, k = s mod M; summed over the sets.  hist[a] for
+    a < n_cells - 1; the last cell counts n_cells - 1 or more."""
+    S = np.asarray(supports, dtype=np.int64)
+    if S.ndim == 1:
+        S = S[None, :]
+    hist = np.zeros(n_cells, dtype=np.int64)
+    for row in S:
+        counts = np.bincount(row % M, minlength=M)
+        hist += np.bincount(np.minimum(counts, n_cells - 1), minlength=n_cells)
+    return hist
+
+
+def alias_count_pmf(N: int, K: int, M: int, a: int) -> float:
+    """P(a bin holds exactly a locations) for K distinct locations drawn
+    uniformly from [0, N) and a bin of d = N/M candidates: hypergeometric,
+    C(d, a) C(N - d, K - a) / C(N, K)."""
+    from math import comb
+    d = N // M
+    if a < 0 or a > d or a > K:
+        return 0.0
+    return comb(d, a) * comb(N - d, K - a) / comb(N, K)

@@ -523,9 +523,10 @@ int orc_hankel_svals(int n, const double* min, double* sv) {
 }
 
 /* indices of the ks largest values (ties: smaller index first), returned in
- * ascending index order */
-static int top_ks(int n, const double* v, const unsigned char* allowed, int ks, int* out) {
-  unsigned char taken[64] = {0};
+ * ascending index order; taken is n bytes of scratch */
+static int top_ks(int n, const double* v, const unsigned char* allowed, int ks, int* out,
+                  unsigned char* taken) {
+  memset(taken, 0, (size_t)n);
   int cnt = 0;
   for (int r = 0; r < ks; ++r) {
     int best = -1;
@@ -570,32 +571,44 @@ int orc_subspace_pursuit(int rows, int cols, const double* Phin, const double* y
   const cplx* Phi = (const cplx*)Phin;
   const cplx* y = (const cplx*)yn;
   cplx* b = (cplx*)bout;
-  if (rows < 1 || rows > 32 || cols < 1 || cols > 32) return -1;
+  if (rows < 1 || rows > 32 || cols < 1 || cols > (1 << 16) || ks > 4) return -1;
   for (int j = 0; j < cols; ++j) b[j] = 0;
   if (ks > cols) ks = cols;
   if (ks <= 0) return 0;
-  double corr[32];
+  /* per-column scratch: correlations / magnitudes, membership flags */
+  double* corr = (double*)malloc((size_t)cols * sizeof(double));
+  unsigned char* flags = (unsigned char*)malloc((size_t)cols * 3);
+  if (!corr || !flags) {
+    free(corr);
+    free(flags);
+    return -1;
+  }
+  unsigned char *taken = flags, *in2 = flags + cols, *allow = flags + 2 * cols;
   cplx res[32], x[8], xn[8], resn[32];
   int T[8], nT;
   /* initialisation: the ks columns most correlated with y */
   for (int j = 0; j < cols; ++j) {
     cplx c = 0;
-    for (int i = 0; i < rows; ++i) c += conj(Phi[i * cols + j]) * y[i];
+    for (int i = 0; i < rows; ++i) c += conj(Phi[(size_t)i * cols + j]) * y[i];
     corr[j] = cabs(c);
   }
-  nT = top_ks(cols, corr, NULL, ks, T);
+  nT = top_ks(cols, corr, NULL, ks, T, taken);
   double rn = ls_on(rows, cols, Phi, y, T, nT, x, res);
-  if (rn < 0) return -1;
+  if (rn < 0) {
+    free(corr);
+    free(flags);
+    return -1;
+  }
   for (int it = 0; it < iters; ++it) {
     /* expand by the ks columns most correlated with the residual */
     for (int j = 0; j < cols; ++j) {
       cplx c = 0;
-      for (int i = 0; i < rows; ++i) c += conj(Phi[i * cols + j]) * res[i];
+      for (int i = 0; i < rows; ++i) c += conj(Phi[(size_t)i * cols + j]) * res[i];
       corr[j] = cabs(c);
     }
     int add[8];
-    int na = top_ks(cols, corr, NULL, ks, add);
-    unsigned char in2[32] = {0};
+    int na = top_ks(cols, corr, NULL, ks, add, taken);
+    memset(in2, 0, (size_t)cols);
     for (int u = 0; u < nT; ++u) in2[T[u]] = 1;
     for (int u = 0; u < na; ++u) in2[add[u]] = 1;
     int T2[16], n2 = 0;
@@ -604,14 +617,13 @@ int orc_subspace_pursuit(int rows, int cols, const double* Phin, const double* y
     /* least squares on the union, keep the ks largest coefficients */
     cplx x2[16], r2[32];
     if (ls_on(rows, cols, Phi, y, T2, n2, x2, r2) < 0) break;
-    double mag[32] = {0};
-    unsigned char allow[32] = {0};
+    memset(allow, 0, (size_t)cols);
     for (int u = 0; u < n2; ++u) {
-      mag[T2[u]] = cabs(x2[u]);
+      corr[T2[u]] = cabs(x2[u]);
       allow[T2[u]] = 1;
     }
     int Tn[8];
-    int nn = top_ks(cols, mag, allow, ks, Tn);
+    int nn = top_ks(cols, corr, allow, ks, Tn, taken);
     double rnn = ls_on(rows, cols, Phi, y, Tn, nn, xn, resn);
     if (rnn < 0 || rnn >= rn) break; /* no improvement: keep the previous support */
     nT = nn;
@@ -623,6 +635,8 @@ int orc_subspace_pursuit(int rows, int cols, const double* Phin, const double* y
     rn = rnn;
   }
   for (int u = 0; u < nT; ++u) b[T[u]] = x[u];
+  free(corr);
+  free(flags);
   return nT;
 }
 
@@ -647,7 +661,7 @@ int64_t orc_general(const double* xin, const orc_general_params* p, int64_t cap,
       p->keep < 1 || K < 0)
     return -1;
   const int64_t d = N / M;
-  if (r > d) return -1;
+  if (r > d || (!p->prune && d > (1 << 16))) return -1;
   int64_t ns[32];
   if (orc_cs_shifts(p->seed, d, r, ns) != 0) return -1;
   const int nc = 2 * am;
@@ -666,8 +680,41 @@ int64_t orc_general(const double* xin, const orc_general_params* p, int64_t cap,
   }
   /* Part 1 (lines 02-10): consecutive shifts 0..2a_m-1 and the r random
    * shifts, each d * FFT_M */
-  for (int j = 0; j < nc; ++j) orc_syndrome(xin, N, d, j, (double*)&Yc[(size_t)j * M]);
+  if (p->prune)
+    for (int j = 0; j < nc; ++j) orc_syndrome(xin, N, d, j, (double*)&Yc[(size_t)j * M]);
   for (int l = 0; l < r; ++l) orc_syndrome(xin, N, d, ns[l], (double*)&Ys[(size_t)l * M]);
+  if (!p->prune) {
+    /* Sec. III-B without the pruning strategy: every bin's CS model
+     * y = Phi b over all d candidates (Eq. (18)), solved by SP at sparsity
+     * a_m; every non-zero coefficient is output */
+    cplx* Phi = (cplx*)malloc((size_t)r * (size_t)d * sizeof(cplx));
+    cplx* b = (cplx*)malloc((size_t)d * sizeof(cplx));
+    int ok = Phi && b;
+    for (int64_t k = 0; ok && k < M; ++k) {
+      cplx y[32];
+      for (int j = 0; j < r; ++j) {
+        y[j] = Ys[(size_t)j * M + k];
+        for (int64_t t = 0; t < d; ++t) Phi[(size_t)j * d + t] = omega_pow(N, (k + t * M) * ns[j]);
+      }
+      /* a singular first least-squares problem leaves the bin empty */
+      int nz = orc_subspace_pursuit(r, (int)d, (const double*)Phi, (const double*)y, am,
+                                    p->sp_iters, (double*)b);
+      for (int64_t t = 0; nz > 0 && t < d; ++t)
+        if (b[t] != 0) push(&S, &nS, &capS, k + t * M, b[t]);
+      ak[k] = (unsigned char)am;
+    }
+    free(Phi);
+    free(b);
+    if (!ok) {
+      free(S);
+      free(Yc);
+      free(Ys);
+      free(sv);
+      free(ak);
+      return -1;
+    }
+    goto output;
+  }
   /* Part 2 (lines 11-21): singular values of every bin's a_m x a_m Hankel
    * matrix (m_0 .. m_{2a_m-2}, Eq. (26)); the K largest vote */
   for (int64_t k = 0; k < M; ++k) {
@@ -732,6 +779,7 @@ int64_t orc_general(const double* xin, const orc_general_params* p, int64_t cap,
     for (int u = 0; u < nk; ++u)
       if (b[u] != 0) push(&S, &nS, &capS, k + kept[u] * M, b[u]);
   }
+output:
   qsort(S, (size_t)nS, sizeof(entry), cmp_entry);
   const int64_t nout = nS < cap ? nS : cap;
   for (int64_t e = 0; e < nout; ++e) {

@@ -98,9 +98,9 @@ int orc_cs_shifts(uint64_t seed, int64_t d, int r, int64_t* out);
 int orc_hankel_svals(int n, const double* m, double* sv);
 
 /* Subspace Pursuit (Dai and Dai 2009) for y = Phi b with sparsity ks:
- * Phi is rows x cols (row-major, complex), at most `iters` iterations.
- * Writes b (cols complex values, ks of them non-zero) and returns the
- * number of non-zeros (or -1). */
+ * Phi is rows x cols (row-major, complex; rows <= 32, cols <= 2^16,
+ * ks <= 8), at most `iters` iterations.  Writes b (cols complex values, ks
+ * of them non-zero) and returns the number of non-zeros (or -1). */
 int orc_subspace_pursuit(int rows, int cols, const double* Phi, const double* y, int ks,
                          int iters, double* b);
 
@@ -113,11 +113,15 @@ typedef struct {
   uint64_t seed;    /* draws the random shifts                              */
   int32_t keep;     /* candidates kept per significant term (2: O(a) = 2a)  */
   int32_t sp_iters; /* Subspace Pursuit iteration cap                       */
+  int32_t prune;    /* 1: Algorithm 2 with the pruning strategy (Sec. III-C);
+                       0: the CS model of Sec. III-B without it -- every bin
+                       solved by SP at sparsity a_m over all d candidates   */
+  int32_t pad_;
 } orc_general_params;
 
 /* Algorithm 2.  Writes the recovered (s, X[s]) in ascending s (at most cap)
- * and, if a_k is not NULL, the vote a_k of every bin (M bytes).  Returns the
- * number of entries or -1. */
+ * and, if a_k is not NULL, the vote a_k of every bin (M bytes; a_m for
+ * every bin without pruning).  Returns the number of entries or -1. */
 int64_t orc_general(const double* x, const orc_general_params* p, int64_t cap, int64_t* idx,
                     double* val, unsigned char* a_k);
 

@@ -29,8 +29,9 @@ int ilog2(int64_t v) {
 constexpr int64_t kMaxM = int64_t(1) << 26;  // largest M = N/d (four-step FFT of 2^13 x 2^13)
 
 sft_status fill_defaults(sft_params* p) {
-  if (p->a_max == 0) p->a_max = p->mode == SFT_GENERAL ? 3 : 4;
-  if (p->mode == SFT_GENERAL && p->n_cs_shifts == 0) p->n_cs_shifts = 3 * p->a_max;
+  const bool gen = sft::is_general_mode(p->mode);
+  if (p->a_max == 0) p->a_max = gen ? 3 : 4;
+  if (gen && p->n_cs_shifts == 0) p->n_cs_shifts = 3 * p->a_max;
   if (p->max_iters == 0) p->max_iters = p->a_max;
   const bool fp64 = p->precision == SFT_FP64;
   if (!(p->zero_tol > 0)) p->zero_tol = fp64 ? 1e-10 : 1e-6;
@@ -52,10 +53,13 @@ sft_status validate(const sft_params& p) {
   if (p.a_max < 1 || p.a_max > 4) return why(SFT_EINVAL, "a_max must lie in [1, 4]");
   if (p.precision != SFT_FP64 && p.precision != SFT_MIXED)
     return why(SFT_EINVAL, "unknown precision");
-  if (p.mode != SFT_EXACT_ITER && p.mode != SFT_EXACT_FIXED && p.mode != SFT_GENERAL)
+  if (p.mode != SFT_EXACT_ITER && p.mode != SFT_EXACT_FIXED && !sft::is_general_mode(p.mode))
     return why(SFT_EINVAL, "unknown mode");
-  if (p.mode == SFT_GENERAL && (p.n_cs_shifts < 1 || p.n_cs_shifts > 16 || p.n_cs_shifts > p.d))
+  if (sft::is_general_mode(p.mode) &&
+      (p.n_cs_shifts < 1 || p.n_cs_shifts > 16 || p.n_cs_shifts > p.d))
     return why(SFT_EINVAL, "n_cs_shifts must lie in [1, min(16, d)]");
+  if (p.mode == SFT_GENERAL_UNPRUNED && p.d > 4096)
+    return why(SFT_EUNSUPPORTED, "SFT_GENERAL_UNPRUNED needs d <= 4096");
   if (p.reserved_ != 0) return why(SFT_EINVAL, "reserved_ must be 0");
   const int64_t M0 = p.N / p.d;
   if (p.mode == SFT_EXACT_ITER) {
@@ -119,14 +123,14 @@ cudaError_t upload_tables(sft_plan_s* P, size_t* total) {
     hi[i] = make_double2((double)cosl(t), (double)sinl(t));
   }
   cudaError_t e;
-  if (P->p.mode == SFT_GENERAL) {
+  if (sft::is_general_mode(P->p.mode)) {
     P->cs_host = draw_cs_shifts(P->p.seed, P->p.d, P->p.n_cs_shifts);
     if ((e = dalloc(&P->tab.cs_shifts, P->cs_host.size(), total)) != cudaSuccess) return e;
     if ((e = cudaMemcpy(P->tab.cs_shifts, P->cs_host.data(), P->cs_host.size() * sizeof(int64_t),
                         cudaMemcpyHostToDevice)))
       return e;
   }
-  if (P->p.mode != SFT_GENERAL) {
+  if (!sft::is_general_mode(P->p.mode)) {
     // the shifts' row offsets in the compact samples: ITER level l reads
     // rows 0 and M0 / 2^l of its block; FIXED shift j is row j M0
     std::vector<int64_t> xs;
@@ -410,9 +414,9 @@ static sft_status run_host(sft_plan_t P, int64_t n, const void* x_host, int64_t 
 
 static sft_status want_mode(sft_plan_t P, bool general) {
   if (!P) return reject("NULL plan (%lld %lld)", 0, 0);
-  if ((P->p.mode == SFT_GENERAL) != general)
-    return reject(general ? "plan mode %lld is not SFT_GENERAL (%lld)"
-                          : "plan mode %lld is SFT_GENERAL (%lld): use sft_general",
+  if (sft::is_general_mode(P->p.mode) != general)
+    return reject(general ? "plan mode %lld is not a general mode (%lld)"
+                          : "plan mode %lld is a general mode (%lld): use sft_general",
                   P->p.mode, 0);
   return SFT_OK;
 }

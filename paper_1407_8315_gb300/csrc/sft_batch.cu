@@ -35,8 +35,8 @@ struct ShapeKey {
 
 ShapeKey key_of(const sft_params& p) {
   return ShapeKey{p.N,         p.d,       p.a_max,    p.mode == SFT_EXACT_ITER ? p.max_iters : 0,
-                  p.mode,      p.precision, p.mode == SFT_GENERAL ? p.n_cs_shifts : 0,
-                  p.mode == SFT_GENERAL ? p.seed : 0, p.zero_tol, p.root_tol, p.res_tol};
+                  p.mode,      p.precision, sft::is_general_mode(p.mode) ? p.n_cs_shifts : 0,
+                  sft::is_general_mode(p.mode) ? p.seed : 0, p.zero_tol, p.root_tol, p.res_tol};
 }
 
 struct Group {

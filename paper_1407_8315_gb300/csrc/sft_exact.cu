@@ -167,13 +167,16 @@ __global__ void __launch_bounds__(256) k_extract(const In* __restrict__ x, int64
 // M = M1 M2 with n = n1 M2 + n2 and k = k1 + M1 k2:
 //   A[k1][n2] = sum_{n1} x_d[n1 M2 + n2] e^{-2 pi i n1 k1 / M1}        (cols)
 //   Y[k1 + M1 k2] = sum_{n2} A[k1][n2] e^{-2 pi i n2 k1 / M} e^{-2 pi i n2 k2 / M2}
-// k_fft4_cols runs 8192/M1 column FFTs per CTA (each on M1/16 threads) and
-// writes twiddled rows W[k1][n2]; k_fft4_rows runs 8192/M2 row FFTs per CTA
-// and writes Y (times d).  Both move data in coalesced runs.
-constexpr int kFft4Points = 8192;
+// A CTA holds P = blockDim * PTS points: k_fft4_cols runs P/M1 column FFTs
+// (each on M1/PTS threads) and writes twiddled rows W[k1][n2]; k_fft4_rows
+// runs P/M2 row FFTs and writes Y (times d).  Both move data in coalesced
+// runs.  With 8 points per thread P = max(4096, M1): two CTAs per SM, so
+// that one CTA's loads overlap the other's butterflies.
+constexpr int kFft4Points = 8192;  // largest one-CTA FFT; P of the 16-point form
+constexpr int kFft4Cta8 = 4096;
 
-template <class F>
-__global__ void __launch_bounds__(512) k_fft4_cols(
+template <class F, int PTS>
+__global__ void __launch_bounds__(8192 / PTS) k_fft4_cols(
     const typename F::In* __restrict__ x, int64_t x_stride, int64_t N, int64_t d, int log2M1,
     int log2M2, int shift0, int log2Mt, const typename F::Tw* __restrict__ tw,
     typename F::Out* __restrict__ W, int64_t w_sig, int nshift,
@@ -183,26 +186,26 @@ __global__ void __launch_bounds__(512) k_fft4_cols(
   const int64_t shift = shift_list != nullptr ? shift_list[js] : shift0 + js;
   const int M1 = 1 << log2M1, M2 = 1 << log2M2;
   const int log2M = log2M1 + log2M2;
-  const int CB = kFft4Points >> log2M1;  // columns per CTA
-  const int tpg = M1 / 16;               // threads per column
+  const int CB = (int)(blockDim.x * PTS) >> log2M1;  // columns per CTA
+  const int tpg = M1 / PTS;              // threads per column
   const int tid = threadIdx.x, g = tid / tpg, t = tid % tpg;
   const int c0 = blockIdx.x * CB;
   const typename F::In* xs = x_table != nullptr
                                  ? reinterpret_cast<const typename F::In*>(x_table[b])
                                  : x + (int64_t)b * x_stride;
   char* buf = smem + (size_t)g * padded(M1) * F::kBytesPerPoint;
-  typename F::In v[16];
+  typename F::In v[PTS];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
+  for (int i = 0; i < PTS; ++i) {
     const int64_t n = (int64_t)(t + i * tpg) * M2 + c0 + g;
     v[i] = __ldg(xs + ((n * d + shift) & (N - 1)));
   }
 #pragma unroll
-  for (int i = 0; i < 16; ++i) F::st(buf, M1, t + i * tpg, F::from_in(v[i]));
+  for (int i = 0; i < PTS; ++i) F::st(buf, M1, t + i * tpg, F::from_in(v[i]));
   __syncthreads();
-  cta_fft<F>(buf, log2M1, log2Mt, tw, t, tpg);
+  cta_fft<F, PTS>(buf, log2M1, log2Mt, tw, t, tpg);
   // twiddle e^{-2 pi i n2 k1 / M} (table of e^{-2 pi i q / Mt}, Mt >= M)
-  for (int i = 0; i < 16; ++i) {
+  for (int i = 0; i < PTS; ++i) {
     const int k1 = t + i * tpg;
     const int64_t q = ((int64_t)(c0 + g) * k1) & ((int64_t(1) << log2M) - 1);
     F::st(buf, M1, k1, F::mul_tw(F::ld(buf, M1, k1), __ldg(tw + (q << (log2Mt - log2M)))));
@@ -216,8 +219,8 @@ __global__ void __launch_bounds__(512) k_fft4_cols(
   }
 }
 
-template <class F>
-__global__ void __launch_bounds__(512) k_fft4_rows(
+template <class F, int PTS>
+__global__ void __launch_bounds__(8192 / PTS) k_fft4_rows(
     const typename F::Out* __restrict__ W, int64_t w_sig, int log2M1, int log2M2, int64_t d,
     int log2Mt, const typename F::Tw* __restrict__ tw, void* __restrict__ out_v, int64_t out_sig,
     int64_t out_row, int row0, unsigned long long* __restrict__ ymax2, int shift0) {
@@ -225,8 +228,8 @@ __global__ void __launch_bounds__(512) k_fft4_rows(
   typedef typename F::Out Out;
   const int b = blockIdx.z, js = blockIdx.y;
   const int M1 = 1 << log2M1, M2 = 1 << log2M2;
-  const int RB = kFft4Points >> log2M2;  // rows per CTA
-  const int tpg = M2 / 16;
+  const int RB = (int)(blockDim.x * PTS) >> log2M2;  // rows per CTA
+  const int tpg = M2 / PTS;
   const int tid = threadIdx.x, g = tid / tpg, t = tid % tpg;
   const int r0 = blockIdx.x * RB;
   const Out* Wi = W + (int64_t)b * w_sig + (int64_t)js * ((int64_t)M1 * M2);
@@ -237,17 +240,24 @@ __global__ void __launch_bounds__(512) k_fft4_rows(
   }
   __syncthreads();
   char* buf = smem + (size_t)g * padded(M2) * F::kBytesPerPoint;
-  cta_fft<F>(buf, log2M2, log2Mt, tw, t, tpg);
+  cta_fft<F, PTS>(buf, log2M2, log2Mt, tw, t, tpg);
   __syncthreads();
   Out* o = reinterpret_cast<Out*>(out_v) + (int64_t)b * out_sig + (int64_t)(row0 + js) * out_row;
-  double lmax = 0.0;
+  // running max of |Y|^2 in the output's own precision (FP32 hi parts on
+  // the mixed path: no FP64 instruction per element)
+  typename std::conditional<std::is_same<F, F64>::value, double, float>::type lmax_t = 0;
+  const auto scale = (typename std::conditional<std::is_same<F, F64>::value, double, float>::type)d;
   for (int idx = tid; idx < RB * M2; idx += blockDim.x) {
     const int k2 = idx / RB, gg = idx % RB;
     const char* bg = smem + (size_t)gg * padded(M2) * F::kBytesPerPoint;
-    const Out w = F::out(F::ld(bg, M2, k2), d);
+    const Out w = F::out(F::ld(bg, M2, k2), scale);
     o[(int64_t)(r0 + gg) + (int64_t)M1 * k2] = w;
-    lmax = fmax(lmax, F::out_norm(w));
+    if constexpr (std::is_same<F, F64>::value)
+      lmax_t = fmax(lmax_t, F::out_norm(w));
+    else
+      lmax_t = fmaxf(lmax_t, F::out_norm_hi(w));
   }
+  double lmax = (double)lmax_t;
   if (ymax2 != nullptr && js == 0 && shift0 == 0) {
     __shared__ double wmax[32];
 #pragma unroll
@@ -691,9 +701,13 @@ static cudaError_t prepare_kernels_t() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_gather_fft<F, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_fft4_cols<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(k_fft4_cols<F, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_fft4_rows<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(k_fft4_rows<F, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fft4_cols<F, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fft4_rows<F, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return e;
 }
 
@@ -711,6 +725,7 @@ int launches_per_call(const sft_plan_s* P) {
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int fin = fin_single(P, P->max_signals, nsm) ? 1 : 2;
+  if (P->p.mode == SFT_GENERAL_UNPRUNED) return (P->M0 > kFft4Points ? 2 : 1) + 1 + fin;
   if (P->p.mode == SFT_GENERAL)
     return 2 * (P->M0 > kFft4Points ? 2 : 1) + 5 + (P->p.a_max >= 2 ? 2 : 1) +
            (P->mlp != nullptr ? 1 : 0) + fin;
@@ -788,19 +803,31 @@ void launch_gather_fft(sft_plan_s* P, int64_t B, const GatherSrc& src, int64_t d
   // four-step: columns of length M1, rows of length M2, M1 >= M2
   const int log2M2 = log2M / 2, log2M1 = log2M - log2M2;
   const int64_t Mlev = int64_t(1) << log2M;
-  const unsigned ctas = (unsigned)(Mlev / kFft4Points);
-  const size_t smem = (size_t)padded(kFft4Points) * F::kBytesPerPoint;
+  const int pcta = P->fft_pts == 8 ? std::max(kFft4Cta8, 1 << log2M1) : kFft4Points;
+  const unsigned ctas = (unsigned)(Mlev / pcta);
+  const size_t smem = (size_t)padded(pcta) * F::kBytesPerPoint;
   auto* W = reinterpret_cast<typename F::Out*>(P->ws.fft4);
   const int64_t w_sig = (int64_t)nshift * Mlev;
+  const dim3 grid4(ctas, nshift, (unsigned)B);
   stage_begin(P, stage ? stage : cnames[lvl], st);
-  k_fft4_cols<F><<<dim3(ctas, nshift, (unsigned)B), 512, smem, st>>>(
-      xin, src.stride, src.N, src.d, log2M1, log2M2, shift0, P->log2M0, tw, W, w_sig, nshift,
-      shift_list, src.table);
+  if (P->fft_pts == 8)
+    k_fft4_cols<F, 8><<<grid4, pcta / 8, smem, st>>>(xin, src.stride, src.N, src.d, log2M1, log2M2,
+                                                 shift0, P->log2M0, tw, W, w_sig, nshift,
+                                                 shift_list, src.table);
+  else
+    k_fft4_cols<F, 16><<<grid4, 512, smem, st>>>(xin, src.stride, src.N, src.d, log2M1, log2M2,
+                                                 shift0, P->log2M0, tw, W, w_sig, nshift,
+                                                 shift_list, src.table);
   stage_end(P, st);
   stage_begin(P, stage ? "fft_rows" : rnames[lvl], st);
-  k_fft4_rows<F><<<dim3(ctas, nshift, (unsigned)B), 512, smem, st>>>(
-      W, w_sig, log2M1, log2M2, dscale, P->log2M0, tw, out, P->ws.held_elems, out_row, row0,
-      want_ymax ? P->ws.ymax2 : nullptr, shift0);
+  if (P->fft_pts == 8)
+    k_fft4_rows<F, 8><<<grid4, pcta / 8, smem, st>>>(W, w_sig, log2M1, log2M2, dscale, P->log2M0, tw,
+                                                 out, P->ws.held_elems, out_row, row0,
+                                                 want_ymax ? P->ws.ymax2 : nullptr, shift0);
+  else
+    k_fft4_rows<F, 16><<<grid4, 512, smem, st>>>(W, w_sig, log2M1, log2M2, dscale, P->log2M0, tw,
+                                                 out, P->ws.held_elems, out_row, row0,
+                                                 want_ymax ? P->ws.ymax2 : nullptr, shift0);
   stage_end(P, st);
 }
 
@@ -980,7 +1007,7 @@ cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int64_t M_last = P->M0;
   const uint8_t* T_last = W.T[0];
-  if (P->p.mode == SFT_GENERAL) {
+  if (is_general_mode(P->p.mode)) {
     launch_general(P, B, x, x_stride, nsm, st);
     M_last = 0;  // no unsolved-bin flags on the general path
   } else if (P->p.mode == SFT_EXACT_FIXED) {

@@ -757,9 +757,215 @@ static void general_solve(sft_plan_s* P, int64_t B, int nsm, cudaStream_t st, co
   stage_end(P, st);
 }
 
+// ------------------------------------------ the CS model without pruning
+// Sec. III-B without the pruning strategy: per bin k the r random-shift
+// syndromes y_j = Y_{n_j}[k] = sum_t b_t omega^{(k + tM) n_j} (Eq. (18))
+// over all d candidates, solved by Subspace Pursuit at sparsity a_m, every
+// non-zero coefficient kept.  As omega^{(k + tM) n_j} = omega^{k n_j}
+// e^{2 pi i t n_j / d}, the bin's rows are rotated once (y~_j =
+// omega^{-k n_j} y_j, with the same solution b) and every column entry is
+// read from a shared-memory table of the d-th roots of unity,
+// Phi~[j][t] = E[(t n_j) mod d].  One warp per bin: the lanes stride the d
+// candidates for the correlations and merge their top-a lists; lane 0
+// solves the least-squares problems (at most 2 a_m columns) and shares the
+// residual through shared memory.
+constexpr int kUnprWarps = 8;
+
+struct UnprWarp {
+  cdbl yr[16];   // rotated syndromes y~
+  cdbl res[16];  // current residual (rotated frame)
+  int go;        // lane 0's verdict: continue with this bin
+};
+
+// The ks largest |sum_j conj(E[(t n_j) mod d]) v_j|^2 over t < d (ties: the
+// smaller t), returned ascending in T; every lane returns the same list.
+__device__ int unpr_top(const cdbl* E, int64_t d, const int* nj, int r, const cdbl* v, int ks,
+                        int* T) {
+  const int lane = threadIdx.x & 31;
+  double bv[4];
+  int bt[4];
+  int have = 0;
+  for (int64_t t = lane; t < d; t += 32) {
+    cdbl c = mk(0.0, 0.0);
+    for (int j = 0; j < r; ++j) c = c + conjd(E[((int64_t)nj[j] * t) & (d - 1)]) * v[j];
+    const double val = norm2(c);
+    if (have < ks || val > bv[ks - 1]) {  // lane order visits t ascending: ties keep the first
+      int pos = have < ks ? have : ks - 1;
+      while (pos > 0 && bv[pos - 1] < val) {
+        bv[pos] = bv[pos - 1];
+        bt[pos] = bt[pos - 1];
+        --pos;
+      }
+      bv[pos] = val;
+      bt[pos] = (int)t;
+      if (have < ks) ++have;
+    }
+  }
+  int head = 0, n = 0;
+  int out[4];
+  for (int round = 0; round < ks; ++round) {
+    double v0 = head < have ? bv[head] : -1.0;
+    int t0 = head < have ? bt[head] : 0x7fffffff;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double v1 = __shfl_xor_sync(0xffffffffu, v0, o);
+      const int t1 = __shfl_xor_sync(0xffffffffu, t0, o);
+      if (v1 > v0 || (v1 == v0 && t1 < t0)) {
+        v0 = v1;
+        t0 = t1;
+      }
+    }
+    if (v0 < 0.0) break;
+    if (head < have && bt[head] == t0) ++head;
+    out[n++] = t0;
+  }
+  for (int i = 1; i < n; ++i)  // ascending candidates
+    for (int j = i; j > 0 && out[j - 1] > out[j]; --j) {
+      const int tt = out[j];
+      out[j] = out[j - 1];
+      out[j - 1] = tt;
+    }
+  for (int i = 0; i < n; ++i) T[i] = out[i];
+  return n;
+}
+
+// least squares of the rotated syndromes on the candidates T (lane 0)
+__device__ double unpr_ls(const cdbl* E, int64_t d, const int* nj, int r, const cdbl* yr,
+                          const int* T, int n, cdbl* x, cdbl* res) {
+  cdbl phi[16 * 8];
+  int id[8];
+  for (int u = 0; u < n; ++u) id[u] = u;
+  for (int j = 0; j < r; ++j)
+    for (int u = 0; u < n; ++u) phi[j * n + u] = E[((int64_t)nj[j] * T[u]) & (d - 1)];
+  return ls_cols<8>(r, n, phi, yr, id, n, x, res);
+}
+
+template <class F>
+__global__ void __launch_bounds__(32 * kUnprWarps) k_gen_unpruned(GenArgs g, int64_t B) {
+  typedef typename Store<F>::T T;
+  extern __shared__ __align__(16) char smem_u[];
+  const int64_t d = g.d, M = g.M;
+  const int r = g.r, ks = g.a_max;
+  cdbl* E = reinterpret_cast<cdbl*>(smem_u);
+  UnprWarp* w = reinterpret_cast<UnprWarp*>(E + d) + (threadIdx.x >> 5);
+  int nj[16];
+  for (int j = 0; j < r; ++j) nj[j] = (int)g.cs[j];
+  for (int64_t t = threadIdx.x; t < d; t += blockDim.x) E[t] = omega_pow(g.om, t * M);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * kUnprWarps;
+  for (int64_t e = (int64_t)blockIdx.x * kUnprWarps + (threadIdx.x >> 5); e < B * M; e += nw) {
+    const int b = (int)(e / M);
+    const int64_t k = e - (int64_t)b * M;
+    const T* Y = reinterpret_cast<const T*>(g.Y) + (int64_t)b * g.held_elems;
+    if (lane < r)
+      w->yr[lane] = conjd(omega_pow(g.om, k * g.cs[lane])) *
+                    Store<F>::to_d(Y[(2 * g.a_max + lane) * M + k]);
+    __syncwarp();
+    // initial selection and its least squares
+    int Tc[8], nT = unpr_top(E, d, nj, r, w->yr, ks, Tc);
+    cdbl x[8];
+    double rn = -1.0;
+    if (lane == 0) {
+      rn = unpr_ls(E, d, nj, r, w->yr, Tc, nT, x, w->res);
+      w->go = rn >= 0.0;
+    }
+    __syncwarp();
+    if (!w->go) continue;
+    for (int it = 0; it < g.sp_iters; ++it) {
+      int add[8];
+      const int na = unpr_top(E, d, nj, r, w->res, ks, add);
+      if (lane == 0) {
+        // union, least squares on it, its ks largest coefficients, again
+        int U[8], nu = 0, i = 0, j = 0;
+        while (i < nT || j < na) {
+          const int v = (j >= na || (i < nT && Tc[i] <= add[j])) ? Tc[i] : add[j];
+          if (i < nT && Tc[i] == v) ++i;
+          if (j < na && add[j] == v) ++j;
+          U[nu++] = v;
+        }
+        cdbl xu[8], ru[16];
+        bool ok = unpr_ls(E, d, nj, r, w->yr, U, nu, xu, ru) >= 0.0;
+        if (ok) {
+          double mag[8];
+          for (int u = 0; u < nu; ++u) mag[u] = norm2(xu[u]);
+          int sel[8];
+          const int nn = top_ks(nu, mag, nu >= 32 ? 0xffffffffu : ((1u << nu) - 1u), ks, sel);
+          int Tn[8];
+          for (int u = 0; u < nn; ++u) Tn[u] = U[sel[u]];
+          cdbl xn[8], rsn[16];
+          const double rnn = unpr_ls(E, d, nj, r, w->yr, Tn, nn, xn, rsn);
+          ok = rnn >= 0.0 && rnn < rn;
+          if (ok) {
+            nT = nn;
+            for (int u = 0; u < nn; ++u) {
+              Tc[u] = Tn[u];
+              x[u] = xn[u];
+            }
+            for (int q = 0; q < r; ++q) w->res[q] = rsn[q];
+            rn = rnn;
+          }
+        }
+        w->go = ok;
+      }
+      __syncwarp();
+      if (!w->go) break;  // (only lane 0's selection and coefficients are used)
+    }
+    if (lane == 0) {
+      int64_t s_out[8];
+      cdbl p_out[8];
+      int nout = 0;
+      for (int u = 0; u < nT; ++u) {
+        if (x[u].x == 0.0 && x[u].y == 0.0) continue;
+        s_out[nout] = k + (int64_t)Tc[u] * M;
+        p_out[nout] = x[u];
+        ++nout;
+      }
+      if (nout > 0)
+        file_n<F>(nout, s_out, p_out, M, g.slot_cnt + (int64_t)b * M, g.slot_s + (int64_t)b * M * 4,
+                  reinterpret_cast<T*>(g.slot_p) + (int64_t)b * M * 4, g.flags + b);
+    }
+    __syncwarp();
+  }
+}
+
+static size_t unpruned_smem(int64_t d) { return (size_t)d * sizeof(cdbl) + kUnprWarps * sizeof(UnprWarp); }
+
+template <class F>
+static void launch_unpruned_t(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int nsm,
+                              cudaStream_t st) {
+  const Workspace& W = P->ws;
+  const int am = P->p.a_max, r = P->p.n_cs_shifts;
+  // only the r random shifts (rows 2a_m .. 2a_m + r - 1 of the general layout)
+  launch_gather_fft_any(P, B, x, x_stride, P->p.d, P->log2M0, 0, r, W.held[0], P->M0, 2 * am,
+                        false, st, P->tab.cs_shifts, "gather_fft_random");
+  GenArgs g{P->p.N, P->M0, P->p.d, P->p.K, am, r, 2, 8, W.held[0], W.held_elems, nullptr,
+            nullptr, nullptr, nullptr, P->tab.cs_shifts, nullptr, W.slot_cnt, W.slot_s,
+            W.slot_p, W.flags,
+            OmegaTab{P->tab.om_hi, P->tab.om_lo, P->tab.om_lo_bits, P->p.N - 1}};
+  const size_t smem = unpruned_smem(P->p.d);
+  // the attribute is set to the largest table (d = 4096) so that no plan
+  // lowers it under another's captured launches
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_gen_unpruned<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)unpruned_smem(4096));
+    attr_set = true;
+  }
+  const int64_t warps = B * P->M0;
+  const int64_t ctas = std::min<int64_t>((warps + kUnprWarps - 1) / kUnprWarps, (int64_t)nsm * 8);
+  stage_begin(P, "gen_unpruned_sp", st);
+  k_gen_unpruned<F><<<(unsigned)ctas, 32 * kUnprWarps, smem, st>>>(g, B);
+  stage_end(P, st);
+}
+
 template <class F>
 static void launch_general_t(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int nsm,
                              cudaStream_t st) {
+  if (P->p.mode == SFT_GENERAL_UNPRUNED) {
+    launch_unpruned_t<F>(P, B, x, x_stride, nsm, st);
+    return;
+  }
   GenArgs g = general_front<F>(P, B, x, x_stride, st);
   if (P->mlp != nullptr && P->mlp_prop != nullptr) {
     mlp_propose(P, B, nsm, st);

@@ -11,6 +11,11 @@
 
 namespace sft {
 
+// Algorithm 2 with or without the pruning strategy
+inline bool is_general_mode(int mode) {
+  return mode == SFT_GENERAL || mode == SFT_GENERAL_UNPRUNED;
+}
+
 // Device workspace of one call for up to B signals.  Per signal:
 //   held[2]   ping-pong syndrome buffers, `held_elems` double2 each
 //             (ITER level l keeps rows j < 2l+2 of length M_l; FIXED keeps
@@ -51,8 +56,9 @@ struct Workspace {
 inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, int mode,
                                int a_max, int n_cs = 0, int levels = 0, int xc_esize = 0) {
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+  const bool gen = is_general_mode(mode);
   const int64_t held_elems = mode == SFT_EXACT_FIXED ? 2 * a_max * M0
-                             : mode == SFT_GENERAL   ? (2 * a_max + n_cs) * M0
+                             : gen                   ? (2 * a_max + n_cs) * M0
                                                      : 2 * M0;
   const int nbuf = mode == SFT_EXACT_ITER ? 2 : 1;  // only ITER keeps two levels
   size_t off = 0;
@@ -79,7 +85,7 @@ inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, 
   if (mode == SFT_GENERAL) off = al(off + (size_t)(B * M0 * a_max) * 8);
   // four-step FFT intermediate: one M0-point plane per shift of a launch
   const int nsh = mode == SFT_EXACT_FIXED ? 2 * a_max
-                  : mode == SFT_GENERAL   ? (2 * a_max > n_cs ? 2 * a_max : n_cs)
+                  : gen                   ? (2 * a_max > n_cs ? 2 * a_max : n_cs)
                                           : 2;
   const size_t o_f4 = off;
   if (M0 > 8192) off = al(off + (size_t)(B * nsh * M0) * 16);

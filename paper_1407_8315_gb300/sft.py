@@ -18,10 +18,11 @@ import numpy as np
 from . import _build_lib
 
 SFT_OK, SFT_EINVAL, SFT_ENOMEM, SFT_ECUDA, SFT_ETIMEOUT, SFT_EUNSUPPORTED = range(6)
-SFT_EXACT_ITER, SFT_EXACT_FIXED, SFT_GENERAL = 0, 1, 2
+SFT_EXACT_ITER, SFT_EXACT_FIXED, SFT_GENERAL, SFT_GENERAL_UNPRUNED = 0, 1, 2, 3
 SFT_FP64, SFT_MIXED = 0, 1
 
-_MODES = {"iter": SFT_EXACT_ITER, "fixed": SFT_EXACT_FIXED, "general": SFT_GENERAL}
+_MODES = {"iter": SFT_EXACT_ITER, "fixed": SFT_EXACT_FIXED, "general": SFT_GENERAL,
+          "general-unpruned": SFT_GENERAL_UNPRUNED}
 _PRECS = {"fp64": SFT_FP64, "mixed": SFT_MIXED}
 
 
@@ -132,6 +133,8 @@ def load(build_if_missing: bool = False):
     lib.sft_plan_attach_mlp.argtypes = [C.c_void_p, C.c_void_p]
     lib.sft_exact_auto.argtypes = [P(sft_params), C.c_int64, C.c_void_p, C.c_int64, C.c_int64,
                                    C.c_int64, P(sft_result), C.c_void_p, C.c_void_p]
+    lib.sft_alias_histogram.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
+                                        C.c_void_p, C.c_void_p]
     lib.sft_strerror.argtypes = [C.c_int]
     lib.sft_strerror.restype = C.c_char_p
     lib.sft_last_cuda_error.argtypes = []
@@ -298,7 +301,7 @@ class Plan:
         p = sft_params_default(N, K, d, mode, precision)
         if a_max:
             p.a_max = int(a_max)
-            if mode == "general" and not n_cs_shifts:
+            if mode in ("general", "general-unpruned") and not n_cs_shifts:
                 p.n_cs_shifts = 3 * int(a_max)
         p.max_iters = int(max_iters) if max_iters else int(p.a_max)
         p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
@@ -566,3 +569,19 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+def alias_histogram(supports, M: int, n_cells: int = 9, stream=None):
+    """Collision counts of Sec. II-C: supports is a device int64 tensor
+    [n_sets, K]; returns a device int64 tensor hist[n_cells] with hist[a] the
+    number of (set, bin) pairs whose bin k < M holds exactly a locations
+    (the last cell: n_cells - 1 or more)."""
+    import torch
+    if supports.dtype != torch.int64 or not supports.is_cuda or supports.dim() != 2:
+        raise ValueError("supports must be a 2-D int64 CUDA tensor")
+    s = supports.contiguous()
+    hist = torch.empty(int(n_cells), dtype=torch.int64, device=s.device)
+    _check(load().sft_alias_histogram(C.c_void_p(s.data_ptr()), s.shape[0], s.shape[1], int(M),
+                                      int(n_cells), C.c_void_p(hist.data_ptr()),
+                                      C.c_void_p(_stream_ptr(stream))), "sft_alias_histogram")
+    return hist

@@ -79,6 +79,18 @@ def test_general_plan_rejects_bad_shift_counts(lib, r, d):
     assert lib.sft_plan_create(C.byref(p), 1, C.byref(h)) == sft.SFT_EINVAL
 
 
+def test_unpruned_plan_defaults_and_limits(lib):
+    """The CS model without pruning takes the general defaults (a_m = 3,
+    r = 9) and a shared-memory table of d roots: d above 4096 is refused."""
+    from paper_1407_8315_gb300 import sft
+    p = sft.sft_params_default(1 << 20, 16, 8192, "general-unpruned", "mixed")
+    assert p.mode == sft.SFT_GENERAL_UNPRUNED and p.a_max == 3 and p.n_cs_shifts == 9
+    h = C.c_void_p()
+    assert lib.sft_plan_create(C.byref(p), 1, C.byref(h)) == sft.SFT_EUNSUPPORTED
+    p.n_cs_shifts = 17
+    assert lib.sft_plan_create(C.byref(p), 1, C.byref(h)) == sft.SFT_EINVAL
+
+
 def test_plan_create_rejects_too_many_bins(lib):
     """N/d = 2^27 bins is above the four-step FFT limit (2^26)."""
     from paper_1407_8315_gb300 import sft

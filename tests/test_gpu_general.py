@@ -103,3 +103,47 @@ def test_exact_entry_rejects_general_plan(gpu):
     x = torch.zeros((1, 1 << 14), dtype=torch.complex64, device="cuda")
     with pytest.raises(SftError):
         plan.exact(x, 64)
+
+
+@pytest.mark.parametrize("N,K,d,a_max,prec,snr", [
+    (1 << 14, 32, 16, 3, "mixed", 20),
+    (1 << 16, 16, 128, 3, "fp64", 30),
+    (1 << 16, 64, 64, 4, "mixed", 30),
+    (1 << 18, 8, 2048, 3, "mixed", 10),
+    (1 << 20, 1024, 32, 3, "mixed", 30),
+])
+def test_unpruned_matches_oracle(gpu, orc, N, K, d, a_max, prec, snr):
+    """The CS model without pruning (Sec. III-B): every bin by Subspace
+    Pursuit at sparsity a_m over all d candidates, against the oracle's
+    prune=False path -- identical supports (every non-zero coefficient of
+    every bin), values within the precision's tolerance.  d from 16 to 2048
+    (the shared-memory root table), M = 2^15 runs the four-step FFT."""
+    from paper_1407_8315_gb300 import Plan
+    M = N // d
+    plan = Plan(N, K, d, "general-unpruned", prec, max_signals=2, a_max=a_max, seed=snr + d)
+    dt = np.complex128 if prec == "fp64" else np.complex64
+    xs = np.stack([siggen.noisy_signal(N, K, 500 + d + i, snr, mag=(1, 10), dtype=dt)[0]
+                   for i in range(2)])
+    cap = M * a_max
+    idx, val, cnt, unres, ovf = _run(gpu, plan, xs, cap)
+    tol = FP64_VAL_TOL if prec == "fp64" else MIXED_VAL_TOL
+    for b in range(2):
+        oi, ov, _ = orc.general(xs[b], M, K, a_max=a_max, seed=snr + d, cap=cap, prune=False)
+        n = int(cnt[b])
+        o = np.argsort(idx[b, :n], kind="stable")
+        gi, gv = idx[b, :n][o], val[b, :n][o]
+        assert ovf[b] == 0 and unres[b] == 0
+        np.testing.assert_array_equal(gi, oi, err_msg=f"signal {b}: supports differ")
+        scale = np.abs(ov).max()
+        assert np.abs(gv - ov).max() <= tol * scale
+
+
+def test_unpruned_overflow_keeps_cap_entries(gpu):
+    """A result capacity below a_m N/d sets the overflow flag and fills the
+    capacity."""
+    from paper_1407_8315_gb300 import Plan
+    N, K, d = 1 << 14, 32, 16
+    plan = Plan(N, K, d, "general-unpruned", "mixed", seed=1)
+    x = siggen.noisy_signal(N, K, 7, 20, mag=(1, 10))[0][None, :]
+    idx, val, cnt, unres, ovf = _run(gpu, plan, x, 64)
+    assert int(ovf[0]) == 1 and int(cnt[0]) == 64

@@ -171,3 +171,64 @@ def test_snr_out_drops_above_n_over_k_2_9(orc):
         idx, val, _ = orc.general(x, M, K, a_max=3, seed=seed)
         outs.append(_snr_out(X, idx, val))
     assert np.mean(outs) < 8.5, outs
+
+
+# ---------------------------------------------- the CS model without pruning
+def test_unpruned_matches_per_bin_subspace_pursuit(orc):
+    """Sec. III-B without pruning, rebuilt independently in numpy: per bin k
+    the sensing matrix Phi[j][t] = omega^{(k + tM) n_j} (Eq. (18)) over all d
+    candidates, y_j = d * FFT_M(x[n d + n_j])[k], Subspace Pursuit at
+    sparsity a_m, every non-zero coefficient placed at k + tM."""
+    N, M, am = 1 << 10, 32, 2
+    d, r = N // M, 3 * am
+    x, _, _, _ = siggen.noisy_signal(N, 12, 4, 20, mag=(1, 10))
+    x = x.astype(np.complex128)
+    ns = orc.cs_shifts(9, d, r)
+    Y = np.stack([d * np.fft.fft(x[(np.arange(M) * d + n) % N]) for n in ns])
+    want = {}
+    for k in range(M):
+        s = k + np.arange(d) * M
+        Phi = np.exp(2j * np.pi * np.outer(ns, s) / N)
+        b = orc.subspace_pursuit(Phi, Y[:, k], am)
+        for t in np.nonzero(b)[0]:
+            want[int(s[t])] = b[t]
+    idx, val, ak = orc.general(x, M, 0, a_max=am, seed=9, cap=M * am, prune=False)
+    assert (ak == am).all()
+    assert sorted(want) == sorted(idx.tolist())
+    got = dict(zip(idx.tolist(), val))
+    err = max(abs(got[s] - v) / abs(v) for s, v in want.items())
+    assert err < 1e-9, err
+
+
+def test_unpruned_noiseless_recovers_planted_spectrum(orc):
+    """Without noise, bins holding at most a_m terms and r = 3 a_m random
+    shifts over d = 16 candidates: SP at sparsity a_m fits every bin
+    exactly, so the coefficients above rounding are the planted spectrum
+    (the other a_m - a selected coefficients are zero up to rounding)."""
+    checked = 0
+    for seed in range(6):
+        N, K, M, am = 1 << 14, 96, 1 << 10, 3
+        x, s, v = siggen.exact_signal(N, K, seed, mag=(1, 10))
+        if np.bincount(s % M, minlength=M).max() > am:
+            continue
+        idx, val, _ = orc.general(x, M, K, a_max=am, seed=seed, cap=M * am, prune=False)
+        big = np.abs(val) > 1e-8 * np.abs(v).max()
+        np.testing.assert_array_equal(idx[big], s)
+        assert np.abs(val[big] - v).max() < 1e-9 * np.abs(v).max()
+        checked += 1
+    assert checked >= 3
+
+
+def test_unpruned_reaches_snr_in_at_small_n_over_k(orc):
+    """Tables III-V: without pruning the output SNR also reaches the input
+    SNR at N/K = 2^8 (28.7 dB at 30 dB there): at least 28.5 dB.  Here
+    d = 8 candidates per bin, so r = 8 shifts (3 a_m = 9 exceeds d)."""
+    N, K = 1 << 16, 1 << 8
+    M = 32 * K
+    outs = []
+    for seed in range(3):
+        x, _, _, _ = siggen.noisy_signal(N, K, 300 + seed, 30, mag=(1, 10))
+        X = np.fft.fft(x.astype(np.complex128))
+        idx, val, _ = orc.general(x, M, K, a_max=3, r=8, seed=seed, cap=3 * M, prune=False)
+        outs.append(_snr_out(X, idx, val))
+    assert np.mean(outs) > 28.5, outs
