@@ -194,6 +194,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--sub-batches", type=int, default=0,
+                    help="sub-batches per call on forked streams (0: the plan's choice)")
     ap.add_argument("--crossover", action="store_true",
                     help="dense-FFT crossover study: one JSON line per (N, K, path) against "
                          "cuFFT on the same batch, then a summary line")
@@ -359,10 +361,11 @@ def kernel_source_hash(kernel: str):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload: str, kernel: str):
+def ncu_traffic(workload: str, kernel: str, signals: float):
     """DRAM bytes per launch of `kernel` in `workload` from the committed ncu
-    summary, or None when it is missing or the kernel's source changed since
-    the counters were taken."""
+    summary, scaled to `signals` signals per launch (the traffic grows with
+    the signals), or None when it is missing or the kernel's source changed
+    since the counters were taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             t = json.load(f)
@@ -371,7 +374,7 @@ def ncu_traffic(workload: str, kernel: str):
     ent = t.get(workload, {}).get(kernel)
     if not ent or ent.get("source_sha") != kernel_source_hash(kernel):
         return None
-    return ent.get("dram_bytes_per_launch")
+    return ent["dram_bytes_per_launch"] * signals / ent.get("signals_per_launch", signals)
 
 
 def kernel_of(stage: str, M: int = 0) -> str:
@@ -394,6 +397,7 @@ def kernel_of(stage: str, M: int = 0) -> str:
 
 
 def roofline(wl, stages, B, clk):
+    # B: signals per launch (the call's signals over its sub-batches)
     """Dominant kernel (largest share of the step) and its roofline.  The
     gather/FFT kernels of the mixed form are bound by the FP32 pipes (the
     float-float FFT), so 'achieved' counts the FFT's radix-2 butterflies at
@@ -417,7 +421,7 @@ def roofline(wl, stages, B, clk):
     sec = dom["ms"] / 1e3
     roof = {"kernel": dom_name, "share": dom["ms"] / step_ms,
             "ms_per_launch": dom["ms"] / dom["launches"], "peak_source": src,
-            "traffic": ncu_traffic(wl.name, dom_name)}
+            "traffic": ncu_traffic(wl.name, dom_name, B)}
     mhz = (clk or {}).get("sm_mhz") or 2070.0
     if dom["ops"] and wl.precision != "fp64":
         peak = 152 * 128 * mhz * 1e6 / 1e12
@@ -636,6 +640,7 @@ def run_plan_workload(args, wl):
         tol = dict(zero_tol=mixed.zero_tol, root_tol=mixed.root_tol, res_tol=mixed.res_tol)
     plan = Plan(wl.N, wl.K, wl.d, wl.mode, wl.precision, max_signals=B, a_max=wl.a_max,
                 seed=wl.plan_seed, n_cs_shifts=wl.r if wl.general else 0, **tol)
+    plan.set_sub_batches(args.sub_batches)
     fn = plan.general if wl.general else plan.exact
     fn_host = plan.general_host if wl.general else plan.exact_host
     cap = wl.cap
@@ -738,7 +743,9 @@ def run_plan_workload(args, wl):
         dist.destroy_process_group()
         return
 
-    roof = roofline(wl, stages, B, clk)
+    n_sub = plan.sub_batches(B)
+    roof = roofline(wl, stages, B / n_sub, clk)
+    roof["signals_per_launch"] = B / n_sub
     stage_ms = {k: round(v[0] / v[1], 5) for k, v in stages.items()}
 
     # ---- CPU baseline (the oracle on the host cores) and error vs the oracle
@@ -769,7 +776,7 @@ def run_plan_workload(args, wl):
         "config": {"workload": wl.desc, "batch_per_gpu": B, "mode": wl.mode,
                    "precision": "plain FP64" if wl.precision == "fp64"
                    else "mixed (compensated-FP32 FFT, FP64 solves)",
-                   "parallelism": f"replicas x{ws}",
+                   "parallelism": f"replicas x{ws}", "sub_batches_per_call": n_sub,
                    "l2": f"flushed between timed steps ({FLUSH_BYTES >> 20} MiB write, outside "
                          f"the step events)"},
         **quality, "vs_oracle": err,

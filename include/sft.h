@@ -360,7 +360,8 @@ sft_status sft_exact_auto(const sft_params* p, int64_t n_signals, const void* x,
 /* Collision counts (Sec. II-C, Lemma 2 and Fig. 2): for n_sets support sets
  * of K locations each, the number of bins k < M holding exactly a of a
  * set's locations (k = s mod M), summed over the sets.
- *   supports  device int64 [n_sets][K]; any values (only s mod M is used)
+ *   supports  device int64 [n_sets][K]; any values (only s mod M is used);
+ *             may be NULL when n_sets or K is 0
  *   M         number of bins, a power of two <= 2^15
  *   n_cells   2..33: hist[a] for a < n_cells - 1, hist[n_cells - 1] counts
  *             the bins holding n_cells - 1 or more
@@ -373,6 +374,18 @@ sft_status sft_alias_histogram(const int64_t* supports, int64_t n_sets, int64_t 
 /* Number of kernel launches one call of this plan on max_signals signals
  * issues (sft_exact / sft_general). */
 int32_t sft_plan_launches_per_call(sft_plan_t plan);
+
+/* Sub-batching.  A call on n signals may be split into S sub-batches of
+ * consecutive signals (sizes differ by at most one), each enqueued on its
+ * own stream forked from and joined back into the call's stream, so that
+ * the latency-bound stages of one overlap the throughput-bound stages of
+ * another.  Results are identical for every S.  n = 0 (the default)
+ * chooses S = min(4, n_signals / 32) (at least 1); 1..4
+ * fixes it (capped at the call's signal count).  The plan creates its
+ * three extra streams when it is created.  sft_plan_sub_batches returns the S a
+ * call of n_signals signals would use.  SFT_EINVAL for n outside 0..4. */
+sft_status sft_plan_set_sub_batches(sft_plan_t plan, int32_t n);
+int32_t sft_plan_sub_batches(sft_plan_t plan, int64_t n_signals);
 
 /* Per-stage timing.  With profiling enabled, every launch of an sft_exact
  * call on this plan is bracketed by CUDA events recorded on the call's

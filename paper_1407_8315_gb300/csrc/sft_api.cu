@@ -83,6 +83,14 @@ void free_plan_memory(sft_plan_s* P) {
                   P->mlp_prop};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  for (int s = 0; s < sft::kMaxSub; ++s) {
+    if (P->sub_st[s]) cudaStreamDestroy(P->sub_st[s]);
+    if (P->sub_join[s]) cudaEventDestroy(P->sub_join[s]);
+    P->sub_st[s] = nullptr;
+    P->sub_join[s] = nullptr;
+  }
+  if (P->sub_fork) cudaEventDestroy(P->sub_fork);
+  P->sub_fork = nullptr;
 }
 
 // SplitMix64 (Steele, Lea, Flood 2014), output i of the stream of `seed`
@@ -255,6 +263,12 @@ sft_status sft_plan_create(const sft_params* pin, int64_t max_signals, sft_plan_
   cudaError_t e = upload_tables(P, &total);
   if (e == cudaSuccess) e = alloc_workspace(P, &total);
   if (e == cudaSuccess) e = sft::prepare_kernels(P);
+  // the sub-batch streams and events (created here, outside any capture)
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->sub_fork, cudaEventDisableTiming);
+  for (int s = 1; e == cudaSuccess && s < sft::kMaxSub; ++s) {
+    e = cudaStreamCreateWithFlags(&P->sub_st[s], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->sub_join[s], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     note_cuda(e);
     free_plan_memory(P);
@@ -461,6 +475,16 @@ static void free_event_pool(sft_plan_s* P) {
   for (cudaEvent_t e : P->event_pool) cudaEventDestroy(e);
   P->event_pool.clear();
   P->events_used = 0;
+}
+
+sft_status sft_plan_set_sub_batches(sft_plan_t P, int32_t n) {
+  if (!P || n < 0 || n > sft::kMaxSub) return SFT_EINVAL;
+  P->sub_batches = n;
+  return SFT_OK;
+}
+
+int32_t sft_plan_sub_batches(sft_plan_t P, int64_t n_signals) {
+  return P ? sft::sub_batches_for(P, n_signals) : 0;
 }
 
 sft_status sft_plan_set_profiling(sft_plan_t P, int32_t enable) {

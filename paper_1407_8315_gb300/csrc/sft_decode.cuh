@@ -286,6 +286,87 @@ __device__ __forceinline__ int ff_residual_ok(const float4* raw, const int64_t* 
   return 1;
 }
 
+// The one-alias decode of the mixed path entirely in float-float on the
+// FP32 pipes, from the syndromes `raw` (Sec. II-A: z = m_1 / m_0, snapped to
+// S_k; p = (1/nm) sum_i conj(w^i) m_i; the residual test).  It takes the
+// FP64 decoder's decisions: every FP32 quantity that decides is formed as
+// the FP64 decoder forms it (the float rounding of the float-float value is
+// the float rounding of its FP64 value), and wherever a float-float result
+// lies within its error bound of a threshold (a candidate midpoint, the
+// root_tol bound, theta, the residual bound) or leaves the float range it
+// returns -1 and the caller runs the FP64 decoder.  Returns 1 on success
+// (s, the value p_ff and the residual res_out filled), 0 on failure.
+__device__ __forceinline__ float ff_re(const FF::V& v) { return __fadd_rn(v.rh, v.rl); }
+__device__ __forceinline__ float ff_im(const FF::V& v) { return __fadd_rn(v.ih, v.il); }
+__device__ __forceinline__ float ff_norm(const FF::V& v) {
+  const float x = ff_re(v), y = ff_im(v);
+  return x * x + y * y;
+}
+// x <= lim decided in FP32 unless within 1e-5 of lim (relative): -1 there
+__device__ __forceinline__ int ff_le(float x, double lim) {
+  if (!(x < 1e36f) || !(lim < 1e36)) return -1;
+  if (fabs((double)x - lim) <= 1e-5 * lim) return -1;
+  return (double)x <= lim ? 1 : 0;
+}
+
+template <int nm>
+__device__ __forceinline__ int decode_a1_ff(const float4* raw, int64_t k, const BinGeom& g,
+                                            const Tol2& tol, const OmegaTabFF& omff, int64_t* s,
+                                            float4* p_ff, float4* res_out) {
+  const FF::V m0 = FF::from4(raw[0]), m1 = FF::from4(raw[1]);
+  const float m0x = ff_re(m0), m0y = ff_im(m0), m1x = ff_re(m1), m1y = ff_im(m1);
+  if (m0x == 0.0f && m0y == 0.0f) return 0;
+  const float den = m0x * m0x + m0y * m0y;
+  if (!(den > 1e-30f && den < 1e30f)) return -1;
+  const float inv = __frcp_rn(den);
+  const float zx = (m1x * m0x + m1y * m0y) * inv, zy = (m1y * m0x - m1x * m0y) * inv;
+  if (zx == 0.0f && zy == 0.0f) return 0;
+  // the nearest candidate from the FP32 angle (as snap_root_f)
+  const float ang = atan2f(zy, zx);
+  const float df = (float)g.d;
+  const float q = fmaf(ang, df * 0.15915494309189533577f, -(float)k / (float)g.M);
+  const float fr = q - rintf(q);
+  if (fabsf(fabsf(fr) - 0.5f) < fmaxf(1e-3f, 8e-7f * df)) return -1;
+  int64_t t = ((int64_t)rintf(q)) % g.d;
+  if (t < 0) t += g.d;
+  s[0] = k + t * g.M;
+  const FF::V w = omega_ff(omff, s[0]);
+  const float dx = zx - ff_re(w), dy = zy - ff_im(w);
+  const float dz = dx * dx + dy * dy, r2 = (float)tol.root2;
+  if (fabsf(dz - r2) <= 1e-4f * r2) return -1;
+  if (!(dz <= r2)) return 0;
+  // least squares over the nm equations: p = (1/nm) sum_i conj(w^i) m_i
+  FF::V acc = m0, wp = w;
+#pragma unroll
+  for (int i = 1; i < nm; ++i) {
+    const FF::V mi = FF::from4(raw[i]);
+    acc = FF::add(acc, FF::mul4(mi, wp.rh, wp.rl, -wp.ih, -wp.il));
+    if (i + 1 < nm) wp = FF::mulv(wp, w);
+  }
+  constexpr float inv_nm = 1.0f / (float)nm;  // a power of two: exact
+  const FF::V p{acc.rh * inv_nm, acc.rl * inv_nm, acc.ih * inv_nm, acc.il * inv_nm};
+  const int small = ff_le(ff_norm(p), tol.theta2);
+  if (small != 0) return small < 0 ? -1 : 0;
+  // residual r_i = m_i - p w^i over all equations
+  float mmax2 = 0.0f, rmax2 = 0.0f;
+  FF::V r[nm];
+  FF::V pw = p;
+#pragma unroll
+  for (int i = 0; i < nm; ++i) {
+    const FF::V mi = FF::from4(raw[i]);
+    r[i] = FF::sub(mi, pw);
+    if (i + 1 < nm) pw = FF::mulv(pw, w);
+    mmax2 = fmaxf(mmax2, ff_norm(mi));
+    rmax2 = fmaxf(rmax2, ff_norm(r[i]));
+  }
+  const int fits = ff_le(rmax2, tol.res2 * (double)mmax2);
+  if (fits <= 0) return fits;
+  *p_ff = FF::to4(p);
+#pragma unroll
+  for (int i = 0; i < nm; ++i) res_out[i] = FF::to4(r[i]);
+  return 1;
+}
+
 // Decode bin k with `a` aliases from m[0..nm).  On success fills s[0..a)
 // (ascending), p[0..a), replaces m[0..nm) by the residual m - Z p and
 // returns true; on failure m is unchanged.

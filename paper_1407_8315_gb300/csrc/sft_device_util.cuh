@@ -27,6 +27,20 @@ __device__ __forceinline__ void file_solution(const int64_t* s, const cdbl* p, i
   }
 }
 
+// File one recovered frequency whose value is already float-float.
+__device__ __forceinline__ void file_one_ff(int64_t s, float4 p, int64_t M0, uint8_t* cnt,
+                                            int64_t* ss, float4* sp, int32_t* flag) {
+  const int64_t k0 = s & (M0 - 1);
+  const int c = cnt[k0];
+  if (c < 4) {
+    ss[k0 * 4 + c] = s;
+    sp[k0 * 4 + c] = p;
+    cnt[k0] = (uint8_t)(c + 1);
+  } else {
+    atomicOr(flag, 1);
+  }
+}
+
 // Append (b, k) to a device queue when `pred`; one atomic per warp.  Every
 // lane of the warp must call this (inactive lanes with pred = false).
 __device__ __forceinline__ void queue_push(bool pred, int b, int k, int2* q, int* count) {

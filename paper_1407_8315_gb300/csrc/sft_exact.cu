@@ -174,6 +174,9 @@ __global__ void __launch_bounds__(256) k_extract(const In* __restrict__ x, int64
 // that one CTA's loads overlap the other's butterflies.
 constexpr int kFft4Points = 8192;  // largest one-CTA FFT; P of the 16-point form
 constexpr int kFft4Cta8 = 4096;
+// automatic sub-batching: as many sub-batches (up to 4) as hold this many
+// signals each
+constexpr int64_t kSubMinSignals = 32;
 
 template <class F, int PTS>
 __global__ void __launch_bounds__(8192 / PTS) k_fft4_cols(
@@ -403,24 +406,39 @@ __global__ void __launch_bounds__(kDecThreads) k_iter_decode(LevelArgs g, const 
     const Tol2 tol{g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]),
                    g.root_tol * g.root_tol, g.res_tol * g.res_tol};
     T raw[nm];
-    cdbl m[nm];
 #pragma unroll
-    for (int j = 0; j < nm; ++j) {
-      raw[j] = cur[j * M + k];
-      m[j] = Store<F>::to_d(raw[j]);
-    }
+    for (int j = 0; j < nm; ++j) raw[j] = cur[j * M + k];
     int64_t s[4];
     cdbl p[4];
+    cdbl m[nm];
     uint8_t t = 1;
-    bool ok;
+    bool ok = false, filed = false;
     float4 res[nm];
-    if constexpr (std::is_same<F, FF>::value)
-      ok = decode_bin<A, nm>(m, k, geom, tol, s, p, raw, &g.omff, res);
-    else
-      ok = decode_bin<A, nm>(m, k, geom, tol, s, p);
+    // one alias on the mixed path: float-float unless a value lies at a
+    // decision boundary (then the FP64 decoder below)
+    int fast = -1;
+    if constexpr (std::is_same<F, FF>::value && A == 1) {
+      float4 pf;
+      fast = decode_a1_ff<nm>(raw, k, geom, tol, g.omff, s, &pf, res);
+      if (fast == 1) {
+        file_one_ff(s[0], pf, M0, g.slot_cnt + (int64_t)b * M0, g.slot_s + (int64_t)b * M0 * 4,
+                    reinterpret_cast<float4*>(g.slot_p) + (int64_t)b * M0 * 4, g.flags + b);
+        ok = filed = true;
+      }
+    }
+    if (fast < 0) {
+#pragma unroll
+      for (int j = 0; j < nm; ++j) m[j] = Store<F>::to_d(raw[j]);
+      if constexpr (std::is_same<F, FF>::value)
+        ok = decode_bin<A, nm>(m, k, geom, tol, s, p, raw, &g.omff, res);
+      else
+        ok = decode_bin<A, nm>(m, k, geom, tol, s, p);
+    }
     if (ok) {
-      file_solution<F, A>(s, p, M0, g.slot_cnt + (int64_t)b * M0, g.slot_s + (int64_t)b * M0 * 4,
-                          reinterpret_cast<T*>(g.slot_p) + (int64_t)b * M0 * 4, g.flags + b);
+      if (!filed)
+        file_solution<F, A>(s, p, M0, g.slot_cnt + (int64_t)b * M0,
+                            g.slot_s + (int64_t)b * M0 * 4,
+                            reinterpret_cast<T*>(g.slot_p) + (int64_t)b * M0 * 4, g.flags + b);
       // the recovered terms leave every syndrome held for this bin
       if constexpr (std::is_same<F, FF>::value) {
 #pragma unroll
@@ -497,22 +515,34 @@ __global__ void __launch_bounds__(kDecThreads) k_fixed_round(FixedArgs g, const 
       const Tol2 tol{g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]),
                      g.root_tol * g.root_tol, g.res_tol * g.res_tol};
       T raw[NM];
-      cdbl m[NM];
 #pragma unroll
-      for (int j = 0; j < NM; ++j) {
-        raw[j] = Y[j * M + k];
-        m[j] = Store<F>::to_d(raw[j]);
-      }
+      for (int j = 0; j < NM; ++j) raw[j] = Y[j * M + k];
       int64_t s[4];
       cdbl p[4];
-      bool ok;
-      if constexpr (std::is_same<F, FF>::value)
-        ok = decode_bin<A, NM>(m, k, geom, tol, s, p, raw, &g.omff, nullptr);
-      else
-        ok = decode_bin<A, NM>(m, k, geom, tol, s, p);
+      bool ok = false, filed = false;
+      int fast = -1;
+      if constexpr (std::is_same<F, FF>::value && A == 1) {
+        float4 pf, res[NM];
+        fast = decode_a1_ff<NM>(raw, k, geom, tol, g.omff, s, &pf, res);
+        if (fast == 1) {
+          file_one_ff(s[0], pf, M, g.slot_cnt + (int64_t)b * M, g.slot_s + (int64_t)b * M * 4,
+                      reinterpret_cast<float4*>(g.slot_p) + (int64_t)b * M * 4, g.flags + b);
+          ok = filed = true;
+        }
+      }
+      if (fast < 0) {
+        cdbl m[NM];
+#pragma unroll
+        for (int j = 0; j < NM; ++j) m[j] = Store<F>::to_d(raw[j]);
+        if constexpr (std::is_same<F, FF>::value)
+          ok = decode_bin<A, NM>(m, k, geom, tol, s, p, raw, &g.omff, nullptr);
+        else
+          ok = decode_bin<A, NM>(m, k, geom, tol, s, p);
+      }
       if (ok) {
-        file_solution<F, A>(s, p, M, g.slot_cnt + (int64_t)b * M, g.slot_s + (int64_t)b * M * 4,
-                            reinterpret_cast<T*>(g.slot_p) + (int64_t)b * M * 4, g.flags + b);
+        if (!filed)
+          file_solution<F, A>(s, p, M, g.slot_cnt + (int64_t)b * M, g.slot_s + (int64_t)b * M * 4,
+                              reinterpret_cast<T*>(g.slot_p) + (int64_t)b * M * 4, g.flags + b);
       } else if (qout == nullptr) {
         g.T[(int64_t)b * M + k] = 1;
       } else {
@@ -720,11 +750,11 @@ static bool fin_single(const sft_plan_s* P, int64_t B, int nsm) {
   return B >= nsm && P->M0 <= 65536;
 }
 
-int launches_per_call(const sft_plan_s* P) {
-  int dev = 0, nsm = 152;
-  if (cudaGetDevice(&dev) == cudaSuccess)
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int fin = fin_single(P, P->max_signals, nsm) ? 1 : 2;
+int sub_batches_for(const sft_plan_s* P, int64_t B);
+
+// launches of one sub-batch of B signals
+static int launches_one(const sft_plan_s* P, int64_t B, int nsm) {
+  const int fin = fin_single(P, B, nsm) ? 1 : 2;
   if (P->p.mode == SFT_GENERAL_UNPRUNED) return (P->M0 > kFft4Points ? 2 : 1) + 1 + fin;
   if (P->p.mode == SFT_GENERAL)
     return 2 * (P->M0 > kFft4Points ? 2 : 1) + 5 + (P->p.a_max >= 2 ? 2 : 1) +
@@ -735,6 +765,17 @@ int launches_per_call(const sft_plan_s* P) {
   int fft = 0;
   for (int l = 0; l < P->levels; ++l) fft += (P->M0 >> l) > kFft4Points ? 2 : 1;
   return ext + fft + 2 * P->levels + fin;
+}
+
+int launches_per_call(const sft_plan_s* P) {
+  int dev = 0, nsm = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t B = P->max_signals;
+  const int S = sub_batches_for(P, B);
+  int n = 0;
+  for (int s = 0; s < S; ++s) n += launches_one(P, B / S + (s < B % S ? 1 : 0), nsm);
+  return n;
 }
 
 static cudaEvent_t pool_event(sft_plan_s* P) {
@@ -997,8 +1038,8 @@ static void launch_iter(sft_plan_s* P, int64_t B, const void* x, int64_t x_strid
   }
 }
 
-cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride,
-                         const sft_result* r, cudaStream_t st) {
+static cudaError_t launch_one(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride,
+                              const sft_result* r, cudaStream_t st) {
   const Workspace& W = P->ws;
   const OmegaTab om{P->tab.om_hi, P->tab.om_lo, P->tab.om_lo_bits, P->p.N - 1};
   const bool fp64 = P->p.precision == SFT_FP64;
@@ -1039,6 +1080,63 @@ cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
     k_finalize<FF><<<fgrid, 1024, 0, st>>>(f);
   stage_end(P, st);
   return cudaGetLastError();
+}
+
+int sub_batches_for(const sft_plan_s* P, int64_t B) {
+  if (P->sub_fork == nullptr) return 1;  // a plan without streams (sft_exact_noalloc)
+  int S = P->sub_batches;
+  if (S <= 0) S = (int)std::min<int64_t>(kMaxSub, std::max<int64_t>(1, B / kSubMinSignals));
+  if (S > kMaxSub) S = kMaxSub;
+  if (S > B) S = (int)std::max<int64_t>(B, 1);
+  return S;
+}
+
+// Splits the call into sub-batches of consecutive signals, each enqueued on
+// its own stream after a fork from `st` and joined back into `st`: the
+// latency-bound stages of one sub-batch (the decoders of the later levels,
+// FP64-pipe bound and few warps) run beside the FFTs of another (FP32
+// pipes).  Each sub-batch works in its own slice of the workspace.
+cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride,
+                         const sft_result* r, cudaStream_t st) {
+  const int S = sub_batches_for(P, B);
+  if (S <= 1) return launch_one(P, B, x, x_stride, r, st);
+  cudaError_t e = cudaSuccess;
+  const size_t esize = P->p.precision == SFT_FP64 ? 16 : 8;
+  const Workspace W0 = P->ws;
+  const void* const* xt0 = P->x_table;
+  const sft_result* rt0 = P->r_table;
+  const int64_t* kt0 = P->K_table;
+  int16_t* prop0 = P->mlp_prop;
+  e = cudaEventRecord(P->sub_fork, st);
+  int64_t b0 = 0;
+  for (int s = 0; s < S && e == cudaSuccess; ++s) {
+    const int64_t Bs = B / S + (s < B % S ? 1 : 0);
+    cudaStream_t ss = s == 0 ? st : P->sub_st[s];
+    if (s > 0) e = cudaStreamWaitEvent(ss, P->sub_fork, 0);
+    if (e != cudaSuccess) break;
+    P->ws = sub_workspace(W0, b0, s);
+    P->x_table = xt0 ? xt0 + b0 : nullptr;
+    P->r_table = rt0 ? rt0 + b0 : nullptr;
+    P->K_table = kt0 ? kt0 + b0 : nullptr;
+    P->mlp_prop = prop0 ? prop0 + b0 * P->M0 * 8 : nullptr;
+    sft_result rs = *r;
+    if (r->idx) rs.idx = r->idx + b0 * r->cap;
+    if (r->val) rs.val = r->val + 2 * b0 * r->cap;
+    if (r->count) rs.count = r->count + b0;
+    if (r->unresolved) rs.unresolved = r->unresolved + b0;
+    if (r->overflow) rs.overflow = r->overflow + b0;
+    const void* xs = x ? static_cast<const char*>(x) + (size_t)b0 * (size_t)x_stride * esize : x;
+    e = launch_one(P, Bs, xs, x_stride, &rs, ss);
+    if (e == cudaSuccess && s > 0) e = cudaEventRecord(P->sub_join[s], ss);
+    b0 += Bs;
+  }
+  P->ws = W0;
+  P->x_table = xt0;
+  P->r_table = rt0;
+  P->K_table = kt0;
+  P->mlp_prop = prop0;
+  for (int s = 1; s < S && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(st, P->sub_join[s], 0);
+  return e;
 }
 
 }  // namespace sft

@@ -293,21 +293,49 @@ __device__ __forceinline__ int gen_block_scan(int v, int* total) {
 // one CTA's signal: MSB-first radix select, 8 passes of 8 bits.  Returns the
 // K-th largest key and, in *rem_out, how many of the keys equal to it are
 // among the K largest (0 < K <= n).
+//
+// The histogram counts are aggregated per warp (one shared atomic per
+// distinct digit in a warp, not one per key), and once the keys still
+// matching the selected prefix fit in shared memory they are copied there,
+// so that the remaining passes read no global memory.
+constexpr int kSelCand = 4096;
+
+__device__ __forceinline__ void hist_add(unsigned* hist, unsigned digit, bool pred) {
+  const unsigned act = __activemask();
+  const unsigned mm = __ballot_sync(act, pred);
+  if (pred) {
+    const unsigned peers = __match_any_sync(mm, digit);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[digit], (unsigned)__popc(peers));
+  }
+}
+
 __device__ unsigned long long radix_select_desc(const unsigned long long* keys, int64_t n,
                                                 long long K, long long* rem_out) {
   __shared__ unsigned hist[256];
   __shared__ unsigned long long s_prefix;
   __shared__ long long s_rem;
+  __shared__ unsigned s_sel_count;
+  __shared__ int s_nc;
+  __shared__ unsigned long long cand[kSelCand];
   const int tid = threadIdx.x, nthr = blockDim.x;
   unsigned long long prefix = 0ull, mask = 0ull;
   long long rem = K;  // rank (from the top) still to find among keys matching prefix
+  bool in_smem = false;
+  int nc = 0;
   for (int pass = 0; pass < 8; ++pass) {
     const int shift = 56 - 8 * pass;
     for (int i = tid; i < 256; i += nthr) hist[i] = 0u;
     __syncthreads();
-    for (int64_t i = tid; i < n; i += nthr) {
-      const unsigned long long key = keys[i];
-      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
+    if (in_smem) {
+      for (int i = tid; i < nc; i += nthr) {
+        const unsigned long long key = cand[i];
+        hist_add(hist, (unsigned)((key >> shift) & 255ull), (key & mask) == prefix);
+      }
+    } else {
+      for (int64_t i = tid; i < n; i += nthr) {
+        const unsigned long long key = keys[i];
+        hist_add(hist, (unsigned)((key >> shift) & 255ull), (key & mask) == prefix);
+      }
     }
     __syncthreads();
     if (tid == 0) {
@@ -322,11 +350,23 @@ __device__ unsigned long long radix_select_desc(const unsigned long long* keys, 
       }
       s_prefix = prefix | ((unsigned long long)sel << shift);
       s_rem = rem - cum;
+      s_sel_count = hist[sel];
+      s_nc = 0;
     }
     __syncthreads();
     prefix = s_prefix;
     rem = s_rem;
     mask |= 255ull << shift;
+    // gather the keys matching the new prefix into shared memory once they fit
+    if (!in_smem && pass < 7 && s_sel_count <= (unsigned)kSelCand) {
+      for (int64_t i = tid; i < n; i += nthr) {
+        const unsigned long long key = keys[i];
+        if ((key & mask) == prefix) cand[atomicAdd(&s_nc, 1)] = key;
+      }
+      __syncthreads();
+      nc = s_nc;
+      in_smem = true;
+    }
     __syncthreads();
   }
   *rem_out = rem;
@@ -577,7 +617,33 @@ __device__ void solve_bin(const GenArgs& g, int b, int64_t k, int e) {
     double bv[2 * A];
     int bt[2 * A];
     int have = 0;
-    for (int64_t t = 0; t < d; ++t) {
+    // one alias: |P~(z)|^2 = 1 + |c0|^2 - 2 |c0| cos(arg z - arg(-c0)) on the
+    // unit circle, so the two smallest are the two candidates nearest the
+    // root -c0 in angle, t = floor(u) and floor(u) + 1 with u the root's
+    // fractional candidate index -- decided in FP32 unless u lies near an
+    // integer (where the second place is a near tie: the full pass decides)
+    int64_t t_hi = d;
+    if constexpr (A == 1) {
+      const float zx = (float)(-c[0].x), zy = (float)(-c[0].y);
+      const float az = fabsf(zx) + fabsf(zy);
+      if (nk == 2 && az > 1e-30f && az < 1e30f) {
+        const float df = (float)d;
+        const float u = fmaf(atan2f(zy, zx), df * 0.15915494309189533577f,
+                             -(float)k / (float)M);
+        const float fl = floorf(u), fr = u - fl;
+        const float margin = fmaxf(1e-3f, 8e-7f * df);
+        if (fr > margin && fr < 1.0f - margin) {
+          int64_t t0 = ((int64_t)fl) % d;
+          if (t0 < 0) t0 += d;
+          const int64_t t1 = (t0 + 1) % d;
+          bt[0] = (int)min(t0, t1);
+          bt[1] = (int)max(t0, t1);
+          have = 2;
+          t_hi = 0;  // no full pass
+        }
+      }
+    }
+    for (int64_t t = 0; t < t_hi; ++t) {
       const cdbl z = omega_pow(g.om, k + t * M);
       cdbl P = mk(1.0, 0.0);
 #pragma unroll

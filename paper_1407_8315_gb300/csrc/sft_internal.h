@@ -16,6 +16,11 @@ inline bool is_general_mode(int mode) {
   return mode == SFT_GENERAL || mode == SFT_GENERAL_UNPRUNED;
 }
 
+// A call may be split into up to kMaxSub sub-batches of signals, each on
+// its own stream (its launches overlap the others'), each with its own
+// block of 16 queue counters.
+constexpr int kMaxSub = 4;
+
 // Device workspace of one call for up to B signals.  Per signal:
 //   held[2]   ping-pong syndrome buffers, `held_elems` double2 each
 //             (ITER level l keeps rows j < 2l+2 of length M_l; FIXED keeps
@@ -26,8 +31,9 @@ inline bool is_general_mode(int mode) {
 //             k0 = s mod M0 (at most 4 per bin): count, location, value
 //   ymax2     bit pattern of max_k |Y_{d,0}[k]|^2 (zero threshold)
 //   flags     bit 0: a level-0 bin received more than 4 frequencies
-// plus qcount[16], the queue fill counters of one call.  ymax2, flags,
-// qcount and slot_cnt form one contiguous region cleared before each call.
+// plus qcount[16 kMaxSub], the queue fill counters of one call (16 per
+// sub-batch).  ymax2, flags, qcount and slot_cnt form one contiguous region
+// cleared before each call.
 struct Workspace {
   void* held[2] = {nullptr, nullptr};  // double2 or float-float float4 elements
   int64_t held_elems = 0;
@@ -45,7 +51,32 @@ struct Workspace {
   double* sv = nullptr;  // general path: a_m singular values per bin
   void* xc = nullptr;    // exact paths: the call's samples, shift-major (input type)
   int64_t xc_sig = 0;    // elements of xc per signal
+  // bytes per signal of the per-signal arrays (sub-batch views)
+  int64_t M0 = 0, fft4_sig_bytes = 0, sv_sig = 0, xc_sig_bytes = 0;
 };
+
+// The workspace seen by signals [b0, ...) of a call as sub-batch `sub`:
+// every per-signal array offset by b0 signals, the queues by b0 M0 entries
+// and the counters by 16 sub.
+inline Workspace sub_workspace(const Workspace& W, int64_t b0, int sub) {
+  Workspace V = W;
+  const int64_t M0 = W.M0;
+  for (int i = 0; i < 2; ++i) {
+    if (W.held[i]) V.held[i] = static_cast<char*>(W.held[i]) + b0 * W.held_elems * 16;
+    if (W.T[i]) V.T[i] = W.T[i] + b0 * M0;
+    if (W.queue[i]) V.queue[i] = W.queue[i] + b0 * M0;
+  }
+  V.slot_cnt = W.slot_cnt + b0 * M0;
+  V.slot_s = W.slot_s + b0 * M0 * 4;
+  V.slot_p = static_cast<char*>(W.slot_p) + b0 * M0 * 4 * 16;
+  V.ymax2 = W.ymax2 + b0;
+  V.flags = W.flags + b0;
+  V.qcount = W.qcount + 16 * sub;
+  if (W.fft4) V.fft4 = static_cast<char*>(W.fft4) + b0 * W.fft4_sig_bytes;
+  if (W.sv) V.sv = W.sv + b0 * W.sv_sig;
+  if (W.xc) V.xc = static_cast<char*>(W.xc) + b0 * W.xc_sig_bytes;
+  return V;
+}
 
 // Lays the workspace of B signals out from `base` (or only sizes it when
 // base is null) and returns its byte size; every array is 256-byte aligned.
@@ -74,7 +105,7 @@ inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, 
     off = al(off + (size_t)(B * M0) * 8);
   }
   const size_t o_zero = off;
-  const size_t zero_bytes = (size_t)B * 16 + 64 + (size_t)(B * M0);
+  const size_t zero_bytes = (size_t)B * 16 + 64 * kMaxSub + (size_t)(B * M0);
   off = al(off + zero_bytes);
   const size_t o_ss = off;
   off = al(off + (size_t)(B * M0 * 4) * 8);
@@ -109,13 +140,17 @@ inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, 
     W->ymax2 = reinterpret_cast<unsigned long long*>(z);
     W->flags = reinterpret_cast<int32_t*>(z + (size_t)B * 8);
     W->qcount = reinterpret_cast<int32_t*>(z + (size_t)B * 16);
-    W->slot_cnt = reinterpret_cast<uint8_t*>(z + (size_t)B * 16 + 64);
+    W->slot_cnt = reinterpret_cast<uint8_t*>(z + (size_t)B * 16 + 64 * kMaxSub);
     W->slot_s = reinterpret_cast<int64_t*>(base + o_ss);
     W->slot_p = base + o_sp;
     W->fft4 = M0 > 8192 ? base + o_f4 : nullptr;
     W->sv = mode == SFT_GENERAL ? reinterpret_cast<double*>(base + o_sv) : nullptr;
     W->xc = xc_sig > 0 ? base + o_xc : nullptr;
     W->xc_sig = xc_sig;
+    W->M0 = M0;
+    W->fft4_sig_bytes = (int64_t)nsh * M0 * 16;
+    W->sv_sig = M0 * a_max;
+    W->xc_sig_bytes = xc_sig * xc_esize;
   }
   return off;
 }
@@ -175,6 +210,12 @@ struct sft_plan_s {
   // 8 proposed candidates t per queued bin (int16, -1 = none)
   struct sft_mlp_s* mlp = nullptr;
   int16_t* mlp_prop = nullptr;
+  // sub-batches per call (0: chosen from the batch size) and their streams
+  // (created on first use; stream 0 is the caller's)
+  int sub_batches = 0;
+  cudaStream_t sub_st[sft::kMaxSub] = {};
+  cudaEvent_t sub_fork = nullptr;
+  cudaEvent_t sub_join[sft::kMaxSub] = {};
   // profiling
   bool profiling = false;
   std::vector<sft::StageRec> stage_recs;   // records since the last read
@@ -189,6 +230,8 @@ cudaError_t launch_exact(sft_plan_s* plan, int64_t n_signals, const void* x, int
 // One-time per-plan kernel attributes (dynamic shared memory limits).
 cudaError_t prepare_kernels(sft_plan_s* plan);
 int launches_per_call(const sft_plan_s* plan);
+// sub-batches of a call of B signals (sft_plan_set_sub_batches)
+int sub_batches_for(const sft_plan_s* plan, int64_t B);
 // Gather + FFT of `nshift` shifts (consecutive from shift0, or shift_list)
 // into rows row0.. of `out`, either precision; `stage` names the profiling
 // stage (nullptr: the level's default name).

@@ -31,7 +31,11 @@ __global__ void __launch_bounds__(kStudyThreads) k_alias_hist(const int64_t* __r
     __syncthreads();
     for (int64_t i = tid; i < M; i += blockDim.x) {
       const unsigned c = cnt[i];
-      atomicAdd(&h[c < (unsigned)(n_cells - 1) ? c : (unsigned)(n_cells - 1)], 1ull);
+      const unsigned cell = c < (unsigned)(n_cells - 1) ? c : (unsigned)(n_cells - 1);
+      // one atomic per distinct cell in the warp (most bins share cell 0)
+      const unsigned peers = __match_any_sync(__activemask(), cell);
+      if ((int)(threadIdx.x & 31) == __ffs(peers) - 1)
+        atomicAdd(&h[cell], (unsigned long long)__popc(peers));
     }
     __syncthreads();
     if (tid < n_cells && h[tid] != 0ull) atomicAdd(hist + tid, h[tid]);
@@ -46,7 +50,8 @@ bool pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 extern "C" sft_status sft_alias_histogram(const int64_t* supports, int64_t n_sets, int64_t K,
                                           int64_t M, int32_t n_cells, int64_t* hist,
                                           void* stream) {
-  if (!supports || !hist || n_sets < 0 || K < 0 || n_cells < 2 || n_cells > 33) {
+  if ((!supports && n_sets > 0 && K > 0) || !hist || n_sets < 0 || K < 0 || n_cells < 2 ||
+      n_cells > 33) {
     sft::set_error_detail("sft_alias_histogram: NULL pointer or bad sizes");
     return SFT_EINVAL;
   }

@@ -133,6 +133,9 @@ def load(build_if_missing: bool = False):
     lib.sft_plan_attach_mlp.argtypes = [C.c_void_p, C.c_void_p]
     lib.sft_exact_auto.argtypes = [P(sft_params), C.c_int64, C.c_void_p, C.c_int64, C.c_int64,
                                    C.c_int64, P(sft_result), C.c_void_p, C.c_void_p]
+    lib.sft_plan_set_sub_batches.argtypes = [C.c_void_p, C.c_int32]
+    lib.sft_plan_sub_batches.argtypes = [C.c_void_p, C.c_int64]
+    lib.sft_plan_sub_batches.restype = C.c_int32
     lib.sft_alias_histogram.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                         C.c_void_p, C.c_void_p]
     lib.sft_strerror.argtypes = [C.c_int]
@@ -348,6 +351,14 @@ class Plan:
     @property
     def cs_shifts(self) -> np.ndarray:
         return sft_plan_cs_shifts(self.handle)
+
+    def set_sub_batches(self, n: int):
+        """Sub-batches per call: 0 chooses from the call's size, 1..4 fixes it."""
+        _check(load().sft_plan_set_sub_batches(C.c_void_p(self.handle), int(n)),
+               "sft_plan_set_sub_batches")
+
+    def sub_batches(self, n_signals: int) -> int:
+        return int(load().sft_plan_sub_batches(C.c_void_p(self.handle), int(n_signals)))
 
     def set_profiling(self, enable: bool = True):
         sft_plan_set_profiling(self.handle, enable)

@@ -206,7 +206,8 @@ def test_host_entry_page_locked_in_place(gpu):
                      torch.empty(3, dtype=torch.int64, pin_memory=True).numpy(),
                      torch.empty(3, dtype=torch.int32, pin_memory=True).numpy(),
                      torch.empty(3, dtype=torch.int32, pin_memory=True).numpy())
-    for _ in range(2):
+    for S in (1, 3):
+        plan.set_sub_batches(S)  # one sub-batch per signal in the second pass
         h = plan.exact_host(px.numpy(), cap, out)
         np.testing.assert_array_equal(h.count, dc)
         np.testing.assert_array_equal(h.unresolved, du)
@@ -244,3 +245,36 @@ def test_plans_of_different_sizes_coexist(gpu, orc):
     for _ in range(2):
         _compare(orc, big, xb, "iter", 2048, MIXED_VAL_TOL)
         _compare(orc, small, xs, "iter", 256, MIXED_VAL_TOL)
+
+
+@pytest.mark.parametrize("mode,prec", [("iter", "mixed"), ("fixed", "mixed"), ("iter", "fp64")])
+def test_sub_batches_give_identical_results(gpu, mode, prec):
+    """A call split into 1..4 sub-batches on forked streams returns bitwise
+    the same results (each sub-batch works in its own workspace slice); 70
+    signals, so the sub-batches differ in size."""
+    import torch
+    from paper_1407_8315_gb300 import Plan
+    N, K, M, B = 1 << 14, 60, 256, 70
+    dt = np.complex128 if prec == "fp64" else np.complex64
+    xs, _, _ = siggen.batch_exact(N, K, [9000 + i for i in range(B)], mag=(1, 10), dtype=dt)
+    plan = Plan(N, K, N // M, mode, prec, max_signals=B)
+    x = torch.from_numpy(xs).cuda()
+    ref = None
+    for S in (1, 2, 3, 4):
+        plan.set_sub_batches(S)
+        assert plan.sub_batches(B) == S
+        out = plan.exact(x, 2 * K)
+        torch.cuda.synchronize()
+        got = [t.cpu().numpy() for t in out]
+        if ref is None:
+            ref = got
+        else:
+            for j in (2, 3, 4):  # counts, unresolved, overflow
+                np.testing.assert_array_equal(ref[j], got[j])
+            for b in range(B):  # the written entries (the rest is uninitialised)
+                n = int(ref[2][b])
+                np.testing.assert_array_equal(ref[0][b, :n], got[0][b, :n])
+                np.testing.assert_array_equal(ref[1][b, :n], got[1][b, :n])
+    plan.set_sub_batches(0)
+    assert plan.sub_batches(B) == 2 and plan.sub_batches(31) == 1
+    assert plan.sub_batches(96) == 3 and plan.sub_batches(1000) == 4

@@ -38,6 +38,8 @@ def test_alias_histogram_edges(gpu):
     from paper_1407_8315_gb300 import sft
     empty = gpu.zeros((0, 8), dtype=gpu.int64, device="cuda")
     assert sft.alias_histogram(empty, 64, 5).cpu().tolist() == [0] * 5
+    no_locations = gpu.zeros((3, 0), dtype=gpu.int64, device="cuda")
+    assert sft.alias_histogram(no_locations, 64, 5).cpu().tolist() == [3 * 64, 0, 0, 0, 0]
     big = gpu.zeros((1, 8), dtype=gpu.int64, device="cuda")
     with pytest.raises(sft.SftError):
         sft.alias_histogram(big, 1 << 16, 5)
