@@ -72,6 +72,7 @@ def _load():
             lib.orc_syndrome.argtypes = [P(C.c_double), C.c_int64, C.c_int64, C.c_int64,
                                          P(C.c_double)]
             lib.orc_poly_roots.argtypes = [C.c_int, P(C.c_double), P(C.c_double)]
+            lib.orc_bm_locator.argtypes = [C.c_int, P(C.c_double), P(C.c_double)]
             lib.orc_decode.argtypes = [C.c_int, P(C.c_double), C.c_int, C.c_int64, C.c_int64,
                                        C.c_int64, C.c_double, C.c_double, C.c_double,
                                        P(C.c_int64), P(C.c_double)]
@@ -136,12 +137,22 @@ def poly_roots(c) -> np.ndarray:
 def decode(a: int, m, k: int, M: int, N: int, theta: float, root_tol: float, res_tol: float):
     """SynDec of one bin: returns (ok, s[a], p[a])."""
     m = _c128(m)
-    s = np.zeros(4, dtype=np.int64)
-    p = np.zeros(4, dtype=np.complex128)
+    s = np.zeros(8, dtype=np.int64)
+    p = np.zeros(8, dtype=np.complex128)
     ok = _load().orc_decode(int(a), _dp(m), m.size, int(k), int(M), int(N), float(theta),
                             float(root_tol), float(res_tol),
                             s.ctypes.data_as(C.POINTER(C.c_int64)), _dp(p))
     return bool(ok), s[:a].copy(), p[:a].copy()
+
+
+def bm_locator(m, a: int):
+    """Berlekamp-Massey locator for a aliases from m_0..m_{2a-1}: returns c
+    (c_0..c_{a-1} of P(z) = z^a + sum c_j z^j) or None when the shortest
+    recurrence is not of length a."""
+    m = _c128(m)
+    c = np.zeros(8, dtype=np.complex128)
+    ok = _load().orc_bm_locator(int(a), _dp(m), _dp(c))
+    return c[:a].copy() if ok else None
 
 
 def exact(x, M0: int, a_max: int = 4, mode: int = ITER, max_iters: int | None = None,

@@ -216,38 +216,112 @@ int orc_poly_roots(int a, const double* cin, double* zout) {
 
 /* ---------------------------------------------------------------- SynDec */
 
+/* Step (i) for a > 4 (Sec. II-B cites Berlekamp-Massey for it): the
+ * shortest linear recurrence m_n + sum_{i=1}^{L} C_i m_{n-i} = 0 (n >= L)
+ * that generates m_0..m_{2a-1}, built one syndrome at a time (Massey,
+ * "Shift-register synthesis and BCH decoding", 1969).  A discrepancy counts
+ * as zero only when it is exactly zero.  The locator exists when L = a;
+ * then Eq. (4)-(5) hold with c_j = C_{a-j}. */
+int orc_bm_locator(int a, const double* min, double* cout) {
+  const cplx* m = (const cplx*)min;
+  cplx* c = (cplx*)cout;
+  if (a < 1 || a > 8) return 0;
+  cplx C[17] = {0}, Bp[17] = {0}, T[17];
+  C[0] = 1;
+  Bp[0] = 1;
+  int L = 0, shift = 1;
+  cplx bd = 1;
+  for (int n = 0; n < 2 * a; ++n) {
+    cplx delta = m[n];
+    for (int i = 1; i <= L; ++i) delta += C[i] * m[n - i];
+    if (delta == 0) {
+      ++shift;
+      continue;
+    }
+    const cplx f = delta / bd;
+    if (2 * L <= n) {
+      memcpy(T, C, sizeof T);
+      for (int i = 0; i + shift <= 16; ++i) C[i + shift] -= f * Bp[i];
+      L = n + 1 - L;
+      memcpy(Bp, T, sizeof T);
+      bd = delta;
+      shift = 1;
+    } else {
+      for (int i = 0; i + shift <= 16; ++i) C[i + shift] -= f * Bp[i];
+      ++shift;
+    }
+  }
+  if (L != a) return 0;
+  for (int j = 0; j < a; ++j) c[j] = C[a - j];
+  return 1;
+}
+
 int orc_decode(int a, const double* min, int n_m, int64_t k, int64_t M, int64_t N,
                double theta, double root_tol, double res_tol,
                int64_t* s_out, double* p_out) {
-  if (a < 1 || a > 4 || n_m < 2 * a || M <= 0 || N % M != 0) return 0;
+  if (a < 1 || a > 8 || n_m < 2 * a || n_m > 16 || M <= 0 || N % M != 0) return 0;
   const cplx* m = (const cplx*)min;
   int64_t d = N / M;
+  if (d < a) return 0;
+  int64_t s[8];
+  cplx c[8];
 
-  /* Step (i), Eq. (4)-(5): the a x a Hankel system
-   *   sum_j c_j m_{i+j} = -m_{a+i},  i = 0..a-1. */
-  cplx H[16], rhs[4], c[4];
-  for (int i = 0; i < a; ++i) {
-    for (int j = 0; j < a; ++j) H[i * a + j] = m[i + j];
-    rhs[i] = -m[a + i];
-  }
-  if (!solve_lin(a, H, rhs, c)) return 0;
+  if (a <= 4) {
+    /* Step (i), Eq. (4)-(5): the a x a Hankel system
+     *   sum_j c_j m_{i+j} = -m_{a+i},  i = 0..a-1. */
+    cplx H[16], rhs[4];
+    for (int i = 0; i < a; ++i) {
+      for (int j = 0; j < a; ++j) H[i * a + j] = m[i + j];
+      rhs[i] = -m[a + i];
+    }
+    if (!solve_lin(a, H, rhs, c)) return 0;
 
-  /* Step (ii): the roots z_j of P(z) = z^a + c_{a-1} z^{a-1} + ... + c_0. */
-  cplx z[4];
-  orc_poly_roots(a, (const double*)c, (double*)z);
+    /* Step (ii): the roots z_j of P(z) = z^a + c_{a-1} z^{a-1} + ... + c_0. */
+    cplx z[4];
+    orc_poly_roots(a, (const double*)c, (double*)z);
 
-  /* Alg. 1 lines 29-30.  s_j = ln(z_j) N / (i 2 pi) taken as the member of
-   * S_k = {k + tM} nearest to it; the root belongs to U_k only if z_j lies
-   * within root_tol of omega^{s_j}. */
-  int64_t s[4];
-  for (int j = 0; j < a; ++j) {
-    if (!(cabs(z[j]) > 0) || !isfinite(creal(z[j])) || !isfinite(cimag(z[j]))) return 0;
-    double pos = carg(z[j]) / TWO_PI * (double)N; /* real-valued location */
-    double tf = nearbyint((pos - (double)k) / (double)M);
-    int64_t t = (int64_t)tf % d;
-    if (t < 0) t += d;
-    s[j] = k + t * M;
-    if (!(cabs(z[j] - omega_pow(N, s[j])) <= root_tol)) return 0;
+    /* Alg. 1 lines 29-30.  s_j = ln(z_j) N / (i 2 pi) taken as the member of
+     * S_k = {k + tM} nearest to it; the root belongs to U_k only if z_j lies
+     * within root_tol of omega^{s_j}. */
+    for (int j = 0; j < a; ++j) {
+      if (!(cabs(z[j]) > 0) || !isfinite(creal(z[j])) || !isfinite(cimag(z[j]))) return 0;
+      double pos = carg(z[j]) / TWO_PI * (double)N; /* real-valued location */
+      double tf = nearbyint((pos - (double)k) / (double)M);
+      int64_t t = (int64_t)tf % d;
+      if (t < 0) t += d;
+      s[j] = k + t * M;
+      if (!(cabs(z[j] - omega_pow(N, s[j])) <= root_tol)) return 0;
+    }
+  } else {
+    /* a > 4: Berlekamp-Massey locator, and as no closed form gives the
+     * roots, the candidate search of Step (ii): |P(omega^{k+tM})| at every
+     * t < d, the a smallest kept (ties: smaller t).  They must be roots up
+     * to root_tol (1 + sum |c_j|). */
+    if (!orc_bm_locator(a, (const double*)m, (double*)c)) return 0;
+    double bound = 1;
+    for (int j = 0; j < a; ++j) bound += cabs(c[j]);
+    bound *= root_tol;
+    double bv[8];
+    int64_t bt[8];
+    int have = 0;
+    for (int64_t t = 0; t < d; ++t) {
+      cplx z = omega_pow(N, k + t * M), P = 1;
+      for (int j = a - 1; j >= 0; --j) P = P * z + c[j];
+      const double v = cabs(P);
+      if (have < a || v < bv[a - 1]) {
+        int pos = have < a ? have : a - 1;
+        while (pos > 0 && bv[pos - 1] > v) {
+          bv[pos] = bv[pos - 1];
+          bt[pos] = bt[pos - 1];
+          --pos;
+        }
+        bv[pos] = v;
+        bt[pos] = t;
+        if (have < a) ++have;
+      }
+    }
+    if (!(bv[a - 1] <= bound)) return 0;
+    for (int j = 0; j < a; ++j) s[j] = k + bt[j] * M;
   }
   /* sort ascending and require distinct locations */
   for (int i = 1; i < a; ++i)
@@ -262,13 +336,13 @@ int orc_decode(int a, const double* min, int n_m, int64_t k, int64_t M, int64_t 
   /* Step (iii): substitute the z_j = omega^{s_j} into all available
    * equations of Eq. (3), m_i = sum_j p_j z_j^i (i < n_m), and solve them in
    * the least-squares sense through the normal equations (Z^H Z) p = Z^H m. */
-  cplx G[16], g[4], p[4];
+  cplx G[64], g[8], p[8];
   for (int u = 0; u < a; ++u) {
     g[u] = 0;
     for (int v = 0; v < a; ++v) G[u * a + v] = 0;
   }
   for (int i = 0; i < n_m; ++i) {
-    cplx zi[4];
+    cplx zi[8];
     for (int j = 0; j < a; ++j) zi[j] = omega_pow(N, s[j] * (int64_t)i);
     for (int u = 0; u < a; ++u) {
       g[u] += conj(zi[u]) * m[i];
@@ -327,7 +401,7 @@ int64_t orc_exact(const double* xin, const orc_exact_params* prm, int64_t cap,
                   int64_t* idx, double* val, int64_t* unresolved) {
   const int64_t N = prm->N, M0 = prm->M0;
   const int am = prm->a_max;
-  if (!is_pow2(N) || !is_pow2(M0) || M0 > N || am < 1 || am > 4) return -1;
+  if (!is_pow2(N) || !is_pow2(M0) || M0 > N || am < 1 || am > 8) return -1;
   const int64_t d0 = N / M0;
   const int iters = prm->mode == ORC_ITER ? prm->max_iters : 1;
   if (prm->mode == ORC_ITER && (iters < 1 || iters > am)) return -1;
@@ -357,7 +431,7 @@ int64_t orc_exact(const double* xin, const orc_exact_params* prm, int64_t cap,
     theta = prm->zero_tol * ymax;
     for (int64_t k = 0; k < M0; ++k) {
       int active = 0;
-      cplx m[8];
+      cplx m[16];
       for (int j = 0; j < nsh; ++j) {
         m[j] = HELD(j, k);
         if (cabs(m[j]) > theta) active = 1;
@@ -365,8 +439,8 @@ int64_t orc_exact(const double* xin, const orc_exact_params* prm, int64_t cap,
       if (!active) continue;
       int ok = 0;
       for (int a = 1; a <= am && !ok; ++a) {
-        int64_t s[4];
-        cplx p[4];
+        int64_t s[8];
+        cplx p[8];
         if (orc_decode(a, (const double*)m, nsh, k, M0, N, theta, prm->root_tol,
                        prm->res_tol, s, (double*)p)) {
           for (int j = 0; j < a; ++j) push(&S, &nS, &capS, s[j], p[j]);
@@ -408,10 +482,10 @@ int64_t orc_exact(const double* xin, const orc_exact_params* prm, int64_t cap,
       const int a = l + 1, nm = 2 * l + 2;
       for (int64_t k = 0; k < M; ++k) {
         if (!(T[k] || cabs(HELD(2 * l, k)) > theta || cabs(HELD(2 * l + 1, k)) > theta)) continue;
-        cplx m[8];
+        cplx m[16];
         for (int j = 0; j < nm; ++j) m[j] = HELD(j, k);
-        int64_t s[4];
-        cplx p[4];
+        int64_t s[8];
+        cplx p[8];
         if (orc_decode(a, (const double*)m, nm, k, M, N, theta, prm->root_tol, prm->res_tol, s,
                        (double*)p)) {
           /* lines 31-32: S = S u s, x^[s_j] = p_j; the solved terms leave

@@ -39,9 +39,17 @@ int orc_syndrome(const double* x, int64_t N, int64_t d, int64_t shift, double* Y
  * analytical solutions (quadratic, Cardano, Ferrari).  Returns 0 / -1. */
 int orc_poly_roots(int a, const double* c, double* z);
 
+/* Berlekamp-Massey locator for a aliases from m_0..m_{2a-1} (Step (i) for
+ * a > 4): writes c[a] with sum_j c_j m_{i+j} = -m_{a+i} and returns 1 when
+ * the shortest recurrence has length exactly a, else 0. */
+int orc_bm_locator(int a, const double* m, double* c);
+
 /* SynDec of one bin (Sec. II-B steps (i)-(iii), Alg. 1 lines 23-35).
- *   a      number of aliases assumed (1..4)
- *   m      n_m syndromes m_0..m_{n_m-1} of bin k (n_m >= 2a)
+ *   a      number of aliases assumed (1..8): a <= 4 by the Hankel solve and
+ *          the analytical roots snapped to S_k; a > 4 by the
+ *          Berlekamp-Massey locator and the a smallest |P| over the d
+ *          candidates of S_k (each at most root_tol (1 + sum |c_j|))
+ *   m      n_m syndromes m_0..m_{n_m-1} of bin k (2a <= n_m <= 16)
  *   k, M, N  bin index, number of bins, signal length
  *   theta  zero threshold; root_tol, res_tol  validation tolerances
  * On success writes s_out[a] (ascending) and p_out[a] and returns 1;
@@ -55,7 +63,7 @@ enum { ORC_ITER = 0, ORC_FIXED = 1 };
 typedef struct {
   int64_t N;          /* signal length (power of two)                        */
   int64_t M0;         /* number of bins at the first level, d0 = N / M0       */
-  int32_t a_max;      /* largest alias count decoded (1..4)                  */
+  int32_t a_max;      /* largest alias count decoded (1..8)                  */
   int32_t max_iters;  /* ITER: number of levels (<= a_max)                    */
   int32_t mode;       /* ORC_ITER (Algorithm 1) or ORC_FIXED (non-iterative)  */
   int32_t pad_;

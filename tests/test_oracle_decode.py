@@ -111,3 +111,47 @@ def test_poly_roots_biquadratic(orc):
     z = orc.poly_roots([-1, 0, 0, 0])
     for rt in (1, -1, 1j, -1j):
         assert np.min(np.abs(z - rt)) < 1e-12
+
+
+# ---------------------------------------------- more than four aliases
+@pytest.mark.parametrize("a", [1, 3, 5, 6, 7, 8])
+def test_bm_locator_is_the_root_polynomial(orc, a):
+    """Berlekamp-Massey on the 2a syndromes of a planted a-alias bin returns
+    the locator whose roots are the planted z_j = omega^{s_j}: its
+    coefficients are those of prod_j (z - z_j) (numpy.poly)."""
+    N, M = 1 << 20, 1024
+    for trial in range(10):
+        s, p, m = _planted_bin(N, M, (91 * trial) % M, a, 500 * a + trial, 2 * a)
+        c = orc.bm_locator(m, a)
+        assert c is not None
+        want = np.poly(np.exp(2j * np.pi * s / N))[::-1][:a]  # c_0 .. c_{a-1}
+        assert np.abs(c - want).max() < 1e-6 * max(1.0, np.abs(want).max()), (a, trial)
+
+
+@pytest.mark.parametrize("a", [5, 6, 7, 8])
+@pytest.mark.parametrize("n_extra", [0, 2])
+def test_decode_above_four_planted(orc, a, n_extra):
+    """a > 4: Berlekamp-Massey locator, candidate search over the d members
+    of S_k, least-squares values: the planted bin comes back exactly (with
+    up to 16 syndromes, the most a bin holds at a_m = 8)."""
+    N, M = 1 << 20, 1024
+    for trial in range(12):
+        k = (53 * trial + 7) % M
+        s, p, m = _planted_bin(N, M, k, a, 900 * a + trial, min(16, 2 * a + n_extra))
+        ok, s_out, p_out = orc.decode(a, m, k, M, N, 1e-9, 0.1, 1e-9)
+        assert ok, (a, trial)
+        np.testing.assert_array_equal(s_out, s)
+        assert np.abs(p_out - p).max() < 1e-8 * np.abs(p).max()
+
+
+@pytest.mark.parametrize("a", [5, 7])
+def test_decode_above_four_rejects_more_aliases(orc, a):
+    """A bin with a + 1 aliases fails validation when decoded with a (its
+    2a syndromes carry too little information).  (A bin with fewer aliases
+    never reaches the a-alias decoder: FIXED tries a = 1, 2, ... in turn and
+    ITER's residual counts after level l are 0 or at least l + 2.)"""
+    N, M = 1 << 20, 1024
+    for trial in range(12):
+        k = (29 * trial + 3) % M
+        _, _, m_more = _planted_bin(N, M, k, a + 1, 31 * a + trial, 2 * a)
+        assert not orc.decode(a, m_more, k, M, N, 1e-9, 0.1, 1e-9)[0], (a, trial)

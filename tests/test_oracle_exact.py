@@ -158,6 +158,28 @@ def test_complex64_input_has_no_false_frequencies(orc):
             assert np.median(np.abs(val - vals[j]) / np.abs(vals[j])) < 1e-5
 
 
+@pytest.mark.parametrize("mode", ["iter", "fixed"])
+def test_up_to_eight_aliases_matches_support_simulation(orc, mode):
+    """a_m = 8 (Berlekamp-Massey locator and candidate search above four
+    aliases, Sec. II-B): at K / M0 = 1 the non-iterative method solves every
+    bin holding at most 8 frequencies and Algorithm 1 runs 8 levels; both
+    recover exactly the set the decision rule predicts, with the planted
+    values."""
+    N, K, M0 = 1 << 18, 1024, 1024
+    for seed in range(3):
+        x, supp, vals = siggen.exact_signal(N, K, 40 + seed, mag=(1, 10))
+        if mode == "iter":
+            want, want_unres = simulate_iter(supp, M0, 8)
+            idx, val, un = orc.exact(x, M0, 8, orc.ITER, cap=8 * M0)
+        else:
+            want, want_unres = simulate_fixed(supp, M0, 8)
+            idx, val, un = orc.exact(x, M0, 8, orc.FIXED, cap=8 * M0)
+        assert idx.tolist() == want, (seed, len(idx), len(want))
+        assert un == want_unres, seed
+        j = np.searchsorted(supp, idx)
+        assert np.abs(val - vals[j]).max() < 1e-8 * np.abs(vals).max(), seed
+
+
 def test_bad_parameters_rejected(orc):
     x = np.zeros(1000, complex)  # N not a power of two
     with pytest.raises(ValueError):
@@ -166,7 +188,7 @@ def test_bad_parameters_rejected(orc):
     with pytest.raises(ValueError):
         orc.exact(x, 12)
     with pytest.raises(ValueError):
-        orc.exact(x, 16, a_max=5)
+        orc.exact(x, 16, a_max=9)
 
 
 def test_empty_signal(orc):
