@@ -95,7 +95,10 @@ typedef struct {
   int64_t K;           /* sparsity; the result capacity must be >= K         */
   int64_t d;           /* (initial) downsampling factor; d | N, M = N/d a     */
                        /* power of two, M <= 2^26 (M > 8192: four-step FFT)  */
-  int32_t a_max;       /* largest alias count, 1..4 (0 -> 4 exact, 3 general) */
+  int32_t a_max;       /* largest alias count: ITER 1..8, FIXED 1..4 or 8,   */
+                       /* general 1..4 (0 -> 4 exact, 3 general); above 4    */
+                       /* the locator is found by Berlekamp-Massey and the   */
+                       /* roots by a search over the d candidates of the bin */
   int32_t max_iters;   /* ITER: number of levels, 1..a_max (0 -> a_max);     */
                        /* M / 2^(max_iters-1) must be >= 1                   */
   int32_t mode;        /* sft_mode                                           */
@@ -243,10 +246,10 @@ int32_t sft_batch_info(sft_batch_t ctx, int32_t* n_groups, int64_t* n_graph_node
  *                                  (x and the arrays of r are device memory)
  * Returns SFT_EINVAL (with the required and the maximum size in
  * sft_last_cuda_error) when n_signals signals of this shape do not fit the
- * array: per signal 179 * N/d + 16 bytes for SFT_EXACT_ITER (242 * N/d + 16
+ * array: per signal 275 * N/d + 16 bytes for SFT_EXACT_ITER (338 * N/d + 16
  * for SFT_EXACT_FIXED with a_max = 4), plus 16 * (N/d + 2 * (2^ceil(log2(N)/2)
- * + 2^floor(log2(N)/2))) bytes of tables, 64 bytes of counters and 256-byte
- * alignment of each array (at N = 2^22, N/d = 2^13: 11 signals per call).
+ * + 2^floor(log2(N)/2))) bytes of tables, 256 bytes of counters and 256-byte
+ * alignment of each array (at N = 2^22, N/d = 2^13: 7 signals per call).
  * The first call on each
  * device looks up the array's device address on that device (make it before
  * any stream capture).  All calls share the array and it keeps the last

@@ -50,7 +50,11 @@ sft_status validate(const sft_params& p) {
     return why(SFT_EINVAL, "N must be a power of two in [2^3, 2^30]");
   if (p.K < 0 || p.K > p.N) return why(SFT_EINVAL, "K must lie in [0, N]");
   if (!is_pow2(p.d) || p.d > p.N) return why(SFT_EINVAL, "d must be a power of two <= N");
-  if (p.a_max < 1 || p.a_max > 4) return why(SFT_EINVAL, "a_max must lie in [1, 4]");
+  if (p.a_max < 1 || p.a_max > 8) return why(SFT_EINVAL, "a_max must lie in [1, 8]");
+  if (sft::is_general_mode(p.mode) && p.a_max > 4)
+    return why(SFT_EUNSUPPORTED, "the general modes take a_max <= 4");
+  if (p.mode == SFT_EXACT_FIXED && p.a_max > 4 && p.a_max != 8)
+    return why(SFT_EUNSUPPORTED, "SFT_EXACT_FIXED takes a_max <= 4 or a_max = 8");
   if (p.precision != SFT_FP64 && p.precision != SFT_MIXED)
     return why(SFT_EINVAL, "unknown precision");
   if (p.mode != SFT_EXACT_ITER && p.mode != SFT_EXACT_FIXED && !sft::is_general_mode(p.mode))

@@ -1,7 +1,7 @@
 // sft_auto.cu -- unknown K (Sec. II-E, the bottom-up strategy).
 //
 // Every signal starts at d = N / M_start; while a run leaves a bin unsolved
-// (or a level-0 bin overflowed its four solution slots) the signal is run
+// (or a level-0 bin overflowed its solution slots) the signal is run
 // again with d halved (M doubled).  All signals still running at one M go
 // through one launch sequence of a plan for that M, reading their inputs
 // and writing their results through per-signal pointer tables, so each

@@ -380,7 +380,7 @@ __device__ __forceinline__ bool decode_bin(cdbl* m, int64_t k, const BinGeom& g,
                                            int64_t* s, cdbl* p, const float4* raw = nullptr,
                                            const OmegaTabFF* omff = nullptr,
                                            float4* res_out = nullptr) {
-  static_assert(nm >= 2 * a && nm <= 8, "need 2a <= nm <= 8 syndromes");
+  static_assert(nm >= 2 * a && nm <= 16, "need 2a <= nm <= 16 syndromes");
   if constexpr (a == 1) {
     // c_0 = -m_1 / m_0, the single root z = m_1 / m_0 (Sec. II-A).  Only
     // the root's angle (to pick the candidate) and its distance to that

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "sft_common.cuh"
+#include "sft_slots.h"
 
 namespace sft {
 
@@ -17,9 +18,9 @@ __device__ __forceinline__ void file_solution(const int64_t* s, const cdbl* p, i
   for (int j = 0; j < A; ++j) {
     const int64_t k0 = s[j] & (M0 - 1);
     const int c = cnt[k0];
-    if (c < 4) {
-      ss[k0 * 4 + c] = s[j];
-      sp[k0 * 4 + c] = Store<F>::from_d(p[j]);
+    if (c < kSlots) {
+      ss[k0 * kSlots + c] = s[j];
+      sp[k0 * kSlots + c] = Store<F>::from_d(p[j]);
       cnt[k0] = (uint8_t)(c + 1);
     } else {
       atomicOr(flag, 1);
@@ -32,9 +33,9 @@ __device__ __forceinline__ void file_one_ff(int64_t s, float4 p, int64_t M0, uin
                                             int64_t* ss, float4* sp, int32_t* flag) {
   const int64_t k0 = s & (M0 - 1);
   const int c = cnt[k0];
-  if (c < 4) {
-    ss[k0 * 4 + c] = s;
-    sp[k0 * 4 + c] = p;
+  if (c < kSlots) {
+    ss[k0 * kSlots + c] = s;
+    sp[k0 * kSlots + c] = p;
     cnt[k0] = (uint8_t)(c + 1);
   } else {
     atomicOr(flag, 1);
@@ -62,9 +63,9 @@ __device__ __forceinline__ void file_n(int n, const int64_t* s, const cdbl* p, i
   for (int j = 0; j < n; ++j) {
     const int64_t k0 = s[j] & (M0 - 1);
     const int c = cnt[k0];
-    if (c < 4) {
-      ss[k0 * 4 + c] = s[j];
-      sp[k0 * 4 + c] = Store<F>::from_d(p[j]);
+    if (c < kSlots) {
+      ss[k0 * kSlots + c] = s[j];
+      sp[k0 * kSlots + c] = Store<F>::from_d(p[j]);
       cnt[k0] = (uint8_t)(c + 1);
     } else {
       atomicOr(flag, 1);

@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(1024) k_gen_vote(GenArgs g) {
 // in phi), normal equations by Gaussian elimination with partial pivoting;
 // returns |y - Phi_T x|^2 or -1 when singular
 template <int C>
-__device__ double ls_cols(int rows, int cols, const cdbl* phi, const cdbl* y, const int* T, int nT,
+__device__ __noinline__ double ls_cols(int rows, int cols, const cdbl* phi, const cdbl* y, const int* T, int nT,
                           cdbl* x, cdbl* res) {
   cdbl G[C * C], gv[C];
   for (int u = 0; u < nT; ++u) {
@@ -525,7 +525,7 @@ __device__ int top_ks(int n, const double* v, unsigned allowed, int ks, int* out
 // its ks largest coefficients, least squares again; stop when the residual
 // does not shrink.  Writes the support and the coefficients; returns |T|.
 template <int C>
-__device__ int subspace_pursuit(int rows, int cols, const cdbl* phi, const cdbl* y, int ks,
+__device__ __noinline__ int subspace_pursuit(int rows, int cols, const cdbl* phi, const cdbl* y, int ks,
                                 int iters, int* T, cdbl* x) {
   const unsigned all = (cols >= 32) ? 0xffffffffu : ((1u << cols) - 1u);
   double corr[C];
@@ -722,8 +722,8 @@ __device__ void solve_bin(const GenArgs& g, int b, int64_t k, int e) {
     }
   }
   if (nout == 0) return;
-  file_n<F>(nout, s_out, p_out, g.M, g.slot_cnt + (int64_t)b * g.M, g.slot_s + (int64_t)b * g.M * 4,
-            reinterpret_cast<T*>(g.slot_p) + (int64_t)b * g.M * 4, g.flags + b);
+  file_n<F>(nout, s_out, p_out, g.M, g.slot_cnt + (int64_t)b * g.M, g.slot_s + (int64_t)b * g.M * kSlots,
+            reinterpret_cast<T*>(g.slot_p) + (int64_t)b * g.M * kSlots, g.flags + b);
 }
 
 // The one-alias bins (the front of the queue; every warp full and of one
@@ -988,8 +988,8 @@ __global__ void __launch_bounds__(32 * kUnprWarps) k_gen_unpruned(GenArgs g, int
         ++nout;
       }
       if (nout > 0)
-        file_n<F>(nout, s_out, p_out, M, g.slot_cnt + (int64_t)b * M, g.slot_s + (int64_t)b * M * 4,
-                  reinterpret_cast<T*>(g.slot_p) + (int64_t)b * M * 4, g.flags + b);
+        file_n<F>(nout, s_out, p_out, M, g.slot_cnt + (int64_t)b * M, g.slot_s + (int64_t)b * M * kSlots,
+                  reinterpret_cast<T*>(g.slot_p) + (int64_t)b * M * kSlots, g.flags + b);
     }
     __syncwarp();
   }

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/sft.h"
+#include "sft_slots.h"
 
 namespace sft {
 
@@ -28,9 +29,9 @@ constexpr int kMaxSub = 4;
 //   T[2]      unsolved-bin flags per level, M0 bytes each
 //   queue[2]  active (signal, bin) pairs awaiting decoding, M0 int2 each
 //   slot_*    frequencies recovered so far, filed by their level-0 bin
-//             k0 = s mod M0 (at most 4 per bin): count, location, value
+//             k0 = s mod M0 (at most kSlots = 8 per bin): count, location, value
 //   ymax2     bit pattern of max_k |Y_{d,0}[k]|^2 (zero threshold)
-//   flags     bit 0: a level-0 bin received more than 4 frequencies
+//   flags     bit 0: a level-0 bin received more than kSlots frequencies
 // plus qcount[16 kMaxSub], the queue fill counters of one call (16 per
 // sub-batch).  ymax2, flags, qcount and slot_cnt form one contiguous region
 // cleared before each call.
@@ -67,8 +68,8 @@ inline Workspace sub_workspace(const Workspace& W, int64_t b0, int sub) {
     if (W.queue[i]) V.queue[i] = W.queue[i] + b0 * M0;
   }
   V.slot_cnt = W.slot_cnt + b0 * M0;
-  V.slot_s = W.slot_s + b0 * M0 * 4;
-  V.slot_p = static_cast<char*>(W.slot_p) + b0 * M0 * 4 * 16;
+  V.slot_s = W.slot_s + b0 * M0 * kSlots;
+  V.slot_p = static_cast<char*>(W.slot_p) + b0 * M0 * kSlots * 16;
   V.ymax2 = W.ymax2 + b0;
   V.flags = W.flags + b0;
   V.qcount = W.qcount + 16 * sub;
@@ -108,9 +109,9 @@ inline size_t layout_workspace(Workspace* W, char* base, int64_t B, int64_t M0, 
   const size_t zero_bytes = (size_t)B * 16 + 64 * kMaxSub + (size_t)(B * M0);
   off = al(off + zero_bytes);
   const size_t o_ss = off;
-  off = al(off + (size_t)(B * M0 * 4) * 8);
+  off = al(off + (size_t)(B * M0 * kSlots) * 8);
   const size_t o_sp = off;
-  off = al(off + (size_t)(B * M0 * 4) * 16);
+  off = al(off + (size_t)(B * M0 * kSlots) * 16);
   // singular values of every bin (general path)
   const size_t o_sv = off;
   if (mode == SFT_GENERAL) off = al(off + (size_t)(B * M0 * a_max) * 8);

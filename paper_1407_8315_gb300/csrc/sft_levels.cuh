@@ -1,0 +1,307 @@
+// sft_levels.cuh -- the per-bin stages of the exact paths: the fold, peel
+// and activity test of each level and the per-level decoder of Algorithm 1
+// (ITER), and the activity scan and the decode rounds of the non-iterative
+// method (FIXED).  Shared by the translation unit of the launchers and the
+// one that instantiates the decoders of more than four aliases.
+#pragma once
+
+#include <type_traits>
+
+#include "sft_decode.cuh"
+#include "sft_device_util.cuh"
+
+struct sft_plan_s;
+
+namespace sft {
+
+// ------------------------------------------------- per-level decode (ITER)
+struct LevelArgs {
+  int64_t N, M, d, M0;
+  const void* prev;  // level l-1 rows, length 2M (Store<F>::T)
+  void* cur;         // level l rows, length M
+  int64_t held_elems;
+  const uint8_t* Tprev;
+  uint8_t* Tcur;
+  uint8_t* slot_cnt;
+  int64_t* slot_s;
+  void* slot_p;  // Store<F>::T
+  const unsigned long long* ymax2;
+  int32_t* flags;
+  double zero_tol, root_tol, res_tol;
+  OmegaTab om;
+  OmegaTabFF omff;
+};
+
+// |m|^2 > theta^2 decided from the float-float hi parts when they are
+// clearly on one side (relative error of the hi-part norm < 1e-6), in FP64
+// otherwise -- the same decision the FP64 comparison takes.
+__device__ __forceinline__ bool above_ff(const FF::V& m, double theta2) {
+  const float nh = m.rh * m.rh + m.ih * m.ih;
+  const float t2 = (float)theta2;
+  if (nh > t2 * 1.0001f) return true;
+  if (nh < t2 * 0.9999f) return false;
+  const double x = (double)m.rh + (double)m.rl, y = (double)m.ih + (double)m.il;
+  return x * x + y * y > theta2;
+}
+
+constexpr int kFoldThreads = 256;
+constexpr int kDecThreads = 128;
+
+// Level l, phase 1, one thread per bin: fold the held syndromes, SubFreq on
+// the two new shifts, activity test (line 09), write the syndromes back and
+// queue the active bins for decoding.
+template <class F, int A>
+__global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* queue, int* qcount) {
+  constexpr int l = A - 1, nm = 2 * A;
+  typedef typename Store<F>::T T;
+  const int b = blockIdx.y;
+  const int64_t M = g.M, M0 = g.M0;
+  const int64_t k = (int64_t)blockIdx.x * kFoldThreads + threadIdx.x;
+  bool active = false;
+  if (k < M) {
+    const T* prev = reinterpret_cast<const T*>(g.prev) + (int64_t)b * g.held_elems;
+    T* cur = reinterpret_cast<T*>(g.cur) + (int64_t)b * g.held_elems;
+    const uint8_t* cnt = g.slot_cnt + (int64_t)b * M0;
+    const int64_t* ss = g.slot_s + (int64_t)b * M0 * kSlots;
+    const T* sp = reinterpret_cast<const T*>(g.slot_p) + (int64_t)b * M0 * kSlots;
+    uint8_t t = 0;
+    if (l > 0) t = (uint8_t)(g.Tprev[(int64_t)b * M0 + k] | g.Tprev[(int64_t)b * M0 + k + M]);
+    const double theta2 = g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]);
+    const int64_t nsub = M0 / M;
+    if constexpr (std::is_same<F, F64>::value) {
+      cdbl m[nm];
+      // fold the syndromes held from level l-1 (length 2M) to length M
+#pragma unroll
+      for (int j = 0; j < 2 * l; ++j)
+        m[j] = Store<F>::to_d(prev[j * 2 * M + k]) + Store<F>::to_d(prev[j * 2 * M + k + M]);
+      m[2 * l] = Store<F>::to_d(cur[(2 * l) * M + k]);
+      m[2 * l + 1] = Store<F>::to_d(cur[(2 * l + 1) * M + k]);
+      // SubFreq: remove every frequency recovered at earlier levels from the
+      // two new shifts; they are filed under the level-0 bins k + u M
+      if (l > 0) {
+        for (int64_t u = 0; u < nsub; ++u) {
+          const int64_t k0 = k + u * M;
+          const int c = cnt[k0];
+          for (int e = 0; e < c; ++e) {
+            const int64_t sl = ss[k0 * kSlots + e];
+            const cdbl p = Store<F>::to_d(sp[k0 * kSlots + e]);
+            m[2 * l] = m[2 * l] - p * omega_pow(g.om, sl * (2 * l));
+            m[2 * l + 1] = m[2 * l + 1] - p * omega_pow(g.om, sl * (2 * l + 1));
+          }
+        }
+      }
+      active = t || norm2(m[2 * l]) > theta2 || norm2(m[2 * l + 1]) > theta2;
+#pragma unroll
+      for (int j = 0; j < nm; ++j) cur[j * M + k] = Store<F>::from_d(m[j]);
+    } else {
+      FF::V m[nm];
+#pragma unroll
+      for (int j = 0; j < 2 * l; ++j)
+        m[j] = FF::add(FF::from4(prev[j * 2 * M + k]), FF::from4(prev[j * 2 * M + k + M]));
+      m[2 * l] = FF::from4(cur[(2 * l) * M + k]);
+      m[2 * l + 1] = FF::from4(cur[(2 * l + 1) * M + k]);
+      if constexpr (l > 0) {
+        // the 2^l level-0 bins folded into k, in chunks of up to 8: all
+        // counts of a chunk are loaded before its first entry, so that the
+        // loads of different sub-bins overlap
+        constexpr int NS = 1 << l;
+        constexpr int CH = NS < 8 ? NS : 8;
+        for (int u0 = 0; u0 < NS; u0 += CH) {
+          int c[CH];
+#pragma unroll
+          for (int u = 0; u < CH; ++u) c[u] = cnt[k + (int64_t)(u0 + u) * M];
+#pragma unroll
+          for (int u = 0; u < CH; ++u) {
+            const int64_t k0 = k + (int64_t)(u0 + u) * M;
+            for (int e = 0; e < c[u]; ++e) {
+              const int64_t sl = ss[k0 * kSlots + e];
+              const FF::V p = FF::from4(sp[k0 * kSlots + e]);
+              m[2 * l] = FF::sub(m[2 * l], FF::mulv(p, omega_ff(g.omff, sl * (2 * l))));
+              m[2 * l + 1] =
+                  FF::sub(m[2 * l + 1], FF::mulv(p, omega_ff(g.omff, sl * (2 * l + 1))));
+            }
+          }
+        }
+      }
+      active = t || above_ff(m[2 * l], theta2) || above_ff(m[2 * l + 1], theta2);
+#pragma unroll
+      for (int j = 0; j < nm; ++j) cur[j * M + k] = FF::to4(m[j]);
+    }
+    if (!active) g.Tcur[(int64_t)b * M0 + k] = 0;
+  }
+  queue_push(active, b, (int)k, queue, qcount);
+}
+
+// Level l, phase 2: decode the queued bins with a = l + 1 (lines 23-35),
+// grid-stride over the queue so that every warp is full.
+template <class F, int A>
+__global__ void __launch_bounds__(kDecThreads) k_iter_decode(LevelArgs g, const int2* queue,
+                                                             const int* qcount) {
+  constexpr int nm = 2 * A;
+  typedef typename Store<F>::T T;
+  const int n = *qcount;
+  const BinGeom geom{g.N, g.M, g.d, g.om};
+  for (int e = blockIdx.x * kDecThreads + threadIdx.x; e < n; e += gridDim.x * kDecThreads) {
+    const int2 q = queue[e];
+    const int b = q.x;
+    const int64_t k = q.y, M = g.M, M0 = g.M0;
+    T* cur = reinterpret_cast<T*>(g.cur) + (int64_t)b * g.held_elems;
+    const Tol2 tol{g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]),
+                   g.root_tol * g.root_tol, g.res_tol * g.res_tol};
+    T raw[nm];
+#pragma unroll
+    for (int j = 0; j < nm; ++j) raw[j] = cur[j * M + k];
+    int64_t s[4];
+    cdbl p[4];
+    cdbl m[nm];
+    uint8_t t = 1;
+    bool ok = false, filed = false;
+    float4 res[nm];
+    // one alias on the mixed path: float-float unless a value lies at a
+    // decision boundary (then the FP64 decoder below)
+    int fast = -1;
+    if constexpr (std::is_same<F, FF>::value && A == 1) {
+      float4 pf;
+      fast = decode_a1_ff<nm>(raw, k, geom, tol, g.omff, s, &pf, res);
+      if (fast == 1) {
+        file_one_ff(s[0], pf, M0, g.slot_cnt + (int64_t)b * M0, g.slot_s + (int64_t)b * M0 * kSlots,
+                    reinterpret_cast<float4*>(g.slot_p) + (int64_t)b * M0 * kSlots, g.flags + b);
+        ok = filed = true;
+      }
+    }
+    if (fast < 0) {
+#pragma unroll
+      for (int j = 0; j < nm; ++j) m[j] = Store<F>::to_d(raw[j]);
+      if constexpr (std::is_same<F, FF>::value)
+        ok = decode_bin<A, nm>(m, k, geom, tol, s, p, raw, &g.omff, res);
+      else
+        ok = decode_bin<A, nm>(m, k, geom, tol, s, p);
+    }
+    if (ok) {
+      if (!filed)
+        file_solution<F, A>(s, p, M0, g.slot_cnt + (int64_t)b * M0,
+                            g.slot_s + (int64_t)b * M0 * kSlots,
+                            reinterpret_cast<T*>(g.slot_p) + (int64_t)b * M0 * kSlots, g.flags + b);
+      // the recovered terms leave every syndrome held for this bin
+      if constexpr (std::is_same<F, FF>::value) {
+#pragma unroll
+        for (int j = 0; j < nm; ++j) cur[j * M + k] = res[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < nm; ++j) cur[j * M + k] = Store<F>::from_d_small(m[j]);
+      }
+      t = 0;
+    }
+    g.Tcur[(int64_t)b * M0 + k] = t;
+  }
+}
+
+// ---------------------------------------------- non-iterative decode (FIXED)
+struct FixedArgs {
+  int64_t N, M, d;
+  int a_max;
+  const void* Y;  // 2 a_max rows of length M (Store<F>::T)
+  int64_t held_elems;
+  uint8_t* T;
+  uint8_t* slot_cnt;
+  int64_t* slot_s;
+  void* slot_p;
+  const unsigned long long* ymax2;
+  int32_t* flags;
+  double zero_tol, root_tol, res_tol;
+  OmegaTab om;
+  OmegaTabFF omff;  // float-float omega tables (mixed path)
+};
+
+// activity of every bin (any of the 2 a_max syndromes above theta)
+template <class F, int NM>
+__global__ void __launch_bounds__(kFoldThreads) k_fixed_scan(FixedArgs g, int2* queue, int* qcount) {
+  typedef typename Store<F>::T T;
+  const int b = blockIdx.y;
+  const int64_t M = g.M;
+  const int64_t k = (int64_t)blockIdx.x * kFoldThreads + threadIdx.x;
+  bool active = false;
+  if (k < M) {
+    const T* Y = reinterpret_cast<const T*>(g.Y) + (int64_t)b * g.held_elems;
+    const double theta2 = g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]);
+#pragma unroll
+    for (int j = 0; j < NM; ++j) {
+      if constexpr (std::is_same<F, F64>::value)
+        active = active || norm2(Store<F>::to_d(Y[j * M + k])) > theta2;
+      else
+        active = active || above_ff(FF::from4(Y[j * M + k]), theta2);
+    }
+    g.T[(int64_t)b * M + k] = 0;
+  }
+  queue_push(active, b, (int)k, queue, qcount);
+}
+
+// round a: decode the queued bins with a aliases; failures go to the next
+// round's queue, or are marked unsolved after the last round (a = a_max)
+template <class F, int A, int NM>
+__global__ void __launch_bounds__(kDecThreads) k_fixed_round(FixedArgs g, const int2* qin,
+                                                             const int* nin, int2* qout,
+                                                             int* nout) {
+  typedef typename Store<F>::T T;
+  const int n = *nin;
+  const BinGeom geom{g.N, g.M, g.d, g.om};
+  const int64_t M = g.M;
+  for (int e0 = blockIdx.x * kDecThreads; e0 < n; e0 += gridDim.x * kDecThreads) {
+    const int e = e0 + threadIdx.x;
+    bool fail = false;
+    int b = 0, k = 0;
+    if (e < n) {
+      const int2 q = qin[e];
+      b = q.x;
+      k = q.y;
+      const T* Y = reinterpret_cast<const T*>(g.Y) + (int64_t)b * g.held_elems;
+      const Tol2 tol{g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]),
+                     g.root_tol * g.root_tol, g.res_tol * g.res_tol};
+      T raw[NM];
+#pragma unroll
+      for (int j = 0; j < NM; ++j) raw[j] = Y[j * M + k];
+      int64_t s[4];
+      cdbl p[4];
+      bool ok = false, filed = false;
+      int fast = -1;
+      if constexpr (std::is_same<F, FF>::value && A == 1) {
+        float4 pf, res[NM];
+        fast = decode_a1_ff<NM>(raw, k, geom, tol, g.omff, s, &pf, res);
+        if (fast == 1) {
+          file_one_ff(s[0], pf, M, g.slot_cnt + (int64_t)b * M, g.slot_s + (int64_t)b * M * kSlots,
+                      reinterpret_cast<float4*>(g.slot_p) + (int64_t)b * M * kSlots, g.flags + b);
+          ok = filed = true;
+        }
+      }
+      if (fast < 0) {
+        cdbl m[NM];
+#pragma unroll
+        for (int j = 0; j < NM; ++j) m[j] = Store<F>::to_d(raw[j]);
+        if constexpr (std::is_same<F, FF>::value)
+          ok = decode_bin<A, NM>(m, k, geom, tol, s, p, raw, &g.omff, nullptr);
+        else
+          ok = decode_bin<A, NM>(m, k, geom, tol, s, p);
+      }
+      if (ok) {
+        if (!filed)
+          file_solution<F, A>(s, p, M, g.slot_cnt + (int64_t)b * M, g.slot_s + (int64_t)b * M * kSlots,
+                              reinterpret_cast<T*>(g.slot_p) + (int64_t)b * M * kSlots, g.flags + b);
+      } else if (qout == nullptr) {
+        g.T[(int64_t)b * M + k] = 1;
+      } else {
+        fail = true;
+      }
+    }
+    if (qout != nullptr) queue_push(fail, b, k, qout, nout);
+  }
+}
+
+// Bins with more than four aliases (sft_wide.cu): ITER level A - 1 >= 4
+// (fold, then the warp-per-bin decoder), and the FIXED scan and rounds for
+// a_max = 8 (rounds 1-4 as above on 16 syndromes, rounds 5-8 warp-per-bin).
+void launch_level_wide(sft_plan_s* P, int A, const LevelArgs& g, int2* q, int* c, dim3 fgrid,
+                       int64_t maxq, int nsm, cudaStream_t st, const char* fold_name,
+                       const char* dec_name);
+void launch_fixed_wide(sft_plan_s* P, int64_t B, const FixedArgs& g, int nsm, cudaStream_t st);
+
+}  // namespace sft

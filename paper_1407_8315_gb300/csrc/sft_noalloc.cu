@@ -132,11 +132,13 @@ extern "C" sft_status sft_exact_noalloc(const sft_params* pin, int64_t n, const 
   if (!(p.root_tol > 0)) p.root_tol = 0.1;
   if (!(p.res_tol > 0)) p.res_tol = fp64 ? 1e-9 : 1e-6;
   if (!pow2(p.N) || p.N < 8 || p.N > (int64_t(1) << 30) || p.K < 0 || p.K > p.N ||
-      !pow2(p.d) || p.d > p.N || p.a_max < 1 || p.a_max > 4 || p.reserved_ != 0 ||
+      !pow2(p.d) || p.d > p.N || p.a_max < 1 || p.a_max > 8 || p.reserved_ != 0 ||
       (p.precision != SFT_FP64 && p.precision != SFT_MIXED))
     return fail(SFT_EINVAL, "invalid parameters");
   if (p.mode != SFT_EXACT_ITER && p.mode != SFT_EXACT_FIXED)
     return fail(p.mode == SFT_GENERAL ? SFT_EUNSUPPORTED : SFT_EINVAL, "mode not supported");
+  if (p.mode == SFT_EXACT_FIXED && p.a_max > 4 && p.a_max != 8)
+    return fail(SFT_EUNSUPPORTED, "SFT_EXACT_FIXED takes a_max <= 4 or a_max = 8");
   const int64_t M0 = p.N / p.d;
   if (M0 > 8192) return fail(SFT_EUNSUPPORTED, "N/d above 8192");
   if (p.mode == SFT_EXACT_ITER &&

@@ -56,7 +56,7 @@ def test_params_default(lib):
 
 
 @pytest.mark.parametrize("field,value,status", [
-    ("N", 1000, 1), ("N", 4, 1), ("d", 3, 1), ("d", 1 << 23, 1), ("a_max", 5, 1),
+    ("N", 1000, 1), ("N", 4, 1), ("d", 3, 1), ("d", 1 << 23, 1), ("a_max", 9, 1),
     ("max_iters", 5, 1), ("mode", 7, 1), ("precision", 9, 1), ("reserved_", 1, 1),
 ])
 def test_plan_create_rejects_before_touching_the_gpu(lib, field, value, status):
@@ -89,6 +89,21 @@ def test_unpruned_plan_defaults_and_limits(lib):
     assert lib.sft_plan_create(C.byref(p), 1, C.byref(h)) == sft.SFT_EUNSUPPORTED
     p.n_cs_shifts = 17
     assert lib.sft_plan_create(C.byref(p), 1, C.byref(h)) == sft.SFT_EINVAL
+
+
+def test_more_than_four_aliases_only_on_the_exact_paths(lib):
+    """a_max up to 8 is valid for the exact modes; the general modes keep
+    a_max <= 4 (SFT_EUNSUPPORTED)."""
+    from paper_1407_8315_gb300 import sft
+    h = C.c_void_p()
+    p = sft.sft_params_default(1 << 20, 1024, 32, "general", "mixed")
+    p.a_max = 5
+    assert lib.sft_plan_create(C.byref(p), 1, C.byref(h)) == sft.SFT_EUNSUPPORTED
+    p = sft.sft_params_default(1 << 20, 1024, 256, "fixed", "mixed")
+    p.a_max = 9
+    assert lib.sft_plan_create(C.byref(p), 1, C.byref(h)) == sft.SFT_EINVAL
+    p.a_max = 6  # FIXED decodes from 2 a_max = 16 syndromes only at a_max = 8
+    assert lib.sft_plan_create(C.byref(p), 1, C.byref(h)) == sft.SFT_EUNSUPPORTED
 
 
 def test_plan_create_rejects_too_many_bins(lib):

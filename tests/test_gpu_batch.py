@@ -109,7 +109,7 @@ def test_batch_rejects_bad_signal(gpu):
     torch = gpu
     from paper_1407_8315_gb300 import sft
     params, xs = _make(4, 9)
-    params[2].a_max = 7
+    params[2].a_max = 9
     batch = sft.Batch()
     xt = [torch.from_numpy(x).cuda() for x in xs]
     with pytest.raises(sft.SftError) as ei:
