@@ -115,6 +115,8 @@ class W:
             return (lg, 0) if Ml <= 8192 else (lg - lg // 2, lg // 2)
 
         fixed_ns = 2 * self.a_max
+        if stage == "extract":  # the samples every later FFT reads, copied once
+            return {"bytes": 2 * self.h2d_per_signal(), "fft_ops": 0}
         if stage.startswith("gather_fft_l"):
             Ml, ns = self.M >> int(stage[-1]), 2
             stages, reads = split(Ml)[0], True
@@ -403,13 +405,14 @@ def kernel_of(stage: str, M: int = 0) -> str:
 
 
 def roofline(wl, stages, B, clk):
-    # B: signals per launch (the call's signals over its sub-batches)
     """Dominant kernel (largest share of the step) and its roofline.  The
     gather/FFT kernels of the mixed form are bound by the FP32 pipes (the
     float-float FFT), so 'achieved' counts the FFT's radix-2 butterflies at
     their float-float cost in FP32 instructions against 152 SMs x 128 FP32
     lanes x the sampled SM clock; the HBM view (input bytes / time against
-    the measured copy bandwidth) is given beside it."""
+    the measured copy bandwidth) is given beside it.  B is the number of
+    signals per launch (the attribution pass runs each call as one
+    sub-batch)."""
     peaks, src = measured_peaks()
     groups = {}
     for name, (ms_tot, nl) in stages.items():
