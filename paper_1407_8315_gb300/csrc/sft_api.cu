@@ -90,8 +90,10 @@ void free_plan_memory(sft_plan_s* P) {
   for (int s = 0; s < sft::kMaxSub; ++s) {
     if (P->sub_st[s]) cudaStreamDestroy(P->sub_st[s]);
     if (P->sub_join[s]) cudaEventDestroy(P->sub_join[s]);
+    if (P->sub_extracted[s]) cudaEventDestroy(P->sub_extracted[s]);
     P->sub_st[s] = nullptr;
     P->sub_join[s] = nullptr;
+    P->sub_extracted[s] = nullptr;
   }
   if (P->sub_fork) cudaEventDestroy(P->sub_fork);
   P->sub_fork = nullptr;
@@ -273,6 +275,8 @@ sft_status sft_plan_create(const sft_params* pin, int64_t max_signals, sft_plan_
     e = cudaStreamCreateWithFlags(&P->sub_st[s], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->sub_join[s], cudaEventDisableTiming);
   }
+  for (int s = 0; e == cudaSuccess && s < sft::kMaxSub; ++s)
+    e = cudaEventCreateWithFlags(&P->sub_extracted[s], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     note_cuda(e);
     free_plan_memory(P);
@@ -408,8 +412,10 @@ static sft_status run_host(sft_plan_t P, int64_t n, const void* x_host, int64_t 
   if (e == cudaSuccess) e = cudaMemsetAsync(P->ws.zero_base, 0, P->ws.zero_bytes, s);
   // host-resident samples are read over NVLink-C2C, where wide requests pay
   P->x_on_host = xd != P->x_stage;
+  P->r_on_host = in_place;
   if (e == cudaSuccess) e = sft::launch_exact(P, n, xd, x_stride, &rd, s);
   P->x_on_host = false;
+  P->r_on_host = false;
   if (!in_place) {
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(rh->idx, rd.idx, (size_t)n * cap * 8, cudaMemcpyDeviceToHost, s);

@@ -300,6 +300,8 @@ struct FinArgs {
 
 // bins per finalize tile (1024 threads x 4 bins)
 constexpr int kFinTile = 4096;
+// entries staged in shared memory per window of the finalize (24 KB)
+constexpr int kFinStage = 1024;
 
 // Block-wide exclusive scan of one int per thread (blockDim = 1024).
 __device__ __forceinline__ int block_excl_scan(int v, int* total) {
@@ -365,7 +367,7 @@ __global__ void __launch_bounds__(256) k_fin_count(FinArgs g) {
 // Finalize pass 2: each tile's entries go to its offset (sum of the earlier
 // tiles) plus the block scan of its bins, in bin order; tile 0 writes the
 // counters.
-template <class F>
+template <class F, bool kStaged>
 __global__ void __launch_bounds__(1024) k_finalize(FinArgs g) {
   typedef typename Store<F>::T T;
   const int b = blockIdx.y, tile = blockIdx.x;
@@ -386,8 +388,8 @@ __global__ void __launch_bounds__(1024) k_finalize(FinArgs g) {
   int mine = 0;
   for (int64_t k0 = lo; k0 < hi; ++k0) mine += cnt[k0];
   int total_tile = 0;
-  int pos = block_excl_scan(mine, &total_tile);  // synchronises: s_base visible
-  pos += s_base;
+  const int lpos = block_excl_scan(mine, &total_tile);  // synchronises: s_base visible
+  const int base = s_base;
   int64_t cap = g.cap;
   int64_t* idx = g.idx + (int64_t)b * g.cap;
   double2* val = g.val + (int64_t)b * g.cap;
@@ -403,15 +405,50 @@ __global__ void __launch_bounds__(1024) k_finalize(FinArgs g) {
     unresolved = rt.unresolved;
     overflow = rt.overflow;
   }
-  for (int64_t k0 = lo; k0 < hi; ++k0) {
-    const int c = cnt[k0];
-    for (int e = 0; e < c; ++e, ++pos) {
-      if (pos < cap) {
-        idx[pos] = g.slot_s[((int64_t)b * M0 + k0) * kSlots + e];
-        const cdbl v = Store<F>::to_d(sp[((int64_t)b * M0 + k0) * kSlots + e]);
-        val[pos] = make_double2(v.x, v.y);
+  if constexpr (!kStaged) {
+    // device-resident results: each thread writes its own entries
+    int pos = base + lpos;
+    for (int64_t k0 = lo; k0 < hi; ++k0) {
+      const int c = cnt[k0];
+      for (int e = 0; e < c; ++e, ++pos) {
+        if (pos < cap) {
+          idx[pos] = g.slot_s[((int64_t)b * M0 + k0) * kSlots + e];
+          const cdbl v = Store<F>::to_d(sp[((int64_t)b * M0 + k0) * kSlots + e]);
+          val[pos] = make_double2(v.x, v.y);
+        }
       }
     }
+  }
+  // results in page-locked host memory (written over the host link): the
+  // tile's entries form one contiguous run [base, base + total_tile) of the
+  // output; they are gathered in shared memory in windows of kFinStage and
+  // written out by consecutive threads, so that the stores are coalesced
+  __shared__ int64_t s_idx[kStaged ? kFinStage : 1];
+  __shared__ double2 s_val[kStaged ? kFinStage : 1];
+  for (int w0 = 0; kStaged && w0 < total_tile; w0 += kFinStage) {
+    if (lpos < w0 + kFinStage && lpos + mine > w0) {
+      int p = lpos;
+      for (int64_t k0 = lo; k0 < hi && p < w0 + kFinStage; ++k0) {
+        const int c = cnt[k0];
+        for (int e = 0; e < c; ++e, ++p) {
+          if (p >= w0 && p < w0 + kFinStage) {
+            s_idx[p - w0] = g.slot_s[((int64_t)b * M0 + k0) * kSlots + e];
+            const cdbl v = Store<F>::to_d(sp[((int64_t)b * M0 + k0) * kSlots + e]);
+            s_val[p - w0] = make_double2(v.x, v.y);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const int n = min(kFinStage, total_tile - w0);
+    for (int i = tid; i < n; i += blockDim.x) {
+      const int64_t gp = (int64_t)base + w0 + i;
+      if (gp < cap) {
+        idx[gp] = s_idx[i];
+        val[gp] = s_val[i];
+      }
+    }
+    __syncthreads();
   }
   if (g.n_tiles == 1) {
     // one tile per signal (no count pass): the unresolved bins here
@@ -629,6 +666,7 @@ static void launch_extract(sft_plan_s* P, int64_t B, const void* x, int64_t x_st
         reinterpret_cast<const typename F::In*>(x), x_stride, P->x_table, P->p.N, P->p.d, P->M0,
         levels, fixed_nsh, reinterpret_cast<typename F::In*>(P->ws.xc), P->ws.xc_sig);
   stage_end(P, st);
+  if (P->sub_extract_now != nullptr) cudaEventRecord(P->sub_extract_now, st);
 }
 
 template <class F>
@@ -816,9 +854,11 @@ static cudaError_t launch_one(sft_plan_s* P, int64_t B, const void* x, int64_t x
   stage_begin(P, "finalize", st);
   if (!single) k_fin_count<<<fgrid, 256, 0, st>>>(f);
   if (fp64)
-    k_finalize<F64><<<fgrid, 1024, 0, st>>>(f);
+    P->r_on_host ? k_finalize<F64, true><<<fgrid, 1024, 0, st>>>(f)
+                 : k_finalize<F64, false><<<fgrid, 1024, 0, st>>>(f);
   else
-    k_finalize<FF><<<fgrid, 1024, 0, st>>>(f);
+    P->r_on_host ? k_finalize<FF, true><<<fgrid, 1024, 0, st>>>(f)
+                 : k_finalize<FF, false><<<fgrid, 1024, 0, st>>>(f);
   stage_end(P, st);
   return cudaGetLastError();
 }
@@ -854,7 +894,17 @@ cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
     const int64_t Bs = B / S + (s < B % S ? 1 : 0);
     cudaStream_t ss = s == 0 ? st : P->sub_st[s];
     if (s > 0) e = cudaStreamWaitEvent(ss, P->sub_fork, 0);
+    // host-resident input: extract after the previous sub-batch has
+    if (e == cudaSuccess && s > 0 && P->x_on_host)
+      e = cudaStreamWaitEvent(ss, P->sub_extracted[s - 1], 0);
     if (e != cudaSuccess) break;
+    if (P->x_on_host) {
+      // recorded again after the extraction (a mode without one still
+      // releases the next sub-batch)
+      P->sub_extract_now = P->sub_extracted[s];
+      e = cudaEventRecord(P->sub_extract_now, ss);
+      if (e != cudaSuccess) break;
+    }
     P->ws = sub_workspace(W0, b0, s);
     P->x_table = xt0 ? xt0 + b0 : nullptr;
     P->r_table = rt0 ? rt0 + b0 : nullptr;
@@ -876,6 +926,7 @@ cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
   P->r_table = rt0;
   P->K_table = kt0;
   P->mlp_prop = prop0;
+  P->sub_extract_now = nullptr;
   for (int s = 1; s < S && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(st, P->sub_join[s], 0);
   return e;
 }

@@ -207,6 +207,9 @@ struct sft_plan_s {
   // the current call reads page-locked host memory in place (the compact
   // extraction then asks for full-width L2 lines)
   bool x_on_host = false;
+  // the current call writes its results in place into page-locked host
+  // memory (the finalize then stages them for coalesced stores)
+  bool r_on_host = false;
   // learned proposal (general plans): the attached network (not owned) and
   // 8 proposed candidates t per queued bin (int16, -1 = none)
   struct sft_mlp_s* mlp = nullptr;
@@ -217,6 +220,13 @@ struct sft_plan_s {
   cudaStream_t sub_st[sft::kMaxSub] = {};
   cudaEvent_t sub_fork = nullptr;
   cudaEvent_t sub_join[sft::kMaxSub] = {};
+  // host-resident input: sub-batch s + 1 extracts its samples after sub-batch
+  // s has (the extractions share the host link; chained, each sub-batch's
+  // computation overlaps the next one's extraction).  sub_extracted[s] is
+  // recorded after sub-batch s's extraction; sub_extract_now is the event
+  // of the sub-batch being enqueued (null outside a split host call).
+  cudaEvent_t sub_extracted[sft::kMaxSub] = {};
+  cudaEvent_t sub_extract_now = nullptr;
   // profiling
   bool profiling = false;
   std::vector<sft::StageRec> stage_recs;   // records since the last read
