@@ -367,6 +367,201 @@ __device__ __forceinline__ int decode_a1_ff(const float4* raw, int64_t k, const 
   return 1;
 }
 
+// ----------------------------------------------- float-float arithmetic
+// Real float-float numbers (h + l, |l| <= ulp(h)/2) and the complex
+// operations the two-alias decoder needs, on the FP32 pipes: products by
+// FMA-based TwoProd, quotients and square roots by one float-float
+// correction of the correctly rounded FP32 result (Dekker 1971; Karp and
+// Markstein 1997), ~44 significant bits.
+struct FR {
+  float h, l;
+};
+__device__ __forceinline__ FR fr_norm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return FR{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ FR fr_add(FR a, FR b) {
+  float s, e;
+  FF::two_sum(a.h, b.h, s, e);
+  return fr_norm(s, __fadd_rn(__fadd_rn(a.l, b.l), e));
+}
+__device__ __forceinline__ FR fr_sub(FR a, FR b) { return fr_add(a, FR{-b.h, -b.l}); }
+__device__ __forceinline__ FR fr_mul(FR a, FR b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return fr_norm(p, e);
+}
+__device__ __forceinline__ FR fr_div(FR a, FR b) {
+  const float q = __fdiv_rn(a.h, b.h);
+  const FR r = fr_sub(a, fr_mul(FR{q, 0.0f}, b));
+  return fr_norm(q, __fdiv_rn(__fadd_rn(r.h, r.l), b.h));
+}
+__device__ __forceinline__ FR fr_sqrt(FR a) {
+  if (!(a.h > 0.0f)) return FR{0.0f, 0.0f};
+  const float s = __fsqrt_rn(a.h);
+  const FR r = fr_sub(a, fr_mul(FR{s, 0.0f}, FR{s, 0.0f}));
+  return fr_norm(s, __fdiv_rn(__fadd_rn(r.h, r.l), 2.0f * s));
+}
+__device__ __forceinline__ FR re_of(const FF::V& v) { return FR{v.rh, v.rl}; }
+__device__ __forceinline__ FR im_of(const FF::V& v) { return FR{v.ih, v.il}; }
+__device__ __forceinline__ FF::V cmk(FR x, FR y) { return FF::V{x.h, x.l, y.h, y.l}; }
+__device__ __forceinline__ FF::V cconj(const FF::V& v) { return FF::V{v.rh, v.rl, -v.ih, -v.il}; }
+__device__ __forceinline__ FF::V cscale(const FF::V& v, FR s) {
+  return cmk(fr_mul(re_of(v), s), fr_mul(im_of(v), s));
+}
+__device__ __forceinline__ FR cnorm2(const FF::V& v) {
+  return fr_add(fr_mul(re_of(v), re_of(v)), fr_mul(im_of(v), im_of(v)));
+}
+// a / b = a conj(b) / |b|^2
+__device__ __forceinline__ FF::V cdiv(const FF::V& a, const FF::V& b) {
+  const FR n = cnorm2(b);
+  const FF::V t = FF::mulv(a, cconj(b));
+  return cmk(fr_div(re_of(t), n), fr_div(im_of(t), n));
+}
+// principal square root, as csqrt_fast
+__device__ __forceinline__ FF::V csqrt_ff(const FF::V& v) {
+  const FR r = fr_sqrt(cnorm2(v));
+  if (r.h == 0.0f) return FF::V{0.0f, 0.0f, 0.0f, 0.0f};
+  const FR x = re_of(v), y = im_of(v);
+  const FR half{0.5f, 0.0f};
+  if (x.h >= 0.0f) {
+    const FR t = fr_sqrt(fr_mul(half, fr_add(r, x)));
+    return cmk(t, fr_div(fr_mul(y, half), t));
+  }
+  const FR t = fr_sqrt(fr_mul(half, fr_sub(r, x)));
+  const FR ay = y.h < 0.0f ? FR{-y.h, -y.l} : y;
+  return cmk(fr_div(fr_mul(ay, half), t), y.h < 0.0f ? FR{-t.h, -t.l} : t);
+}
+
+// The two-alias decode of the mixed path in float-float (Sec. II-B steps
+// (i)-(iii) for a = 2): the 2 x 2 Hankel solve by Gaussian elimination with
+// partial pivoting, the quadratic's roots in the cancellation-free form, the
+// snap of each root to S_k, the values by the normal equations over all nm
+// equations, the theta and residual tests.  As decode_a1_ff: every deciding
+// quantity is compared in FP32 against its threshold, and a value within
+// the float-float error's margin of it (or a degenerate pivot, root or
+// normal matrix) returns -1 so that the caller runs the FP64 decoder.
+// Returns 1 on success (s ascending, p_ff, res_out filled), 0 on failure.
+template <int nm>
+__device__ __forceinline__ int decode_a2_ff(const float4* raw, int64_t k, const BinGeom& g,
+                                            const Tol2& tol, const OmegaTabFF& omff, int64_t* s,
+                                            float4* p_ff, float4* res_out) {
+  FF::V m[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) m[i] = FF::from4(raw[i]);
+  const float n0 = ff_norm(m[0]), n1 = ff_norm(m[1]), n2 = ff_norm(m[2]);
+  const float amax2 = fmaxf(n0, fmaxf(n1, n2));
+  if (!(amax2 > 1e-30f && amax2 < 1e30f)) return -1;
+  // (i) sum_j c_j m_{i+j} = -m_{2+i}: pivot on the larger of |m0|, |m1|
+  const bool swap = n1 > n0;
+  const FF::V a0 = swap ? m[1] : m[0], a1 = swap ? m[2] : m[1];  // pivot row
+  const FF::V o0 = swap ? m[0] : m[1], o1 = swap ? m[1] : m[2];  // other row
+  const FF::V r0 = swap ? m[3] : m[2], r1 = swap ? m[2] : m[3];  // -rhs
+  const float best = fmaxf(n0, n1);
+  if (best <= 1e-28f * amax2 * 1.1f) return -1;
+  const FF::V f = cdiv(o0, a0);
+  const FF::V a22 = FF::sub(o1, FF::mulv(f, a1));
+  const float n22 = ff_norm(a22);
+  if (n22 <= 1e-28f * amax2 * 1.1f) return -1;
+  const FF::V b2 = FF::sub(FF::mulv(f, r0), r1);  // -r1 - f (-r0)
+  const FF::V c1 = cdiv(b2, a22);
+  const FF::V c0 = cdiv(FF::sub(FF::V{-r0.rh, -r0.rl, -r0.ih, -r0.il}, FF::mulv(a1, c1)), a0);
+  // (ii) z^2 + c1 z + c0: q = -(c1 + sqrt(D)) / 2 on the larger branch
+  const FF::V D = FF::sub(FF::mulv(c1, c1), cscale(c0, FR{4.0f, 0.0f}));
+  const FF::V sq = csqrt_ff(D);
+  const FF::V qp = FF::add(c1, sq), qm = FF::sub(c1, sq);
+  const FF::V qs = ff_norm(qp) >= ff_norm(qm) ? qp : qm;
+  const FF::V q = cscale(qs, FR{-0.5f, 0.0f});
+  const float nq = ff_norm(q);
+  if (!(nq > 1e-30f && nq < 1e30f)) return -1;
+  FF::V z[2] = {q, cdiv(c0, q)};
+  FF::V w[2];
+  const float r2 = (float)tol.root2;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float zx = ff_re(z[j]), zy = ff_im(z[j]);
+    if (!(zx * zx + zy * zy > 1e-30f)) return -1;
+    const float df = (float)g.d;
+    const float qa = fmaf(atan2f(zy, zx), df * 0.15915494309189533577f, -(float)k / (float)g.M);
+    const float fr = qa - rintf(qa);
+    if (fabsf(fabsf(fr) - 0.5f) < fmaxf(1e-3f, 8e-7f * df)) return -1;
+    int64_t t = ((int64_t)rintf(qa)) % g.d;
+    if (t < 0) t += g.d;
+    s[j] = k + t * g.M;
+    w[j] = omega_ff(omff, s[j]);
+    const float dx = zx - ff_re(w[j]), dy = zy - ff_im(w[j]);
+    const float dz = dx * dx + dy * dy;
+    if (fabsf(dz - r2) <= 1e-4f * r2) return -1;
+    if (!(dz <= r2)) return 0;
+  }
+  if (s[0] == s[1]) return 0;
+  if (s[0] > s[1]) {
+    const int64_t ts = s[0];
+    s[0] = s[1];
+    s[1] = ts;
+    const FF::V tw = w[0];
+    w[0] = w[1];
+    w[1] = tw;
+  }
+  // (iii) normal equations: G = [[nm, S], [conj(S), nm]], S = sum_i
+  // (conj(w0) w1)^i; g_u = sum_i conj(w_u)^i m_i
+  const FF::V u = FF::mulv(cconj(w[0]), w[1]);
+  FF::V S{1.0f, 0.0f, 0.0f, 0.0f}, up = u;
+  FF::V g0 = m[0], g1 = m[0];
+  FF::V c0p = cconj(w[0]), c1p = cconj(w[1]);
+  const FF::V cw0 = c0p, cw1 = c1p;
+#pragma unroll
+  for (int i = 1; i < nm; ++i) {
+    const FF::V mi = FF::from4(raw[i]);
+    S = FF::add(S, up);
+    g0 = FF::add(g0, FF::mulv(mi, c0p));
+    g1 = FF::add(g1, FF::mulv(mi, c1p));
+    if (i + 1 < nm) {
+      up = FF::mulv(up, u);
+      c0p = FF::mulv(c0p, cw0);
+      c1p = FF::mulv(c1p, cw1);
+    }
+  }
+  const FR fnm{(float)nm, 0.0f};
+  const FR nS = cnorm2(S);
+  // nm^2 - |S|^2 = nm a22 with a22 the second pivot of the FP64 solve,
+  // which fails when a22 <= 1e-14 nm^2 (this margin leaves it to FP64)
+  const FR det = fr_sub(fr_mul(fnm, fnm), nS);
+  if (!(det.h > 1.1e-14f * (float)(nm * nm * nm))) return -1;
+  // p1 = (nm g1 - conj(S) g0) / det,  p0 = (g0 - S p1) / nm
+  const FF::V num1 = FF::sub(cscale(g1, fnm), FF::mulv(cconj(S), g0));
+  const FF::V p1 = cmk(fr_div(re_of(num1), det), fr_div(im_of(num1), det));
+  const FF::V t0 = FF::sub(g0, FF::mulv(S, p1));
+  const FF::V p0 = cmk(fr_div(re_of(t0), fnm), fr_div(im_of(t0), fnm));
+  const int small0 = ff_le(ff_norm(p0), tol.theta2), small1 = ff_le(ff_norm(p1), tol.theta2);
+  if (small0 < 0 || small1 < 0) return -1;
+  if (small0 || small1) return 0;
+  // the residual over all equations
+  float mmax2 = 0.0f, rmax2 = 0.0f;
+  FF::V r[nm];
+  FF::V f0 = p0, f1 = p1;
+#pragma unroll
+  for (int i = 0; i < nm; ++i) {
+    const FF::V mi = FF::from4(raw[i]);
+    r[i] = FF::sub(mi, FF::add(f0, f1));
+    if (i + 1 < nm) {
+      f0 = FF::mulv(f0, w[0]);
+      f1 = FF::mulv(f1, w[1]);
+    }
+    mmax2 = fmaxf(mmax2, ff_norm(mi));
+    rmax2 = fmaxf(rmax2, ff_norm(r[i]));
+  }
+  const int fits = ff_le(rmax2, tol.res2 * (double)mmax2);
+  if (fits <= 0) return fits;
+  p_ff[0] = FF::to4(p0);
+  p_ff[1] = FF::to4(p1);
+#pragma unroll
+  for (int i = 0; i < nm; ++i) res_out[i] = FF::to4(r[i]);
+  return 1;
+}
+
 // Decode bin k with `a` aliases from m[0..nm).  On success fills s[0..a)
 // (ascending), p[0..a), replaces m[0..nm) by the residual m - Z p and
 // returns true; on failure m is unchanged.

@@ -127,6 +127,40 @@ __device__ __forceinline__ In ld_row(const In* p, bool narrow) {
   return narrow ? ld_row64(p) : __ldg(p);
 }
 
+// Two complex64 samples in one 16-byte load (p 16-byte aligned).
+__device__ __forceinline__ float4 ld_pair(const float4* p, bool narrow) {
+  if (!narrow) return __ldg(p);
+  float4 v;
+  asm volatile("ld.global.nc.L2::64B.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
+// The run of `cnt` (even, <= 16) samples x[n d + j], j < cnt, of one row:
+// for complex64 rows that cannot wrap (d >= 16) and 16-byte aligned signals,
+// as cnt / 2 16-byte loads; otherwise one load per sample.
+template <class In, bool kNarrow>
+__device__ __forceinline__ void load_run(const In* xs, int64_t n, int64_t d, int64_t N, int cnt,
+                                         In* v) {
+  if constexpr (std::is_same<In, float2>::value) {
+    if (d >= 16 && (reinterpret_cast<uintptr_t>(xs) & 15u) == 0) {
+      const float4* p = reinterpret_cast<const float4*>(xs + n * d);
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (2 * j < cnt) {
+          const float4 q = ld_pair(p + j, kNarrow);
+          v[2 * j] = make_float2(q.x, q.y);
+          v[2 * j + 1] = make_float2(q.z, q.w);
+        }
+      return;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    if (j < cnt) v[j] = ld_row(xs + ((n * d + j) & (N - 1)), kNarrow);
+}
+
 template <class In, bool kNarrow>
 __global__ void __launch_bounds__(256) k_extract(const In* __restrict__ x, int64_t x_stride,
                                                  const void* const* __restrict__ x_table,
@@ -139,9 +173,7 @@ __global__ void __launch_bounds__(256) k_extract(const In* __restrict__ x, int64
   In* cb = C + (int64_t)b * c_sig;
   In v[16];
   if (fixed_nsh > 0) {
-#pragma unroll
-    for (int j = 0; j < 16; ++j)
-      if (j < fixed_nsh) v[j] = ld_row(xs + ((n * d + j) & (N - 1)), kNarrow);
+    load_run<In, kNarrow>(xs, n, d, N, fixed_nsh, v);
 #pragma unroll
     for (int j = 0; j < 16; ++j)
       if (j < fixed_nsh) cb[(int64_t)j * M0 + n] = v[j];
@@ -149,9 +181,7 @@ __global__ void __launch_bounds__(256) k_extract(const In* __restrict__ x, int64
   }
   // rows n with n mod 2^l == 0 feed level l (shifts 2l, 2l+1)
   const int lv = min(levels, (n == 0 ? 8 : __ffsll(n) - 1 + 1));
-#pragma unroll
-  for (int j = 0; j < 16; ++j)
-    if (j < 2 * lv) v[j] = ld_row(xs + ((n * d + j) & (N - 1)), kNarrow);
+  load_run<In, kNarrow>(xs, n, d, N, 2 * lv, v);
   int64_t off = 0, Ml = M0;
 #pragma unroll
   for (int l = 0; l < 8; ++l) {

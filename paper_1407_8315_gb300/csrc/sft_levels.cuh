@@ -160,12 +160,18 @@ __global__ void __launch_bounds__(kDecThreads) k_iter_decode(LevelArgs g, const 
     // one alias on the mixed path: float-float unless a value lies at a
     // decision boundary (then the FP64 decoder below)
     int fast = -1;
-    if constexpr (std::is_same<F, FF>::value && A == 1) {
-      float4 pf;
-      fast = decode_a1_ff<nm>(raw, k, geom, tol, g.omff, s, &pf, res);
+    if constexpr (std::is_same<F, FF>::value && A <= 2) {
+      float4 pf[2];
+      if constexpr (A == 1)
+        fast = decode_a1_ff<nm>(raw, k, geom, tol, g.omff, s, pf, res);
+      else
+        fast = decode_a2_ff<nm>(raw, k, geom, tol, g.omff, s, pf, res);
       if (fast == 1) {
-        file_one_ff(s[0], pf, M0, g.slot_cnt + (int64_t)b * M0, g.slot_s + (int64_t)b * M0 * kSlots,
-                    reinterpret_cast<float4*>(g.slot_p) + (int64_t)b * M0 * kSlots, g.flags + b);
+#pragma unroll
+        for (int j = 0; j < A; ++j)
+          file_one_ff(s[j], pf[j], M0, g.slot_cnt + (int64_t)b * M0,
+                      g.slot_s + (int64_t)b * M0 * kSlots,
+                      reinterpret_cast<float4*>(g.slot_p) + (int64_t)b * M0 * kSlots, g.flags + b);
         ok = filed = true;
       }
     }
@@ -264,12 +270,18 @@ __global__ void __launch_bounds__(kDecThreads) k_fixed_round(FixedArgs g, const 
       cdbl p[4];
       bool ok = false, filed = false;
       int fast = -1;
-      if constexpr (std::is_same<F, FF>::value && A == 1) {
-        float4 pf, res[NM];
-        fast = decode_a1_ff<NM>(raw, k, geom, tol, g.omff, s, &pf, res);
+      if constexpr (std::is_same<F, FF>::value && A <= 2) {
+        float4 pf[2], res[NM];
+        if constexpr (A == 1)
+          fast = decode_a1_ff<NM>(raw, k, geom, tol, g.omff, s, pf, res);
+        else
+          fast = decode_a2_ff<NM>(raw, k, geom, tol, g.omff, s, pf, res);
         if (fast == 1) {
-          file_one_ff(s[0], pf, M, g.slot_cnt + (int64_t)b * M, g.slot_s + (int64_t)b * M * kSlots,
-                      reinterpret_cast<float4*>(g.slot_p) + (int64_t)b * M * kSlots, g.flags + b);
+#pragma unroll
+          for (int j = 0; j < A; ++j)
+            file_one_ff(s[j], pf[j], M, g.slot_cnt + (int64_t)b * M,
+                        g.slot_s + (int64_t)b * M * kSlots,
+                        reinterpret_cast<float4*>(g.slot_p) + (int64_t)b * M * kSlots, g.flags + b);
           ok = filed = true;
         }
       }
