@@ -435,6 +435,33 @@ __device__ __forceinline__ FF::V csqrt_ff(const FF::V& v) {
   return cmk(fr_div(fr_mul(ay, half), t), y.h < 0.0f ? FR{-t.h, -t.l} : t);
 }
 
+// One Newton step on P(z) = z^a + sum_j c_j z^j from the float-float root
+// z, and a bound on the remaining error of the root: |P| plus the
+// float-float errors of the coefficients (1e-13 times the locator solve's
+// condition estimate `cond`) and of the evaluation, all weighted by
+// sum |c_j| and divided by |P'|.  A root of a cluster (small |P'|) or of an
+// ill-conditioned locator gets a large bound, and the caller's decisions
+// then go to the FP64 decoder whenever the bound could move them.
+template <int a>
+__device__ __forceinline__ float root_polish(const FF::V* c, FF::V& z, float cond) {
+  FF::V P{1.0f, 0.0f, 0.0f, 0.0f}, dP{0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int j = a - 1; j >= 0; --j) {
+    dP = FF::add(FF::mulv(dP, z), P);
+    P = FF::add(FF::mulv(P, z), c[j]);
+  }
+  const float nd = ff_norm(dP);
+  if (!(nd > 1e-30f && nd < 1e30f)) return INFINITY;
+  z = FF::sub(z, cdiv(P, dP));
+  float cs = 1.0f;
+#pragma unroll
+  for (int j = 0; j < a; ++j) cs += sqrtf(ff_norm(c[j]));
+  // the step's size, squared, is ~|P|^2 / |P'|^2; after the step the error
+  // is quadratically smaller for a simple root, but a cluster keeps it
+  const float step = sqrtf(ff_norm(P) / nd);
+  return fminf(step, 1.0f) * 0.5f + 1e-13f * fmaxf(cond, 1.0f) * cs / sqrtf(nd);
+}
+
 // The two-alias decode of the mixed path in float-float (Sec. II-B steps
 // (i)-(iii) for a = 2): the 2 x 2 Hankel solve by Gaussian elimination with
 // partial pivoting, the quadratic's roots in the cancellation-free form, the
@@ -460,11 +487,11 @@ __device__ __forceinline__ int decode_a2_ff(const float4* raw, int64_t k, const 
   const FF::V o0 = swap ? m[0] : m[1], o1 = swap ? m[1] : m[2];  // other row
   const FF::V r0 = swap ? m[3] : m[2], r1 = swap ? m[2] : m[3];  // -rhs
   const float best = fmaxf(n0, n1);
-  if (best <= 1e-28f * amax2 * 1.1f) return -1;
+  if (best <= 1e-24f * amax2) return -1;
   const FF::V f = cdiv(o0, a0);
   const FF::V a22 = FF::sub(o1, FF::mulv(f, a1));
   const float n22 = ff_norm(a22);
-  if (n22 <= 1e-28f * amax2 * 1.1f) return -1;
+  if (n22 <= 1e-24f * amax2) return -1;
   const FF::V b2 = FF::sub(FF::mulv(f, r0), r1);  // -r1 - f (-r0)
   const FF::V c1 = cdiv(b2, a22);
   const FF::V c0 = cdiv(FF::sub(FF::V{-r0.rh, -r0.rl, -r0.ih, -r0.il}, FF::mulv(a1, c1)), a0);
@@ -478,15 +505,20 @@ __device__ __forceinline__ int decode_a2_ff(const float4* raw, int64_t k, const 
   if (!(nq > 1e-30f && nq < 1e30f)) return -1;
   FF::V z[2] = {q, cdiv(c0, q)};
   FF::V w[2];
+  const FF::V cc[2] = {c0, c1};
+  const float cond = sqrtf(amax2 / fminf(best, n22));
   const float r2 = (float)tol.root2;
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
+    const float err = root_polish<2>(cc, z[j], cond);
     const float zx = ff_re(z[j]), zy = ff_im(z[j]);
-    if (!(zx * zx + zy * zy > 1e-30f)) return -1;
+    if (!(zx * zx + zy * zy > 1e-30f && zx * zx + zy * zy < 1e30f)) return -1;
     const float df = (float)g.d;
     const float qa = fmaf(atan2f(zy, zx), df * 0.15915494309189533577f, -(float)k / (float)g.M);
     const float fr = qa - rintf(qa);
-    if (fabsf(fabsf(fr) - 0.5f) < fmaxf(1e-3f, 8e-7f * df)) return -1;
+    const float err_t = 10.0f * err * df * 0.15915494309189533577f;
+    if (!(err_t < 0.25f)) return -1;
+    if (fabsf(fabsf(fr) - 0.5f) < fmaxf(fmaxf(1e-3f, 8e-7f * df), err_t)) return -1;
     int64_t t = ((int64_t)rintf(qa)) % g.d;
     if (t < 0) t += g.d;
     s[j] = k + t * g.M;
@@ -494,6 +526,7 @@ __device__ __forceinline__ int decode_a2_ff(const float4* raw, int64_t k, const 
     const float dx = zx - ff_re(w[j]), dy = zy - ff_im(w[j]);
     const float dz = dx * dx + dy * dy;
     if (fabsf(dz - r2) <= 1e-4f * r2) return -1;
+    if (fabsf(sqrtf(dz) - sqrtf(r2)) < 10.0f * err) return -1;
     if (!(dz <= r2)) return 0;
   }
   if (s[0] == s[1]) return 0;
@@ -527,9 +560,10 @@ __device__ __forceinline__ int decode_a2_ff(const float4* raw, int64_t k, const 
   const FR fnm{(float)nm, 0.0f};
   const FR nS = cnorm2(S);
   // nm^2 - |S|^2 = nm a22 with a22 the second pivot of the FP64 solve,
-  // which fails when a22 <= 1e-14 nm^2 (this margin leaves it to FP64)
+  // which fails when |a22| <= 1e-14 nm; the float-float difference carries
+  // an absolute error near 1e-14 nm^2, so below 1e-12 nm^2 FP64 decides
   const FR det = fr_sub(fr_mul(fnm, fnm), nS);
-  if (!(det.h > 1.1e-14f * (float)(nm * nm * nm))) return -1;
+  if (!(det.h > 1e-12f * (float)(nm * nm))) return -1;
   // p1 = (nm g1 - conj(S) g0) / det,  p0 = (g0 - S p1) / nm
   const FF::V num1 = FF::sub(cscale(g1, fnm), FF::mulv(cconj(S), g0));
   const FF::V p1 = cmk(fr_div(re_of(num1), det), fr_div(im_of(num1), det));

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kDecThreads) k_iter_decode(LevelArgs g, const 
     // decision boundary (then the FP64 decoder below)
     int fast = -1;
     if constexpr (std::is_same<F, FF>::value && A <= 2) {
-      float4 pf[2];
+      float4 pf[A];
       if constexpr (A == 1)
         fast = decode_a1_ff<nm>(raw, k, geom, tol, g.omff, s, pf, res);
       else
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kDecThreads) k_fixed_round(FixedArgs g, const 
       bool ok = false, filed = false;
       int fast = -1;
       if constexpr (std::is_same<F, FF>::value && A <= 2) {
-        float4 pf[2], res[NM];
+        float4 pf[A], res[NM];
         if constexpr (A == 1)
           fast = decode_a1_ff<NM>(raw, k, geom, tol, g.omff, s, pf, res);
         else
