@@ -280,7 +280,7 @@ int orc_decode(int a, const double* min, int n_m, int64_t k, int64_t M, int64_t 
     cplx z[4];
     orc_poly_roots(a, (const double*)c, (double*)z);
 
-    /* Alg. 1 lines 29-30.  s_j = ln(z_j) N / (i 2 pi) taken as the member of
+    /* Algorithm 1, location check of SynDec.  s_j = ln(z_j) N / (i 2 pi) taken as the member of
      * S_k = {k + tM} nearest to it; the root belongs to U_k only if z_j lies
      * within root_tol of omega^{s_j}. */
     for (int j = 0; j < a; ++j) {
@@ -453,21 +453,21 @@ int64_t orc_exact(const double* xin, const orc_exact_params* prm, int64_t cap,
     /* Iterative sFFT-DT, Algorithm 1.  Level l works at d = 2^l d0 with
      * M = M0 / 2^l bins and decodes a = l + 1 aliases from 2l + 2 syndromes.
      * The syndromes of shifts < 2l held from earlier levels are folded,
-     * Y_{2d,j}[k] = Y_{d,j}[k] + Y_{d,j}[k + M/2] (reading of line 10). */
+     * Y_{2d,j}[k] = Y_{d,j}[k] + Y_{d,j}[k + M/2] (reading of Algorithm 1's level step). */
     int64_t M = M0, d = d0;
     for (int l = 0; l < iters; ++l) {
       if (l > 0) {
-        /* line 14: d = 2d; line 15: T taken modulo N/d (T holds bins) */
+        /* next level: d = 2d, and T is taken modulo N/d (T holds bins) */
         M >>= 1;
         d <<= 1;
         for (int j = 0; j < 2 * l; ++j)
           for (int64_t k = 0; k < M; ++k) HELD(j, k) += HELD(j, k + M);
         for (int64_t k = 0; k < M; ++k) T[k] = (unsigned char)(T[k] | T[k + M]);
       }
-      /* lines 03-06: the two new shifts 2l, 2l+1 at the current d */
+      /* Algorithm 1: the two new shifts 2l, 2l+1 at the current d */
       orc_syndrome(xin, N, d, 2 * l, (double*)&HELD(2 * l, 0));
       orc_syndrome(xin, N, d, 2 * l + 1, (double*)&HELD(2 * l + 1, 0));
-      /* line 07, SubFreq (lines 17-22): remove every frequency solved so far */
+      /* SubFreq: remove every frequency solved so far */
       for (int64_t e = 0; e < nS; ++e) {
         int64_t kd = S[e].s % M;
         HELD(2 * l, kd) -= S[e].v * omega_pow(N, S[e].s * (int64_t)(2 * l));
@@ -478,7 +478,7 @@ int64_t orc_exact(const double* xin, const orc_exact_params* prm, int64_t cap,
         for (int64_t k = 0; k < M; ++k) ymax = fmax(ymax, cabs(HELD(0, k)));
         theta = prm->zero_tol * ymax;
       }
-      /* lines 08-13 */
+      /* activity test and SynDec of every active bin */
       const int a = l + 1, nm = 2 * l + 2;
       for (int64_t k = 0; k < M; ++k) {
         if (!(T[k] || cabs(HELD(2 * l, k)) > theta || cabs(HELD(2 * l + 1, k)) > theta)) continue;
@@ -488,7 +488,7 @@ int64_t orc_exact(const double* xin, const orc_exact_params* prm, int64_t cap,
         cplx p[8];
         if (orc_decode(a, (const double*)m, nm, k, M, N, theta, prm->root_tol, prm->res_tol, s,
                        (double*)p)) {
-          /* lines 31-32: S = S u s, x^[s_j] = p_j; the solved terms leave
+          /* SynDec success: S = S u s, x^[s_j] = p_j; the solved terms leave
            * every syndrome held for this bin */
           for (int i = 0; i < a; ++i) {
             push(&S, &nS, &capS, s[i], p[i]);
@@ -496,7 +496,7 @@ int64_t orc_exact(const double* xin, const orc_exact_params* prm, int64_t cap,
           }
           T[k] = 0;
         } else {
-          T[k] = 1; /* line 34 */
+          T[k] = 1; /* SynDec failure: the bin joins T */
         }
       }
     }
@@ -752,7 +752,7 @@ int64_t orc_general(const double* xin, const orc_general_params* p, int64_t cap,
     free(ak);
     return -1;
   }
-  /* Part 1 (lines 02-10): consecutive shifts 0..2a_m-1 and the r random
+  /* Algorithm 2, Part 1: consecutive shifts 0..2a_m-1 and the r random
    * shifts, each d * FFT_M */
   if (p->prune)
     for (int j = 0; j < nc; ++j) orc_syndrome(xin, N, d, j, (double*)&Yc[(size_t)j * M]);
@@ -789,7 +789,7 @@ int64_t orc_general(const double* xin, const orc_general_params* p, int64_t cap,
     }
     goto output;
   }
-  /* Part 2 (lines 11-21): singular values of every bin's a_m x a_m Hankel
+  /* Algorithm 2, Part 2: singular values of every bin's a_m x a_m Hankel
    * matrix (m_0 .. m_{2a_m-2}, Eq. (26)); the K largest vote */
   for (int64_t k = 0; k < M; ++k) {
     cplx m[8];
@@ -804,7 +804,7 @@ int64_t orc_general(const double* xin, const orc_general_params* p, int64_t cap,
   qsort(sv, (size_t)(M * am), sizeof(keyed), cmp_desc);
   const int64_t nvote = K < M * am ? K : M * am;
   for (int64_t e = 0; e < nvote; ++e) ak[sv[e].i / am] += 1;
-  /* Parts 3-4 (lines 22-29): pruning Steps 2-3 and Subspace Pursuit */
+  /* Algorithm 2, Parts 3-4: pruning Steps 2-3 and Subspace Pursuit */
   for (int64_t k = 0; k < M; ++k) {
     const int a = ak[k];
     if (a == 0) continue;

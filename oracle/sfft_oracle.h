@@ -30,7 +30,7 @@ int orc_fft(int64_t n, double* a, int sign);
 /* O(n^2) DFT straight from the definition (for pinning orc_fft). */
 int orc_dft_brute(int64_t n, const double* in, double* out, int sign);
 
-/* Syndrome spectrum of one shift (Eq. (2), Alg. 1 lines 03-06):
+/* Syndrome spectrum of one shift (Eq. (2); the syndrome step of Algorithm 1):
  *   Y[k] = d * sum_{n<M} x[n d + shift] e^{-2 pi i k n / M},  M = N/d.
  * Returns 0, or -1 on bad sizes. */
 int orc_syndrome(const double* x, int64_t N, int64_t d, int64_t shift, double* Y);
@@ -44,7 +44,7 @@ int orc_poly_roots(int a, const double* c, double* z);
  * the shortest recurrence has length exactly a, else 0. */
 int orc_bm_locator(int a, const double* m, double* c);
 
-/* SynDec of one bin (Sec. II-B steps (i)-(iii), Alg. 1 lines 23-35).
+/* SynDec of one bin (Sec. II-B steps (i)-(iii); SynDec of Algorithm 1).
  *   a      number of aliases assumed (1..8): a <= 4 by the Hankel solve and
  *          the analytical roots snapped to S_k; a > 4 by the
  *          Berlekamp-Massey locator and the a smallest |P| over the d

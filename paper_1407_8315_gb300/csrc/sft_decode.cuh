@@ -7,7 +7,7 @@
 //  (ii)  take the roots of P(z) = z^a + c_{a-1} z^{a-1} + ... + c_0 by the
 //        analytical solutions for a <= 4 (quadratic, Cardano, Ferrari);
 //        each root gives the location s_j = ln(z_j) N / (i 2 pi), taken as
-//        the member k + tM of S_k nearest to it (Alg. 1 lines 29-30);
+//        the member k + tM of S_k nearest to it (location check of SynDec, Algorithm 1);
 //  (iii) solve all n_m equations of Eq. (3) for the values p_j in the least
 //        squares sense (normal equations).
 // Accept iff every root lies within root_tol of omega^{s_j}, the s_j are

@@ -3,23 +3,23 @@
 //
 // Per call, batched over B signals of one plan (M bins, d = N / M):
 //   gather + FFT   the 2 a_m consecutive shifts 0 .. 2a_m-1 and the r random
-//                  shifts n_l (Part 1, lines 02-10)
+//                  shifts n_l (Algorithm 2, Part 1)
 //   k_gen_bound,   per bin a lower bound ||H||_F / sqrt(a_m) of the largest
 //   k_gen_tau,     singular value, its K-th largest tau_L per signal, and
 //   k_gen_prune    the bins whose upper bound ||H||_F reaches tau_L (the
 //                  others cannot hold a vote) queued for
 //   k_gen_svals    the a_m singular values of the a_m x a_m Hankel matrix of
 //                  m_0 .. m_{2a_m-2} (Eq. (26)) by one-sided Jacobi in FP64
-//                  (Part 2, lines 11-15), grid-stride over the queue
+//                  (Algorithm 2, Part 2), grid-stride over the queue
 //   k_gen_vote     one CTA per signal: the K largest singular values (radix
 //                  select on their FP64 bit patterns, ties to the lower
-//                  index) vote a_k per bin (lines 16-21); bins with a_k > 0
+//                  index) vote a_k per bin (Algorithm 2, Part 2); bins with a_k > 0
 //                  are queued
 //   k_gen_solve1,  per voted bin (one-alias bins, then the others): the a_k x a_k
 //   _multi         Hankel locator, |P~| at all
 //                  d candidates of U_k with the 2 a_k smallest kept (pruning
 //                  Steps 2-3), Subspace Pursuit on the pruned sensing matrix
-//                  Phi_p (Parts 3-4, lines 22-29)
+//                  Phi_p (Algorithm 2, Parts 3-4)
 //   k_finalize     as for the exact transform
 #include <algorithm>
 #include <cstdio>
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(1024) k_gen_tau(GenArgs g) {
   if (threadIdx.x == 0) g.tau_lo[b] = tau;
 }
 
-// Lines 16-21: the K largest of the M a_m singular values of one signal
+// Algorithm 2, the vote: the K largest of the M a_m singular values of one signal
 // (radix select on their bit patterns); of the values equal to the K-th
 // largest tau, those of lowest index are selected.
 __global__ void __launch_bounds__(1024) k_gen_vote(GenArgs g) {

@@ -48,7 +48,7 @@ constexpr int kFoldThreads = 256;
 constexpr int kDecThreads = 128;
 
 // Level l, phase 1, one thread per bin: fold the held syndromes, SubFreq on
-// the two new shifts, activity test (line 09), write the syndromes back and
+// the two new shifts, activity test of Algorithm 1, write the syndromes back and
 // queue the active bins for decoding.
 template <class F, int A>
 __global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* queue, int* qcount) {
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* q
   queue_push(active, b, (int)k, queue, qcount);
 }
 
-// Level l, phase 2: decode the queued bins with a = l + 1 (lines 23-35),
+// Level l, phase 2: decode the queued bins with a = l + 1 (SynDec, Algorithm 1),
 // grid-stride over the queue so that every warp is full.
 template <class F, int A>
 __global__ void __launch_bounds__(kDecThreads) k_iter_decode(LevelArgs g, const int2* queue,

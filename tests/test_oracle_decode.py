@@ -50,7 +50,7 @@ def test_decode_zero_bin_fails(orc):
 
 
 def test_decode_wrong_bin_index_fails(orc):
-    """The decoded locations must lie in S_k (Alg. 1 line 30)."""
+    """The decoded locations must lie in S_k (location check of SynDec, Algorithm 1)."""
     N, M = 1 << 16, 256
     s, p, m = _planted_bin(N, M, 17, 2, 5, 4)
     ok, _, _ = orc.decode(2, m, 18, M, N, 1e-9, 0.1, 1e-9)
