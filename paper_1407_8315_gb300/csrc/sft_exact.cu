@@ -4,12 +4,12 @@
 // Per call, batched over B signals of one plan:
 //   ITER, level l = 0 .. L-1 (M = M0 / 2^l, d = 2^l d0):
 //     k_gather_fft   shifts 2l, 2l+1:  Y_{d,j} = d FFT_M(x[n d + j])
-//                    (Alg. 1 lines 03-06), written into the level's buffer
+//                    (syndrome step of Algorithm 1), written into the level's buffer
 //     k_iter_fold    one thread per bin: fold the held syndromes
 //                    (Y_{2d,j}[k] = Y_{d,j}[k] + Y_{d,j}[k + M]), SubFreq on
-//                    the two new shifts (lines 17-22), the activity test
-//                    (line 09); active bins are queued
-//     k_iter_decode  SynDec with a = l + 1 (lines 23-35) over the queue, so
+//                    the two new shifts (SubFreq), the activity test
+//                    of Algorithm 1; active bins are queued
+//     k_iter_decode  SynDec with a = l + 1 (Algorithm 1) over the queue, so
 //                    the FP64-heavy decode runs with full warps
 //   FIXED: k_gather_fft for the 2 a_max shifts at d0, k_fixed_scan (queue
 //          the active bins), k_fixed_round for a = 1 .. a_max (the bins no
@@ -61,13 +61,20 @@ __global__ void __launch_bounds__(8192 / PTS) k_gather_fft(
     const int n = tid + i * nthr;
     if (n < M) v[i] = __ldg(xs + (((int64_t)n * d + shift) & (N - 1)));
   }
+  if (M == PTS * nthr) {
+    // the first pass from registers (the gathered samples are its inputs)
+    first_pass_regs<F, PTS>(smem, M, v, tid);
+    __syncthreads();
+    cta_fft<F, PTS>(smem, log2M, log2Mt, tw, tid, nthr, 1);
+  } else {
 #pragma unroll
-  for (int i = 0; i < PTS; ++i) {
-    const int n = tid + i * nthr;
-    if (n < M) F::st(smem, M, n, F::from_in(v[i]));
+    for (int i = 0; i < PTS; ++i) {
+      const int n = tid + i * nthr;
+      if (n < M) F::st(smem, M, n, F::from_in(v[i]));
+    }
+    __syncthreads();
+    cta_fft<F, PTS>(smem, log2M, log2Mt, tw, tid, nthr);
   }
-  __syncthreads();
-  cta_fft<F, PTS>(smem, log2M, log2Mt, tw, tid, nthr);
   Out* o = reinterpret_cast<Out*>(out_v) + (int64_t)b * out_sig + (int64_t)(row0 + js) * out_row;
   double lmax = 0.0;
   if constexpr (std::is_same<F, F64>::value) {
@@ -234,10 +241,10 @@ __global__ void __launch_bounds__(8192 / PTS) k_fft4_cols(
     const int64_t n = (int64_t)(t + i * tpg) * M2 + c0 + g;
     v[i] = __ldg(xs + ((n * d + shift) & (N - 1)));
   }
-#pragma unroll
-  for (int i = 0; i < PTS; ++i) F::st(buf, M1, t + i * tpg, F::from_in(v[i]));
+  // the column's first pass from registers (tpg = M1 / PTS)
+  first_pass_regs<F, PTS>(buf, M1, v, t);
   __syncthreads();
-  cta_fft<F, PTS>(buf, log2M1, log2Mt, tw, t, tpg);
+  cta_fft<F, PTS>(buf, log2M1, log2Mt, tw, t, tpg, 1);
   // twiddle e^{-2 pi i n2 k1 / M} (table of e^{-2 pi i q / Mt}, Mt >= M)
   for (int i = 0; i < PTS; ++i) {
     const int k1 = t + i * tpg;

@@ -97,18 +97,35 @@ __device__ __forceinline__ void stockham_pass(char* buf, int M, int Ns, int log2
   __syncthreads();
 }
 
+// The first radix-PTS pass (Ns = 1: no inter-pass twiddles) straight from
+// registers: with nthr = M / PTS, the inputs of thread tid's group are the
+// samples tid + r nthr, r < PTS, which are exactly the ones it gathered, so
+// they need not round-trip through shared memory.  Stores the pass's
+// outputs; the caller synchronises and continues with cta_fft from Ns = PTS.
+template <class F, int PTS>
+__device__ __forceinline__ void first_pass_regs(char* buf, int M, const typename F::In* in,
+                                                int tid) {
+  typename F::V v[PTS];
+#pragma unroll
+  for (int r = 0; r < PTS; ++r) v[r] = F::from_in(in[r]);
+  dft_reg<F, PTS>(v);
+#pragma unroll
+  for (int r = 0; r < PTS; ++r) F::st(buf, M, tid * PTS + r, v[r]);
+}
+
 // Forward FFT of buf[0..M), M = 2^log2M (1 <= log2M <= 13 here), executed by
 // nthr threads holding PTS = 16 or 8 points each (nthr * PTS >= M): radix-PTS
-// passes and one radix-2/4/8 pass for the remaining factor.  Caller
+// passes and one radix-2/4/8 pass for the remaining factor, starting after
+// the first `done` radix-PTS passes (0, or 1 after first_pass_regs).  Caller
 // synchronises before the call.
 template <class F, int PTS = 16>
 __device__ void cta_fft(char* buf, int log2M, int log2Mt, const typename F::Tw* __restrict__ tw,
-                        int tid, int nthr) {
+                        int tid, int nthr, int done = 0) {
   static_assert(PTS == 16 || PTS == 8, "16 or 8 points per thread");
   constexpr int LP = PTS == 16 ? 4 : 3;
   const int M = 1 << log2M;
-  int Ns = 1;
-  int rem = log2M;
+  int Ns = 1 << (LP * done);
+  int rem = log2M - LP * done;
   while (rem >= LP) {
     stockham_pass<F, PTS, PTS>(buf, M, Ns, log2Mt, tw, tid, nthr);
     Ns <<= LP;
