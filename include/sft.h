@@ -390,6 +390,21 @@ int32_t sft_plan_launches_per_call(sft_plan_t plan);
 sft_status sft_plan_set_sub_batches(sft_plan_t plan, int32_t n);
 int32_t sft_plan_sub_batches(sft_plan_t plan, int64_t n_signals);
 
+/* Four-lane decoders (exact paths, mixed precision; off by default).  SynDec
+ * of a bin with a = 3 or 4 aliases (Sec. II-B steps (i)-(iii)) is a serial
+ * chain of FP64 operations, so on few signals the last levels of ITER and
+ * the last rounds of FIXED take the time of one bin's chain.  With
+ * enable != 0, a call that runs as one sub-batch decodes a queue of at most
+ * 64 bins per SM with four lanes per bin: both small solves by row-per-lane
+ * elimination, one root, one or two Gram sums and one right-hand side per
+ * lane, the validation residual split by equation.  That shortens the chain
+ * but spends about twice the FP64 issue slots per bin, so longer queues and
+ * calls split into sub-batches keep the one-lane decoder.  The supports are
+ * those of the one-lane decoder; the values agree to float-float rounding
+ * (~1e-13), not bit for bit, with calls that use the one-lane decoder (other
+ * sub-batch counts, batches).  SFT_EINVAL on a NULL plan. */
+sft_status sft_plan_set_quad_decoders(sft_plan_t plan, int32_t enable);
+
 /* Per-stage timing.  With profiling enabled, every launch of an sft_exact
  * call on this plan is bracketed by CUDA events recorded on the call's
  * stream.  sft_plan_stage_times synchronises the device, sums the elapsed

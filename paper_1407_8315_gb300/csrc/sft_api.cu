@@ -497,6 +497,12 @@ int32_t sft_plan_sub_batches(sft_plan_t P, int64_t n_signals) {
   return P ? sft::sub_batches_for(P, n_signals) : 0;
 }
 
+sft_status sft_plan_set_quad_decoders(sft_plan_t P, int32_t enable) {
+  if (!P) return SFT_EINVAL;
+  P->quad_ok = enable != 0;
+  return SFT_OK;
+}
+
 sft_status sft_plan_set_profiling(sft_plan_t P, int32_t enable) {
   if (!P) return SFT_EINVAL;
   if (!enable) {

@@ -42,6 +42,33 @@ __device__ __forceinline__ void file_one_ff(int64_t s, float4 p, int64_t M0, uin
   }
 }
 
+// Append (b, k) to a device queue when `pred`; one atomic per block of NT
+// threads (a per-warp atomic on one counter serialises in L2 when the
+// queues are long).  Every thread of the block must call this.
+template <int NT>
+__device__ __forceinline__ void block_queue_push(bool pred, int b, int k, int2* q, int* count) {
+  static_assert(NT % 32 == 0 && NT <= 1024, "whole warps");
+  __shared__ int wofs[NT / 32];
+  const int lane = (int)(threadIdx.x & 31u), w = (int)(threadIdx.x >> 5);
+  const unsigned mask = __ballot_sync(0xffffffffu, pred);
+  if (lane == 0) wofs[w] = __popc(mask);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) {
+      const int c = wofs[i];
+      wofs[i] = tot;
+      tot += c;
+    }
+    const int base = tot > 0 ? atomicAdd(count, tot) : 0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) wofs[i] += base;
+  }
+  __syncthreads();
+  if (pred) q[wofs[w] + __popc(mask & ((1u << lane) - 1u))] = make_int2(b, k);
+}
+
 // Append (b, k) to a device queue when `pred`; one atomic per warp.  Every
 // lane of the warp must call this (inactive lanes with pred = false).
 __device__ __forceinline__ void queue_push(bool pred, int b, int k, int2* q, int* count) {

@@ -551,18 +551,24 @@ static bool fin_single(const sft_plan_s* P, int64_t B, int nsm) {
 int sub_batches_for(const sft_plan_s* P, int64_t B);
 
 // launches of one sub-batch of B signals
-static int launches_one(const sft_plan_s* P, int64_t B, int nsm) {
+static int launches_one(const sft_plan_s* P, int64_t B, int nsm, bool quad) {
   const int fin = fin_single(P, B, nsm) ? 1 : 2;
   if (P->p.mode == SFT_GENERAL_UNPRUNED) return (P->M0 > kFft4Points ? 2 : 1) + 1 + fin;
   if (P->p.mode == SFT_GENERAL)
     return 2 * (P->M0 > kFft4Points ? 2 : 1) + 5 + (P->p.a_max >= 2 ? 2 : 1) +
            (P->mlp != nullptr ? 1 : 0) + fin;
   const int ext = P->ws.xc != nullptr ? 1 : 0;
-  if (P->p.mode == SFT_EXACT_FIXED)
-    return ext + (P->M0 > kFft4Points ? 2 : 1) + 1 + P->p.a_max + fin;
+  // with `quad`, the mixed path launches a four-lane decoder beside the
+  // one-lane decoder of three and four aliases
+  const bool q4 = quad && P->p.precision != SFT_FP64;
+  if (P->p.mode == SFT_EXACT_FIXED) {
+    const int nq = q4 && P->p.a_max <= 4 ? std::max(0, P->p.a_max - 2) : 0;
+    return ext + (P->M0 > kFft4Points ? 2 : 1) + 1 + P->p.a_max + nq + fin;
+  }
   int fft = 0;
   for (int l = 0; l < P->levels; ++l) fft += (P->M0 >> l) > kFft4Points ? 2 : 1;
-  return ext + fft + 2 * P->levels + fin;
+  const int nq = q4 ? std::max(0, std::min(P->levels, 4) - 2) : 0;
+  return ext + fft + 2 * P->levels + nq + fin;
 }
 
 int launches_per_call(const sft_plan_s* P) {
@@ -572,7 +578,8 @@ int launches_per_call(const sft_plan_s* P) {
   const int64_t B = P->max_signals;
   const int S = sub_batches_for(P, B);
   int n = 0;
-  for (int s = 0; s < S; ++s) n += launches_one(P, B / S + (s < B % S ? 1 : 0), nsm);
+  const bool quad = P->quad_ok && S <= 1;
+  for (int s = 0; s < S; ++s) n += launches_one(P, B / S + (s < B % S ? 1 : 0), nsm, quad);
   return n;
 }
 
@@ -706,6 +713,18 @@ static void launch_extract(sft_plan_s* P, int64_t B, const void* x, int64_t x_st
   if (P->sub_extract_now != nullptr) cudaEventRecord(P->sub_extract_now, st);
 }
 
+// Queues of at most quad_max_bins bins (64 per SM) go to the four-lane
+// decoders of three and four aliases: below that the one-lane decoder's
+// warps leave most SM sub-partitions idle and its per-bin FP64 chain sets the
+// time; above it the four-lane decoder's extra FP64 issue slots do.
+static int quad_max_bins(int nsm) { return 64 * nsm; }
+static unsigned quad_grid(const sft_plan_s* P, int64_t maxq, int nsm) {
+  constexpr int kGroups = kDecThreads / 4;
+  return (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>(std::min<int64_t>(maxq, quad_max_bins(nsm)) / kGroups + 1,
+                           (int64_t)P->dec_ctas_per_sm * nsm));
+}
+
 template <class F>
 static void launch_fixed(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride,
                          const OmegaTab& om, int nsm, cudaStream_t st) {
@@ -756,9 +775,19 @@ static void launch_fixed(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
     constexpr int A = decltype(a_tag)::value, NM = decltype(nm_tag)::value;
     const bool last = A == P->p.a_max;
     stage_begin(P, rnames[A - 1], st);
-    k_fixed_round<F, A, NM><<<dgrid, kDecThreads, 0, st>>>(
-        g, (A & 1) ? q0 : q1, c + (A - 1), last ? nullptr : ((A & 1) ? q1 : q0),
-        last ? nullptr : c + A);
+    const int2* qi = (A & 1) ? q0 : q1;
+    int2* qo = last ? nullptr : ((A & 1) ? q1 : q0);
+    int* co = last ? nullptr : c + A;
+    // three and four aliases on the mixed path: the queue length picks the
+    // one-lane or the four-lane round on the device
+    constexpr bool kQuad = std::is_same<F, FF>::value && A >= 3;
+    const int nq = kQuad && P->quad_now ? quad_max_bins(nsm) : -1;
+    k_fixed_round<F, A, NM><<<dgrid, kDecThreads, 0, st>>>(g, qi, c + (A - 1), qo, co, nq);
+    if constexpr (kQuad) {
+      if (nq >= 0)
+        k_fixed_round_quad<A, NM><<<quad_grid(P, maxq, nsm), kDecThreads, 0, st>>>(g, qi, c + (A - 1),
+                                                                                qo, co, nq);
+    }
     stage_end(P, st);
   };
   using I1 = std::integral_constant<int, 1>;
@@ -842,11 +871,21 @@ static void launch_iter(sft_plan_s* P, int64_t B, const void* x, int64_t x_strid
     }
     stage_end(P, st);
     stage_begin(P, dnames[l], st);
+    // three and four aliases on the mixed path: both decoders are launched
+    // and the queue length, read on the device, picks one (quad_grid)
+    constexpr bool kQuad = std::is_same<F, FF>::value;
+    const int nq = kQuad && P->quad_now ? quad_max_bins(nsm) : -1;
     switch (l) {
       case 0: k_iter_decode<F, 1><<<dgrid, kDecThreads, 0, st>>>(g, q, c); break;
       case 1: k_iter_decode<F, 2><<<dgrid, kDecThreads, 0, st>>>(g, q, c); break;
-      case 2: k_iter_decode<F, 3><<<dgrid, kDecThreads, 0, st>>>(g, q, c); break;
-      default: k_iter_decode<F, 4><<<dgrid, kDecThreads, 0, st>>>(g, q, c); break;
+      case 2:
+        k_iter_decode<F, 3><<<dgrid, kDecThreads, 0, st>>>(g, q, c, nq);
+        if (nq >= 0) k_iter_decode_quad<3><<<quad_grid(P, maxq, nsm), kDecThreads, 0, st>>>(g, q, c, nq);
+        break;
+      default:
+        k_iter_decode<F, 4><<<dgrid, kDecThreads, 0, st>>>(g, q, c, nq);
+        if (nq >= 0) k_iter_decode_quad<4><<<quad_grid(P, maxq, nsm), kDecThreads, 0, st>>>(g, q, c, nq);
+        break;
     }
     stage_end(P, st);
     *M_last = M;
@@ -917,6 +956,7 @@ int sub_batches_for(const sft_plan_s* P, int64_t B) {
 cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride,
                          const sft_result* r, cudaStream_t st) {
   const int S = sub_batches_for(P, B);
+  P->quad_now = P->quad_ok && S <= 1;
   if (S <= 1) return launch_one(P, B, x, x_stride, r, st);
   cudaError_t e = cudaSuccess;
   const size_t esize = P->p.precision == SFT_FP64 ? 16 : 8;

@@ -200,6 +200,11 @@ struct sft_plan_s {
   const int64_t* K_table = nullptr;  // per-signal K for the general vote
   // launch shape chosen by the batch autotuner
   int dec_ctas_per_sm = 8;
+  // the four-lane decoders of three and four aliases: enabled on this plan
+  // (sft_plan_set_quad_decoders), and in use for the current call (one
+  // sub-batch: nothing else runs beside the decoders)
+  bool quad_ok = false;
+  bool quad_now = false;
   // points per thread of the one-CTA FFT (8: M/8 threads, radix-8 passes,
   // at most 64 registers, twice the resident warps of 16 points per thread;
   // measured faster on every level of the exact transforms)

@@ -9,6 +9,7 @@
 
 #include "sft_decode.cuh"
 #include "sft_device_util.cuh"
+#include "sft_quad.cuh"
 
 struct sft_plan_s;
 
@@ -78,10 +79,12 @@ __global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* q
       m[2 * l + 1] = Store<F>::to_d(cur[(2 * l + 1) * M + k]);
       // SubFreq: remove every frequency recovered at earlier levels from the
       // two new shifts; they are filed under the level-0 bins k + u M
+      bool peeled = false;
       if (l > 0) {
         for (int64_t u = 0; u < nsub; ++u) {
           const int64_t k0 = k + u * M;
           const int c = cnt[k0];
+          peeled = peeled || c > 0;
           for (int e = 0; e < c; ++e) {
             const int64_t sl = ss[k0 * kSlots + e];
             const cdbl p = Store<F>::to_d(sp[k0 * kSlots + e]);
@@ -91,8 +94,13 @@ __global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* q
         }
       }
       active = t || norm2(m[2 * l]) > theta2 || norm2(m[2 * l + 1]) > theta2;
+      // the folded rows are new; the two new shifts change only when peeled
 #pragma unroll
-      for (int j = 0; j < nm; ++j) cur[j * M + k] = Store<F>::from_d(m[j]);
+      for (int j = 0; j < 2 * l; ++j) cur[j * M + k] = Store<F>::from_d(m[j]);
+      if (peeled) {
+        cur[(2 * l) * M + k] = Store<F>::from_d(m[2 * l]);
+        cur[(2 * l + 1) * M + k] = Store<F>::from_d(m[2 * l + 1]);
+      }
     } else {
       FF::V m[nm];
 #pragma unroll
@@ -100,46 +108,60 @@ __global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* q
         m[j] = FF::add(FF::from4(prev[j * 2 * M + k]), FF::from4(prev[j * 2 * M + k + M]));
       m[2 * l] = FF::from4(cur[(2 * l) * M + k]);
       m[2 * l + 1] = FF::from4(cur[(2 * l + 1) * M + k]);
+      bool peeled = false;
       if constexpr (l > 0) {
-        // the 2^l level-0 bins folded into k, in chunks of up to 8: all
-        // counts of a chunk are loaded before its first entry, so that the
-        // loads of different sub-bins overlap
+        // the 2^l level-0 bins folded into k, in chunks of up to 8.  A
+        // chunk's counts (each <= kSlots = 8) are packed into the nibbles of
+        // one word and its entries walked in one loop, sub-bin by sub-bin:
+        // a warp then runs as many iterations as its busiest lane has
+        // entries, not the sum over sub-bins of the busiest lane's count.
         constexpr int NS = 1 << l;
         constexpr int CH = NS < 8 ? NS : 8;
+        static_assert(kSlots <= 15, "counts are packed in 4 bits");
         for (int u0 = 0; u0 < NS; u0 += CH) {
-          int c[CH];
+          uint32_t cp = 0u;
 #pragma unroll
-          for (int u = 0; u < CH; ++u) c[u] = cnt[k + (int64_t)(u0 + u) * M];
-#pragma unroll
-          for (int u = 0; u < CH; ++u) {
+          for (int u = 0; u < CH; ++u) cp |= (uint32_t)cnt[k + (int64_t)(u0 + u) * M] << (4 * u);
+          peeled = peeled || cp != 0u;
+          int e = 0;
+          while (cp != 0u) {
+            const int u = (__ffs((int)cp) - 1) >> 2;
+            const int cu = (int)((cp >> (4 * u)) & 15u);
             const int64_t k0 = k + (int64_t)(u0 + u) * M;
-            for (int e = 0; e < c[u]; ++e) {
-              const int64_t sl = ss[k0 * kSlots + e];
-              const FF::V p = FF::from4(sp[k0 * kSlots + e]);
-              m[2 * l] = FF::sub(m[2 * l], FF::mulv(p, omega_ff(g.omff, sl * (2 * l))));
-              m[2 * l + 1] =
-                  FF::sub(m[2 * l + 1], FF::mulv(p, omega_ff(g.omff, sl * (2 * l + 1))));
+            const int64_t sl = ss[k0 * kSlots + e];
+            const FF::V p = FF::from4(sp[k0 * kSlots + e]);
+            m[2 * l] = FF::sub(m[2 * l], FF::mulv(p, omega_ff(g.omff, sl * (2 * l))));
+            m[2 * l + 1] = FF::sub(m[2 * l + 1], FF::mulv(p, omega_ff(g.omff, sl * (2 * l + 1))));
+            if (++e == cu) {
+              cp &= ~(15u << (4 * u));
+              e = 0;
             }
           }
         }
       }
       active = t || above_ff(m[2 * l], theta2) || above_ff(m[2 * l + 1], theta2);
 #pragma unroll
-      for (int j = 0; j < nm; ++j) cur[j * M + k] = FF::to4(m[j]);
+      for (int j = 0; j < 2 * l; ++j) cur[j * M + k] = FF::to4(m[j]);
+      if (peeled) {
+        cur[(2 * l) * M + k] = FF::to4(m[2 * l]);
+        cur[(2 * l + 1) * M + k] = FF::to4(m[2 * l + 1]);
+      }
     }
     if (!active) g.Tcur[(int64_t)b * M0 + k] = 0;
   }
-  queue_push(active, b, (int)k, queue, qcount);
+  block_queue_push<kFoldThreads>(active, b, (int)k, queue, qcount);
 }
 
 // Level l, phase 2: decode the queued bins with a = l + 1 (SynDec, Algorithm 1),
 // grid-stride over the queue so that every warp is full.
 template <class F, int A>
 __global__ void __launch_bounds__(kDecThreads) k_iter_decode(LevelArgs g, const int2* queue,
-                                                             const int* qcount) {
+                                                             const int* qcount,
+                                                             int n_quad_max = -1) {
   constexpr int nm = 2 * A;
   typedef typename Store<F>::T T;
   const int n = *qcount;
+  if (n <= n_quad_max) return;  // the four-lane decoder takes short queues
   const BinGeom geom{g.N, g.M, g.d, g.om};
   for (int e = blockIdx.x * kDecThreads + threadIdx.x; e < n; e += gridDim.x * kDecThreads) {
     const int2 q = queue[e];
@@ -202,6 +224,42 @@ __global__ void __launch_bounds__(kDecThreads) k_iter_decode(LevelArgs g, const 
   }
 }
 
+// Level l >= 2 of the mixed path: the queued bins decoded with a = l + 1 in
+// {3, 4} by four lanes each (decode_quad), eight bins per warp.  Four lanes
+// per bin shorten a bin's FP64 chain but spend about twice the FP64 issue
+// slots per bin, so this decoder takes a queue of at most n_quad_max bins
+// and the one-lane decoder (launched beside it) a longer one.
+template <int A>
+__global__ void __launch_bounds__(kDecThreads) k_iter_decode_quad(LevelArgs g, const int2* queue,
+                                                                  const int* qcount,
+                                                                  int n_quad_max) {
+  constexpr int nm = 2 * A, kGroups = kDecThreads / 4;
+  const int n = *qcount;
+  if (n > n_quad_max) return;
+  const BinGeom geom{g.N, g.M, g.d, g.om};
+  const int lane = (int)(threadIdx.x & 31u);
+  const Quad G{0xFu << (lane & ~3), lane & 3};
+  for (int e = blockIdx.x * kGroups + (int)(threadIdx.x >> 2); e < n; e += gridDim.x * kGroups) {
+    const int2 qe = queue[e];
+    const int b = qe.x;
+    const int64_t k = qe.y, M = g.M, M0 = g.M0;
+    float4* cur = reinterpret_cast<float4*>(g.cur) + (int64_t)b * g.held_elems;
+    const Tol2 tol{g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]),
+                   g.root_tol * g.root_tol, g.res_tol * g.res_tol};
+    int64_t s[A];
+    cdbl p[A];
+    const bool ok = decode_quad<A, nm>(G, cur, cur, M, k, geom, tol, g.omff, s, p);
+    if (G.q == 0) {
+      if (ok)
+        file_solution<FF, A>(s, p, M0, g.slot_cnt + (int64_t)b * M0,
+                             g.slot_s + (int64_t)b * M0 * kSlots,
+                             reinterpret_cast<float4*>(g.slot_p) + (int64_t)b * M0 * kSlots,
+                             g.flags + b);
+      g.Tcur[(int64_t)b * M0 + k] = ok ? 0 : 1;
+    }
+  }
+}
+
 // ---------------------------------------------- non-iterative decode (FIXED)
 struct FixedArgs {
   int64_t N, M, d;
@@ -239,7 +297,7 @@ __global__ void __launch_bounds__(kFoldThreads) k_fixed_scan(FixedArgs g, int2* 
     }
     g.T[(int64_t)b * M + k] = 0;
   }
-  queue_push(active, b, (int)k, queue, qcount);
+  block_queue_push<kFoldThreads>(active, b, (int)k, queue, qcount);
 }
 
 // round a: decode the queued bins with a aliases; failures go to the next
@@ -247,9 +305,10 @@ __global__ void __launch_bounds__(kFoldThreads) k_fixed_scan(FixedArgs g, int2* 
 template <class F, int A, int NM>
 __global__ void __launch_bounds__(kDecThreads) k_fixed_round(FixedArgs g, const int2* qin,
                                                              const int* nin, int2* qout,
-                                                             int* nout) {
+                                                             int* nout, int n_quad_max = -1) {
   typedef typename Store<F>::T T;
   const int n = *nin;
+  if (n <= n_quad_max) return;  // the four-lane decoder takes short queues
   const BinGeom geom{g.N, g.M, g.d, g.om};
   const int64_t M = g.M;
   for (int e0 = blockIdx.x * kDecThreads; e0 < n; e0 += gridDim.x * kDecThreads) {
@@ -302,6 +361,49 @@ __global__ void __launch_bounds__(kDecThreads) k_fixed_round(FixedArgs g, const 
         g.T[(int64_t)b * M + k] = 1;
       } else {
         fail = true;
+      }
+    }
+    if (qout != nullptr) queue_push(fail, b, k, qout, nout);
+  }
+}
+
+// Round a in {3, 4} of the mixed path by four lanes per bin (decode_quad),
+// for a queue of at most n_quad_max bins (the one-lane round, launched
+// beside it, takes a longer one).  The syndromes stay as they are.
+template <int A, int NM>
+__global__ void __launch_bounds__(kDecThreads) k_fixed_round_quad(FixedArgs g, const int2* qin,
+                                                                  const int* nin, int2* qout,
+                                                                  int* nout, int n_quad_max) {
+  constexpr int kGroups = kDecThreads / 4;
+  const int n = *nin;
+  if (n > n_quad_max) return;
+  const BinGeom geom{g.N, g.M, g.d, g.om};
+  const int64_t M = g.M;
+  const int lane = (int)(threadIdx.x & 31u);
+  const Quad G{0xFu << (lane & ~3), lane & 3};
+  for (int e0 = blockIdx.x * kGroups; e0 < n; e0 += gridDim.x * kGroups) {
+    const int e = e0 + (int)(threadIdx.x >> 2);
+    bool fail = false;
+    int b = 0, k = 0;
+    if (e < n) {
+      const int2 qe = qin[e];
+      b = qe.x;
+      k = qe.y;
+      const float4* Y = reinterpret_cast<const float4*>(g.Y) + (int64_t)b * g.held_elems;
+      const Tol2 tol{g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]),
+                     g.root_tol * g.root_tol, g.res_tol * g.res_tol};
+      int64_t s[A];
+      cdbl p[A];
+      const bool ok = decode_quad<A, NM>(G, Y, nullptr, M, k, geom, tol, g.omff, s, p);
+      if (G.q == 0) {
+        if (ok)
+          file_solution<FF, A>(s, p, M, g.slot_cnt + (int64_t)b * M, g.slot_s + (int64_t)b * M * kSlots,
+                               reinterpret_cast<float4*>(g.slot_p) + (int64_t)b * M * kSlots,
+                               g.flags + b);
+        else if (qout == nullptr)
+          g.T[(int64_t)b * M + k] = 1;
+        else
+          fail = true;
       }
     }
     if (qout != nullptr) queue_push(fail, b, k, qout, nout);

@@ -136,6 +136,7 @@ def load(build_if_missing: bool = False):
     lib.sft_plan_set_sub_batches.argtypes = [C.c_void_p, C.c_int32]
     lib.sft_plan_sub_batches.argtypes = [C.c_void_p, C.c_int64]
     lib.sft_plan_sub_batches.restype = C.c_int32
+    lib.sft_plan_set_quad_decoders.argtypes = [C.c_void_p, C.c_int32]
     lib.sft_alias_histogram.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                         C.c_void_p, C.c_void_p]
     lib.sft_strerror.argtypes = [C.c_int]
@@ -359,6 +360,12 @@ class Plan:
 
     def sub_batches(self, n_signals: int) -> int:
         return int(load().sft_plan_sub_batches(C.c_void_p(self.handle), int(n_signals)))
+
+    def set_quad_decoders(self, enable: bool = True):
+        """Four lanes per bin for three and four aliases on calls that run as
+        one sub-batch (short queues only; values to ~1e-13, not bitwise)."""
+        _check(load().sft_plan_set_quad_decoders(C.c_void_p(self.handle), int(bool(enable))),
+               "sft_plan_set_quad_decoders")
 
     def set_profiling(self, enable: bool = True):
         sft_plan_set_profiling(self.handle, enable)

@@ -120,6 +120,7 @@ def test_null_arguments(lib):
     assert lib.sft_params_default(None, 8, 1, 1, 0, 0) == 1
     assert lib.sft_exact(None, 1, None, 0, None, None) == 1
     assert lib.sft_plan_workspace_bytes(None) == 0
+    assert lib.sft_plan_set_quad_decoders(None, 1) == 1
 
 
 def test_mlp_config_and_create_validation(lib):

@@ -283,6 +283,57 @@ def test_sub_batches_give_identical_results(gpu, mode, prec):
     assert plan.sub_batches(96) == 3 and plan.sub_batches(1000) == 4
 
 
+def _same_supports_close_values(ref, got, B, rel):
+    """Equal counts, flags and supports; values within rel of each signal's
+    largest value."""
+    for j in (2, 3, 4):
+        np.testing.assert_array_equal(ref[j], got[j])
+    for b in range(B):
+        n = int(ref[2][b])
+        o1, o2 = np.argsort(ref[0][b, :n]), np.argsort(got[0][b, :n])
+        np.testing.assert_array_equal(ref[0][b, :n][o1], got[0][b, :n][o2])
+        if n:
+            v1, v2 = ref[1][b, :n][o1], got[1][b, :n][o2]
+            assert np.abs(v1 - v2).max() <= rel * np.abs(v1).max()
+
+
+@pytest.mark.parametrize("mode", ["iter", "fixed"])
+@pytest.mark.parametrize("a_max", [3, 4])
+def test_quad_decoders_match_the_oracle(gpu, orc, mode, a_max):
+    """The four-lane decoders of three and four aliases (a plan option, used
+    on calls that run as one sub-batch): supports bit-exact with the oracle
+    and values within the mixed bound; against the one-lane decoder the same
+    supports and values within float-float rounding.  N = 2^18, K = M = 1024
+    (many bins of three and four aliases), 16 signals."""
+    import torch
+    from paper_1407_8315_gb300 import Plan
+    N, K, M, B = 1 << 18, 1024, 1024, 16
+    xs, _, _ = siggen.batch_exact(N, K, range(500, 500 + B), mag=(1, 10), dtype=np.complex64)
+    plan = Plan(N, K, N // M, mode, "mixed", max_signals=B, a_max=a_max)
+    ref = _run_gpu(torch, plan, xs, 2 * K)
+    plan.set_quad_decoders(True)
+    _compare(orc, plan, xs, mode, cap=2 * K, val_tol=MIXED_VAL_TOL)
+    _same_supports_close_values(ref, _run_gpu(torch, plan, xs, 2 * K), B, 1e-9)
+
+
+@pytest.mark.parametrize("mode", ["iter", "fixed"])
+def test_quad_decoders_with_long_queues_in_one_sub_batch(gpu, orc, mode):
+    """128 signals in one sub-batch with the four-lane decoders enabled: the
+    queues of the later levels may exceed the four-lane limit (64 bins per
+    SM), so one call can use either decoder per level; the results still
+    match the oracle and the one-lane call."""
+    import torch
+    from paper_1407_8315_gb300 import Plan
+    N, K, M, B = 1 << 18, 1024, 1024, 128
+    xs, _, _ = siggen.batch_exact(N, K, range(900, 900 + B), mag=(1, 10), dtype=np.complex64)
+    plan = Plan(N, K, N // M, mode, "mixed", max_signals=B, a_max=4)
+    plan.set_sub_batches(1)
+    ref = _run_gpu(torch, plan, xs, 2 * K)
+    plan.set_quad_decoders(True)
+    _compare(orc, plan, xs, mode, cap=2 * K, val_tol=MIXED_VAL_TOL)
+    _same_supports_close_values(ref, _run_gpu(torch, plan, xs, 2 * K), B, 1e-9)
+
+
 @pytest.mark.parametrize("mode,prec", [("iter", "fp64"), ("fixed", "fp64"), ("fixed", "mixed")])
 @pytest.mark.parametrize("N,K,M", [(1 << 18, 1024, 1024), (1 << 20, 8192, 4096)])
 def test_up_to_eight_aliases_matches_oracle(gpu, orc, mode, prec, N, K, M):
