@@ -147,3 +147,31 @@ def test_mlp_config_and_create_validation(lib):
     bad = sft.sft_mlp_config(30, 128, 32, 5, 0, -1.0, 0.9, 0.999, 1e-8)
     assert lib.sft_mlp_create(C.byref(bad), C.byref(h)) == sft.SFT_EINVAL
     assert lib.sft_plan_attach_mlp(None, None) == sft.SFT_EINVAL
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """Without the built CUDA library the binding raises: there is no CPU
+    fallback behind the product entry points."""
+    import paper_1407_8315_gb300.sft as S
+    from paper_1407_8315_gb300 import _build_lib
+    monkeypatch.setattr(S, "_lib", None)
+    monkeypatch.setattr(_build_lib, "LIB", "/nonexistent/libsft.so")
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        S.load()
+
+
+def test_product_code_never_reaches_the_oracle():
+    """The library, its header and its binding neither include, import,
+    call nor load anything of the oracle (test infrastructure only)."""
+    import pathlib
+    import re
+    root = pathlib.Path(__file__).resolve().parents[1]
+    pkg = root / "paper_1407_8315_gb300"
+    bad = re.compile(r'#\s*include\s*[<"][^>"]*oracle|^\s*(import|from)\s+oracle\b|'
+                     r'sfft_oracle|liboracle|\borc_[a-z0-9_]+\s*\(', re.M)
+    files = [p for ext in ("*.py", "*.cu", "*.cuh", "*.h") for p in pkg.rglob(ext)]
+    files += list((root / "include").glob("*.h"))
+    assert files
+    for f in files:
+        m = bad.search(f.read_text())
+        assert m is None, (str(f), m.group(0))
