@@ -52,7 +52,8 @@ EXPORTS = ["sft_params_default", "sft_plan_create", "sft_plan_destroy", "sft_pla
            "sft_batch_info", "sft_mlp_config_for", "sft_mlp_create", "sft_mlp_destroy",
            "sft_mlp_param_count", "sft_mlp_get_params", "sft_mlp_set_params", "sft_mlp_features",
            "sft_mlp_forward", "sft_mlp_grad", "sft_mlp_train", "sft_plan_attach_mlp",
-           "sft_exact_auto"]
+           "sft_exact_auto", "sft_alias_histogram", "sft_plan_set_sub_batches",
+           "sft_plan_sub_batches", "sft_plan_set_quad_decoders"]
 
 _lib = None
 
