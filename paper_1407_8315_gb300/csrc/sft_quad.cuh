@@ -1,7 +1,7 @@
 // sft_quad.cuh -- SynDec of one bin with a = 3 or 4 aliases (Sec. II-B
 // steps (i)-(iii)) on a group of four lanes, eight bins per warp.
 //
-// The one-lane decoder (decode_bin) walks a serial chain of about 1 500 FP64
+// The one-lane decoder (decode_bin) walks a serial chain of about 1 700 FP64
 // instructions per bin at a = 4.  An FP64 warp instruction occupies its SM
 // sub-partition for the same time whatever the number of active lanes, so
 // the chain, not the number of bins, sets the time of the last levels.  Here
