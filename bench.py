@@ -8,6 +8,8 @@ iterative sFFT-DT (Algorithm 1) with d = 512 (M = 2^13 bins), a_m = 4 levels,
 compensated-FP32 FFTs and FP64 solves (sft_exact).
 
 Other workloads (--workload):
+  exact-2^16-fp64   N = 2^16 complex128, K = 64 with |X| = 1, M = 256 (d = 256),
+                    the plain FP64 form, 4096 signals per step
   exact-2^22-fp64   the same signals through the plain FP64 form (complex128)
   exact-2^22-fixed  the same signals, non-iterative FIXED mode
   exact-2^22-dense  K = 8192 (K/M = 1), FIXED with up to 8 aliases per bin
@@ -64,7 +66,7 @@ class W:
 
     def __init__(self, name, metric, desc, N, K, M, mode, precision, batch, a_max,
                  snrs=None, r=0, plan_seed=0, c64_input=False, mlp_rows=0, mlp_snrs=None,
-                 quad=False):
+                 quad=False, mag=(1, 10)):
         self.name, self.metric, self.desc = name, metric, desc
         self.N, self.K, self.M, self.d = N, K, M, N // M
         self.mode, self.precision, self.batch, self.a_max = mode, precision, batch, a_max
@@ -82,44 +84,60 @@ class W:
         self.mlp_rows, self.mlp_snrs = mlp_rows, mlp_snrs
         # four-lane decoders of three and four aliases (few signals per call)
         self.quad = quad
+        # |X| = 1 (mag (1, 1)) or uniform in [1, 10]
+        self.mag = mag
 
     def snr_of(self, b):
         return self.snrs[b % len(self.snrs)] if self.snrs else None
 
     def gen_one(self, seed, b):
         if self.general:
-            x, s, _, _ = siggen.noisy_signal(self.N, self.K, seed, self.snr_of(b), mag=(1, 10),
+            x, s, _, _ = siggen.noisy_signal(self.N, self.K, seed, self.snr_of(b), mag=self.mag,
                                              dtype=self.dtype)
         elif self.c64_input:
-            x, s, _ = siggen.exact_signal(self.N, self.K, seed, mag=(1, 10), dtype=np.complex64)
+            x, s, _ = siggen.exact_signal(self.N, self.K, seed, mag=self.mag, dtype=np.complex64)
             x = x.astype(self.dtype)
         else:
-            x, s, _ = siggen.exact_signal(self.N, self.K, seed, mag=(1, 10), dtype=self.dtype)
+            x, s, _ = siggen.exact_signal(self.N, self.K, seed, mag=self.mag, dtype=self.dtype)
         return x, s
 
     def h2d_per_signal(self):
-        """Bytes of samples each transform must read."""
+        """Algorithmic input bytes of one transform (Sec. 8(d) of the survey's
+        measurement plan): the samples of the shifts the method reads."""
         if self.general:
             return (2 * self.a_max + self.r) * self.M * self.esize
         if self.mode == "fixed":
             return 2 * self.a_max * self.M * self.esize
         return sum(2 * (self.M >> l) * self.esize for l in range(self.a_max))
 
+    def link_bytes_per_signal(self):
+        """Bytes one transform moves across the host link when its input is
+        page-locked host memory read in place: the extraction reads every
+        level-0 row's run of shifts once, at 64 bytes or more per row (rows
+        are d samples apart, far more than a line).  The general path gathers
+        each shift's samples directly, one 32-byte sector per sample."""
+        if self.general:
+            return (2 * self.a_max + self.r) * self.M * 32
+        return self.M * max(64, 2 * self.a_max * self.esize)
+
     def stage_model(self, stage):
         """Algorithmic work of one launch of a gather/FFT stage, per signal:
-        the input bytes it must read, and the FFT's radix-2 butterflies at
-        their float-float cost in FP32 instructions (68 each: one complex
-        float-float multiply, 36, and two complex float-float additions, 16
-        each).  Above 8192 points the FFT runs as columns (log2 M1 stages,
-        reading the input) then rows (log2 M2 stages), M = M1 M2, M1 >= M2.
-        None for other stages."""
+        'bytes', the input samples it must read (the extraction: the samples
+        every later FFT reads, read once and written once); 'fft_flops', the
+        FFT's 5 M log2 M flops per shift; 'ff_instr', the radix-2
+        butterflies at their float-float cost in FP32 instructions (68 each:
+        one complex float-float multiply, 36, and two complex float-float
+        additions, 16 each) -- the issue count of this build's FFT, a
+        diagnostic, not the method's work.  Above 8192 points the FFT runs
+        as columns (log2 M1 stages, reading the input) then rows (log2 M2
+        stages), M = M1 M2, M1 >= M2.  None for other stages."""
         def split(Ml):
             lg = int(math.log2(Ml))
             return (lg, 0) if Ml <= 8192 else (lg - lg // 2, lg // 2)
 
         fixed_ns = 2 * self.a_max
-        if stage == "extract":  # the samples every later FFT reads, copied once
-            return {"bytes": 2 * self.h2d_per_signal(), "fft_ops": 0}
+        if stage == "extract":
+            return {"bytes": 2 * self.h2d_per_signal(), "fft_flops": 0, "ff_instr": 0}
         if stage.startswith("gather_fft_l"):
             Ml, ns = self.M >> int(stage[-1]), 2
             stages, reads = split(Ml)[0], True
@@ -144,10 +162,15 @@ class W:
         else:
             return None
         bfly = ns * (Ml // 2) * stages
-        return {"bytes": ns * Ml * self.esize if reads else 0, "fft_ops": bfly * 68}
+        return {"bytes": ns * Ml * self.esize if reads else 0,
+                "fft_flops": 5 * ns * Ml * stages, "ff_instr": bfly * 68}
 
 
 WORKLOADS = {
+    "exact-2^16-fp64": W("exact-2^16-fp64",
+                         "SFT signals/sec at N=2^16,K=64, plain FP64 form (complex128)",
+                         "exact-iter N=2^16 K=64 |X|=1 d=256 (M=256) a_m=4 c128, plain FP64 form",
+                         1 << 16, 64, 256, "iter", "fp64", 4096, 4, mag=(1, 1)),
     "exact-2^22": W("exact-2^22", HEADLINE_METRIC,
                     "exact-iter N=2^22 K=4096 d=512 (M=2^13) a_m=4 c64 |X|~U[1,10]",
                     1 << 22, 4096, 1 << 13, "iter", "mixed", 152, 4),
@@ -382,77 +405,183 @@ def ncu_traffic(workload: str, kernel: str, signals: float):
             t = json.load(f)
     except (OSError, ValueError):
         return None
-    ent = t.get(workload, {}).get(kernel)
+    w = t.get(workload, {})
+    ent = w.get(kernel) or w.get(kernel.split("<")[0])
     if not ent or ent.get("source_sha") != kernel_source_hash(kernel):
         return None
     return ent["dram_bytes_per_launch"] * signals / ent.get("signals_per_launch", signals)
 
 
-def kernel_of(stage: str, M: int = 0) -> str:
-    """The __global__ function (template instance) that runs a stage (the
-    general path's gather stages run the four-step column kernel above
-    8192 points)."""
+def kernel_of(stage: str, M: int = 0, precision: str = "mixed", a_max: int = 4) -> str:
+    """The __global__ template instance that runs a stage.  The FFT levels
+    share one instance (k_gather_fft<F, 8> at every M up to 8192); each
+    level's fold and decoder is its own instance (the alias count is a
+    template argument).  The general path's gather stages run the four-step
+    column kernel above 8192 points."""
+    F = "F64" if precision == "fp64" else "FF"
     if stage in ("gather_fft_consecutive", "gather_fft_random") and M > 8192:
-        return "k_fft4_cols"
+        return f"k_fft4_cols<{F}, 8>"
     if stage.startswith("gather_fft"):
-        return "k_gather_fft"
+        return f"k_gather_fft<{F}, 8>"
     if stage.startswith("gather_cols"):
-        return "k_fft4_cols"
+        return f"k_fft4_cols<{F}, 8>"
     if stage.startswith("fft_rows"):
-        return "k_fft4_rows"
+        return f"k_fft4_rows<{F}, 8>"
     if stage.startswith("fold_l"):
-        return f"k_iter_fold<a={int(stage[-1]) + 1}>"
+        return f"k_iter_fold<{F}, {int(stage[-1]) + 1}>"
     if stage.startswith("decode_l"):
-        return f"k_iter_decode<a={int(stage[-1]) + 1}>"
+        return f"k_iter_decode<{F}, {int(stage[-1]) + 1}>"
+    if stage.startswith("decode_fixed_a"):
+        return f"k_fixed_round<{F}, {int(stage[-1])}, {2 * a_max}>"
+    if stage == "decode_fixed_scan":
+        return f"k_fixed_scan<{F}, {2 * a_max}>"
+    if stage == "extract":
+        return "k_extract<double2, 1>" if precision == "fp64" else "k_extract<float2, 1>"
+    if stage == "finalize":
+        return f"k_finalize<{F}, 0>"
     return "k_" + stage
 
 
-def roofline(wl, stages, B, clk):
-    """Dominant kernel (largest share of the step) and its roofline.  The
-    gather/FFT kernels of the mixed form are bound by the FP32 pipes (the
-    float-float FFT), so 'achieved' counts the FFT's radix-2 butterflies at
-    their float-float cost in FP32 instructions against 152 SMs x 128 FP32
-    lanes x the sampled SM clock; the HBM view (input bytes / time against
-    the measured copy bandwidth) is given beside it.  B is the number of
-    signals per launch (the attribution pass runs each call as one
-    sub-batch)."""
+# GB300 arithmetic peaks derived from unit counts and the SM clock (no
+# measured figure exists for them): 152 SMs; 128 FP32 lanes per SM, one FMA
+# (2 flops) each per clock; 2 FP64 FMA units per SM (the nominal 1.25
+# TFLOP/s FP64 at 2.07 GHz), each 2 flops per clock.
+N_SM = 152
+FP32_LANES_PER_SM = 128
+FP64_FMA_PER_SM = 2
+
+
+def fp32_peak_tflops(mhz):
+    return N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def fp64_peak_tflops(mhz):
+    return N_SM * FP64_FMA_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def decode_flops(a: int, nm: int) -> float:
+    """Algorithmic FP64 flops of SynDec for one bin decoded with a aliases
+    from nm syndromes (Sec. II-B): (i) the a x a Hankel solve of Eq. (5) by
+    elimination, (2/3) a^3 + a^2 complex multiply-adds; (ii) the locator's
+    roots, a closed-form degree-a solve counted as a^2 complex multiply-adds,
+    and one snap per root (4 flops); (iii) the least-squares values: the
+    normal matrix from geometric sums (2 complex multiply-adds per entry, a^2
+    entries), Z^H m (nm a), the a x a solve ((2/3) a^3 + a^2), and the
+    validation residual over the nm equations (nm a).  A complex
+    multiply-add is 8 real flops."""
+    cma = ((2 / 3) * a ** 3 + a ** 2) + a ** 2 + (2 * a * a + nm * a + (2 / 3) * a ** 3 + a ** 2) \
+        + nm * a
+    return 8 * cma + 4 * a
+
+
+def fold_bytes(level: int, K: int, M0: int) -> float:
+    """Algorithmic bytes of one bin of level l's fold (a3-a4): the 2l held
+    syndromes of the previous level at k and k + M read (4l x 16 B), the two
+    new shifts read (2 x 16 B), the 2l folded syndromes written (2l x 16 B),
+    and the level-0 bins' counts (2^l bytes); the peeled frequencies (24 B
+    each, K spread over the M0 level-0 bins) are read once per level."""
+    return (4 * level + 2) * 16 + 2 * level * 16 + (1 << level) + 24.0 * K / M0 * (1 << level)
+
+
+def roofline(wl, stages, B, clk, qlens=None):
+    """Per template instance of the step (stage events of the attribution
+    pass, B signals per launch) its share and roofline; the dominant one
+    (largest share) is reported in full.
+    - gather/FFT kernels: bound by HBM on their algorithmic input bytes
+      (the method's samples); beside it the FFT's 5 M log2 M flops against
+      the FP32 peak, and the float-float FP32 instruction issue rate as a
+      diagnostic of this build's arithmetic.
+    - decoders: bound by the FP64 pipe on decode_flops() per queued bin
+      (qlens: the bins each level or round decoded, from the plan).
+    - folds, the extraction and the finalize: HBM on their algorithmic
+      bytes."""
     peaks, src = measured_peaks()
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    hbm = peaks["hbm_gbs"]
     groups = {}
     for name, (ms_tot, nl) in stages.items():
-        g = groups.setdefault(kernel_of(name, wl.M), {"ms": 0.0, "launches": 0, "bytes": 0,
-                                                      "ops": 0})
+        kern = kernel_of(name, wl.M, wl.precision, wl.a_max)
+        g = groups.setdefault(kern, {"ms": 0.0, "launches": 0, "bytes": 0.0, "fft_flops": 0.0,
+                                     "ff_instr": 0.0, "fp64_flops": 0.0, "units": 0.0,
+                                     "unit": None, "kind": None})
         g["ms"] += ms_tot
         g["launches"] += nl
         m = wl.stage_model(name)
         if m is not None:
+            g["kind"] = "fft" if name != "extract" else "mem"
             g["bytes"] += m["bytes"] * B * nl
-            g["ops"] += m["fft_ops"] * B * nl
-    dom_name = max(groups, key=lambda k: groups[k]["ms"])
-    dom = groups[dom_name]
+            g["fft_flops"] += m["fft_flops"] * B * nl
+            g["ff_instr"] += m["ff_instr"] * B * nl
+            g["unit"] = "shift" if name != "extract" else "row"
+        elif name.startswith("decode_l") and qlens:
+            lvl = int(name[-1])
+            if lvl < len(qlens):
+                a = lvl + 1
+                g["kind"], g["unit"] = "fp64", "bin"
+                g["units"] += qlens[lvl] * nl
+                g["fp64_flops"] += decode_flops(a, 2 * a) * qlens[lvl] * nl
+        elif name.startswith("decode_fixed_a") and qlens:
+            a = int(name[-1])
+            if a - 1 < len(qlens):
+                g["kind"], g["unit"] = "fp64", "bin"
+                g["units"] += qlens[a - 1] * nl
+                g["fp64_flops"] += decode_flops(a, 2 * wl.a_max) * qlens[a - 1] * nl
+        elif name.startswith("fold_l") and not wl.general:
+            lvl = int(name[-1])
+            g["kind"], g["unit"] = "mem", "bin"
+            g["units"] += B * (wl.M >> lvl) * nl
+            g["bytes"] += fold_bytes(lvl, wl.K, wl.M) * B * (wl.M >> lvl) * nl
+        elif name == "finalize":
+            g["kind"], g["unit"] = "mem", "bin"
+            g["units"] += B * wl.M * nl
+            # counts read, every filed entry read and written once (24 B each)
+            g["bytes"] += (B * wl.M + 2 * 24 * B * wl.K) * nl
+
+    def model(g):
+        sec = g["ms"] / 1e3
+        out = {"share": None, "ms_per_launch": g["ms"] / max(g["launches"], 1)}
+        if g["kind"] in ("fft", "mem") and g["bytes"]:
+            ach = g["bytes"] / sec / 1e9
+            out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                        "frac": ach / hbm})
+            if g["fft_flops"]:
+                fl = g["fft_flops"] / sec / 1e12
+                out["fp32_flop_view"] = {"achieved_tflops": fl,
+                                         "peak_tflops": fp32_peak_tflops(mhz),
+                                         "frac": fl / fp32_peak_tflops(mhz)}
+            if g["ff_instr"] and wl.precision != "fp64":
+                ins = g["ff_instr"] / sec / 1e12
+                pk = N_SM * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
+                out["ff_issue_diag"] = {"achieved_tinstr": ins, "peak_tinstr": pk,
+                                        "frac": ins / pk}
+        elif g["kind"] == "fp64" and g["fp64_flops"]:
+            ach = g["fp64_flops"] / sec / 1e12
+            pk = fp64_peak_tflops(mhz)
+            out.update({"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                        "frac": ach / pk, "bins_per_launch": g["units"] / max(g["launches"], 1)})
+        else:
+            out.update({"bound": None, "achieved": None, "peak": None, "unit": None,
+                        "frac": None})
+        return out
+
     step_ms = sum(g["ms"] for g in groups.values())
-    sec = dom["ms"] / 1e3
-    roof = {"kernel": dom_name, "share": dom["ms"] / step_ms,
-            "ms_per_launch": dom["ms"] / dom["launches"], "peak_source": src,
+    by_kernel = {}
+    for k, g in groups.items():
+        r = model(g)
+        r["share"] = g["ms"] / step_ms
+        by_kernel[k] = r
+    dom_name = max(groups, key=lambda k: groups[k]["ms"])
+    roof = {"kernel": dom_name, **by_kernel[dom_name], "peak_source": src,
             "traffic": ncu_traffic(wl.name, dom_name, B)}
-    mhz = (clk or {}).get("sm_mhz") or 2070.0
-    if dom["ops"] and wl.precision != "fp64":
-        peak = 152 * 128 * mhz * 1e6 / 1e12
-        ach = dom["ops"] / sec / 1e12
-        roof.update({"bound": "alu", "achieved": ach, "peak": peak,
-                     "unit": "T FP32-instr/s", "frac": ach / peak,
-                     "peak_note": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz (sampled)",
-                     "hbm_view": {"achieved_gbs": dom["bytes"] / sec / 1e9,
-                                  "peak_gbs": peaks["hbm_gbs"],
-                                  "frac": dom["bytes"] / sec / 1e9 / peaks["hbm_gbs"]}})
-    elif dom["bytes"]:
-        ach = dom["bytes"] / sec / 1e9
-        roof.update({"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": ach / peaks["hbm_gbs"]})
-    else:
-        # the solve kernels are FP64-pipe bound; no algorithmic flop model
-        # is claimed for them
-        roof.update({"bound": "alu", "achieved": None, "peak": None, "unit": None,
-                     "frac": None})
+    if roof.get("bound") == "alu":
+        roof["peak_note"] = (f"FP64: {N_SM} SMs x {FP64_FMA_PER_SM} FMA units x 2 flops x "
+                             f"{mhz:.0f} MHz (sampled), derived from unit counts")
+    elif roof.get("bound") == "hbm":
+        roof["peak_note"] = f"measured copy bandwidth ({src})"
+    roof["by_kernel"] = {k: {kk: (round(vv, 5) if isinstance(vv, float) else vv)
+                             for kk, vv in v.items() if kk in ("share", "bound", "frac",
+                                                               "ms_per_launch")}
+                         for k, v in sorted(by_kernel.items(), key=lambda kv: -kv[1]["share"])}
     return roof
 
 
@@ -709,6 +838,8 @@ def run_plan_workload(args, wl):
     plan.stage_times()  # reset
     ms_attr = timed_steps(torch, lambda: fn(x_dev, cap, out), n_attr, flush, stream)
     stages = plan.stage_times()
+    # bins decoded per level / round in the last (one sub-batch) call
+    qlens = None if wl.general else plan.queue_lengths()
     plan.set_profiling(False)
     plan.set_sub_batches(args.sub_batches)
 
@@ -766,7 +897,12 @@ def run_plan_workload(args, wl):
     e2e_s = max_over_ranks(torch, dist, ws, host_timed_steps(
         torch, lambda i: fn_host(srcs[i & 1], cap, h_out), args.e2e_steps, flush))
     e2e = {"value": ws * B * args.e2e_steps / e2e_s, "unit": "signals/s",
-           "h2d_bytes_per_step": int(B * wl.h2d_per_signal()),
+           "h2d_bytes_per_step": int(B * wl.link_bytes_per_signal()),
+           "h2d_note": ("bytes requested across NVLink-C2C: one 32-byte sector per gathered "
+                        "sample" if wl.general else
+                        "bytes requested across NVLink-C2C: each level-0 row's run of shifts, "
+                        "at least 64 B per row") +
+                       f"; the method's own input is {wl.h2d_per_signal() / wl.M:.0f} B per row",
            "d2h_bytes_per_step": int(int(h_out.count.sum()) * 24 + B * 16),
            "path": ("sft_general_host" if wl.general else "sft_exact_host") +
                    ", page-locked input read in place (zero-copy gather over NVLink-C2C), "
@@ -778,7 +914,7 @@ def run_plan_workload(args, wl):
         dist.destroy_process_group()
         return
 
-    roof = roofline(wl, stages, B, clk)
+    roof = roofline(wl, stages, B, clk, qlens)
     roof["signals_per_launch"] = B
     roof["timing"] = (f"attribution pass: {n_attr} calls on one stream (one sub-batch), CUDA "
                       f"events around every launch, L2 flushed between calls; "

@@ -100,7 +100,10 @@ typedef struct {
                        /* the locator is found by Berlekamp-Massey and the   */
                        /* roots by a search over the d candidates of the bin */
   int32_t max_iters;   /* ITER: number of levels, 1..a_max (0 -> a_max);     */
-                       /* M / 2^(max_iters-1) must be >= 1                   */
+                       /* M / 2^(max_iters-1) must be >= 1; more than four   */
+                       /* levels only with SFT_FP64 (complex128 input): on   */
+                       /* complex64 input the decisions of levels 4..7 are   */
+                       /* set by the input's rounding (SFT_EUNSUPPORTED)     */
   int32_t mode;        /* sft_mode                                           */
   int32_t precision;   /* sft_precision                                      */
   int32_t n_cs_shifts; /* general modes: random shifts r, 1..16, r <= d (0 -> 3 a_max) */
@@ -149,6 +152,12 @@ sft_status sft_plan_create(const sft_params* p, int64_t max_signals, sft_plan_t*
 
 /* Frees the plan and its device memory (synchronises the device). */
 void sft_plan_destroy(sft_plan_t plan);
+
+/* Copies the plan's parameters, with every default filled in as
+ * sft_plan_create applied them, into *out (host).  Lets a caller check an
+ * input against the plan (element type by precision, row length N) before
+ * a call.  SFT_EINVAL for a NULL plan or pointer. */
+sft_status sft_plan_get_params(sft_plan_t plan, sft_params* out);
 
 /* Device bytes the plan holds (tables + workspace). */
 size_t sft_plan_workspace_bytes(sft_plan_t plan);
@@ -250,9 +259,23 @@ int32_t sft_batch_info(sft_batch_t ctx, int32_t* n_groups, int64_t* n_graph_node
  * for SFT_EXACT_FIXED with a_max = 4), plus 16 * (N/d + 2 * (2^ceil(log2(N)/2)
  * + 2^floor(log2(N)/2))) bytes of tables, 256 bytes of counters and 256-byte
  * alignment of each array (at N = 2^22, N/d = 2^13: 7 signals per call).
- * The first call on each
- * device looks up the array's device address on that device (make it before
- * any stream capture).  All calls share the array and it keeps the last
+ *
+ * Set-up.  The library's module is loaded lazily, so the first call on each
+ * device is where the array's memory is committed on that device and where
+ * the call looks up the array's device address there.  Make that first call
+ * at start-up, before any stream capture and before another memory manager
+ * reserves the device; when the device has no room for the array it returns
+ * SFT_ECUDA with "scratch set-up: out of memory" in sft_last_cuda_error.  A
+ * call that finds a different current context on the device than the one
+ * the address was looked up in (after cudaDeviceReset, for instance) repeats
+ * the look-up and the set-up, so it too should come outside any capture.
+ *
+ * Differences from the plan path: the gather reads each shift's samples
+ * straight from x (no compact extraction pass, which would need the array's
+ * room for a copy of the samples), and the omega and twiddle tables are
+ * computed on the device in FP64 (the plan path computes them on the host in
+ * long double); both round to within an ulp, so results agree with
+ * sft_exact's to rounding.  All calls share the array and it keeps the last
  * call's contents; each call rebuilds what it needs, but calls that overlap
  * on the GPU race and must be serialised by the caller.  Asynchronous on
  * `stream` like sft_exact. */
@@ -377,6 +400,16 @@ sft_status sft_alias_histogram(const int64_t* supports, int64_t n_sets, int64_t 
 /* Number of kernel launches one call of this plan on max_signals signals
  * issues (sft_exact / sft_general). */
 int32_t sft_plan_launches_per_call(sft_plan_t plan);
+
+/* Work counts of the plan's last exact call, for throughput models: the
+ * number of (signal, bin) pairs queued for decoding at each level of
+ * SFT_EXACT_ITER (Algorithm 1's active or unsolved bins, decoded with
+ * a = l + 1), or entering each round a = 1..a_max of SFT_EXACT_FIXED,
+ * summed over the call's signals and sub-batches.  Synchronises the
+ * device; writes up to `cap` entries to out (host) and returns the number
+ * of levels or rounds (0 for the general modes, -1 for a NULL plan or a
+ * CUDA error). */
+int32_t sft_plan_queue_lengths(sft_plan_t plan, int64_t* out, int32_t cap);
 
 /* Sub-batching.  A call on n signals may be split into S sub-batches of
  * consecutive signals (sizes differ by at most one), each enqueued on its

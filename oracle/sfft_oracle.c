@@ -78,7 +78,8 @@ int orc_dft_brute(int64_t n, const double* in, double* out, int sign) {
 
 /* ------------------------------------------------------------ syndromes */
 
-/* Eq. (2) with R1: Y_{d,l} = d * FFT_M(x_{d,l}),  x_{d,l}[n] = x[n d + l]. */
+/* Eq. (2) with X the unnormalised DFT (x its inverse with 1/N):
+ * Y_{d,l} = d * FFT_M(x_{d,l}),  x_{d,l}[n] = x[n d + l]. */
 int orc_syndrome(const double* xin, int64_t N, int64_t d, int64_t shift, double* Yout) {
   if (!is_pow2(N) || d <= 0 || N % d != 0 || shift < 0) return -1;
   int64_t M = N / d;

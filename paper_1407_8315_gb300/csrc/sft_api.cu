@@ -70,6 +70,14 @@ sft_status validate(const sft_params& p) {
     if (p.max_iters < 1 || p.max_iters > p.a_max)
       return why(SFT_EINVAL, "max_iters must lie in [1, a_max]");
     if ((M0 >> (p.max_iters - 1)) < 1) return why(SFT_EINVAL, "N/d too small for max_iters");
+    // Levels 4..7 locate 5..8 aliases among 2^l d candidates from syndromes
+    // that carry complex64 input's rounding; there the decision rule of
+    // Algorithm 1 itself is decided by rounding, so no result is defined
+    // well enough to reproduce.  Those levels are offered for complex128
+    // input only.
+    if (p.precision == SFT_MIXED && p.max_iters > 4)
+      return why(SFT_EUNSUPPORTED,
+                 "SFT_EXACT_ITER above four levels needs SFT_FP64 (complex128 input)");
   }
   if (M0 > kMaxM) return why(SFT_EUNSUPPORTED, "N/d above 2^26");
   return SFT_OK;
@@ -291,6 +299,12 @@ sft_status sft_plan_create(const sft_params* pin, int64_t max_signals, sft_plan_
 static void drop_stage_recs(sft_plan_s* P);
 static void free_event_pool(sft_plan_s* P);
 
+sft_status sft_plan_get_params(sft_plan_t P, sft_params* out) {
+  if (!P || !out) return SFT_EINVAL;
+  *out = P->p;
+  return SFT_OK;
+}
+
 void sft_plan_destroy(sft_plan_t P) {
   if (!P) return;
   cudaDeviceSynchronize();
@@ -303,6 +317,22 @@ void sft_plan_destroy(sft_plan_t P) {
 size_t sft_plan_workspace_bytes(sft_plan_t P) { return P ? P->device_bytes : 0; }
 
 int32_t sft_plan_launches_per_call(sft_plan_t P) { return P ? sft::launches_per_call(P) : 0; }
+
+int32_t sft_plan_queue_lengths(sft_plan_t P, int64_t* out, int32_t cap) {
+  if (!P || (cap > 0 && !out)) return -1;
+  if (sft::is_general_mode(P->p.mode)) return 0;
+  const int n = P->p.mode == SFT_EXACT_ITER ? P->levels : P->p.a_max;
+  if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+  // each sub-batch keeps 16 counters; level l (round l + 1) is counter l
+  int32_t c[16 * sft::kMaxSub];
+  if (cudaMemcpy(c, P->ws.qcount, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  for (int i = 0; i < n && i < cap; ++i) {
+    int64_t t = 0;
+    for (int s = 0; s < P->last_sub; ++s) t += c[16 * s + i];
+    out[i] = t;
+  }
+  return n;
+}
 
 static sft_status reject(const char* fmt, long long a, long long b) {
   std::snprintf(g_cuda_err, sizeof(g_cuda_err), fmt, a, b);

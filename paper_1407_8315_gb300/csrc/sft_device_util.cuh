@@ -8,6 +8,15 @@
 
 namespace sft {
 
+// Index of slot e of level-0 bin k0 within one signal's slot arrays
+// (M0 x kSlots entries).  Slot-major: slot e of every bin is one contiguous
+// run, so consecutive bins' first slots -- the only ones most bins use --
+// share sectors, and a warp reading the slots of 32 consecutive bins reads
+// them coalesced.
+__device__ __forceinline__ int64_t slot_ix(int64_t k0, int e, int64_t M0) {
+  return (int64_t)e * M0 + k0;
+}
+
 // File the a recovered frequencies of one decode event under their level-0
 // bins (the calling thread owns every level-0 bin congruent to its bin).
 template <class F, int A>
@@ -19,8 +28,8 @@ __device__ __forceinline__ void file_solution(const int64_t* s, const cdbl* p, i
     const int64_t k0 = s[j] & (M0 - 1);
     const int c = cnt[k0];
     if (c < kSlots) {
-      ss[k0 * kSlots + c] = s[j];
-      sp[k0 * kSlots + c] = Store<F>::from_d(p[j]);
+      ss[slot_ix(k0, c, M0)] = s[j];
+      sp[slot_ix(k0, c, M0)] = Store<F>::from_d(p[j]);
       cnt[k0] = (uint8_t)(c + 1);
     } else {
       atomicOr(flag, 1);
@@ -34,8 +43,8 @@ __device__ __forceinline__ void file_one_ff(int64_t s, float4 p, int64_t M0, uin
   const int64_t k0 = s & (M0 - 1);
   const int c = cnt[k0];
   if (c < kSlots) {
-    ss[k0 * kSlots + c] = s;
-    sp[k0 * kSlots + c] = p;
+    ss[slot_ix(k0, c, M0)] = s;
+    sp[slot_ix(k0, c, M0)] = p;
     cnt[k0] = (uint8_t)(c + 1);
   } else {
     atomicOr(flag, 1);
@@ -91,8 +100,8 @@ __device__ __forceinline__ void file_n(int n, const int64_t* s, const cdbl* p, i
     const int64_t k0 = s[j] & (M0 - 1);
     const int c = cnt[k0];
     if (c < kSlots) {
-      ss[k0 * kSlots + c] = s[j];
-      sp[k0 * kSlots + c] = Store<F>::from_d(p[j]);
+      ss[slot_ix(k0, c, M0)] = s[j];
+      sp[slot_ix(k0, c, M0)] = Store<F>::from_d(p[j]);
       cnt[k0] = (uint8_t)(c + 1);
     } else {
       atomicOr(flag, 1);

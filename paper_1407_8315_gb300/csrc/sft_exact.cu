@@ -449,8 +449,8 @@ __global__ void __launch_bounds__(1024) k_finalize(FinArgs g) {
       const int c = cnt[k0];
       for (int e = 0; e < c; ++e, ++pos) {
         if (pos < cap) {
-          idx[pos] = g.slot_s[((int64_t)b * M0 + k0) * kSlots + e];
-          const cdbl v = Store<F>::to_d(sp[((int64_t)b * M0 + k0) * kSlots + e]);
+          idx[pos] = g.slot_s[(int64_t)b * M0 * kSlots + slot_ix(k0, e, M0)];
+          const cdbl v = Store<F>::to_d(sp[(int64_t)b * M0 * kSlots + slot_ix(k0, e, M0)]);
           val[pos] = make_double2(v.x, v.y);
         }
       }
@@ -469,8 +469,8 @@ __global__ void __launch_bounds__(1024) k_finalize(FinArgs g) {
         const int c = cnt[k0];
         for (int e = 0; e < c; ++e, ++p) {
           if (p >= w0 && p < w0 + kFinStage) {
-            s_idx[p - w0] = g.slot_s[((int64_t)b * M0 + k0) * kSlots + e];
-            const cdbl v = Store<F>::to_d(sp[((int64_t)b * M0 + k0) * kSlots + e]);
+            s_idx[p - w0] = g.slot_s[(int64_t)b * M0 * kSlots + slot_ix(k0, e, M0)];
+            const cdbl v = Store<F>::to_d(sp[(int64_t)b * M0 * kSlots + slot_ix(k0, e, M0)]);
             s_val[p - w0] = make_double2(v.x, v.y);
           }
         }
@@ -956,6 +956,7 @@ int sub_batches_for(const sft_plan_s* P, int64_t B) {
 cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride,
                          const sft_result* r, cudaStream_t st) {
   const int S = sub_batches_for(P, B);
+  P->last_sub = S;
   P->quad_now = P->quad_ok && S <= 1;
   if (S <= 1) return launch_one(P, B, x, x_stride, r, st);
   cudaError_t e = cudaSuccess;

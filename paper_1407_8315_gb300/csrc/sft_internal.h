@@ -222,6 +222,7 @@ struct sft_plan_s {
   // sub-batches per call (0: chosen from the batch size) and their streams
   // (created on first use; stream 0 is the caller's)
   int sub_batches = 0;
+  int last_sub = 1;  // sub-batches of the last call (its queue counters)
   cudaStream_t sub_st[sft::kMaxSub] = {};
   cudaEvent_t sub_fork = nullptr;
   cudaEvent_t sub_join[sft::kMaxSub] = {};

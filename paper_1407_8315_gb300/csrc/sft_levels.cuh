@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* q
           const int c = cnt[k0];
           peeled = peeled || c > 0;
           for (int e = 0; e < c; ++e) {
-            const int64_t sl = ss[k0 * kSlots + e];
-            const cdbl p = Store<F>::to_d(sp[k0 * kSlots + e]);
+            const int64_t sl = ss[slot_ix(k0, e, M0)];
+            const cdbl p = Store<F>::to_d(sp[slot_ix(k0, e, M0)]);
             m[2 * l] = m[2 * l] - p * omega_pow(g.om, sl * (2 * l));
             m[2 * l + 1] = m[2 * l + 1] - p * omega_pow(g.om, sl * (2 * l + 1));
           }
@@ -128,8 +128,8 @@ __global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* q
             const int u = (__ffs((int)cp) - 1) >> 2;
             const int cu = (int)((cp >> (4 * u)) & 15u);
             const int64_t k0 = k + (int64_t)(u0 + u) * M;
-            const int64_t sl = ss[k0 * kSlots + e];
-            const FF::V p = FF::from4(sp[k0 * kSlots + e]);
+            const int64_t sl = ss[slot_ix(k0, e, M0)];
+            const FF::V p = FF::from4(sp[slot_ix(k0, e, M0)]);
             m[2 * l] = FF::sub(m[2 * l], FF::mulv(p, omega_ff(g.omff, sl * (2 * l))));
             m[2 * l + 1] = FF::sub(m[2 * l + 1], FF::mulv(p, omega_ff(g.omff, sl * (2 * l + 1))));
             if (++e == cu) {

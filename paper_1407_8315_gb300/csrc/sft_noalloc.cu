@@ -17,14 +17,23 @@
 // exits.  Host code cannot use the array's name as a device address (on the
 // host it only names a stand-in object), so the first call on each device
 // asks the runtime for the array's device address with
-// cudaGetSymbolAddress, with that device current, and remembers it.  That
-// first call should therefore happen before any stream capture.
+// cudaGetSymbolAddress, with that device current, and remembers it together
+// with the identity of the device's current context.  The library's module
+// is loaded lazily, so that first call is also where the array's memory is
+// committed on the device.  It should therefore happen at start-up, before
+// any stream capture and before another memory manager reserves the device.
+// If the context is later destroyed (cudaDeviceReset) and a new one created,
+// the module is loaded again and the array may sit at a new address, with
+// the kernels' raised shared-memory limits gone: a call that finds a context
+// other than the remembered one repeats the look-up and the set-up.
 //
 // Every call shares the same array and leaves its contents behind: the call
 // rebuilds the tables and clears the per-call counters itself.  Two calls
 // whose work overlaps on the GPU (different streams, or different host
 // threads on one device) race on the array and corrupt each other; callers
 // must serialise them.
+#include <cuda.h>
+
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -37,7 +46,12 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[SFT_NOALLOC_SCRATCH_BY
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
-void* g_scratch_dev[kMaxDevices] = {};
+// per device: the array's address in the context it was looked up in
+struct ScratchSlot {
+  unsigned long long ctx_id;
+  void* ptr;
+};
+ScratchSlot g_scratch_dev[kMaxDevices] = {};
 
 char* noalloc_msg() {
   thread_local char buf[256];
@@ -93,17 +107,53 @@ sft_status fail(sft_status st, const char* msg) {
   return st;
 }
 
-// Device address of the scratch array on the current device (set up once).
+// The unique identity of the calling thread's current context (driver entry
+// points resolved through the runtime, so the library needs no link to the
+// driver library).  Called with g_setup_mu held.
+cudaError_t current_context_id(unsigned long long* id) {
+  typedef CUresult (*GetCurrent)(CUcontext*);
+  typedef CUresult (*GetId)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  if (get_current == nullptr || get_id == nullptr) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000,
+                                                     cudaEnableDefault, &q1);
+    if (e == cudaSuccess)
+      e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess) return e;
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return cudaErrorNotSupported;
+    get_current = reinterpret_cast<GetCurrent>(f1);
+    get_id = reinterpret_cast<GetId>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return cudaErrorDeviceUninitialized;
+  if (get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  return cudaSuccess;
+}
+
+// Device address of the scratch array on the current device, in its current
+// context.  The look-up (which also loads the module and so commits the
+// array) and the kernels' shared-memory set-up run on the first call in a
+// context and again whenever the device's context has changed.
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (g_scratch_dev[dev] == nullptr) {
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
+  // makes the device's primary context current (created if need be)
+  void* ptr = nullptr;
+  e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  unsigned long long id = 0;
+  e = current_context_id(&id);
+  if (e != cudaSuccess) return e;
+  ScratchSlot& slot = g_scratch_dev[dev];
+  if (slot.ptr == nullptr || slot.ctx_id != id) {
     // largest dynamic shared memory any gather/FFT launch of this build asks for
     for (int prec = 0; prec < 2; ++prec) {
       sft_plan_s tmp;
@@ -112,9 +162,10 @@ cudaError_t scratch_address(void** out) {
       e = sft::prepare_kernels(&tmp);
       if (e != cudaSuccess) return e;
     }
-    g_scratch_dev[dev] = ptr;
+    slot.ctx_id = id;
+    slot.ptr = ptr;
   }
-  *out = g_scratch_dev[dev];
+  *out = slot.ptr;
   return cudaSuccess;
 }
 
@@ -144,6 +195,9 @@ extern "C" sft_status sft_exact_noalloc(const sft_params* pin, int64_t n, const 
   if (p.mode == SFT_EXACT_ITER &&
       (p.max_iters < 1 || p.max_iters > p.a_max || (M0 >> (p.max_iters - 1)) < 1))
     return fail(SFT_EINVAL, "invalid max_iters");
+  if (p.mode == SFT_EXACT_ITER && p.precision == SFT_MIXED && p.max_iters > 4)
+    return fail(SFT_EUNSUPPORTED,
+                "SFT_EXACT_ITER above four levels needs SFT_FP64 (complex128 input)");
   if (n < 1 || x_stride < p.N) return fail(SFT_EINVAL, "n_signals < 1 or x_stride < N");
   if (r->cap < p.K || r->cap < 1 || !r->idx || !r->val || !r->count || !r->unresolved ||
       !r->overflow)

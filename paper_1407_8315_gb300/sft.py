@@ -44,7 +44,8 @@ class sft_result(C.Structure):
                 ("count", C.c_void_p), ("unresolved", C.c_void_p), ("overflow", C.c_void_p)]
 
 
-EXPORTS = ["sft_params_default", "sft_plan_create", "sft_plan_destroy", "sft_plan_workspace_bytes",
+EXPORTS = ["sft_params_default", "sft_plan_create", "sft_plan_destroy", "sft_plan_get_params",
+           "sft_plan_workspace_bytes",
            "sft_exact", "sft_exact_host", "sft_plan_launches_per_call", "sft_strerror",
            "sft_last_cuda_error", "sft_plan_set_profiling", "sft_plan_stage_times",
            "sft_exact_noalloc", "sft_general", "sft_general_host", "sft_plan_cs_shifts",
@@ -53,7 +54,7 @@ EXPORTS = ["sft_params_default", "sft_plan_create", "sft_plan_destroy", "sft_pla
            "sft_mlp_param_count", "sft_mlp_get_params", "sft_mlp_set_params", "sft_mlp_features",
            "sft_mlp_forward", "sft_mlp_grad", "sft_mlp_train", "sft_plan_attach_mlp",
            "sft_exact_auto", "sft_alias_histogram", "sft_plan_set_sub_batches",
-           "sft_plan_sub_batches", "sft_plan_set_quad_decoders"]
+           "sft_plan_sub_batches", "sft_plan_set_quad_decoders", "sft_plan_queue_lengths"]
 
 _lib = None
 
@@ -91,6 +92,9 @@ def load(build_if_missing: bool = False):
     lib.sft_plan_create.argtypes = [P(sft_params), C.c_int64, P(C.c_void_p)]
     lib.sft_plan_destroy.argtypes = [C.c_void_p]
     lib.sft_plan_destroy.restype = None
+    lib.sft_plan_get_params.argtypes = [C.c_void_p, P(sft_params)]
+    lib.sft_plan_queue_lengths.argtypes = [C.c_void_p, P(C.c_int64), C.c_int32]
+    lib.sft_plan_queue_lengths.restype = C.c_int32
     lib.sft_plan_workspace_bytes.argtypes = [C.c_void_p]
     lib.sft_plan_workspace_bytes.restype = C.c_size_t
     lib.sft_exact.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, P(sft_result),
@@ -171,6 +175,50 @@ def sft_plan_destroy(handle: int):
     load().sft_plan_destroy(C.c_void_p(handle))
 
 
+def sft_plan_get_params(handle: int) -> sft_params:
+    """The plan's parameters with every default filled in."""
+    p = sft_params()
+    _check(load().sft_plan_get_params(C.c_void_p(handle), C.byref(p)), "sft_plan_get_params")
+    return p
+
+
+def _check_signals(x, params: sft_params, what: str, host: bool = False):
+    """Element type and row length of x against the parameters, before the
+    library reads it: complex128 rows for SFT_FP64, complex64 for SFT_MIXED,
+    at least N elements each."""
+    if host:
+        want = np.complex128 if params.precision == SFT_FP64 else np.complex64
+        ok = x.dtype == want
+    else:
+        import torch
+        want = torch.complex128 if params.precision == SFT_FP64 else torch.complex64
+        ok = x.dtype == want
+    if not ok:
+        raise ValueError(f"{what}: signals of dtype {x.dtype}, the plan's precision needs {want}")
+    if x.shape[1] < params.N:
+        raise ValueError(f"{what}: rows of {x.shape[1]} samples, N = {params.N}")
+
+
+def _check_result(out, B: int, cap: int, what: str, device=None):
+    """Shapes (and, for device results, the device) of caller-supplied result
+    arrays: idx and val [B, cap] (or [cap] when B is 1), count, unresolved and
+    overflow [B]; int64 / complex128 / int64 / int32 / int32."""
+    rows = [(out.idx, (B, cap), "int64"), (out.val, (B, cap), "complex128"),
+            (out.count, (B,), "int64"), (out.unresolved, (B,), "int32"),
+            (out.overflow, (B,), "int32")]
+    for t, shape, dt in rows:
+        n = 1
+        for v in t.shape:
+            n *= int(v)
+        if n != shape[0] * (shape[1] if len(shape) > 1 else 1) or not str(t.dtype).endswith(dt):
+            raise ValueError(f"{what}: result array of shape {tuple(t.shape)} / {t.dtype}, "
+                             f"expected {shape} / {dt}")
+        if device is not None and t.device != device:
+            raise ValueError(f"{what}: result array on {t.device}, signals on {device}")
+        if device is not None and not t.is_contiguous():
+            raise ValueError(f"{what}: result arrays must be contiguous")
+
+
 def _stream_ptr(stream) -> int:
     import torch
     if stream is None:
@@ -194,6 +242,7 @@ def sft_exact(handle: int, x, cap: int, out: Result | None = None, stream=None,
         raise ValueError("sft_exact needs a CUDA tensor (use sft_exact_host for host data)")
     if x.stride(1) != 1:
         raise ValueError("signals must be contiguous along N")
+    _check_signals(x, sft_plan_get_params(handle), _entry)
     B = x.shape[0]
     if out is None:
         dev = x.device
@@ -202,6 +251,8 @@ def sft_exact(handle: int, x, cap: int, out: Result | None = None, stream=None,
                      torch.empty(B, dtype=torch.int64, device=dev),
                      torch.empty(B, dtype=torch.int32, device=dev),
                      torch.empty(B, dtype=torch.int32, device=dev))
+    else:
+        _check_result(out, B, cap, _entry, x.device)
     r = sft_result(cap, out.idx.data_ptr(), out.val.data_ptr(), out.count.data_ptr(),
                    out.unresolved.data_ptr(), out.overflow.data_ptr())
     # a single row has no meaningful pitch (numpy/torch may report 0 for it)
@@ -225,10 +276,13 @@ def sft_exact_host(handle: int, x: np.ndarray, cap: int, out: Result | None = No
         x = x[None, :]
     if x.strides[1] != x.itemsize:
         raise ValueError("signals must be contiguous along N")
+    _check_signals(x, sft_plan_get_params(handle), _entry, host=True)
     B = x.shape[0]
     if out is None:
         out = Result(np.empty((B, cap), np.int64), np.empty((B, cap), np.complex128),
                      np.empty(B, np.int64), np.empty(B, np.int32), np.empty(B, np.int32))
+    else:
+        _check_result(out, B, cap, _entry)
     r = sft_result(cap, out.idx.ctypes.data, out.val.ctypes.data, out.count.ctypes.data,
                    out.unresolved.ctypes.data, out.overflow.ctypes.data)
     pitch = x.strides[0] // x.itemsize if B > 1 else x.shape[1]
@@ -269,9 +323,12 @@ def sft_exact_noalloc(params: sft_params, x, cap: int, out: Result | None = None
         x = x.unsqueeze(0)
     if not x.is_cuda or x.stride(1) != 1:
         raise ValueError("sft_exact_noalloc needs a CUDA tensor contiguous along N")
+    _check_signals(x, params, "sft_exact_noalloc")
     B = x.shape[0]
     if out is None:
         out = _device_result(B, cap, x.device)
+    else:
+        _check_result(out, B, cap, "sft_exact_noalloc", x.device)
     r = sft_result(cap, out.idx.data_ptr(), out.val.data_ptr(), out.count.data_ptr(),
                    out.unresolved.data_ptr(), out.overflow.data_ptr())
     pitch = x.stride(0) if B > 1 else x.shape[1]
@@ -279,6 +336,16 @@ def sft_exact_noalloc(params: sft_params, x, cap: int, out: Result | None = None
                                     C.byref(r), C.c_void_p(_stream_ptr(stream))),
            "sft_exact_noalloc")
     return out
+
+
+def sft_plan_queue_lengths(handle: int) -> list:
+    """Bins queued per level (ITER) or per round (FIXED) in the plan's last
+    call, summed over its signals."""
+    out = (C.c_int64 * 16)()
+    n = load().sft_plan_queue_lengths(C.c_void_p(handle), out, 16)
+    if n < 0:
+        raise SftError(SFT_ECUDA, "sft_plan_queue_lengths")
+    return [int(out[i]) for i in range(n)]
 
 
 def sft_plan_set_profiling(handle: int, enable: bool):
@@ -380,6 +447,9 @@ class Plan:
 
     def stage_times(self) -> dict:
         return sft_plan_stage_times(self.handle)
+
+    def queue_lengths(self) -> list:
+        return sft_plan_queue_lengths(self.handle)
 
     def close(self):
         if self.handle:

@@ -107,6 +107,21 @@ def test_more_than_four_aliases_only_on_the_exact_paths(lib):
     assert lib.sft_plan_create(C.byref(p), 1, C.byref(h)) == sft.SFT_EUNSUPPORTED
 
 
+def test_more_than_four_levels_need_complex128_input(lib):
+    """ITER above four levels (5..8 aliases among 2^l d candidates) is
+    offered for complex128 input only: on complex64 input the input's
+    rounding decides which borderline bins validate there, so the mixed form
+    refuses it (SFT_EUNSUPPORTED); FIXED at a_max = 8 stays available."""
+    from paper_1407_8315_gb300 import sft
+    h = C.c_void_p()
+    p = sft.sft_params_default(1 << 18, 1024, 256, "iter", "mixed")
+    p.a_max, p.max_iters = 8, 8
+    assert lib.sft_plan_create(C.byref(p), 1, C.byref(h)) == sft.SFT_EUNSUPPORTED
+    assert "SFT_FP64" in lib.sft_last_cuda_error().decode()
+    p.max_iters = 5
+    assert lib.sft_plan_create(C.byref(p), 1, C.byref(h)) == sft.SFT_EUNSUPPORTED
+
+
 def test_plan_create_rejects_too_many_bins(lib):
     """N/d = 2^27 bins is above the four-step FFT limit (2^26)."""
     from paper_1407_8315_gb300 import sft

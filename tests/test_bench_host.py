@@ -1,7 +1,8 @@
 """Host logic of bench.py on the CPU: the algorithmic work model of the
-gather/FFT stages, the roofline arithmetic built on it, the scaling of the
-committed ncu traffic, the stage-to-kernel map and the end-to-end timing
-helper (the L2 flush stays outside the timed call)."""
+gather/FFT stages and of the decoders, the roofline arithmetic built on it,
+the scaling of the committed ncu traffic, the stage-to-kernel map, the bytes
+that cross the host link and the end-to-end timing helper (the L2 flush
+stays outside the timed call)."""
 import time
 
 import pytest
@@ -9,48 +10,80 @@ import pytest
 import bench
 
 
-def test_stage_model_counts_the_fft_butterflies():
-    """exact-2^22 level 0: two shifts of M = 8192 points; an M-point radix-2
-    FFT has (M/2) log2 M = 4096 * 13 butterflies, 68 FP32 instructions each
-    in float-float, and reads 8192 complex64 samples per shift."""
+def test_stage_model_counts_the_fft_work():
+    """exact-2^22 level 0: two shifts of M = 8192 points read 8192 complex64
+    samples each; the FFT's flops are 5 M log2 M per shift; an M-point
+    radix-2 FFT has (M/2) log2 M = 4096 * 13 butterflies, 68 FP32
+    instructions each in float-float."""
     wl = bench.WORKLOADS["exact-2^22"]
     m = wl.stage_model("gather_fft_l0")
-    assert m == {"bytes": 2 * 8192 * 8, "fft_ops": 2 * 4096 * 13 * 68}
+    assert m == {"bytes": 2 * 8192 * 8, "fft_flops": 5 * 2 * 8192 * 13,
+                 "ff_instr": 2 * 4096 * 13 * 68}
     m3 = wl.stage_model("gather_fft_l3")  # M = 1024 at level 3
-    assert m3 == {"bytes": 2 * 1024 * 8, "fft_ops": 2 * 512 * 10 * 68}
+    assert m3 == {"bytes": 2 * 1024 * 8, "fft_flops": 5 * 2 * 1024 * 10,
+                  "ff_instr": 2 * 512 * 10 * 68}
     assert wl.stage_model("decode_l2") is None
+    # the four levels read 8 B x (2 + 1 + 1/2 + 1/4) = 30 B per level-0 row
+    assert wl.h2d_per_signal() == 30 * 8192
 
 
 def test_stage_model_of_the_four_step_fft():
     """exact-2^27: M = 2^18 runs as columns of 2^9 points (reading the
-    input) then rows of 2^9 points."""
+    input) then rows of 2^9 points; together 5 M log2 M flops per shift."""
     wl = bench.WORKLOADS["exact-2^27"]
     cols, rows = wl.stage_model("gather_cols_l0"), wl.stage_model("fft_rows_l0")
     half = 2 * (1 << 17)  # two shifts x M/2 butterflies per radix-2 stage
-    assert cols == {"bytes": 2 * (1 << 18) * 8, "fft_ops": half * 9 * 68}
-    assert rows == {"bytes": 0, "fft_ops": half * 9 * 68}
+    assert cols["bytes"] == 2 * (1 << 18) * 8 and rows["bytes"] == 0
+    assert cols["ff_instr"] == rows["ff_instr"] == half * 9 * 68
+    assert cols["fft_flops"] + rows["fft_flops"] == 5 * 2 * (1 << 18) * 18
 
 
-def test_roofline_of_the_dominant_gather_fft():
+def test_roofline_of_a_dominant_gather_fft_counts_input_bytes():
+    """The gather/FFT kernels are bound by HBM on the method's input bytes;
+    the FFT flops against the FP32 peak and the float-float issue rate are
+    reported beside the fraction, not as it."""
     wl = bench.WORKLOADS["exact-2^22"]
-    stages = {"gather_fft_l0": (2.0, 1), "decode_l3": (1.0, 1)}  # ms in all, launches
-    roof = bench.roofline(wl, stages, 152, {"sm_mhz": 2000.0})
-    assert roof["kernel"] == "k_gather_fft" and roof["bound"] == "alu"
-    assert roof["share"] == pytest.approx(2.0 / 3.0)
-    ops = 2 * 4096 * 13 * 68 * 152
-    assert roof["achieved"] == pytest.approx(ops / 2e-3 / 1e12)
-    assert roof["peak"] == pytest.approx(152 * 128 * 2000e6 / 1e12)
+    stages = {"gather_fft_l0": (2.0, 1), "gather_fft_l1": (0.5, 1), "decode_l3": (1.0, 1)}
+    roof = bench.roofline(wl, stages, 152, {"sm_mhz": 2000.0}, [9000, 5000, 3000, 1000])
+    assert roof["kernel"] == "k_gather_fft<FF, 8>" and roof["bound"] == "hbm"
+    assert roof["share"] == pytest.approx(2.5 / 3.5)
+    byts = (2 * 8192 * 8 + 2 * 4096 * 8) * 152
+    assert roof["achieved"] == pytest.approx(byts / 2.5e-3 / 1e9)
     assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
-    hbm = roof["hbm_view"]
-    assert hbm["achieved_gbs"] == pytest.approx(2 * 8192 * 8 * 152 / 2e-3 / 1e9)
-    assert hbm["frac"] == pytest.approx(hbm["achieved_gbs"] / hbm["peak_gbs"])
+    assert roof["peak"] == bench.measured_peaks()[0]["hbm_gbs"]
+    fl = roof["fp32_flop_view"]
+    assert fl["peak_tflops"] == pytest.approx(152 * 128 * 2 * 2000e6 / 1e12)
+    assert fl["achieved_tflops"] == pytest.approx(5 * (2 * 8192 * 13 + 2 * 4096 * 12) * 152
+                                                  / 2.5e-3 / 1e12)
+    diag = roof["ff_issue_diag"]
+    assert diag["peak_tinstr"] == pytest.approx(152 * 128 * 2000e6 / 1e12)
+    assert set(roof["by_kernel"]) == {"k_gather_fft<FF, 8>", "k_iter_decode<FF, 4>"}
 
 
-def test_roofline_claims_no_model_for_the_solvers():
+def test_roofline_of_a_dominant_decoder_counts_fp64_flops_per_bin():
+    """A decoder dominating is reported against the FP64 peak derived from
+    the unit counts, on decode_flops() per queued bin of its level."""
     wl = bench.WORKLOADS["exact-2^22"]
-    roof = bench.roofline(wl, {"decode_l3": (3.0, 1), "gather_fft_l0": (1.0, 1)}, 152, None)
-    assert roof["kernel"] == "k_iter_decode<a=4>"
-    assert roof["frac"] is None and roof["achieved"] is None
+    roof = bench.roofline(wl, {"decode_l3": (3.0, 2), "gather_fft_l0": (1.0, 2)}, 152,
+                          {"sm_mhz": 2070.0}, [9000, 5000, 3000, 1000])
+    assert roof["kernel"] == "k_iter_decode<FF, 4>" and roof["bound"] == "alu"
+    fl = bench.decode_flops(4, 8) * 1000 * 2
+    assert roof["achieved"] == pytest.approx(fl / 3e-3 / 1e12)
+    assert roof["peak"] == pytest.approx(152 * 2 * 2 * 2070e6 / 1e12)
+    assert roof["bins_per_launch"] == 1000
+    # without the queue lengths no flop model is claimed
+    bare = bench.roofline(wl, {"decode_l3": (3.0, 1)}, 152, None)
+    assert bare["frac"] is None and bare["achieved"] is None
+
+
+def test_decode_flops_grow_with_the_alias_count():
+    """One alias: 8 complex multiply-adds and change; four aliases with 8
+    syndromes: about 1.8 kflop per bin."""
+    f = [bench.decode_flops(a, 2 * a) for a in (1, 2, 3, 4)]
+    assert f == sorted(f)
+    assert bench.decode_flops(1, 2) == pytest.approx(8 * (2 / 3 + 1 + 1 + 2 + 2 + 2 / 3 + 1 + 2)
+                                                     + 4)
+    assert 1700 < bench.decode_flops(4, 8) < 2000
 
 
 def test_ncu_traffic_scales_with_the_signals():
@@ -58,24 +91,36 @@ def test_ncu_traffic_scales_with_the_signals():
     import os
     with open(os.path.join(bench.ROOT, "profiles", "ncu_traffic.json")) as f:
         ent = json.load(f)["exact-2^22"]["k_gather_fft"]
-    got = bench.ncu_traffic("exact-2^22", "k_gather_fft", 76)
+    got = bench.ncu_traffic("exact-2^22", "k_gather_fft<FF, 8>", 76)
     if ent["source_sha"] == bench.kernel_source_hash("k_gather_fft"):
         assert got == pytest.approx(ent["dram_bytes_per_launch"] * 76 / ent["signals_per_launch"])
     else:  # counters taken on other kernel text are not reported
         assert got is None
-    assert bench.ncu_traffic("exact-2^22", "k_iter_fold<a=2>", 152) is None
+    assert bench.ncu_traffic("exact-2^22", "k_iter_fold<FF, 2>", 152) is None
     assert bench.ncu_traffic("no-such-workload", "k_gather_fft", 152) is None
 
 
-def test_kernel_of_maps_stages_to_kernels():
-    assert bench.kernel_of("gather_fft_l1") == "k_gather_fft"
-    assert bench.kernel_of("gather_fft_consecutive", 1 << 15) == "k_fft4_cols"
-    assert bench.kernel_of("gather_fft_consecutive", 1 << 13) == "k_gather_fft"
-    assert bench.kernel_of("gather_cols_l2") == "k_fft4_cols"
-    assert bench.kernel_of("fft_rows_l0") == "k_fft4_rows"
-    assert bench.kernel_of("fold_l2") == "k_iter_fold<a=3>"
-    assert bench.kernel_of("decode_l0") == "k_iter_decode<a=1>"
-    assert bench.kernel_of("finalize") == "k_finalize"
+def test_kernel_of_maps_stages_to_template_instances():
+    k = bench.kernel_of
+    assert k("gather_fft_l1") == k("gather_fft_l3") == "k_gather_fft<FF, 8>"
+    assert k("gather_fft_l0", 8192, "fp64") == "k_gather_fft<F64, 8>"
+    assert k("gather_fft_consecutive", 1 << 15) == "k_fft4_cols<FF, 8>"
+    assert k("gather_fft_consecutive", 1 << 13) == "k_gather_fft<FF, 8>"
+    assert k("gather_cols_l2") == "k_fft4_cols<FF, 8>"
+    assert k("fft_rows_l0") == "k_fft4_rows<FF, 8>"
+    assert k("fold_l2") == "k_iter_fold<FF, 3>"
+    assert k("decode_l0") == "k_iter_decode<FF, 1>"
+    assert k("decode_fixed_a3", 8192, "mixed", 4) == "k_fixed_round<FF, 3, 8>"
+    assert k("extract") == "k_extract<float2, 1>"
+    assert k("finalize") == "k_finalize<FF, 0>"
+
+
+def test_link_bytes_count_what_crosses_the_host_link():
+    """At least 64 B per level-0 row for the exact paths (above the
+    algorithmic 30 B), one sector per gathered sample on the general path."""
+    assert bench.WORKLOADS["exact-2^22"].link_bytes_per_signal() == 64 * 8192
+    g = bench.WORKLOADS["general-2^20"]
+    assert g.link_bytes_per_signal() == (6 + 9) * (1 << 15) * 32
 
 
 def test_host_timed_steps_leaves_the_flush_out():

@@ -1,6 +1,9 @@
 """Heterogeneous batches (sft_batch): signals of uneven N, K and kind in one
-graph-captured call give exactly the results of transforming each signal on
-its own (same kernels, same per-signal arithmetic), on the first call
+graph-captured call.  Every signal's result is compared with the FP64
+oracle (Algorithm 1 for the exactly sparse signals, Algorithm 2 for the noisy
+ones): supports bit-exact, values within the mixed form's 1e-4.  The batch
+must also give exactly the results of transforming each signal on its own
+(same kernels, same per-signal arithmetic).  Both hold on the first call
 (capture), on a replay with new data, and without the graph."""
 import numpy as np
 import pytest
@@ -8,6 +11,8 @@ import pytest
 import siggen
 
 pytestmark = pytest.mark.gpu
+
+MIXED_VAL_TOL = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -75,8 +80,37 @@ def _check(torch, params, xs, outs, cap):
         np.testing.assert_array_equal(o.val[:n].cpu().numpy(), rv[:n])
 
 
+def _check_oracle(orc, params, xs, outs):
+    """Each signal of the batch against the FP64 oracle of its own kind."""
+    from paper_1407_8315_gb300 import sft
+    worst = 0.0
+    for i, (p, x) in enumerate(zip(params, xs)):
+        o = outs[i]
+        M = p.N // p.d
+        cap = o.idx.shape[0]
+        if p.mode == sft.SFT_GENERAL:
+            oi, ov, _ = orc.general(x, M, p.K, a_max=p.a_max, r=p.n_cs_shifts, seed=p.seed,
+                                    cap=cap)
+            ou = 0
+        else:
+            om = orc.ITER if p.mode == sft.SFT_EXACT_ITER else orc.FIXED
+            oi, ov, ou = orc.exact(x, M, p.a_max, om, max_iters=p.max_iters, cap=cap,
+                                   zero_tol=p.zero_tol, root_tol=p.root_tol, res_tol=p.res_tol)
+        n = int(o.count.item())
+        gi, gv = o.idx[:n].cpu().numpy(), o.val[:n].cpu().numpy()
+        order = np.argsort(gi, kind="stable")
+        gi, gv = gi[order], gv[order]
+        assert int(o.overflow.item()) == 0, i
+        np.testing.assert_array_equal(gi, oi, err_msg=f"signal {i}: supports differ")
+        assert int(o.unresolved.item()) == ou, (i, int(o.unresolved.item()), ou)
+        if n:
+            worst = max(worst, float((np.abs(gv - ov) / np.abs(ov)).max()))
+    assert worst <= MIXED_VAL_TOL, worst
+    return worst
+
+
 @pytest.mark.parametrize("use_graph", [True, False])
-def test_batch_equals_single_signal_calls(gpu, use_graph):
+def test_batch_matches_oracle_and_single_signal_calls(gpu, orc, use_graph):
     torch = gpu
     from paper_1407_8315_gb300 import sft
     cap = 2048
@@ -90,6 +124,7 @@ def test_batch_equals_single_signal_calls(gpu, use_graph):
     assert info["groups"] >= 4 and info["tuned"] == info["groups"]
     if use_graph:
         assert info["graph_nodes"] > info["groups"]
+    _check_oracle(orc, params, xs, outs)
     _check(torch, params, xs, outs, cap)
     # same composition, new data: the graph is replayed with fresh tables
     params2, xs2 = _make(24, 5)
@@ -101,6 +136,7 @@ def test_batch_equals_single_signal_calls(gpu, use_graph):
     batch.run(params2, xt, outs2)
     torch.cuda.synchronize()
     assert batch.info()["graph_nodes"] == info["graph_nodes"]
+    _check_oracle(orc, params2, xs2, outs2)
     _check(torch, params2, xs2, outs2, cap)
     batch.close()
 

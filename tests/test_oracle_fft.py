@@ -48,7 +48,8 @@ def test_fft_rejects_non_power_of_two(orc):
 
 
 def _alias_sum(N, supp, vals, d, l):
-    """Right-hand side of Eq. (2) (with R1): sum over the aliases of bin k of
+    """Right-hand side of Eq. (2), X the unnormalised DFT and x its inverse
+    with 1/N: sum over the aliases of bin k of
     X[k + jM] * omega^{(k + jM) l}, written straight from the planted X."""
     M = N // d
     Y = np.zeros(M, complex)

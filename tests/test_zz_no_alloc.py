@@ -89,3 +89,39 @@ def test_noalloc_rejects_batches_beyond_its_array(torch_gpu):
     assert st == sft.SFT_EINVAL
     msg = lib.sft_last_cuda_error().decode()
     assert "static maximum" in msg and "need" in msg
+
+
+def test_noalloc_call_allocates_nothing(torch_gpu):
+    """The entry point's defining property: once the array is set up on the
+    device (the first call), a call with caller-provided inputs and result
+    arrays changes neither the device's free memory nor what torch's
+    allocator holds."""
+    torch = torch_gpu
+    from paper_1407_8315_gb300 import sft
+    N, K, M, B = 1 << 20, 1024, 1 << 11, 3
+    xs, _, _ = siggen.batch_exact(N, K, range(70, 70 + B), mag=(1, 10), dtype=np.complex64)
+    x = torch.from_numpy(xs).cuda()
+    p = sft.sft_params_default(N, K, N // M, "iter", "mixed")
+    out = sft._device_result(B, 2 * K, x.device)
+    sft.sft_exact_noalloc(p, x, 2 * K, out)  # set-up call
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    sft.sft_exact_noalloc(p, x, 2 * K, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    assert int(out.count.sum().item()) > 0
+
+
+def test_noalloc_refuses_mismatched_inputs(torch_gpu):
+    """The binding checks the element type against the precision and the
+    row length against N before the library reads anything."""
+    torch = torch_gpu
+    from paper_1407_8315_gb300 import sft
+    p = sft.sft_params_default(1 << 14, 16, 16, "iter", "fp64")
+    with pytest.raises(ValueError, match="dtype"):
+        sft.sft_exact_noalloc(p, torch.zeros((1, 1 << 14), dtype=torch.complex64,
+                                             device="cuda"), 16)
+    with pytest.raises(ValueError, match="N ="):
+        sft.sft_exact_noalloc(p, torch.zeros((1, 1 << 13), dtype=torch.complex128,
+                                             device="cuda"), 16)
