@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Throughput of the sFFT-DT hot path on GB300, through the C ABI.
 
-Default workload (one "step"): one batch of B = 152 independent seeded
+Default workload (one "step"): one batch of B = 608 independent seeded
 synthetic signals, N = 2^22 complex64, K = 4096 non-zero frequencies at
 uniform positions with |X| ~ U[1, 10] and uniform phase, transformed by
 iterative sFFT-DT (Algorithm 1) with d = 512 (M = 2^13 bins), a_m = 4 levels,
@@ -173,12 +173,12 @@ WORKLOADS = {
                          1 << 16, 64, 256, "iter", "fp64", 4096, 4, mag=(1, 1)),
     "exact-2^22": W("exact-2^22", HEADLINE_METRIC,
                     "exact-iter N=2^22 K=4096 d=512 (M=2^13) a_m=4 c64 |X|~U[1,10]",
-                    1 << 22, 4096, 1 << 13, "iter", "mixed", 152, 4),
+                    1 << 22, 4096, 1 << 13, "iter", "mixed", 608, 4),
     "exact-2^22-fp64": W("exact-2^22-fp64",
                          "SFT signals/sec at N=2^22,K=4096, plain FP64 form",
                          "exact-iter N=2^22 K=4096 d=512 (M=2^13) a_m=4, the headline's c64 "
                          "signals upcast to c128, plain FP64 form, the mixed form's tolerances",
-                         1 << 22, 4096, 1 << 13, "iter", "fp64", 152, 4, c64_input=True),
+                         1 << 22, 4096, 1 << 13, "iter", "fp64", 608, 4, c64_input=True),
     "exact-2^22-dense": W("exact-2^22-dense",
                           "SFT signals/sec at N=2^22,K=8192 (K/M=1), up to 8 aliases per bin",
                           "exact-fixed N=2^22 K=8192 d=512 (M=2^13) a_m=8 (Berlekamp-Massey and "
@@ -187,7 +187,7 @@ WORKLOADS = {
     "exact-2^22-fixed": W("exact-2^22-fixed",
                           "SFT signals/sec at N=2^22,K=4096, non-iterative (FIXED)",
                           "exact-fixed N=2^22 K=4096 d=512 (M=2^13) a_m=4 c64",
-                          1 << 22, 4096, 1 << 13, "fixed", "mixed", 152, 4),
+                          1 << 22, 4096, 1 << 13, "fixed", "mixed", 608, 4),
     "general-2^20": W("general-2^20",
                       "SFT signals/sec at N=2^20,K=1024 noisy 20/30/40 dB; SNR_out",
                       "general N=2^20 K=1024 d=32 (M=2^15) a_m=3 r=9 c64 SNR 20/30/40 dB",

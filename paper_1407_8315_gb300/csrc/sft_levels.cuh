@@ -48,18 +48,16 @@ __device__ __forceinline__ bool above_ff(const FF::V& m, double theta2) {
 constexpr int kFoldThreads = 256;
 constexpr int kDecThreads = 128;
 
-// Level l, phase 1, one thread per bin: fold the held syndromes, SubFreq on
-// the two new shifts, activity test of Algorithm 1, write the syndromes back and
-// queue the active bins for decoding.
+// Level l, phase 1, bin k (< M) of signal b: fold the held syndromes,
+// SubFreq on the two new shifts, activity test of Algorithm 1, write the
+// syndromes back; returns whether the bin is to be decoded.
 template <class F, int A>
-__global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* queue, int* qcount) {
+__device__ __forceinline__ bool fold_bin(const LevelArgs& g, int b, int64_t k) {
   constexpr int l = A - 1, nm = 2 * A;
   typedef typename Store<F>::T T;
-  const int b = blockIdx.y;
   const int64_t M = g.M, M0 = g.M0;
-  const int64_t k = (int64_t)blockIdx.x * kFoldThreads + threadIdx.x;
   bool active = false;
-  if (k < M) {
+  {
     const T* prev = reinterpret_cast<const T*>(g.prev) + (int64_t)b * g.held_elems;
     T* cur = reinterpret_cast<T*>(g.cur) + (int64_t)b * g.held_elems;
     const uint8_t* cnt = g.slot_cnt + (int64_t)b * M0;
@@ -149,24 +147,29 @@ __global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* q
     }
     if (!active) g.Tcur[(int64_t)b * M0 + k] = 0;
   }
+  return active;
+}
+
+// Level l, phase 1, one thread per bin: fold_bin, and the active bins queued
+// for decoding.
+template <class F, int A>
+__global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* queue, int* qcount) {
+  const int b = blockIdx.y;
+  const int64_t k = (int64_t)blockIdx.x * kFoldThreads + threadIdx.x;
+  const bool active = k < g.M && fold_bin<F, A>(g, b, k);
   block_queue_push<kFoldThreads>(active, b, (int)k, queue, qcount);
 }
 
-// Level l, phase 2: decode the queued bins with a = l + 1 (SynDec, Algorithm 1),
-// grid-stride over the queue so that every warp is full.
+// Level l, phase 2, one queued bin k of signal b: SynDec with a = l + 1
+// (Algorithm 1); a recovered bin is filed and its terms leave the held
+// syndromes, an unsolved one is flagged in T.
 template <class F, int A>
-__global__ void __launch_bounds__(kDecThreads) k_iter_decode(LevelArgs g, const int2* queue,
-                                                             const int* qcount,
-                                                             int n_quad_max = -1) {
+__device__ __forceinline__ void decode_level_bin(const LevelArgs& g, int b, int64_t k) {
   constexpr int nm = 2 * A;
   typedef typename Store<F>::T T;
-  const int n = *qcount;
-  if (n <= n_quad_max) return;  // the four-lane decoder takes short queues
   const BinGeom geom{g.N, g.M, g.d, g.om};
-  for (int e = blockIdx.x * kDecThreads + threadIdx.x; e < n; e += gridDim.x * kDecThreads) {
-    const int2 q = queue[e];
-    const int b = q.x;
-    const int64_t k = q.y, M = g.M, M0 = g.M0;
+  {
+    const int64_t M = g.M, M0 = g.M0;
     T* cur = reinterpret_cast<T*>(g.cur) + (int64_t)b * g.held_elems;
     const Tol2 tol{g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]),
                    g.root_tol * g.root_tol, g.res_tol * g.res_tol};
@@ -221,6 +224,20 @@ __global__ void __launch_bounds__(kDecThreads) k_iter_decode(LevelArgs g, const 
       t = 0;
     }
     g.Tcur[(int64_t)b * M0 + k] = t;
+  }
+}
+
+// Level l, phase 2: decode the queued bins with a = l + 1 (SynDec, Algorithm 1),
+// grid-stride over the queue so that every warp is full.
+template <class F, int A>
+__global__ void __launch_bounds__(kDecThreads) k_iter_decode(LevelArgs g, const int2* queue,
+                                                             const int* qcount,
+                                                             int n_quad_max = -1) {
+  const int n = *qcount;
+  if (n <= n_quad_max) return;  // the four-lane decoder takes short queues
+  for (int e = blockIdx.x * kDecThreads + threadIdx.x; e < n; e += gridDim.x * kDecThreads) {
+    const int2 q = queue[e];
+    decode_level_bin<F, A>(g, q.x, q.y);
   }
 }
 

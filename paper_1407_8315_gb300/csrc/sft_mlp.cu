@@ -4,12 +4,16 @@
 //
 // The network n_in -> 128 -> 128 -> n_out (ReLU) is small enough that one
 // CTA keeps all its weights in shared memory as FP16 (80 KB) and pushes a
-// tile of 32 rows through every layer with FP32 accumulation.  Thread
-// (h, g) of a 256-thread CTA owns hidden unit / output column h for the 16
-// rows of half g: weight reads are consecutive across a warp (no bank
-// conflict), activation reads are warp-wide broadcasts.  W2 and W3 are
-// stored with an odd number of 32-bit words per row so that the backward
-// pass, which walks their columns, is conflict-free as well.
+// tile of 32 rows through every layer with FP32 accumulation.  Every
+// layer's product -- forward, the backward deltas and the weight gradients
+// -- runs on the tensor cores as 16 x 8 output tiles of mma.sync m16n8k8
+// with TF32 operands and FP32 accumulators, one tile per warp at a time.
+// FP16 weights are exact in TF32; an FP32 operand (activations, deltas) is
+// split into a TF32 high part and the TF32 rounding of its remainder, so
+// that the two (or, with both operands split, three) products carry about
+// 22 significant bits of every operand: the FP32 results of the FP16-weight
+// network, not a TF32-rounded one.  Row pitches are chosen for
+// bank-conflict-free fragment loads.
 //
 //   k_mlp_propose<F>   per queued voted bin: features from the held
 //                      syndromes (FP64 de-rotation), forward, the min(2a_k,
@@ -39,9 +43,16 @@ constexpr int kMaxIn = 48;      // 2 (2 a_m + r) <= 2 (8 + 16)
 constexpr int kMaxOut = 136;    // d + a_m + 2 <= 128 + 6, rounded up
 constexpr int kRows = 32;       // rows per tile
 constexpr int kThr = 256;       // threads per CTA
-constexpr int kP2 = 130;        // W2 row pitch in halves (65 words: odd)
-constexpr int kP3 = 138;        // W3 row pitch in halves (69 words: odd)
-constexpr int kZP = kMaxOut + 1;  // logit / delta row pitch in floats (odd)
+// Row pitches of the shared-memory operands, chosen so that the fragment
+// loads of the tensor-core tiles (lane l reads row l/4 [+ 8] at column
+// l%4 [+ 4] of an FP32 operand, or column l/4 at row l%4 [+ 4] of an FP16
+// one) fall into 32 distinct banks, or pairs of lanes share one word:
+constexpr int kP1 = 136;        // W1, halves (68 words = 4 mod 32)
+constexpr int kP2 = 136;        // W2, halves (68 words)
+constexpr int kP3 = 138;        // W3, halves (69 words = 5 mod 32)
+constexpr int kXP = 52;         // features, floats (52 = 20 mod 32)
+constexpr int kAP = 132;        // hidden activations and their deltas, floats (4 mod 32)
+constexpr int kZP = 140;        // logits / output deltas, floats (12 mod 32), >= kMaxOut
 constexpr int kMaxSyn = 24;     // 2 a_m + r
 
 struct MlpDims {
@@ -71,84 +82,178 @@ struct MlpW {
 };
 
 struct WSmem {
-  __half W1[kMaxIn * kH];
+  __half W1[kMaxIn * kP1];
   __half W2[kH * kP2];
   __half W3[kH * kP3];
   float b1[kH], b2[kH], b3[kMaxOut];
 };
 struct FwdSmem {
   WSmem w;
-  float X[kRows * kMaxIn];
-  float A1[kRows * kH];
-  float A2[kRows * kH];
+  float X[kRows * kXP];
+  float A1[kRows * kAP];
+  float A2[kRows * kAP];
   float Z[kRows * kZP];
   double2 MT[kRows * kMaxSyn];  // de-rotated syndromes of the tile
   double2 SC[kRows];            // per-row phase / norm factor
 };
 struct TrainSmem {
   WSmem w;
-  float X[kRows * kMaxIn];
-  float A1[kRows * kH];
-  float A2[kRows * kH];  // second hidden layer, later the first layer's delta
+  float X[kRows * kXP];
+  float A1[kRows * kAP];
+  float A2[kRows * kAP];  // second hidden layer, later the first layer's delta
   float D3[kRows * kZP];
-  float D2[kRows * kH];
+  float D2[kRows * kAP];
   float rowloss[kRows];
   int cls[kRows];
   uint32_t sup[kRows * 4];
 };
+
+// n rounded up to the tensor-core K step (8)
+__device__ __forceinline__ int pad8(int n) { return (n + 7) & ~7; }
 
 __device__ void load_weights(WSmem& s, const MlpDims& D, const MlpW& w, int tid) {
   const MlpOffsets o = mlp_offsets(D);
   const __half* w1 = w.w16;
   const __half* w2 = w1 + (int64_t)D.n_in * kH;
   const __half* w3 = w2 + (int64_t)kH * kH;
-  for (int i = tid; i < D.n_in * kH; i += kThr) s.W1[i] = w1[i];
+  for (int i = tid; i < D.n_in * kH; i += kThr) s.W1[(i >> 7) * kP1 + (i & 127)] = w1[i];
+  // rows of W1 and columns of W3 up to the next multiple of 8 are read by
+  // the tensor-core K steps: zero, so that they add nothing
+  for (int i = D.n_in * kH + tid; i < pad8(D.n_in) * kH; i += kThr)
+    s.W1[(i >> 7) * kP1 + (i & 127)] = __float2half_rn(0.f);
   for (int i = tid; i < kH * kH; i += kThr) s.W2[(i >> 7) * kP2 + (i & 127)] = w2[i];
   for (int i = tid; i < kH * D.n_out; i += kThr) s.W3[(i / D.n_out) * kP3 + i % D.n_out] = w3[i];
+  const int npad = pad8(D.n_out) - D.n_out;
+  for (int i = tid; i < kH * npad; i += kThr)
+    s.W3[(i / npad) * kP3 + D.n_out + i % npad] = __float2half_rn(0.f);
   for (int i = tid; i < kH; i += kThr) {
     s.b1[i] = w.master[o.b1 + i];
     s.b2[i] = w.master[o.b2 + i];
   }
-  for (int i = tid; i < D.n_out; i += kThr) s.b3[i] = w.master[o.b3 + i];
+  for (int i = tid; i < pad8(D.n_out); i += kThr) s.b3[i] = i < D.n_out ? w.master[o.b3 + i] : 0.f;
+}
+
+// ---- tensor-core tiles: mma.sync m16n8k8, TF32 operands, FP32 accumulators
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// x = hi + lo + O(2^-22 |x|): hi the TF32 rounding of x, lo that of x - hi
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+// d += a b for a 16 x 8 (row-major) A, an 8 x 8 (column-major) B fragment
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4],
+                                         const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, "
+      "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// One warp: c += sum_k A(m0 + i, k) B(k, n0 + j) over k < K (a multiple of
+// 8) for the 16 x 8 output tile at (m0, n0).  Lane l holds (row l/4 [+ 8],
+// columns 2 (l%4) [+ 1]) of c.  A is split (hi, lo) in every case; B too when
+// kSplitB (an FP32 operand), else it must be exact in TF32 (FP16 weights).
+template <bool kSplitB, class FA, class FB>
+__device__ __forceinline__ void mma_tile(float (&c)[4], int m0, int n0, int K, FA A, FB B,
+                                         int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  for (int k0 = 0; k0 < K; k0 += 8) {
+    uint32_t ah[4], al[4], bh[2], bl[2];
+    split_tf32(A(m0 + g, k0 + t), ah[0], al[0]);
+    split_tf32(A(m0 + g + 8, k0 + t), ah[1], al[1]);
+    split_tf32(A(m0 + g, k0 + t + 4), ah[2], al[2]);
+    split_tf32(A(m0 + g + 8, k0 + t + 4), ah[3], al[3]);
+    if constexpr (kSplitB) {
+      split_tf32(B(k0 + t, n0 + g), bh[0], bl[0]);
+      split_tf32(B(k0 + t + 4, n0 + g), bh[1], bl[1]);
+    } else {
+      bh[0] = to_tf32(B(k0 + t, n0 + g));
+      bh[1] = to_tf32(B(k0 + t + 4, n0 + g));
+    }
+    mma_tf32(c, ah, bh);
+    mma_tf32(c, al, bh);
+    if constexpr (kSplitB) mma_tf32(c, ah, bl);
+  }
+}
+
+// out[r][n] = act(sum_k in[r][k] W[k][n] + b[n]) for the kRows rows of a
+// tile and n < n_out (K = pad8 of the input width; the padding of `in` and
+// of W is zero).  Warp w owns column tiles w, w + 8, w + 16 (n_out <= 136:
+// at most 17) for both 16-row halves, so every split A fragment it loads
+// serves all of its column tiles.
+template <bool kRelu>
+__device__ __forceinline__ void dense_tile(const float* in, int in_pitch, int K, const __half* W,
+                                           int w_pitch, const float* b, int n_out, float* out,
+                                           int out_pitch, int tid) {
+  constexpr int kNW = kThr / 32, kNT = (kMaxOut + 8 * kNW - 1) / (8 * kNW);
+  static_assert(kRows == 32, "two 16-row halves per tile");
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  const int n_tiles = (n_out + 7) >> 3;
+  float c[2][kNT][4];
+#pragma unroll
+  for (int j = 0; j < kNT; ++j) {
+    const int c0 = (warp + j * kNW) * 8 + 2 * t;
+    const bool on = warp + j * kNW < n_tiles;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      c[h][j][0] = c[h][j][2] = on ? b[c0] : 0.f;
+      c[h][j][1] = c[h][j][3] = on ? b[c0 + 1] : 0.f;
+    }
+  }
+  for (int k0 = 0; k0 < K; k0 += 8) {
+    uint32_t ah[2][4], al[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float* r0 = in + (h * 16 + g) * in_pitch + k0 + t;
+      split_tf32(r0[0], ah[h][0], al[h][0]);
+      split_tf32(r0[8 * in_pitch], ah[h][1], al[h][1]);
+      split_tf32(r0[4], ah[h][2], al[h][2]);
+      split_tf32(r0[8 * in_pitch + 4], ah[h][3], al[h][3]);
+    }
+#pragma unroll
+    for (int j = 0; j < kNT; ++j) {
+      const int nt = warp + j * kNW;
+      if (nt < n_tiles) {
+        const __half* wp = W + (k0 + t) * w_pitch + nt * 8 + g;
+        const uint32_t bf[2] = {to_tf32(__half2float(wp[0])),
+                                to_tf32(__half2float(wp[4 * w_pitch]))};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          mma_tf32(c[h][j], ah[h], bf);
+          mma_tf32(c[h][j], al[h], bf);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kNT; ++j) {
+    const int nt = warp + j * kNW;
+    if (nt < n_tiles) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = h * 16 + g + (q >> 1) * 8, n = nt * 8 + 2 * t + (q & 1);
+          if (n < n_out) out[r * out_pitch + n] = kRelu ? fmaxf(c[h][j][q], 0.0f) : c[h][j][q];
+        }
+    }
+  }
 }
 
 // z1 = X W1 + b1, A1 = relu(z1); A2 = relu(A1 W2 + b2); Z = A2 W3 + b3,
-// for the 32 rows of the tile (FP32 accumulation of FP16 weights)
+// for the 32 rows of the tile (tensor cores, FP32 accumulation)
 __device__ void forward_tile(const WSmem& w, const MlpDims& D, const float* X, float* A1,
                              float* A2, float* Z, int tid) {
-  const int h = tid & (kH - 1), r0 = (tid >> 7) * 16;
-  float acc[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) acc[q] = w.b1[h];
-  for (int i = 0; i < D.n_in; ++i) {
-    const float wv = __half2float(w.W1[i * kH + h]);
-#pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = fmaf(X[(r0 + q) * kMaxIn + i], wv, acc[q]);
-  }
-#pragma unroll
-  for (int q = 0; q < 16; ++q) A1[(r0 + q) * kH + h] = fmaxf(acc[q], 0.0f);
+  dense_tile<true>(X, kXP, pad8(D.n_in), w.W1, kP1, w.b1, kH, A1, kAP, tid);
   __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 16; ++q) acc[q] = w.b2[h];
-  for (int i = 0; i < kH; ++i) {
-    const float wv = __half2float(w.W2[i * kP2 + h]);
-#pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = fmaf(A1[(r0 + q) * kH + i], wv, acc[q]);
-  }
-#pragma unroll
-  for (int q = 0; q < 16; ++q) A2[(r0 + q) * kH + h] = fmaxf(acc[q], 0.0f);
+  dense_tile<true>(A1, kAP, kH, w.W2, kP2, w.b2, kH, A2, kAP, tid);
   __syncthreads();
-  for (int c = h; c < D.n_out; c += kH) {
-#pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = w.b3[c];
-    for (int i = 0; i < kH; ++i) {
-      const float wv = __half2float(w.W3[i * kP3 + c]);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) acc[q] = fmaf(A2[(r0 + q) * kH + i], wv, acc[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 16; ++q) Z[(r0 + q) * kZP + c] = acc[q];
-  }
+  dense_tile<false>(A2, kAP, kH, w.W3, kP3, w.b3, D.n_out, Z, kZP, tid);
   __syncthreads();
 }
 
@@ -213,7 +318,7 @@ __device__ void tile_features(const FeatArgs& g, int e0, int nt, FwdSmem& s, int
       const double2 m = s.MT[rr * kMaxSyn + l], sc = s.SC[rr];
       f = (c & 1) ? (float)(m.x * sc.y + m.y * sc.x) : (float)(m.x * sc.x - m.y * sc.y);
     }
-    s.X[rr * kMaxIn + c] = f;
+    s.X[rr * kXP + c] = f;
   }
   __syncthreads();
 }
@@ -280,7 +385,7 @@ __global__ void __launch_bounds__(kThr) k_mlp_features(FeatArgs g, int n_in, int
     tile_features<F>(g, e0, nt, s, tid);
     for (int it = tid; it < nt * n_in; it += kThr) {
       const int rr = it / n_in, c = it - rr * n_in;
-      feat[(int64_t)(e0 + rr) * n_in + c] = s.X[rr * kMaxIn + c];
+      feat[(int64_t)(e0 + rr) * n_in + c] = s.X[rr * kXP + c];
     }
     if (tid < nt) {
       const int2 q = g.queue[queue_pos(g, e0 + tid)];
@@ -304,7 +409,7 @@ __global__ void __launch_bounds__(kThr) k_mlp_forward(MlpDims D, MlpW w, const f
     const int nt = (int)min((int64_t)kRows, n_rows - e0);
     for (int it = tid; it < kRows * kMaxIn; it += kThr) {
       const int rr = it / kMaxIn, c = it - rr * kMaxIn;
-      s.X[it] = (rr < nt && c < D.n_in) ? feat[(e0 + rr) * D.n_in + c] : 0.0f;
+      s.X[rr * kXP + c] = (rr < nt && c < D.n_in) ? feat[(e0 + rr) * D.n_in + c] : 0.0f;
     }
     __syncthreads();
     forward_tile(s.w, D, s.X, s.A1, s.A2, s.Z, tid);
@@ -342,7 +447,7 @@ __global__ void __launch_bounds__(kThr) k_mlp_train(MlpDims D, MlpW w, const flo
       const int64_t row = perm ? (int64_t)perm[b0 + r0 + rr] : b0 + r0 + rr;
       v = feat[row * D.n_in + c];
     }
-    s.X[it] = v;
+    s.X[rr * kXP + c] = v;
   }
   if (tid < kRows) {
     int c = 0;
@@ -394,72 +499,74 @@ __global__ void __launch_bounds__(kThr) k_mlp_train(MlpDims D, MlpW w, const flo
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     if (tid == 0) atomicAdd(loss_sum, v * inv_bs);
   }
-  // ---- W3, b3
-  for (int i = tid; i < kH * D.n_out; i += kThr) {
-    const int h = i / D.n_out, c = i - h * D.n_out;
-    float acc = 0.0f;
-#pragma unroll 8
-    for (int rr = 0; rr < kRows; ++rr) acc = fmaf(s.A2[rr * kH + h], s.D3[rr * kZP + c], acc);
-    atomicAdd(grad + o.W3 + i, acc);
+  // zero the delta columns between n_out and the next multiple of 8 (the
+  // K padding of the product with W3)
+  for (int it = tid; it < kRows * (pad8(D.n_out) - D.n_out); it += kThr) {
+    const int np = pad8(D.n_out) - D.n_out;
+    s.D3[(it / np) * kZP + D.n_out + it % np] = 0.0f;
   }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
+  // gW[m][n] += sum_r P(r, m) Q(r, n) over the tile's rows, 16 x 8 tiles of
+  // the m_n x n_n gradient block on the warps, added to grad[m * n_n + n]
+  auto weight_grad = [&](int m_n, int n_n, float* gdst, auto P, auto Q) {
+    const int mt = (m_n + 15) >> 4, nt = (n_n + 7) >> 3;
+    for (int tile = warp; tile < mt * nt; tile += kThr / 32) {
+      const int m0 = (tile % mt) * 16, n0 = (tile / mt) * 8;
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_tile<true>(c, m0, n0, kRows, [&](int m, int r) { return P(r, m); }, Q, lane);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int m = m0 + g + (q >> 1) * 8, n = n0 + 2 * t4 + (q & 1);
+        if (m < m_n && n < n_n) atomicAdd(gdst + (int64_t)m * n_n + n, c[q]);
+      }
+    }
+  };
+  // delta[r][n] = (sum_k Din[r][k] W[n][k]) * (act[r][n] > 0), n < 128:
+  // the product with the transposed FP16 weights
+  auto back_delta = [&](const float* Din, int din_pitch, int K, const __half* W, int w_pitch,
+                        const float* act, float* dout) {
+    for (int tile = warp; tile < (kH / 8) * (kRows / 16); tile += kThr / 32) {
+      const int m0 = (tile & 1) * 16, n0 = (tile >> 1) * 8;
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_tile<false>(
+          c, m0, n0, K, [&](int r, int k) { return Din[r * din_pitch + k]; },
+          [&](int k, int n) { return __half2float(W[n * w_pitch + k]); }, lane);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = m0 + g + (q >> 1) * 8, n = n0 + 2 * t4 + (q & 1);
+        dout[r * kAP + n] = act[r * kAP + n] > 0.0f ? c[q] : 0.0f;
+      }
+    }
+  };
+  // ---- W3, b3: A2^T D3
+  weight_grad(kH, D.n_out, grad + o.W3, [&](int r, int h) { return s.A2[r * kAP + h]; },
+              [&](int r, int c) { return s.D3[r * kZP + c]; });
   for (int c = tid; c < D.n_out; c += kThr) {
     float acc = 0.0f;
     for (int rr = 0; rr < kRows; ++rr) acc += s.D3[rr * kZP + c];
     atomicAdd(grad + o.b3 + c, acc);
   }
   // ---- delta of the second hidden layer: (D3 W3^T) * (z2 > 0)
-  const int h = tid & (kH - 1), rq = (tid >> 7) * 16;
-  {
-    float acc[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
-    for (int c = 0; c < D.n_out; ++c) {
-      const float wv = __half2float(s.w.W3[h * kP3 + c]);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) acc[q] = fmaf(s.D3[(rq + q) * kZP + c], wv, acc[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 16; ++q) s.D2[(rq + q) * kH + h] = s.A2[(rq + q) * kH + h] > 0.0f ? acc[q] : 0.0f;
-  }
+  back_delta(s.D3, kZP, pad8(D.n_out), s.w.W3, kP3, s.A2, s.D2);
   __syncthreads();
-  // ---- W2, b2
-  for (int i = tid; i < kH * kH; i += kThr) {
-    const int hp = i >> 7, hh = i & (kH - 1);
-    float acc = 0.0f;
-#pragma unroll 8
-    for (int rr = 0; rr < kRows; ++rr) acc = fmaf(s.A1[rr * kH + hp], s.D2[rr * kH + hh], acc);
-    atomicAdd(grad + o.W2 + i, acc);
-  }
+  // ---- W2, b2: A1^T D2
+  weight_grad(kH, kH, grad + o.W2, [&](int r, int i) { return s.A1[r * kAP + i]; },
+              [&](int r, int h) { return s.D2[r * kAP + h]; });
   if (tid < kH) {
     float acc = 0.0f;
-    for (int rr = 0; rr < kRows; ++rr) acc += s.D2[rr * kH + tid];
+    for (int rr = 0; rr < kRows; ++rr) acc += s.D2[rr * kAP + tid];
     atomicAdd(grad + o.b2 + tid, acc);
   }
   // ---- delta of the first hidden layer (into A2's space): (D2 W2^T) * (z1 > 0)
-  {
-    float acc[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
-    for (int c = 0; c < kH; ++c) {
-      const float wv = __half2float(s.w.W2[h * kP2 + c]);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) acc[q] = fmaf(s.D2[(rq + q) * kH + c], wv, acc[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 16; ++q) s.A2[(rq + q) * kH + h] = s.A1[(rq + q) * kH + h] > 0.0f ? acc[q] : 0.0f;
-  }
+  back_delta(s.D2, kAP, kH, s.w.W2, kP2, s.A1, s.A2);
   __syncthreads();
-  // ---- W1, b1
-  for (int i = tid; i < D.n_in * kH; i += kThr) {
-    const int ii = i >> 7, hh = i & (kH - 1);
-    float acc = 0.0f;
-#pragma unroll 8
-    for (int rr = 0; rr < kRows; ++rr) acc = fmaf(s.X[rr * kMaxIn + ii], s.A2[rr * kH + hh], acc);
-    atomicAdd(grad + o.W1 + i, acc);
-  }
+  // ---- W1, b1: X^T D1
+  weight_grad(D.n_in, kH, grad + o.W1, [&](int r, int i) { return s.X[r * kXP + i]; },
+              [&](int r, int h) { return s.A2[r * kAP + h]; });
   if (tid < kH) {
     float acc = 0.0f;
-    for (int rr = 0; rr < kRows; ++rr) acc += s.A2[rr * kH + tid];
+    for (int rr = 0; rr < kRows; ++rr) acc += s.A2[rr * kAP + tid];
     atomicAdd(grad + o.b1 + tid, acc);
   }
 }
