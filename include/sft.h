@@ -212,10 +212,16 @@ int32_t sft_plan_cs_shifts(sft_plan_t plan, int64_t* out, int32_t cap);
  * every signal's input pointer, result buffers and K from device tables
  * (no copies of the signals), captures the launches of the whole call into
  * one CUDA graph and replays it while the composition of the batch (the
- * shapes and how many signals of each) stays the same.  On the first call
- * of a shape an autotuner times the bin decoders at 2, 4, 8 and 16 CTAs
- * per SM on that call's data and keeps the fastest.  Not thread-safe; calls
- * on one context must not overlap on the GPU. */
+ * shapes and how many signals of each) stays the same.  Exactly sparse
+ * signals that fit one CTA run in one persistent kernel
+ * (sft_batch_set_persistent).  On the first call of a shape class (log2
+ * N/d, a_max, mode, precision) an autotuner times the group's launch
+ * sequence for every combination of FFT points per thread (8 or 16) and
+ * decoder CTAs per SM (2, 4, 8, 16) on that call's data and keeps the
+ * fastest for every later group of the class; the FFT points change the
+ * rounding of the FFT, so values may differ from a single-signal call in
+ * the last bits.  Not thread-safe; calls on one context must not overlap on
+ * the GPU. */
 typedef struct sft_batch_s* sft_batch_t;
 
 sft_status sft_batch_create(sft_batch_t* out);
@@ -237,9 +243,25 @@ sft_status sft_batch_set_options(sft_batch_t ctx, int32_t use_graph, int32_t aut
  * plans (allocates) and captures the graph. */
 sft_status sft_batch(sft_batch_t ctx, int64_t n_signals, const sft_params* params,
                      const void* const* x, const sft_result* results, void* stream);
-/* Groups of the last call, nodes of the current graph, shapes tuned so far. */
+/* Groups of the last call, nodes of the current graph, shape classes
+ * (log2 N/d, a_max, mode, precision) in the autotuner's table. */
 int32_t sft_batch_info(sft_batch_t ctx, int32_t* n_groups, int64_t* n_graph_nodes,
                        int32_t* n_tuned);
+/* The persistent kernel of a batch (not in the paper; Algorithm 1 per
+ * signal, unchanged).  With enable != 0 (the default) every exactly sparse
+ * signal that fits one CTA -- SFT_EXACT_ITER, SFT_MIXED, a_max <= 4,
+ * N/d <= 4096 -- is one item of a device work queue that a single launch of
+ * resident CTAs drains, largest signals first; each CTA runs the whole of
+ * Algorithm 1 for the signal it claimed (gather, FFTs, folds, SubFreq,
+ * decodes, compaction of the result) with the arithmetic of the per-shape
+ * launch sequence, so that results equal those of sft_exact on one signal.
+ * No CTA waits on another: the queue head is the only shared state.  ctas
+ * is the launch's CTA count (0: chosen by the autotuner on the first call
+ * that has such signals).  SFT_EINVAL for a NULL context or ctas < 0. */
+sft_status sft_batch_set_persistent(sft_batch_t ctx, int32_t enable, int32_t ctas);
+/* Signals of the last call that ran in the persistent kernel, and the CTAs
+ * of its launch. */
+int32_t sft_batch_persistent_info(sft_batch_t ctx, int64_t* n_signals, int32_t* ctas);
 
 /* Allocation-free variant of sft_exact (the paper has no counterpart: this
  * is a deployment interface).  Some callers cannot allocate device memory

@@ -241,6 +241,41 @@ struct sft_plan_s {
 };
 
 namespace sft {
+// One exactly sparse signal (ITER, mixed precision, a_max <= 4, N/d <= 4096)
+// of a heterogeneous batch, as the persistent batch kernel sees it: the
+// signal's input and result buffers, the shape and tables of its group's
+// plan, and its own slice of that plan's workspace.
+struct PSig {
+  const float2* x;
+  int64_t N, d0, M0;
+  int levels, log2M0;
+  double zero_tol, root_tol, res_tol;
+  const float4* tw;                  // e^{-2 pi i q / M0}, float-float
+  const double2* om_hi;              // omega tables (FP64 and float-float)
+  const double2* om_lo;
+  const float4* om_hi_ff;
+  const float4* om_lo_ff;
+  int om_lo_bits;
+  void* held[2];                     // float4 rows, held_elems each
+  int64_t held_elems;
+  uint8_t* T[2];
+  uint8_t* slot_cnt;
+  int64_t* slot_s;
+  float4* slot_p;
+  unsigned long long* ymax2;
+  int32_t* flags;
+  sft_result r;                      // one signal's result buffers
+};
+// Largest N/d the persistent kernel takes (one CTA's FFT: 256 threads x 16 points).
+constexpr int64_t kPersistMaxM = 4096;
+// Enqueue the persistent kernel over n signals (device descriptors `sigs`,
+// processed in the order `order`, items claimed through the device counter
+// `head`, which the call clears); `ctas` CTAs (0: as many as fit).
+cudaError_t launch_exact_persistent(const PSig* sigs, const int* order, int n, int* head, int ctas,
+                                    cudaStream_t st);
+// CTAs of the persistent kernel resident per SM (its launch bound).
+int persistent_ctas_per_sm();
+
 // Enqueue one sft_exact call (all launches) on `stream`.
 cudaError_t launch_exact(sft_plan_s* plan, int64_t n_signals, const void* x, int64_t x_stride,
                          const sft_result* r, cudaStream_t stream);

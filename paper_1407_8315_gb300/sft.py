@@ -50,7 +50,8 @@ EXPORTS = ["sft_params_default", "sft_plan_create", "sft_plan_destroy", "sft_pla
            "sft_last_cuda_error", "sft_plan_set_profiling", "sft_plan_stage_times",
            "sft_exact_noalloc", "sft_general", "sft_general_host", "sft_plan_cs_shifts",
            "sft_batch_create", "sft_batch_destroy", "sft_batch_set_options", "sft_batch",
-           "sft_batch_info", "sft_mlp_config_for", "sft_mlp_create", "sft_mlp_destroy",
+           "sft_batch_info", "sft_batch_set_persistent", "sft_batch_persistent_info",
+           "sft_mlp_config_for", "sft_mlp_create", "sft_mlp_destroy",
            "sft_mlp_param_count", "sft_mlp_get_params", "sft_mlp_set_params", "sft_mlp_features",
            "sft_mlp_forward", "sft_mlp_grad", "sft_mlp_train", "sft_plan_attach_mlp",
            "sft_exact_auto", "sft_alias_histogram", "sft_plan_set_sub_batches",
@@ -120,6 +121,9 @@ def load(build_if_missing: bool = False):
                               C.c_void_p]
     lib.sft_batch_info.argtypes = [C.c_void_p, P(C.c_int32), P(C.c_int64), P(C.c_int32)]
     lib.sft_batch_info.restype = C.c_int32
+    lib.sft_batch_set_persistent.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
+    lib.sft_batch_persistent_info.argtypes = [C.c_void_p, P(C.c_int64), P(C.c_int32)]
+    lib.sft_batch_persistent_info.restype = C.c_int32
     lib.sft_mlp_config_for.argtypes = [P(sft_params), P(sft_mlp_config)]
     lib.sft_mlp_create.argtypes = [P(sft_mlp_config), P(C.c_void_p)]
     lib.sft_mlp_destroy.argtypes = [C.c_void_p]
@@ -466,13 +470,26 @@ class Plan:
 class Batch:
     """A heterogeneous batch context (sft_batch_create / sft_batch)."""
 
-    def __init__(self, use_graph: bool = True, autotune: bool = True):
+    def __init__(self, use_graph: bool = True, autotune: bool = True, persistent: bool = True,
+                 persistent_ctas: int = 0):
         h = C.c_void_p()
         _check(load().sft_batch_create(C.byref(h)), "sft_batch_create")
         self.handle = h.value
         _check(load().sft_batch_set_options(C.c_void_p(self.handle), int(use_graph), int(autotune)),
                "sft_batch_set_options")
+        self.set_persistent(persistent, persistent_ctas)
         self._keep = None
+
+    def set_persistent(self, enable: bool = True, ctas: int = 0):
+        """Run the batch's exactly sparse signals that fit one CTA in the
+        persistent kernel (sft_batch_set_persistent); ctas 0: autotuned."""
+        _check(load().sft_batch_set_persistent(C.c_void_p(self.handle), int(bool(enable)),
+                                               int(ctas)), "sft_batch_set_persistent")
+
+    def persistent_info(self):
+        n, c = C.c_int64(), C.c_int32()
+        load().sft_batch_persistent_info(C.c_void_p(self.handle), C.byref(n), C.byref(c))
+        return {"signals": n.value, "ctas": c.value}
 
     @staticmethod
     def _ptr(a) -> int:
