@@ -266,7 +266,7 @@ struct PSig {
   int32_t* flags;
   sft_result r;                      // one signal's result buffers
 };
-// Largest N/d the persistent kernel takes (one CTA's FFT: 256 threads x 16 points).
+// Largest N/d the persistent kernel takes (one CTA's FFT: 128 threads x 32 points).
 constexpr int64_t kPersistMaxM = 4096;
 // Enqueue the persistent kernel over n signals (device descriptors `sigs`,
 // processed in the order `order`, items claimed through the device counter

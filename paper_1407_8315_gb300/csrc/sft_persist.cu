@@ -27,7 +27,10 @@
 
 namespace sft {
 
-constexpr int kPThreads = 256;
+// 128 threads per CTA and two CTAs per SM (255 registers each): while one
+// CTA's signal sits in a barrier-bound stage (few bins to decode), the
+// other's runs.
+constexpr int kPThreads = 128;
 
 // Block-wide exclusive scan of one int per thread (blockDim = kPThreads);
 // *total receives the sum.  Synchronises the block.
@@ -53,21 +56,21 @@ __device__ __forceinline__ int pblock_scan(int v, int* total) {
   return before;
 }
 
-// The forward FFT of buf[0..M) (float-float), M <= 4096, by the CTA's 256
+// The forward FFT of buf[0..M) (float-float), M <= 4096, by the CTA's 128
 // threads: radix-8 passes, then one radix-4 or radix-2 pass for the rest --
 // the pass sequence of the one-CTA FFT at 8 points per thread, each thread
-// here owning two radix-8 groups, so every output is rounded as there.
+// here owning four radix-8 groups, so every output is rounded as there.
 __device__ __forceinline__ void pcta_fft8(char* buf, int log2M, int log2Mt, const float4* tw,
                                           int tid) {
   const int M = 1 << log2M;
   int Ns = 1, rem = log2M;
   while (rem >= 3) {
-    stockham_pass<FF, 8, 16>(buf, M, Ns, log2Mt, tw, tid, kPThreads);
+    stockham_pass<FF, 8, 32>(buf, M, Ns, log2Mt, tw, tid, kPThreads);
     Ns <<= 3;
     rem -= 3;
   }
-  if (rem == 2) stockham_pass<FF, 4, 16>(buf, M, Ns, log2Mt, tw, tid, kPThreads);
-  if (rem == 1) stockham_pass<FF, 2, 16>(buf, M, Ns, log2Mt, tw, tid, kPThreads);
+  if (rem == 2) stockham_pass<FF, 4, 32>(buf, M, Ns, log2Mt, tw, tid, kPThreads);
+  if (rem == 1) stockham_pass<FF, 2, 32>(buf, M, Ns, log2Mt, tw, tid, kPThreads);
 }
 
 // The fold stage and the decode stage of level A - 1 for this thread's bins.
@@ -172,7 +175,7 @@ constexpr size_t kPSmemBytes = kPBufBytes + (size_t)kPersistMaxM * sizeof(int);
 
 // The persistent kernel: resident CTAs claim signals (largest first) until
 // the queue is empty; each runs Algorithm 1 for its signal alone.
-__global__ void __launch_bounds__(kPThreads, 1)
+__global__ void __launch_bounds__(kPThreads, 2)
     k_exact_persistent(const PSig* __restrict__ sigs, const int* __restrict__ order, int n,
                        int* __restrict__ head) {
   extern __shared__ __align__(16) char psmem[];
