@@ -208,10 +208,10 @@ WORKLOADS = {
                                plan_seed=11, mlp_rows=150_000, mlp_snrs=(10, 15, 20, 30)),
     "exact-2^27": W("exact-2^27", "SFT signals/sec at N=2^27,K=2^16 (exact)",
                     "exact-iter N=2^27 K=2^16 d=512 (M=2^18) a_m=4 c64",
-                    1 << 27, 1 << 16, 1 << 18, "iter", "mixed", 2, 4, quad=True),
+                    1 << 27, 1 << 16, 1 << 18, "iter", "mixed", 8, 4, quad=True),
     "general-2^27": W("general-2^27", "SFT signals/sec at N=2^27,K=2^16 noisy 30 dB; SNR_out",
                       "general N=2^27 K=2^16 d=512 (M=2^18) a_m=4 r=12 c64 SNR 30 dB",
-                      1 << 27, 1 << 16, 1 << 18, "general", "mixed", 1, 4, snrs=(30,), r=12,
+                      1 << 27, 1 << 16, 1 << 18, "general", "mixed", 4, 4, snrs=(30,), r=12,
                       plan_seed=2027),
 }
 HETERO = "hetero-4096"
@@ -474,6 +474,33 @@ def decode_flops(a: int, nm: int) -> float:
     return 8 * cma + 4 * a
 
 
+SVD_SWEEPS = 5  # nominal sweeps of the one-sided Jacobi SVD of a small Hankel matrix
+SP_ITERS = 2    # nominal Subspace Pursuit iterations per voted bin
+
+
+def svals_flops(n: int) -> float:
+    """Algorithmic FP64 flops of the singular values of one bin's n x n
+    Hankel matrix (Algorithm 2, Eq. (26)) by one-sided Jacobi: per column
+    pair two squared norms and one complex inner product of length n
+    (16 n flops) and the rotation of the pair (14 n), plus ~20 for the
+    angle; n (n - 1) / 2 pairs per sweep, SVD_SWEEPS sweeps."""
+    return SVD_SWEEPS * n * (n - 1) / 2 * (30 * n + 20)
+
+
+def solve_flops(a: int, d: int, r: int) -> float:
+    """Algorithmic FP64 flops of one voted bin with a_k = a (Algorithm 2,
+    Parts 3-4): the a x a locator solve ((2/3) a^3 + a^2 complex
+    multiply-adds), |P~| at the d candidates ((8a + 6) flops each, the
+    survey's count), and SP_ITERS Subspace Pursuit iterations on r
+    equations over at most 2a columns (correlation 2a r, normal matrix
+    (2a)^2 r, solve (2/3)(2a)^3, residual 2 a r complex multiply-adds);
+    8 real flops per complex multiply-add."""
+    loc = 8 * ((2 / 3) * a ** 3 + a ** 2)
+    cand = d * (8 * a + 6)
+    sp = SP_ITERS * 8 * (2 * a * r + (2 * a) ** 2 * r + (2 / 3) * (2 * a) ** 3 + 2 * a * r)
+    return loc + cand + sp
+
+
 def fold_bytes(level: int, K: int, M0: int) -> float:
     """Algorithmic bytes of one bin of level l's fold (a3-a4): the 2l held
     syndromes of the previous level at k and k + M read (4l x 16 B), the two
@@ -526,6 +553,17 @@ def roofline(wl, stages, B, clk, qlens=None):
                 g["kind"], g["unit"] = "fp64", "bin"
                 g["units"] += qlens[a - 1] * nl
                 g["fp64_flops"] += decode_flops(a, 2 * wl.a_max) * qlens[a - 1] * nl
+        elif name == "gen_svals" and qlens and len(qlens) == 3:
+            g["kind"], g["unit"] = "fp64", "bin"
+            g["units"] += qlens[0] * nl
+            g["fp64_flops"] += svals_flops(wl.a_max) * qlens[0] * nl
+        elif name == "gen_solve" and qlens and len(qlens) == 3:
+            # one-alias voted bins, and the others counted at a_k = 2 (a
+            # lower bound of their work)
+            g["kind"], g["unit"] = "fp64", "bin"
+            g["units"] += (qlens[1] + qlens[2]) * nl
+            g["fp64_flops"] += (solve_flops(1, wl.d, wl.r) * qlens[1] +
+                                solve_flops(2, wl.d, wl.r) * qlens[2]) * nl
         elif name.startswith("fold_l") and not wl.general:
             lvl = int(name[-1])
             g["kind"], g["unit"] = "mem", "bin"
@@ -839,7 +877,7 @@ def run_plan_workload(args, wl):
     ms_attr = timed_steps(torch, lambda: fn(x_dev, cap, out), n_attr, flush, stream)
     stages = plan.stage_times()
     # bins decoded per level / round in the last (one sub-batch) call
-    qlens = None if wl.general else plan.queue_lengths()
+    qlens = plan.queue_lengths()
     plan.set_profiling(False)
     plan.set_sub_batches(args.sub_batches)
 

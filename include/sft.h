@@ -423,14 +423,16 @@ sft_status sft_alias_histogram(const int64_t* supports, int64_t n_sets, int64_t 
  * issues (sft_exact / sft_general). */
 int32_t sft_plan_launches_per_call(sft_plan_t plan);
 
-/* Work counts of the plan's last exact call, for throughput models: the
- * number of (signal, bin) pairs queued for decoding at each level of
- * SFT_EXACT_ITER (Algorithm 1's active or unsolved bins, decoded with
- * a = l + 1), or entering each round a = 1..a_max of SFT_EXACT_FIXED,
- * summed over the call's signals and sub-batches.  Synchronises the
- * device; writes up to `cap` entries to out (host) and returns the number
- * of levels or rounds (0 for the general modes, -1 for a NULL plan or a
- * CUDA error). */
+/* Work counts of the plan's last call, for throughput models, summed over
+ * the call's signals and sub-batches: the number of (signal, bin) pairs
+ * queued for decoding at each level of SFT_EXACT_ITER (Algorithm 1's active
+ * or unsolved bins, decoded with a = l + 1), or entering each round
+ * a = 1..a_max of SFT_EXACT_FIXED; for SFT_GENERAL three counts: the bins
+ * whose Hankel singular values are computed (those the pruning bounds leave
+ * open), the voted bins with a_k = 1, the voted bins with a_k >= 2.
+ * Synchronises the device; writes up to `cap` entries to out (host) and
+ * returns their number (0 for SFT_GENERAL_UNPRUNED, -1 for a NULL plan or
+ * a CUDA error). */
 int32_t sft_plan_queue_lengths(sft_plan_t plan, int64_t* out, int32_t cap);
 
 /* Sub-batching.  A call on n signals may be split into S sub-batches of

@@ -320,15 +320,20 @@ int32_t sft_plan_launches_per_call(sft_plan_t P) { return P ? sft::launches_per_
 
 int32_t sft_plan_queue_lengths(sft_plan_t P, int64_t* out, int32_t cap) {
   if (!P || (cap > 0 && !out)) return -1;
-  if (sft::is_general_mode(P->p.mode)) return 0;
-  const int n = P->p.mode == SFT_EXACT_ITER ? P->levels : P->p.a_max;
+  if (P->p.mode == SFT_GENERAL_UNPRUNED) return 0;
+  const bool gen = P->p.mode == SFT_GENERAL;
+  const int n = gen ? 3 : P->p.mode == SFT_EXACT_ITER ? P->levels : P->p.a_max;
   if (cudaDeviceSynchronize() != cudaSuccess) return -1;
-  // each sub-batch keeps 16 counters; level l (round l + 1) is counter l
+  // each sub-batch keeps 16 counters: exact modes, level l (round l + 1) is
+  // counter l; general mode, counter 1 the bins whose singular values are
+  // computed, counters 0 and 2 the voted bins with one and with more aliases
+  static const int kGen[3] = {1, 0, 2};
   int32_t c[16 * sft::kMaxSub];
   if (cudaMemcpy(c, P->ws.qcount, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
   for (int i = 0; i < n && i < cap; ++i) {
+    const int ci = gen ? kGen[i] : i;
     int64_t t = 0;
-    for (int s = 0; s < P->last_sub; ++s) t += c[16 * s + i];
+    for (int s = 0; s < P->last_sub; ++s) t += c[16 * s + ci];
     out[i] = t;
   }
   return n;

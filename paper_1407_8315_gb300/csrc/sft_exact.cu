@@ -848,6 +848,10 @@ static void launch_iter(sft_plan_s* P, int64_t B, const void* x, int64_t x_strid
     int2* q = W.queue[l & 1];
     int* c = W.qcount + l;
     dim3 fgrid((unsigned)((M + kFoldThreads - 1) / kFoldThreads), (unsigned)B);
+    // fewer bins than a CTA's threads: signals packed densely over the grid
+    const int64_t n_flat = M < kFoldThreads ? B * M : 0;
+    const dim3 fgrid_fold =
+        n_flat > 0 ? dim3((unsigned)((n_flat + kFoldThreads - 1) / kFoldThreads), 1u) : fgrid;
     const int64_t maxq = B * M;
     const unsigned dgrid = (unsigned)std::max<int64_t>(
         1, std::min<int64_t>((maxq + kDecThreads - 1) / kDecThreads, (int64_t)P->dec_ctas_per_sm * nsm));
@@ -864,10 +868,10 @@ static void launch_iter(sft_plan_s* P, int64_t B, const void* x, int64_t x_strid
     }
     stage_begin(P, fnames[l], st);
     switch (l) {
-      case 0: k_iter_fold<F, 1><<<fgrid, kFoldThreads, 0, st>>>(g, q, c); break;
-      case 1: k_iter_fold<F, 2><<<fgrid, kFoldThreads, 0, st>>>(g, q, c); break;
-      case 2: k_iter_fold<F, 3><<<fgrid, kFoldThreads, 0, st>>>(g, q, c); break;
-      default: k_iter_fold<F, 4><<<fgrid, kFoldThreads, 0, st>>>(g, q, c); break;
+      case 0: k_iter_fold<F, 1><<<fgrid_fold, kFoldThreads, 0, st>>>(g, q, c, n_flat); break;
+      case 1: k_iter_fold<F, 2><<<fgrid_fold, kFoldThreads, 0, st>>>(g, q, c, n_flat); break;
+      case 2: k_iter_fold<F, 3><<<fgrid_fold, kFoldThreads, 0, st>>>(g, q, c, n_flat); break;
+      default: k_iter_fold<F, 4><<<fgrid_fold, kFoldThreads, 0, st>>>(g, q, c, n_flat); break;
     }
     stage_end(P, st);
     stage_begin(P, dnames[l], st);
@@ -927,14 +931,17 @@ static cudaError_t launch_one(sft_plan_s* P, int64_t B, const void* x, int64_t x
             reinterpret_cast<double2*>(r->val), r->count, r->unresolved, r->overflow, P->r_table,
             tiles,    tiles + B * n_tiles, n_tiles, single ? P->M0 : (int64_t)kFinTile};
   const dim3 fgrid((unsigned)n_tiles, (unsigned)B);
+  // one tile of fewer than 1024 bins: one thread per bin (whole warps)
+  const int fthr = single ? (int)std::min<int64_t>(1024, std::max<int64_t>(32, (P->M0 + 31) / 32 * 32))
+                          : 1024;
   stage_begin(P, "finalize", st);
   if (!single) k_fin_count<<<fgrid, 256, 0, st>>>(f);
   if (fp64)
-    P->r_on_host ? k_finalize<F64, true><<<fgrid, 1024, 0, st>>>(f)
-                 : k_finalize<F64, false><<<fgrid, 1024, 0, st>>>(f);
+    P->r_on_host ? k_finalize<F64, true><<<fgrid, fthr, 0, st>>>(f)
+                 : k_finalize<F64, false><<<fgrid, fthr, 0, st>>>(f);
   else
-    P->r_on_host ? k_finalize<FF, true><<<fgrid, 1024, 0, st>>>(f)
-                 : k_finalize<FF, false><<<fgrid, 1024, 0, st>>>(f);
+    P->r_on_host ? k_finalize<FF, true><<<fgrid, fthr, 0, st>>>(f)
+                 : k_finalize<FF, false><<<fgrid, fthr, 0, st>>>(f);
   stage_end(P, st);
   return cudaGetLastError();
 }

@@ -151,11 +151,23 @@ __device__ __forceinline__ bool fold_bin(const LevelArgs& g, int b, int64_t k) {
 }
 
 // Level l, phase 1, one thread per bin: fold_bin, and the active bins queued
-// for decoding.
+// for decoding.  Grid (bin tiles, signals); or, when a level has fewer bins
+// than a CTA has threads, n_flat = signals x bins packed densely over
+// blockIdx.x (thread f: signal f / M, bin f mod M), so that no CTA runs
+// mostly idle threads.
 template <class F, int A>
-__global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* queue, int* qcount) {
-  const int b = blockIdx.y;
-  const int64_t k = (int64_t)blockIdx.x * kFoldThreads + threadIdx.x;
+__global__ void __launch_bounds__(kFoldThreads) k_iter_fold(LevelArgs g, int2* queue, int* qcount,
+                                                            int64_t n_flat) {
+  int b;
+  int64_t k;
+  if (n_flat > 0) {
+    const int64_t f = (int64_t)blockIdx.x * kFoldThreads + threadIdx.x;
+    b = (int)(f / g.M);
+    k = f < n_flat ? f - (int64_t)b * g.M : g.M;  // past the end: no bin
+  } else {
+    b = blockIdx.y;
+    k = (int64_t)blockIdx.x * kFoldThreads + threadIdx.x;
+  }
   const bool active = k < g.M && fold_bin<F, A>(g, b, k);
   block_queue_push<kFoldThreads>(active, b, (int)k, queue, qcount);
 }

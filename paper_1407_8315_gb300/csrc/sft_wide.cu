@@ -298,7 +298,7 @@ template <class F, int A>
 void level_wide_a(sft_plan_s* P, const LevelArgs& g, int2* q, int* c, dim3 fgrid, unsigned wg,
                   cudaStream_t st, const char* fold_name, const char* dec_name) {
   stage_begin(P, fold_name, st);
-  k_iter_fold<F, A><<<fgrid, kFoldThreads, 0, st>>>(g, q, c);
+  k_iter_fold<F, A><<<fgrid, kFoldThreads, 0, st>>>(g, q, c, 0);
   stage_end(P, st);
   stage_begin(P, dec_name, st);
   k_iter_decode_wide<F, A><<<wg, 32 * kWideWarps, 0, st>>>(g, q, c);

@@ -86,6 +86,22 @@ def test_decode_flops_grow_with_the_alias_count():
     assert 1700 < bench.decode_flops(4, 8) < 2000
 
 
+def test_general_path_solvers_have_flop_models():
+    """The general path's singular values and per-bin solves are reported
+    against the FP64 peak on their work per bin (bins from the plan's
+    counts: SVD bins, voted one-alias bins, voted multi-alias bins)."""
+    wl = bench.WORKLOADS["general-2^27"]
+    stages = {"gen_svals": (7.0, 1), "gen_solve": (6.0, 1), "gather_fft_random": (0.4, 1)}
+    roof = bench.roofline(wl, stages, 4, {"sm_mhz": 2070.0}, [800000, 200000, 50000])
+    assert roof["kernel"] == "k_gen_svals" and roof["bound"] == "alu"
+    assert roof["achieved"] == pytest.approx(bench.svals_flops(4) * 800000 / 7e-3 / 1e12)
+    sol = roof["by_kernel"]["k_gen_solve"]
+    assert sol["bound"] == "alu" and sol["frac"] > 0
+    # 4 x 4 Hankel, 5 sweeps of 6 pairs at 140 flops
+    assert bench.svals_flops(4) == 5 * 6 * 140
+    assert bench.solve_flops(1, 32, 9) > 32 * 14
+
+
 def test_ncu_traffic_scales_with_the_signals():
     import json
     import os
