@@ -61,37 +61,46 @@ __global__ void __launch_bounds__(8192 / PTS) k_gather_fft(
     const int n = tid + i * nthr;
     if (n < M) v[i] = __ldg(xs + (((int64_t)n * d + shift) & (N - 1)));
   }
+  int done = 0;
   if (M == PTS * nthr) {
     // the first pass from registers (the gathered samples are its inputs)
     first_pass_regs<F, PTS>(smem, M, v, tid);
-    __syncthreads();
-    cta_fft<F, PTS>(smem, log2M, log2Mt, tw, tid, nthr, 1);
+    done = 1;
   } else {
 #pragma unroll
     for (int i = 0; i < PTS; ++i) {
       const int n = tid + i * nthr;
       if (n < M) F::st(smem, M, n, F::from_in(v[i]));
     }
-    __syncthreads();
-    cta_fft<F, PTS>(smem, log2M, log2Mt, tw, tid, nthr);
   }
+  __syncthreads();
   Out* o = reinterpret_cast<Out*>(out_v) + (int64_t)b * out_sig + (int64_t)(row0 + js) * out_row;
   double lmax = 0.0;
-  if constexpr (std::is_same<F, F64>::value) {
-    for (int k = tid; k < M; k += nthr) {
-      const double2 w = F::out(F::ld(smem, M, k), (double)dscale);
+  float fmax_hi = 0.0f;
+  // Y[k] = d FFT(x)[k] to the held rows (and max |Y|^2 for the zero
+  // threshold), written by the FFT's last pass directly
+  auto emit = [&](int k, const typename F::V& val) {
+    if constexpr (std::is_same<F, F64>::value) {
+      const double2 w = F::out(val, (double)dscale);
       o[k] = w;
       lmax = fmax(lmax, w.x * w.x + w.y * w.y);
-    }
-  } else {
-    float fmax_hi = 0.0f;
-    for (int k = tid; k < M; k += nthr) {
-      const float4 w = F::out(F::ld(smem, M, k), (float)dscale);
+    } else {
+      const float4 w = F::out(val, (float)dscale);
       o[k] = w;
       fmax_hi = fmaxf(fmax_hi, F::out_norm_hi(w));
     }
-    lmax = (double)fmax_hi;
+  };
+  // (below 256 points a CTA is one warp and the separate, coalesced output
+  // loop measured faster)
+  if (M < 256 || !cta_fft_out<F, PTS>(smem, log2M, log2Mt, tw, tid, nthr, done, emit)) {
+    if (M < 256) {
+      cta_fft<F, PTS>(smem, log2M, log2Mt, tw, tid, nthr, done);
+      __syncthreads();
+    }
+    // the transform's result is in smem
+    for (int k = tid; k < M; k += nthr) emit(k, F::ld(smem, M, k));
   }
+  if constexpr (!std::is_same<F, F64>::value) lmax = (double)fmax_hi;
   if (ymax2 != nullptr && shift == 0) {
     // block max of |Y_{d,0}|^2 -> per-signal atomic max on the bit pattern
     // (non-negative doubles order like their unsigned bit patterns)
