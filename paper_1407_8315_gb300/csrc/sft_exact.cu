@@ -253,14 +253,19 @@ __global__ void __launch_bounds__(8192 / PTS) k_fft4_cols(
   // the column's first pass from registers (tpg = M1 / PTS)
   first_pass_regs<F, PTS>(buf, M1, v, t);
   __syncthreads();
-  cta_fft<F, PTS>(buf, log2M1, log2Mt, tw, t, tpg, 1);
-  // twiddle e^{-2 pi i n2 k1 / M} (table of e^{-2 pi i q / Mt}, Mt >= M)
-  for (int i = 0; i < PTS; ++i) {
-    const int k1 = t + i * tpg;
+  // the twiddle e^{-2 pi i n2 k1 / M} (table of e^{-2 pi i q / Mt}, Mt >= M)
+  // applied by the column FFT's last pass as it stores
+  auto twiddled = [&](int k1, const typename F::V& val) {
     const int64_t q = ((int64_t)(c0 + g) * k1) & ((int64_t(1) << log2M) - 1);
-    F::st(buf, M1, k1, F::mul_tw(F::ld(buf, M1, k1), __ldg(tw + (q << (log2Mt - log2M)))));
+    F::st(buf, M1, k1, F::mul_tw(val, __ldg(tw + (q << (log2Mt - log2M)))));
+  };
+  if (!cta_fft_st<F, PTS>(buf, log2M1, log2Mt, tw, t, tpg, 1, twiddled)) {
+    for (int i = 0; i < PTS; ++i) {
+      const int k1 = t + i * tpg;
+      twiddled(k1, F::ld(buf, M1, k1));
+    }
+    __syncthreads();
   }
-  __syncthreads();
   typename F::Out* Wo = W + (int64_t)b * w_sig + (int64_t)js * ((int64_t)M1 * M2);
   for (int idx = tid; idx < CB * M1; idx += blockDim.x) {
     const int k1 = idx / CB, c = idx % CB;

@@ -127,6 +127,43 @@ __device__ __forceinline__ void stockham_pass_out(char* buf, int M, int Ns, int 
   }
 }
 
+// stockham_pass whose stores go through st(index, value) (which must store
+// into buf, e.g. after a per-point multiply): loads, barrier, st, barrier.
+template <class F, int R, int PTS, class St>
+__device__ __forceinline__ void stockham_pass_st(char* buf, int M, int Ns, int log2Mt,
+                                                 const typename F::Tw* __restrict__ tw, int tid,
+                                                 int nthr, St&& st) {
+  constexpr int G = PTS / R;
+  const int groups = M / R;
+  typename F::V v[G][R];
+  const int twstep_log = log2Mt - (31 - __clz(Ns * R));
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int j = tid + g * nthr;
+    if (j < groups) {
+      const int kk = j & (Ns - 1);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        v[g][r] = F::ld(buf, M, j + r * groups);
+        if (r > 0 && Ns > 1) v[g][r] = F::mul_tw(v[g][r], __ldg(tw + ((r * kk) << twstep_log)));
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int j = tid + g * nthr;
+    if (j < groups) {
+      const int kk = j & (Ns - 1);
+      dft_reg<F, R>(v[g]);
+      const int base = (j - kk) * R + kk;
+#pragma unroll
+      for (int r = 0; r < R; ++r) st(base + r * Ns, v[g][r]);
+    }
+  }
+  __syncthreads();
+}
+
 // The first radix-PTS pass (Ns = 1: no inter-pass twiddles) straight from
 // registers: with nthr = M / PTS, the inputs of thread tid's group are the
 // samples tid + r nthr, r < PTS, which are exactly the ones it gathered, so
@@ -168,6 +205,37 @@ __device__ void cta_fft(char* buf, int log2M, int log2Mt, const typename F::Tw* 
   if (rem == 1) stockham_pass<F, 2, PTS>(buf, M, Ns, log2Mt, tw, tid, nthr);
 }
 
+// cta_fft whose last pass stores through st(index, value) (into buf); false,
+// having run no pass, when no pass is left after the first `done`.
+template <class F, int PTS, class St>
+__device__ bool cta_fft_st(char* buf, int log2M, int log2Mt, const typename F::Tw* __restrict__ tw,
+                           int tid, int nthr, int done, St&& st) {
+  static_assert(PTS == 16 || PTS == 8, "16 or 8 points per thread");
+  constexpr int LP = PTS == 16 ? 4 : 3;
+  const int M = 1 << log2M;
+  int Ns = 1 << (LP * done);
+  int rem = log2M - LP * done;
+  if (rem <= 0) return false;
+  while (rem > LP) {
+    stockham_pass<F, PTS, PTS>(buf, M, Ns, log2Mt, tw, tid, nthr);
+    Ns <<= LP;
+    rem -= LP;
+  }
+  if (rem == LP) {
+    if constexpr (PTS == 16)
+      stockham_pass_st<F, 16, PTS>(buf, M, Ns, log2Mt, tw, tid, nthr, st);
+    else
+      stockham_pass_st<F, 8, PTS>(buf, M, Ns, log2Mt, tw, tid, nthr, st);
+  } else if (rem == 3) {
+    stockham_pass_st<F, 8, PTS>(buf, M, Ns, log2Mt, tw, tid, nthr, st);
+  } else if (rem == 2) {
+    stockham_pass_st<F, 4, PTS>(buf, M, Ns, log2Mt, tw, tid, nthr, st);
+  } else {
+    stockham_pass_st<F, 2, PTS>(buf, M, Ns, log2Mt, tw, tid, nthr, st);
+  }
+  return true;
+}
+
 // cta_fft whose last pass hands each output to out(index, value) instead of
 // storing it (the same pass sequence and arithmetic).  Returns false, having
 // run no pass, when no pass is left after the first `done` (the transform is
@@ -189,7 +257,7 @@ __device__ bool cta_fft_out(char* buf, int log2M, int log2Mt, const typename F::
   // rem = LP, or the remainder pass; with PTS = 16 a remainder of 3 is one
   // radix-8 pass
   if (rem == LP) {
-    if (rem == 4 && PTS == 16)
+    if constexpr (PTS == 16)
       stockham_pass_out<F, 16, PTS>(buf, M, Ns, log2Mt, tw, tid, nthr, out);
     else
       stockham_pass_out<F, 8, PTS>(buf, M, Ns, log2Mt, tw, tid, nthr, out);
