@@ -251,11 +251,29 @@ struct Store<F64> {
   __device__ static __forceinline__ double2 from_d(cdbl c) { return make_double2(c.x, c.y); }
   __device__ static __forceinline__ double2 from_d_small(cdbl c) { return make_double2(c.x, c.y); }
 };
+// float -> double by moving the bits (sign, exponent rebiased by
+// 1023 - 127 = 896, significand shifted by 52 - 23 = 29): exact, and on the
+// integer pipes -- a conversion instruction occupies GB300's scarce FP64
+// unit.  Zeros keep their sign; subnormals, infinities and NaNs take the
+// conversion instruction.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+  if (e == 0u || e == 0xFFu) {
+    if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sign);
+    return (double)f;
+  }
+  return __longlong_as_double(
+      (long long)(sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29)));
+}
+
 template <>
 struct Store<FF> {
   typedef float4 T;
+  // hi + lo in FP64: both parts converted exactly, one FP64 addition each
   __device__ static __forceinline__ cdbl to_d(float4 v) {
-    return cdbl{(double)v.x + (double)v.y, (double)v.z + (double)v.w};
+    return cdbl{f2d_exact(v.x) + f2d_exact(v.y), f2d_exact(v.z) + f2d_exact(v.w)};
   }
   __device__ static __forceinline__ float4 from_d(cdbl c) {
     const float xh = (float)c.x, yh = (float)c.y;
