@@ -302,12 +302,17 @@ __device__ __forceinline__ float ff_norm(const FF::V& v) {
   const float x = ff_re(v), y = ff_im(v);
   return x * x + y * y;
 }
-// x <= lim decided in FP32 unless within 1e-5 of lim (relative): -1 there
-__device__ __forceinline__ int ff_le(float x, double lim) {
-  if (!(x < 1e36f) || !(lim < 1e36)) return -1;
-  if (fabs((double)x - lim) <= 1e-5 * lim) return -1;
-  return (double)x <= lim ? 1 : 0;
+// x <= lim decided in FP32 unless within 1e-5 of lim (relative): -1 there.
+// x carries FP32 rounding of its FP64 counterpart and lim is rounded once
+// to float, both ~1e-7 relative, far inside the 1e-5 margin, so outside it
+// the decision is the FP64 one.  One conversion is the only FP64-pipe
+// instruction.
+__device__ __forceinline__ int ff_le_f(float x, float lf) {
+  if (!(x < 1e36f) || !(lf < 1e36f)) return -1;
+  if (fabsf(x - lf) <= 1e-5f * lf) return -1;
+  return x <= lf ? 1 : 0;
 }
+__device__ __forceinline__ int ff_le(float x, double lim) { return ff_le_f(x, (float)lim); }
 
 template <int nm>
 __device__ __forceinline__ int decode_a1_ff(const float4* raw, int64_t k, const BinGeom& g,
@@ -359,7 +364,7 @@ __device__ __forceinline__ int decode_a1_ff(const float4* raw, int64_t k, const 
     mmax2 = fmaxf(mmax2, ff_norm(mi));
     rmax2 = fmaxf(rmax2, ff_norm(r[i]));
   }
-  const int fits = ff_le(rmax2, tol.res2 * (double)mmax2);
+  const int fits = ff_le_f(rmax2, (float)tol.res2 * mmax2);
   if (fits <= 0) return fits;
   *p_ff = FF::to4(p);
 #pragma unroll
@@ -587,7 +592,7 @@ __device__ __forceinline__ int decode_a2_ff(const float4* raw, int64_t k, const 
     mmax2 = fmaxf(mmax2, ff_norm(mi));
     rmax2 = fmaxf(rmax2, ff_norm(r[i]));
   }
-  const int fits = ff_le(rmax2, tol.res2 * (double)mmax2);
+  const int fits = ff_le_f(rmax2, (float)tol.res2 * mmax2);
   if (fits <= 0) return fits;
   p_ff[0] = FF::to4(p0);
   p_ff[1] = FF::to4(p1);

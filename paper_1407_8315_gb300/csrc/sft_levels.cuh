@@ -31,16 +31,35 @@ struct LevelArgs {
   double zero_tol, root_tol, res_tol;
   OmegaTab om;
   OmegaTabFF omff;
+  float zero_tol2_f;  // zero_tol^2 rounded to float
 };
 
+// The zero threshold theta^2 = zero_tol^2 max_k |Y_{d,0}[k]|^2 as a float,
+// off the FP64 pipe: the max is stored as the double of an FP32 value (the
+// FFT's running max of FP32 norms), so its bits move back to the float
+// exactly; zero_tol^2 comes rounded to float.  The product is within two
+// ulps of the float rounding of the FP64 threshold, far inside above_ff's
+// 1e-4 margin.
+__device__ __forceinline__ float theta2_f(float zero_tol2_f, unsigned long long ymax_bits) {
+  const uint32_t e = (uint32_t)(ymax_bits >> 52) & 0x7FFu;
+  if (e == 0u) return 0.0f;
+  if (e < 897u || e > 1150u)  // outside the normal float range: convert
+    return zero_tol2_f * (float)__longlong_as_double((long long)ymax_bits);
+  const uint32_t fb = ((uint32_t)(ymax_bits >> 63) << 31) | ((e - 896u) << 23) |
+                      (uint32_t)((ymax_bits >> 29) & 0x7FFFFFu);
+  return zero_tol2_f * __uint_as_float(fb);
+}
+
 // |m|^2 > theta^2 decided from the float-float hi parts when they are
-// clearly on one side (relative error of the hi-part norm < 1e-6), in FP64
-// otherwise -- the same decision the FP64 comparison takes.
-__device__ __forceinline__ bool above_ff(const FF::V& m, double theta2) {
+// clearly on one side (relative error of the hi-part norm < 1e-6; t2 the
+// float threshold), in FP64 otherwise -- the same decision the FP64
+// comparison takes.  The FP64 threshold is formed only in that rare case.
+__device__ __forceinline__ bool above_ff(const FF::V& m, float t2, double zero_tol,
+                                         unsigned long long ymax_bits) {
   const float nh = m.rh * m.rh + m.ih * m.ih;
-  const float t2 = (float)theta2;
   if (nh > t2 * 1.0001f) return true;
   if (nh < t2 * 0.9999f) return false;
+  const double theta2 = zero_tol * zero_tol * __longlong_as_double((long long)ymax_bits);
   const double x = (double)m.rh + (double)m.rl, y = (double)m.ih + (double)m.il;
   return x * x + y * y > theta2;
 }
@@ -65,7 +84,7 @@ __device__ __forceinline__ bool fold_bin(const LevelArgs& g, int b, int64_t k) {
     const T* sp = reinterpret_cast<const T*>(g.slot_p) + (int64_t)b * M0 * kSlots;
     uint8_t t = 0;
     if (l > 0) t = (uint8_t)(g.Tprev[(int64_t)b * M0 + k] | g.Tprev[(int64_t)b * M0 + k + M]);
-    const double theta2 = g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]);
+    const unsigned long long ymax_bits = g.ymax2[b];
     const int64_t nsub = M0 / M;
     if constexpr (std::is_same<F, F64>::value) {
       cdbl m[nm];
@@ -91,6 +110,7 @@ __device__ __forceinline__ bool fold_bin(const LevelArgs& g, int b, int64_t k) {
           }
         }
       }
+      const double theta2 = g.zero_tol * g.zero_tol * __longlong_as_double((long long)ymax_bits);
       active = t || norm2(m[2 * l]) > theta2 || norm2(m[2 * l + 1]) > theta2;
       // the folded rows are new; the two new shifts change only when peeled
 #pragma unroll
@@ -137,7 +157,9 @@ __device__ __forceinline__ bool fold_bin(const LevelArgs& g, int b, int64_t k) {
           }
         }
       }
-      active = t || above_ff(m[2 * l], theta2) || above_ff(m[2 * l + 1], theta2);
+      const float t2 = theta2_f(g.zero_tol2_f, ymax_bits);
+      active = t || above_ff(m[2 * l], t2, g.zero_tol, ymax_bits) ||
+               above_ff(m[2 * l + 1], t2, g.zero_tol, ymax_bits);
 #pragma unroll
       for (int j = 0; j < 2 * l; ++j) cur[j * M + k] = FF::to4(m[j]);
       if (peeled) {
@@ -311,6 +333,7 @@ struct FixedArgs {
   double zero_tol, root_tol, res_tol;
   OmegaTab om;
   OmegaTabFF omff;  // float-float omega tables (mixed path)
+  float zero_tol2_f;  // zero_tol^2 rounded to float
 };
 
 // activity of every bin (any of the 2 a_max syndromes above theta)
@@ -323,13 +346,16 @@ __global__ void __launch_bounds__(kFoldThreads) k_fixed_scan(FixedArgs g, int2* 
   bool active = false;
   if (k < M) {
     const T* Y = reinterpret_cast<const T*>(g.Y) + (int64_t)b * g.held_elems;
-    const double theta2 = g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]);
+    const unsigned long long ymax_bits = g.ymax2[b];
 #pragma unroll
     for (int j = 0; j < NM; ++j) {
-      if constexpr (std::is_same<F, F64>::value)
+      if constexpr (std::is_same<F, F64>::value) {
+        const double theta2 = g.zero_tol * g.zero_tol * __longlong_as_double((long long)ymax_bits);
         active = active || norm2(Store<F>::to_d(Y[j * M + k])) > theta2;
-      else
-        active = active || above_ff(FF::from4(Y[j * M + k]), theta2);
+      } else {
+        active = active || above_ff(FF::from4(Y[j * M + k]), theta2_f(g.zero_tol2_f, ymax_bits),
+                                    g.zero_tol, ymax_bits);
+      }
     }
     g.T[(int64_t)b * M + k] = 0;
   }
