@@ -199,6 +199,11 @@ struct BinGeom {
 struct Tol2 {
   double theta2, root2, res2;
 };
+// The same thresholds rounded to float, for the float-float decoders (their
+// decisions keep margins far wider than the rounding).
+struct Tol2f {
+  float theta2, root2, res2;
+};
 
 // Location of root z: the member k + tM of S_k nearest to it, i.e.
 // t = round((arg(z) N / (2 pi) - k) / M) mod d.  The FP32 estimate is exact
@@ -316,7 +321,7 @@ __device__ __forceinline__ int ff_le(float x, double lim) { return ff_le_f(x, (f
 
 template <int nm>
 __device__ __forceinline__ int decode_a1_ff(const float4* raw, int64_t k, const BinGeom& g,
-                                            const Tol2& tol, const OmegaTabFF& omff, int64_t* s,
+                                            const Tol2f& tol, const OmegaTabFF& omff, int64_t* s,
                                             float4* p_ff, float4* res_out) {
   const FF::V m0 = FF::from4(raw[0]), m1 = FF::from4(raw[1]);
   const float m0x = ff_re(m0), m0y = ff_im(m0), m1x = ff_re(m1), m1y = ff_im(m1);
@@ -337,7 +342,7 @@ __device__ __forceinline__ int decode_a1_ff(const float4* raw, int64_t k, const 
   s[0] = k + t * g.M;
   const FF::V w = omega_ff(omff, s[0]);
   const float dx = zx - ff_re(w), dy = zy - ff_im(w);
-  const float dz = dx * dx + dy * dy, r2 = (float)tol.root2;
+  const float dz = dx * dx + dy * dy, r2 = tol.root2;
   if (fabsf(dz - r2) <= 1e-4f * r2) return -1;
   if (!(dz <= r2)) return 0;
   // least squares over the nm equations: p = (1/nm) sum_i conj(w^i) m_i
@@ -350,7 +355,7 @@ __device__ __forceinline__ int decode_a1_ff(const float4* raw, int64_t k, const 
   }
   constexpr float inv_nm = 1.0f / (float)nm;  // a power of two: exact
   const FF::V p{acc.rh * inv_nm, acc.rl * inv_nm, acc.ih * inv_nm, acc.il * inv_nm};
-  const int small = ff_le(ff_norm(p), tol.theta2);
+  const int small = ff_le_f(ff_norm(p), tol.theta2);
   if (small != 0) return small < 0 ? -1 : 0;
   // residual r_i = m_i - p w^i over all equations
   float mmax2 = 0.0f, rmax2 = 0.0f;
@@ -364,7 +369,7 @@ __device__ __forceinline__ int decode_a1_ff(const float4* raw, int64_t k, const 
     mmax2 = fmaxf(mmax2, ff_norm(mi));
     rmax2 = fmaxf(rmax2, ff_norm(r[i]));
   }
-  const int fits = ff_le_f(rmax2, (float)tol.res2 * mmax2);
+  const int fits = ff_le_f(rmax2, tol.res2 * mmax2);
   if (fits <= 0) return fits;
   *p_ff = FF::to4(p);
 #pragma unroll
@@ -478,7 +483,7 @@ __device__ __forceinline__ float root_polish(const FF::V* c, FF::V& z, float con
 // Returns 1 on success (s ascending, p_ff, res_out filled), 0 on failure.
 template <int nm>
 __device__ __forceinline__ int decode_a2_ff(const float4* raw, int64_t k, const BinGeom& g,
-                                            const Tol2& tol, const OmegaTabFF& omff, int64_t* s,
+                                            const Tol2f& tol, const OmegaTabFF& omff, int64_t* s,
                                             float4* p_ff, float4* res_out) {
   FF::V m[4];
 #pragma unroll
@@ -512,7 +517,7 @@ __device__ __forceinline__ int decode_a2_ff(const float4* raw, int64_t k, const 
   FF::V w[2];
   const FF::V cc[2] = {c0, c1};
   const float cond = sqrtf(amax2 / fminf(best, n22));
-  const float r2 = (float)tol.root2;
+  const float r2 = tol.root2;
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     const float err = root_polish<2>(cc, z[j], cond);
@@ -574,7 +579,7 @@ __device__ __forceinline__ int decode_a2_ff(const float4* raw, int64_t k, const 
   const FF::V p1 = cmk(fr_div(re_of(num1), det), fr_div(im_of(num1), det));
   const FF::V t0 = FF::sub(g0, FF::mulv(S, p1));
   const FF::V p0 = cmk(fr_div(re_of(t0), fnm), fr_div(im_of(t0), fnm));
-  const int small0 = ff_le(ff_norm(p0), tol.theta2), small1 = ff_le(ff_norm(p1), tol.theta2);
+  const int small0 = ff_le_f(ff_norm(p0), tol.theta2), small1 = ff_le_f(ff_norm(p1), tol.theta2);
   if (small0 < 0 || small1 < 0) return -1;
   if (small0 || small1) return 0;
   // the residual over all equations
@@ -592,7 +597,7 @@ __device__ __forceinline__ int decode_a2_ff(const float4* raw, int64_t k, const 
     mmax2 = fmaxf(mmax2, ff_norm(mi));
     rmax2 = fmaxf(rmax2, ff_norm(r[i]));
   }
-  const int fits = ff_le_f(rmax2, (float)tol.res2 * mmax2);
+  const int fits = ff_le_f(rmax2, tol.res2 * mmax2);
   if (fits <= 0) return fits;
   p_ff[0] = FF::to4(p0);
   p_ff[1] = FF::to4(p1);

@@ -762,7 +762,8 @@ static void launch_fixed(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
               W.slot_s, W.slot_p, W.ymax2, W.flags, P->p.zero_tol, P->p.root_tol,
               P->p.res_tol, om,
               OmegaTabFF{P->tab.om_hi_ff, P->tab.om_lo_ff, P->tab.om_lo_bits, P->p.N - 1},
-              (float)(P->p.zero_tol * P->p.zero_tol)};
+              (float)(P->p.zero_tol * P->p.zero_tol), (float)(P->p.root_tol * P->p.root_tol),
+              (float)(P->p.res_tol * P->p.res_tol)};
   if (P->p.a_max > 4) {
     // a_max = 8: 16 syndromes, rounds 5-8 by the warp-per-bin decoder
     launch_fixed_wide(P, B, g, nsm, st);
@@ -859,7 +860,8 @@ static void launch_iter(sft_plan_s* P, int64_t B, const void* x, int64_t x_strid
     }
     LevelArgs g{P->p.N, M, d, P->M0, prev, cur, W.held_elems, W.T[(l + 1) & 1], W.T[l & 1],
                 W.slot_cnt, W.slot_s, W.slot_p, W.ymax2, W.flags, P->p.zero_tol,
-                P->p.root_tol, P->p.res_tol, om, omff, (float)(P->p.zero_tol * P->p.zero_tol)};
+                P->p.root_tol, P->p.res_tol, om, omff, (float)(P->p.zero_tol * P->p.zero_tol),
+                (float)(P->p.root_tol * P->p.root_tol), (float)(P->p.res_tol * P->p.res_tol)};
     int2* q = W.queue[l & 1];
     int* c = W.qcount + l;
     dim3 fgrid((unsigned)((M + kFoldThreads - 1) / kFoldThreads), (unsigned)B);

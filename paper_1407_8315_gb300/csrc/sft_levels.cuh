@@ -31,7 +31,7 @@ struct LevelArgs {
   double zero_tol, root_tol, res_tol;
   OmegaTab om;
   OmegaTabFF omff;
-  float zero_tol2_f;  // zero_tol^2 rounded to float
+  float zero_tol2_f, root_tol2_f, res_tol2_f;  // the squared tolerances rounded to float
 };
 
 // The zero threshold theta^2 = zero_tol^2 max_k |Y_{d,0}[k]|^2 as a float,
@@ -212,8 +212,10 @@ __device__ __forceinline__ void decode_level_bin(const LevelArgs& g, int b, int6
   {
     const int64_t M = g.M, M0 = g.M0;
     T* cur = reinterpret_cast<T*>(g.cur) + (int64_t)b * g.held_elems;
-    const Tol2 tol{g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]),
+    const unsigned long long ymax_bits = g.ymax2[b];
+    const Tol2 tol{g.zero_tol * g.zero_tol * __longlong_as_double((long long)ymax_bits),
                    g.root_tol * g.root_tol, g.res_tol * g.res_tol};
+    const Tol2f tolf{theta2_f(g.zero_tol2_f, ymax_bits), g.root_tol2_f, g.res_tol2_f};
     T raw[nm];
 #pragma unroll
     for (int j = 0; j < nm; ++j) raw[j] = cur[j * M + k];
@@ -229,9 +231,9 @@ __device__ __forceinline__ void decode_level_bin(const LevelArgs& g, int b, int6
     if constexpr (std::is_same<F, FF>::value && A <= 2) {
       float4 pf[A];
       if constexpr (A == 1)
-        fast = decode_a1_ff<nm>(raw, k, geom, tol, g.omff, s, pf, res);
+        fast = decode_a1_ff<nm>(raw, k, geom, tolf, g.omff, s, pf, res);
       else
-        fast = decode_a2_ff<nm>(raw, k, geom, tol, g.omff, s, pf, res);
+        fast = decode_a2_ff<nm>(raw, k, geom, tolf, g.omff, s, pf, res);
       if (fast == 1) {
 #pragma unroll
         for (int j = 0; j < A; ++j)
@@ -333,7 +335,7 @@ struct FixedArgs {
   double zero_tol, root_tol, res_tol;
   OmegaTab om;
   OmegaTabFF omff;  // float-float omega tables (mixed path)
-  float zero_tol2_f;  // zero_tol^2 rounded to float
+  float zero_tol2_f, root_tol2_f, res_tol2_f;  // the squared tolerances rounded to float
 };
 
 // activity of every bin (any of the 2 a_max syndromes above theta)
@@ -382,8 +384,10 @@ __global__ void __launch_bounds__(kDecThreads) k_fixed_round(FixedArgs g, const 
       b = q.x;
       k = q.y;
       const T* Y = reinterpret_cast<const T*>(g.Y) + (int64_t)b * g.held_elems;
-      const Tol2 tol{g.zero_tol * g.zero_tol * __longlong_as_double((long long)g.ymax2[b]),
+      const unsigned long long ymax_bits = g.ymax2[b];
+      const Tol2 tol{g.zero_tol * g.zero_tol * __longlong_as_double((long long)ymax_bits),
                      g.root_tol * g.root_tol, g.res_tol * g.res_tol};
+      const Tol2f tolf{theta2_f(g.zero_tol2_f, ymax_bits), g.root_tol2_f, g.res_tol2_f};
       T raw[NM];
 #pragma unroll
       for (int j = 0; j < NM; ++j) raw[j] = Y[j * M + k];
@@ -394,9 +398,9 @@ __global__ void __launch_bounds__(kDecThreads) k_fixed_round(FixedArgs g, const 
       if constexpr (std::is_same<F, FF>::value && A <= 2) {
         float4 pf[A], res[NM];
         if constexpr (A == 1)
-          fast = decode_a1_ff<NM>(raw, k, geom, tol, g.omff, s, pf, res);
+          fast = decode_a1_ff<NM>(raw, k, geom, tolf, g.omff, s, pf, res);
         else
-          fast = decode_a2_ff<NM>(raw, k, geom, tol, g.omff, s, pf, res);
+          fast = decode_a2_ff<NM>(raw, k, geom, tolf, g.omff, s, pf, res);
         if (fast == 1) {
 #pragma unroll
           for (int j = 0; j < A; ++j)

@@ -225,7 +225,9 @@ __global__ void __launch_bounds__(kPThreads, 2)
                         S.res_tol,
                         OmegaTab{S.om_hi, S.om_lo, S.om_lo_bits, S.N - 1},
                         OmegaTabFF{S.om_hi_ff, S.om_lo_ff, S.om_lo_bits, S.N - 1},
-                        (float)(S.zero_tol * S.zero_tol)};
+                        (float)(S.zero_tol * S.zero_tol),
+                        (float)(S.root_tol * S.root_tol),
+                        (float)(S.res_tol * S.res_tol)};
       }
       __syncthreads();
       switch (l) {
