@@ -474,6 +474,29 @@ def decode_flops(a: int, nm: int) -> float:
     return 8 * cma + 4 * a
 
 
+# FP32 instructions of one complex float-float multiply-add (a complex
+# float-float product, 36, and a complex float-float addition, 16), and of
+# one root's snap (FP32 angle, rounding, candidate index).
+FF_CMA_INSTR = 52
+FF_SNAP_INSTR = 24
+
+
+def decode_ff_instr(a: int, nm: int) -> float:
+    """FP32 instructions of SynDec for one bin decoded in float-float (the
+    mixed path's one- and two-alias decoders): decode_flops()'s complex
+    multiply-adds at FF_CMA_INSTR each, plus FF_SNAP_INSTR per root.  These
+    decoders run on the FP32 pipes, so their roofline is the FP32 issue
+    rate, not the FP64 pipe."""
+    cma = (decode_flops(a, nm) - 4 * a) / 8
+    return FF_CMA_INSTR * cma + FF_SNAP_INSTR * a
+
+
+def ff_decoder(precision: str, a: int) -> bool:
+    """Whether the decoder of `a` aliases runs in float-float (mixed path,
+    one or two aliases) rather than FP64."""
+    return precision != "fp64" and a <= 2
+
+
 SVD_SWEEPS = 5  # nominal sweeps of the one-sided Jacobi SVD of a small Hankel matrix
 SP_ITERS = 2    # nominal Subspace Pursuit iterations per voted bin
 
@@ -519,7 +542,9 @@ def roofline(wl, stages, B, clk, qlens=None):
       the FP32 peak, and the float-float FP32 instruction issue rate as a
       diagnostic of this build's arithmetic.
     - decoders: bound by the FP64 pipe on decode_flops() per queued bin
-      (qlens: the bins each level or round decoded, from the plan).
+      (qlens: the bins each level or round decoded, from the plan); the
+      mixed path's one- and two-alias decoders run in float-float and are
+      bound by the FP32 issue rate on decode_ff_instr() per bin.
     - folds, the extraction and the finalize: HBM on their algorithmic
       bytes."""
     peaks, src = measured_peaks()
@@ -544,15 +569,25 @@ def roofline(wl, stages, B, clk, qlens=None):
             lvl = int(name[-1])
             if lvl < len(qlens):
                 a = lvl + 1
-                g["kind"], g["unit"] = "fp64", "bin"
+                g["unit"] = "bin"
                 g["units"] += qlens[lvl] * nl
-                g["fp64_flops"] += decode_flops(a, 2 * a) * qlens[lvl] * nl
+                if ff_decoder(wl.precision, a):
+                    g["kind"] = "ff"
+                    g["ff_instr"] += decode_ff_instr(a, 2 * a) * qlens[lvl] * nl
+                else:
+                    g["kind"] = "fp64"
+                    g["fp64_flops"] += decode_flops(a, 2 * a) * qlens[lvl] * nl
         elif name.startswith("decode_fixed_a") and qlens:
             a = int(name[-1])
             if a - 1 < len(qlens):
-                g["kind"], g["unit"] = "fp64", "bin"
+                g["unit"] = "bin"
                 g["units"] += qlens[a - 1] * nl
-                g["fp64_flops"] += decode_flops(a, 2 * wl.a_max) * qlens[a - 1] * nl
+                if ff_decoder(wl.precision, a):
+                    g["kind"] = "ff"
+                    g["ff_instr"] += decode_ff_instr(a, 2 * wl.a_max) * qlens[a - 1] * nl
+                else:
+                    g["kind"] = "fp64"
+                    g["fp64_flops"] += decode_flops(a, 2 * wl.a_max) * qlens[a - 1] * nl
         elif name == "gen_svals" and qlens and len(qlens) == 3:
             g["kind"], g["unit"] = "fp64", "bin"
             g["units"] += qlens[0] * nl
@@ -592,6 +627,11 @@ def roofline(wl, stages, B, clk, qlens=None):
                 pk = N_SM * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
                 out["ff_issue_diag"] = {"achieved_tinstr": ins, "peak_tinstr": pk,
                                         "frac": ins / pk}
+        elif g["kind"] == "ff" and g["ff_instr"]:
+            ach = g["ff_instr"] / sec / 1e12
+            pk = N_SM * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
+            out.update({"bound": "alu", "achieved": ach, "peak": pk, "unit": "Tinstr/s",
+                        "frac": ach / pk, "bins_per_launch": g["units"] / max(g["launches"], 1)})
         elif g["kind"] == "fp64" and g["fp64_flops"]:
             ach = g["fp64_flops"] / sec / 1e12
             pk = fp64_peak_tflops(mhz)
@@ -611,7 +651,10 @@ def roofline(wl, stages, B, clk, qlens=None):
     dom_name = max(groups, key=lambda k: groups[k]["ms"])
     roof = {"kernel": dom_name, **by_kernel[dom_name], "peak_source": src,
             "traffic": ncu_traffic(wl.name, dom_name, B)}
-    if roof.get("bound") == "alu":
+    if roof.get("bound") == "alu" and roof.get("unit") == "Tinstr/s":
+        roof["peak_note"] = (f"FP32 issue: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x "
+                             f"{mhz:.0f} MHz (sampled), derived from unit counts")
+    elif roof.get("bound") == "alu":
         roof["peak_note"] = (f"FP64: {N_SM} SMs x {FP64_FMA_PER_SM} FMA units x 2 flops x "
                              f"{mhz:.0f} MHz (sampled), derived from unit counts")
     elif roof.get("bound") == "hbm":

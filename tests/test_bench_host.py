@@ -76,6 +76,31 @@ def test_roofline_of_a_dominant_decoder_counts_fp64_flops_per_bin():
     assert bare["frac"] is None and bare["achieved"] is None
 
 
+def test_float_float_decoders_are_measured_against_the_fp32_issue_rate():
+    """The mixed path decodes one and two aliases in float-float on the FP32
+    pipes: those decoders are reported against the FP32 issue rate on
+    decode_ff_instr() per bin; three and four aliases (FP64) and the FP64
+    path's decoders stay against the FP64 peak."""
+    wl = bench.WORKLOADS["exact-2^22"]
+    roof = bench.roofline(wl, {"decode_l0": (2.0, 1), "decode_l2": (1.0, 1)}, 152,
+                          {"sm_mhz": 2000.0}, [900000, 90000, 15000, 2000])
+    assert roof["kernel"] == "k_iter_decode<FF, 1>" and roof["unit"] == "Tinstr/s"
+    assert roof["achieved"] == pytest.approx(bench.decode_ff_instr(1, 2) * 900000 / 2e-3 / 1e12)
+    assert roof["peak"] == pytest.approx(152 * 128 * 2000e6 / 1e12)
+    assert "FP32 issue" in roof["peak_note"]
+    assert roof["by_kernel"]["k_iter_decode<FF, 3>"]["bound"] == "alu"
+    f64 = bench.roofline(bench.WORKLOADS["exact-2^16-fp64"], {"decode_l0": (2.0, 1)}, 152,
+                         {"sm_mhz": 2000.0}, [900000, 90000, 15000, 2000])
+    assert f64["unit"] == "TFLOP/s"
+    assert f64["achieved"] == pytest.approx(bench.decode_flops(1, 2) * 900000 / 2e-3 / 1e12)
+    # one complex float-float multiply-add per complex multiply-add of the
+    # flop model, one snap per root
+    assert bench.decode_ff_instr(2, 4) == pytest.approx(
+        bench.FF_CMA_INSTR * (bench.decode_flops(2, 4) - 8) / 8 + 2 * bench.FF_SNAP_INSTR)
+    assert bench.ff_decoder("mixed", 2) and not bench.ff_decoder("mixed", 3)
+    assert not bench.ff_decoder("fp64", 1)
+
+
 def test_decode_flops_grow_with_the_alias_count():
     """One alias: 8 complex multiply-adds and change; four aliases with 8
     syndromes: about 1.8 kflop per bin."""
