@@ -102,8 +102,8 @@ class W:
         return x, s
 
     def h2d_per_signal(self):
-        """Algorithmic input bytes of one transform (Sec. 8(d) of the survey's
-        measurement plan): the samples of the shifts the method reads."""
+        """Algorithmic input bytes of one transform: the samples of the
+        shifts the method reads."""
         if self.general:
             return (2 * self.a_max + self.r) * self.M * self.esize
         if self.mode == "fixed":
@@ -514,7 +514,7 @@ def solve_flops(a: int, d: int, r: int) -> float:
     """Algorithmic FP64 flops of one voted bin with a_k = a (Algorithm 2,
     Parts 3-4): the a x a locator solve ((2/3) a^3 + a^2 complex
     multiply-adds), |P~| at the d candidates ((8a + 6) flops each, the
-    survey's count), and SP_ITERS Subspace Pursuit iterations on r
+    the method's count), and SP_ITERS Subspace Pursuit iterations on r
     equations over at most 2a columns (correlation 2a r, normal matrix
     (2a)^2 r, solve (2/3)(2a)^3, residual 2 a r complex multiply-adds);
     8 real flops per complex multiply-add."""
@@ -525,7 +525,7 @@ def solve_flops(a: int, d: int, r: int) -> float:
 
 
 def fold_bytes(level: int, K: int, M0: int) -> float:
-    """Algorithmic bytes of one bin of level l's fold (a3-a4): the 2l held
+    """Algorithmic bytes of one bin of level l's fold: the 2l held
     syndromes of the previous level at k and k + M read (4l x 16 B), the two
     new shifts read (2 x 16 B), the 2l folded syndromes written (2l x 16 B),
     and the level-0 bins' counts (2^l bytes); the peeled frequencies (24 B
