@@ -353,6 +353,10 @@ struct FinArgs {
 constexpr int kFinTile = 4096;
 // entries staged in shared memory per window of the finalize (24 KB)
 constexpr int kFinStage = 1024;
+// steps of 32 bins a warp of the device-resident finalize loads at once,
+// and that finalize's largest CTA (registers for the steps' loads)
+constexpr int kFinSteps = 4;
+constexpr int kFinDevThreads = 512;
 
 // Block-wide exclusive scan of one int per thread (blockDim = 1024).
 __device__ __forceinline__ int block_excl_scan(int v, int* total) {
@@ -419,7 +423,7 @@ __global__ void __launch_bounds__(256) k_fin_count(FinArgs g) {
 // tiles) plus the block scan of its bins, in bin order; tile 0 writes the
 // counters.
 template <class F, bool kStaged>
-__global__ void __launch_bounds__(1024) k_finalize(FinArgs g) {
+__global__ void __launch_bounds__(kStaged ? 1024 : kFinDevThreads) k_finalize(FinArgs g) {
   typedef typename Store<F>::T T;
   const int b = blockIdx.y, tile = blockIdx.x;
   const int tid = threadIdx.x;
@@ -433,14 +437,7 @@ __global__ void __launch_bounds__(1024) k_finalize(FinArgs g) {
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (tid == 0) s_base = acc;
   }
-  const int64_t per = (g.tile_bins + blockDim.x - 1) / blockDim.x;
-  const int64_t t_hi = min((int64_t)(tile + 1) * g.tile_bins, M0);
-  const int64_t lo = min((int64_t)tile * g.tile_bins + per * tid, t_hi), hi = min(lo + per, t_hi);
-  int mine = 0;
-  for (int64_t k0 = lo; k0 < hi; ++k0) mine += cnt[k0];
-  int total_tile = 0;
-  const int lpos = block_excl_scan(mine, &total_tile);  // synchronises: s_base visible
-  const int base = s_base;
+  const int64_t t_lo = (int64_t)tile * g.tile_bins, t_hi = min(t_lo + g.tile_bins, M0);
   int64_t cap = g.cap;
   int64_t* idx = g.idx + (int64_t)b * g.cap;
   double2* val = g.val + (int64_t)b * g.cap;
@@ -456,16 +453,77 @@ __global__ void __launch_bounds__(1024) k_finalize(FinArgs g) {
     unresolved = rt.unresolved;
     overflow = rt.overflow;
   }
+  int total_tile = 0;
   if constexpr (!kStaged) {
-    // device-resident results: each thread writes its own entries
-    int pos = base + lpos;
-    for (int64_t k0 = lo; k0 < hi; ++k0) {
-      const int c = cnt[k0];
-      for (int e = 0; e < c; ++e, ++pos) {
-        if (pos < cap) {
-          idx[pos] = g.slot_s[(int64_t)b * M0 * kSlots + slot_ix(k0, e, M0)];
-          const cdbl v = Store<F>::to_d(sp[(int64_t)b * M0 * kSlots + slot_ix(k0, e, M0)]);
-          val[pos] = make_double2(v.x, v.y);
+    // device-resident results: warp w owns a chunk of consecutive bins of
+    // the tile (a multiple of 32) and walks it 32 bins at a time, lane l on
+    // bin k0 + l, so that the counts, the slots (slot e of consecutive bins
+    // is contiguous) and the output runs are all accessed coalesced.  Each
+    // warp's output offset is the block scan of the chunk totals; inside a
+    // step, a shuffle scan of the 32 counts.
+    const int lane = tid & 31, w = tid >> 5, nw = (int)(blockDim.x >> 5);
+    const int64_t chunk = (t_hi - t_lo + 32 * nw - 1) / (32 * nw) * 32;
+    const int64_t c_lo = min(t_lo + w * chunk, t_hi), c_hi = min(c_lo + chunk, t_hi);
+    const uint8_t* __restrict__ cn = cnt;
+    const int64_t* __restrict__ ssb = g.slot_s + (int64_t)b * M0 * kSlots;
+    const T* __restrict__ spb = sp + (int64_t)b * M0 * kSlots;
+    int wsum = 0;
+    for (int64_t k = c_lo + lane; k < c_hi; k += 32) wsum += cn[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    // lane 0 of each warp carries the chunk total: its exclusive prefix is
+    // the chunk's offset in the tile (synchronises: s_base visible)
+    const int wpre = block_excl_scan(lane == 0 ? wsum : 0, &total_tile);
+    int pos0 = s_base + __shfl_sync(0xffffffffu, wpre, 0);
+    // kFinSteps steps of 32 bins at a time: their counts, then the first
+    // entry of every bin of the group loaded before any is stored (more
+    // loads in flight per warp), then the rare further entries
+    for (int64_t k0 = c_lo; k0 < c_hi; k0 += 32 * kFinSteps) {
+      int c[kFinSteps], pos[kFinSteps];
+#pragma unroll
+      for (int j = 0; j < kFinSteps; ++j) {
+        const int64_t k = k0 + 32 * j + lane;
+        c[j] = k < c_hi ? (int)cn[k] : 0;
+      }
+#pragma unroll
+      for (int j = 0; j < kFinSteps; ++j) {
+        int incl = c[j];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        pos[j] = pos0 + incl - c[j];
+        pos0 += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      int64_t s0[kFinSteps];
+      T v0[kFinSteps];
+#pragma unroll
+      for (int j = 0; j < kFinSteps; ++j) {
+        if (c[j] > 0) {
+          const int64_t k = k0 + 32 * j + lane;
+          s0[j] = ssb[slot_ix(k, 0, M0)];
+          v0[j] = spb[slot_ix(k, 0, M0)];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kFinSteps; ++j) {
+        if (c[j] > 0 && pos[j] < cap) {
+          const cdbl v = Store<F>::to_d(v0[j]);
+          idx[pos[j]] = s0[j];
+          val[pos[j]] = make_double2(v.x, v.y);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kFinSteps; ++j) {
+        const int64_t k = k0 + 32 * j + lane;
+        for (int e = 1; e < c[j]; ++e) {
+          if (pos[j] + e < cap) {
+            const int64_t s_e = ssb[slot_ix(k, e, M0)];
+            const cdbl v = Store<F>::to_d(spb[slot_ix(k, e, M0)]);
+            idx[pos[j] + e] = s_e;
+            val[pos[j] + e] = make_double2(v.x, v.y);
+          }
         }
       }
     }
@@ -476,6 +534,16 @@ __global__ void __launch_bounds__(1024) k_finalize(FinArgs g) {
   // written out by consecutive threads, so that the stores are coalesced
   __shared__ int64_t s_idx[kStaged ? kFinStage : 1];
   __shared__ double2 s_val[kStaged ? kFinStage : 1];
+  int64_t lo = 0, hi = 0;
+  int mine = 0, lpos = 0;
+  if constexpr (kStaged) {
+    const int64_t per = (g.tile_bins + blockDim.x - 1) / blockDim.x;
+    lo = min(t_lo + per * tid, t_hi);
+    hi = min(lo + per, t_hi);
+    for (int64_t k0 = lo; k0 < hi; ++k0) mine += cnt[k0];
+    lpos = block_excl_scan(mine, &total_tile);  // synchronises: s_base visible
+  }
+  const int base = s_base;
   for (int w0 = 0; kStaged && w0 < total_tile; w0 += kFinStage) {
     if (lpos < w0 + kFinStage && lpos + mine > w0) {
       int p = lpos;
@@ -948,9 +1016,11 @@ static cudaError_t launch_one(sft_plan_s* P, int64_t B, const void* x, int64_t x
             reinterpret_cast<double2*>(r->val), r->count, r->unresolved, r->overflow, P->r_table,
             tiles,    tiles + B * n_tiles, n_tiles, single ? P->M0 : (int64_t)kFinTile};
   const dim3 fgrid((unsigned)n_tiles, (unsigned)B);
-  // one tile of fewer than 1024 bins: one thread per bin (whole warps)
-  const int fthr = single ? (int)std::min<int64_t>(1024, std::max<int64_t>(32, (P->M0 + 31) / 32 * 32))
-                          : 1024;
+  // at most 1024 threads (results in host memory, staged) or
+  // kFinDevThreads; a tile of fewer bins gets whole warps, a thread per bin
+  const int fmax = P->r_on_host ? 1024 : kFinDevThreads;
+  const int fthr = single ? (int)std::min<int64_t>(fmax, std::max<int64_t>(32, (P->M0 + 31) / 32 * 32))
+                          : fmax;
   stage_begin(P, "finalize", st);
   if (!single) k_fin_count<<<fgrid, 256, 0, st>>>(f);
   if (fp64)
