@@ -473,6 +473,19 @@ sft_status sft_plan_set_profiling(sft_plan_t plan, int32_t enable);
 sft_status sft_plan_stage_times(sft_plan_t plan, int32_t cap, const char** names, double* ms,
                                 int64_t* launches, int32_t* n);
 
+/* The same records as a timeline: one entry per profiled launch since the
+ * previous read, in enqueue order.  names[i] is the stage (static string),
+ * sub[i] the sub-batch whose stream ran it (0 for a call that is not split),
+ * t0_ms[i] / t1_ms[i] its start and end in ms after the start of the first
+ * record.  Synchronises the device, writes up to `cap` entries (host
+ * arrays, owned by the caller), *n receives the number of records, and the
+ * record is reset (like sft_plan_stage_times).  Shows how the sub-batches'
+ * stages overlap, e.g. the host-link extraction of one against the compute
+ * of another.  SFT_EINVAL on a NULL plan or n, or cap > 0 with a NULL
+ * array; SFT_ECUDA if the synchronisation fails. */
+sft_status sft_plan_stage_timeline(sft_plan_t plan, int32_t cap, const char** names, int32_t* sub,
+                                   double* t0_ms, double* t1_ms, int32_t* n);
+
 /* Human-readable name of a status code (static storage). */
 const char* sft_strerror(sft_status s);
 

@@ -582,6 +582,33 @@ sft_status sft_plan_stage_times(sft_plan_t P, int32_t cap, const char** names, d
   return SFT_OK;
 }
 
+sft_status sft_plan_stage_timeline(sft_plan_t P, int32_t cap, const char** names, int32_t* sub,
+                                   double* t0_ms, double* t1_ms, int32_t* n) {
+  if (!P || !n || cap < 0 || (cap > 0 && (!names || !sub || !t0_ms || !t1_ms))) return SFT_EINVAL;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    note_cuda(e);
+    return SFT_ECUDA;
+  }
+  int32_t k = 0;
+  for (auto& r : P->stage_recs) {
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, P->stage_recs.front().t0, r.t0) != cudaSuccess ||
+        cudaEventElapsedTime(&b, P->stage_recs.front().t0, r.t1) != cudaSuccess)
+      continue;
+    if (k < cap) {
+      names[k] = r.name;
+      sub[k] = r.sub;
+      t0_ms[k] = a;
+      t1_ms[k] = b;
+    }
+    ++k;
+  }
+  drop_stage_recs(P);
+  *n = k;
+  return SFT_OK;
+}
+
 const char* sft_strerror(sft_status s) {
   switch (s) {
     case SFT_OK: return "SFT_OK";

@@ -156,14 +156,14 @@ __device__ __forceinline__ float4 ld_pair(const float4* p, bool narrow) {
 // The run of `cnt` (even, <= 16) samples x[n d + j], j < cnt, of one row:
 // for complex64 rows that cannot wrap (d >= 16) and 16-byte aligned signals,
 // as cnt / 2 16-byte loads; otherwise one load per sample.
-template <class In, bool kNarrow>
+template <class In, bool kNarrow, int CAP = 16>
 __device__ __forceinline__ void load_run(const In* xs, int64_t n, int64_t d, int64_t N, int cnt,
                                          In* v) {
   if constexpr (std::is_same<In, float2>::value) {
     if (d >= 16 && (reinterpret_cast<uintptr_t>(xs) & 15u) == 0) {
       const float4* p = reinterpret_cast<const float4*>(xs + n * d);
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
+      for (int j = 0; j < CAP / 2; ++j)
         if (2 * j < cnt) {
           const float4 q = ld_pair(p + j, kNarrow);
           v[2 * j] = make_float2(q.x, q.y);
@@ -173,41 +173,83 @@ __device__ __forceinline__ void load_run(const In* xs, int64_t n, int64_t d, int
     }
   }
 #pragma unroll
-  for (int j = 0; j < 16; ++j)
+  for (int j = 0; j < CAP; ++j)
     if (j < cnt) v[j] = ld_row(xs + ((n * d + j) & (N - 1)), kNarrow);
 }
 
-template <class In, bool kNarrow>
-__global__ void __launch_bounds__(256) k_extract(const In* __restrict__ x, int64_t x_stride,
-                                                 const void* const* __restrict__ x_table,
-                                                 int64_t N, int64_t d, int64_t M0, int levels,
-                                                 int fixed_nsh, In* __restrict__ C, int64_t c_sig) {
-  const int b = blockIdx.y;
-  const int64_t n = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  if (n >= M0) return;
-  const In* xs = x_table != nullptr ? reinterpret_cast<const In*>(x_table[b]) : x + (int64_t)b * x_stride;
-  In* cb = C + (int64_t)b * c_sig;
-  In v[16];
+// ITER: the levels row n feeds (rows n with n mod 2^l == 0 feed level l,
+// shifts 2l and 2l + 1)
+__device__ __forceinline__ int row_levels(int64_t n, int levels) {
+  return min(levels, (n == 0 ? 8 : __ffsll(n) - 1 + 1));
+}
+
+// Row n's run v[0..cnt) into the level arrays cb of its signal: FIXED
+// (fixed_nsh > 0) shift-major [fixed_nsh][M0]; ITER level l at offset
+// sum_{l' < l} 2 M_l', entry n >> l.
+template <class In, int CAP>
+__device__ __forceinline__ void store_run(In* cb, int64_t n, int64_t M0, int fixed_nsh, int cnt,
+                                          const In* v) {
   if (fixed_nsh > 0) {
-    load_run<In, kNarrow>(xs, n, d, N, fixed_nsh, v);
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
-      if (j < fixed_nsh) cb[(int64_t)j * M0 + n] = v[j];
+    for (int j = 0; j < CAP; ++j)
+      if (j < cnt) cb[(int64_t)j * M0 + n] = v[j];
     return;
   }
-  // rows n with n mod 2^l == 0 feed level l (shifts 2l, 2l+1)
-  const int lv = min(levels, (n == 0 ? 8 : __ffsll(n) - 1 + 1));
-  load_run<In, kNarrow>(xs, n, d, N, 2 * lv, v);
   int64_t off = 0, Ml = M0;
 #pragma unroll
-  for (int l = 0; l < 8; ++l) {
-    if (l < lv) {
+  for (int l = 0; l < CAP / 2; ++l) {
+    if (2 * l < cnt) {
       cb[off + (n >> l)] = v[2 * l];
       cb[off + Ml + (n >> l)] = v[2 * l + 1];
     }
     off += 2 * Ml;
     Ml >>= 1;
   }
+}
+
+// CTAs per SM of the extraction from page-locked host memory
+constexpr int kExtractHostCtas = 1;
+
+// One row n of signal b: its run of shifts into the level arrays.
+template <class In, bool kNarrow>
+__device__ __forceinline__ void extract_row(const In* __restrict__ x, int64_t x_stride,
+                                            const void* const* __restrict__ x_table, int64_t N,
+                                            int64_t d, int64_t M0, int levels, int fixed_nsh,
+                                            In* __restrict__ C, int64_t c_sig, int b, int64_t n) {
+  const In* xs = x_table != nullptr ? reinterpret_cast<const In*>(x_table[b]) : x + (int64_t)b * x_stride;
+  In v[16];
+  const int cnt = fixed_nsh > 0 ? fixed_nsh : 2 * row_levels(n, levels);
+  load_run<In, kNarrow>(xs, n, d, N, cnt, v);
+  store_run<In, 16>(C + (int64_t)b * c_sig, n, M0, fixed_nsh, cnt, v);
+}
+
+// Device input: grid (row tiles, signals), one thread per row.  Input in
+// page-locked host memory (kNarrow false, n_flat > 0): a bounded grid
+// striding over the rows of all signals -- they arrive over the host link
+// far slower than the SMs could take them, and CTAs waiting on the link for
+// the whole extraction would hold every SM, leaving none for the compute of
+// the call's other sub-batches (measured: more CTAs, or more rows in flight
+// per thread, only slowed the call).
+template <class In, bool kNarrow>
+__global__ void __launch_bounds__(256) k_extract(const In* __restrict__ x, int64_t x_stride,
+                                                 const void* const* __restrict__ x_table,
+                                                 int64_t N, int64_t d, int64_t M0, int levels,
+                                                 int fixed_nsh, In* __restrict__ C, int64_t c_sig,
+                                                 int64_t n_flat) {
+  if constexpr (!kNarrow) {
+    if (n_flat > 0) {
+      // grid-stride over the n_flat = signals x M0 rows (row f: signal f / M0)
+      for (int64_t f = (int64_t)blockIdx.x * 256 + threadIdx.x; f < n_flat;
+           f += (int64_t)gridDim.x * 256)
+        extract_row<In, kNarrow>(x, x_stride, x_table, N, d, M0, levels, fixed_nsh, C, c_sig,
+                                 (int)(f / M0), f % M0);
+      return;
+    }
+  }
+  const int64_t n = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (n >= M0) return;
+  extract_row<In, kNarrow>(x, x_stride, x_table, N, d, M0, levels, fixed_nsh, C, c_sig,
+                           (int)blockIdx.y, n);
 }
 
 // ------------------------------------------- four-step FFT for M > 8192
@@ -676,7 +718,7 @@ static cudaEvent_t pool_event(sft_plan_s* P) {
 
 void stage_begin(sft_plan_s* P, const char* name, cudaStream_t st) {
   if (!P->profiling) return;
-  StageRec r{name, pool_event(P), pool_event(P)};
+  StageRec r{name, pool_event(P), pool_event(P), P->cur_sub};
   cudaEventRecord(r.t0, st);
   P->stage_recs.push_back(r);
 }
@@ -778,19 +820,24 @@ void launch_gather_fft_any(sft_plan_s* P, int64_t B, const void* x, int64_t x_st
 // Copies the samples of the call into the compact arrays (P->ws.xc).
 template <class F>
 static void launch_extract(sft_plan_s* P, int64_t B, const void* x, int64_t x_stride, int levels,
-                           int fixed_nsh, cudaStream_t st) {
+                           int fixed_nsh, int nsm, cudaStream_t st) {
   const dim3 grid((unsigned)((P->M0 + 255) / 256), (unsigned)B);
   stage_begin(P, "extract", st);
   // device-resident samples: 64-byte L2 requests (one row's run of shifts);
-  // host-resident ones (read over NVLink-C2C): full-width requests
-  if (P->x_on_host)
-    k_extract<typename F::In, false><<<grid, 256, 0, st>>>(
+  // host-resident ones (read over NVLink-C2C): full-width requests, from a
+  // grid of kExtractHostCtas CTAs per SM striding over all rows
+  if (P->x_on_host) {
+    const int64_t rows = B * P->M0;
+    const unsigned hgrid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((rows + 255) / 256, (int64_t)kExtractHostCtas * nsm));
+    k_extract<typename F::In, false><<<hgrid, 256, 0, st>>>(
         reinterpret_cast<const typename F::In*>(x), x_stride, P->x_table, P->p.N, P->p.d, P->M0,
-        levels, fixed_nsh, reinterpret_cast<typename F::In*>(P->ws.xc), P->ws.xc_sig);
-  else
+        levels, fixed_nsh, reinterpret_cast<typename F::In*>(P->ws.xc), P->ws.xc_sig, rows);
+  } else {
     k_extract<typename F::In, true><<<grid, 256, 0, st>>>(
         reinterpret_cast<const typename F::In*>(x), x_stride, P->x_table, P->p.N, P->p.d, P->M0,
-        levels, fixed_nsh, reinterpret_cast<typename F::In*>(P->ws.xc), P->ws.xc_sig);
+        levels, fixed_nsh, reinterpret_cast<typename F::In*>(P->ws.xc), P->ws.xc_sig, 0);
+  }
   stage_end(P, st);
   if (P->sub_extract_now != nullptr) cudaEventRecord(P->sub_extract_now, st);
 }
@@ -815,7 +862,7 @@ static void launch_fixed(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
   if (W.xc != nullptr) {
     // rows j M0 .. of the compact array hold shift j (index space rounded
     // up to a power of two)
-    launch_extract<F>(P, B, x, x_stride, 0, nsh, st);
+    launch_extract<F>(P, B, x, x_stride, 0, nsh, nsm, st);
     int64_t Nc = P->M0;
     while (Nc < nsh * P->M0) Nc <<= 1;
     const GatherSrc src{W.xc, W.xc_sig, Nc, 1, nullptr};
@@ -905,7 +952,7 @@ static void launch_iter(sft_plan_s* P, int64_t B, const void* x, int64_t x_strid
   const Workspace& W = P->ws;
   const OmegaTabFF omff{P->tab.om_hi_ff, P->tab.om_lo_ff, P->tab.om_lo_bits, P->p.N - 1};
   int64_t M = P->M0, d = P->p.d, xc_off = 0;
-  if (W.xc != nullptr) launch_extract<F>(P, B, x, x_stride, P->levels, 0, st);
+  if (W.xc != nullptr) launch_extract<F>(P, B, x, x_stride, P->levels, 0, nsm, st);
   for (int l = 0; l < P->levels; ++l) {
     if (l > 0) {
       xc_off += 2 * M;
@@ -1078,6 +1125,7 @@ cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
       if (e != cudaSuccess) break;
     }
     P->ws = sub_workspace(W0, b0, s);
+    P->cur_sub = s;
     P->x_table = xt0 ? xt0 + b0 : nullptr;
     P->r_table = rt0 ? rt0 + b0 : nullptr;
     P->K_table = kt0 ? kt0 + b0 : nullptr;
@@ -1094,6 +1142,7 @@ cudaError_t launch_exact(sft_plan_s* P, int64_t B, const void* x, int64_t x_stri
     b0 += Bs;
   }
   P->ws = W0;
+  P->cur_sub = 0;
   P->x_table = xt0;
   P->r_table = rt0;
   P->K_table = kt0;

@@ -174,6 +174,7 @@ namespace sft {
 struct StageRec {
   const char* name;
   cudaEvent_t t0, t1;
+  int sub;  // sub-batch (stream) of the launch
 };
 }  // namespace sft
 
@@ -223,6 +224,7 @@ struct sft_plan_s {
   // (created on first use; stream 0 is the caller's)
   int sub_batches = 0;
   int last_sub = 1;  // sub-batches of the last call (its queue counters)
+  int cur_sub = 0;   // sub-batch being enqueued (profiling records)
   cudaStream_t sub_st[sft::kMaxSub] = {};
   cudaEvent_t sub_fork = nullptr;
   cudaEvent_t sub_join[sft::kMaxSub] = {};

@@ -55,7 +55,8 @@ EXPORTS = ["sft_params_default", "sft_plan_create", "sft_plan_destroy", "sft_pla
            "sft_mlp_param_count", "sft_mlp_get_params", "sft_mlp_set_params", "sft_mlp_features",
            "sft_mlp_forward", "sft_mlp_grad", "sft_mlp_train", "sft_plan_attach_mlp",
            "sft_exact_auto", "sft_alias_histogram", "sft_plan_set_sub_batches",
-           "sft_plan_sub_batches", "sft_plan_set_quad_decoders", "sft_plan_queue_lengths"]
+           "sft_plan_sub_batches", "sft_plan_set_quad_decoders", "sft_plan_queue_lengths",
+           "sft_plan_stage_timeline"]
 
 _lib = None
 
@@ -107,6 +108,8 @@ def load(build_if_missing: bool = False):
     lib.sft_plan_set_profiling.argtypes = [C.c_void_p, C.c_int32]
     lib.sft_plan_stage_times.argtypes = [C.c_void_p, C.c_int32, P(C.c_char_p), P(C.c_double),
                                          P(C.c_int64), P(C.c_int32)]
+    lib.sft_plan_stage_timeline.argtypes = [C.c_void_p, C.c_int32, P(C.c_char_p), P(C.c_int32),
+                                            P(C.c_double), P(C.c_double), P(C.c_int32)]
     lib.sft_exact_noalloc.argtypes = [P(sft_params), C.c_int64, C.c_void_p, C.c_int64,
                                       P(sft_result), C.c_void_p]
     lib.sft_general.argtypes = lib.sft_exact.argtypes
@@ -369,6 +372,19 @@ def sft_plan_stage_times(handle: int) -> dict:
     return {names[i].decode(): (ms[i], int(cnt[i])) for i in range(min(n.value, cap))}
 
 
+def sft_plan_stage_timeline(handle: int, cap: int = 4096) -> list:
+    """[(stage, sub-batch, start ms, end ms)] per profiled launch since the
+    previous read, relative to the first launch's start; resets."""
+    names = (C.c_char_p * cap)()
+    sub = (C.c_int32 * cap)()
+    t0 = (C.c_double * cap)()
+    t1 = (C.c_double * cap)()
+    n = C.c_int32(0)
+    _check(load().sft_plan_stage_timeline(C.c_void_p(handle), cap, names, sub, t0, t1,
+                                          C.byref(n)), "sft_plan_stage_timeline")
+    return [(names[i].decode(), int(sub[i]), t0[i], t1[i]) for i in range(min(n.value, cap))]
+
+
 class Plan:
     """Convenience owner of one sft plan."""
 
@@ -448,6 +464,9 @@ class Plan:
                                           C.c_void_p(mlp.handle if mlp is not None else None)),
                "sft_plan_attach_mlp")
         self._mlp = mlp
+
+    def stage_timeline(self) -> list:
+        return sft_plan_stage_timeline(self.handle)
 
     def stage_times(self) -> dict:
         return sft_plan_stage_times(self.handle)

@@ -378,3 +378,31 @@ def test_up_to_eight_aliases_matches_oracle(gpu, orc, mode, prec, N, K, M):
             rg = np.abs(Y[:, k] - Z @ gv[sel]).max()
             ro = np.abs(Y[:, k] - Z @ ov[sel]).max()
             assert rg <= max(2 * ro, tol["res_tol"] * np.abs(Y[:, k]).max()), (b, k, rg, ro)
+
+
+def test_stage_timeline_shows_every_sub_batch(gpu):
+    """With profiling on, a call split into four sub-batches reports every
+    launch once in the timeline, on its sub-batch, with ordered times; the
+    per-stage sums match the stage names of sft_plan_stage_times."""
+    from paper_1407_8315_gb300 import Plan
+    N, K, M = 1 << 16, 64, 1 << 10
+    plan = Plan(N, K, N // M, "iter", "mixed", max_signals=8)
+    plan.set_sub_batches(4)
+    xs = np.stack([siggen.exact_signal(N, K, s)[0] for s in range(8)]).astype(np.complex64)
+    x = gpu.from_numpy(xs).cuda()
+    plan.set_profiling(True)
+    plan.exact(x, 4 * M)
+    tl = plan.stage_timeline()
+    plan.exact(x, 4 * M)
+    st = plan.stage_times()
+    plan.set_profiling(False)
+    assert {s for _, s, _, _ in tl} == {0, 1, 2, 3}
+    assert all(0.0 <= t0 <= t1 for _, _, t0, t1 in tl)
+    assert min(t0 for _, _, t0, _ in tl) == 0.0
+    assert {n for n, _, _, _ in tl} == set(st)
+    for name, (ms, launches) in st.items():
+        assert sum(1 for n, _, _, _ in tl if n == name) == launches
+    # each sub-batch runs its stages in order on its own stream
+    for s in range(4):
+        mine = [(t0, t1) for _, q, t0, t1 in tl if q == s]
+        assert all(a[1] <= b[0] + 1e-3 for a, b in zip(mine, mine[1:]))
