@@ -120,10 +120,14 @@ __device__ __forceinline__ bool fold_bin(const LevelArgs& g, int b, int64_t k) {
         cur[(2 * l + 1) * M + k] = Store<F>::from_d(m[2 * l + 1]);
       }
     } else {
-      FF::V m[nm];
+      // the held rows fold first, each written back at once: they take no
+      // part in the peel or the activity test, so none stays live (in
+      // registers) across the peel walk
 #pragma unroll
       for (int j = 0; j < 2 * l; ++j)
-        m[j] = FF::add(FF::from4(prev[j * 2 * M + k]), FF::from4(prev[j * 2 * M + k + M]));
+        cur[j * M + k] =
+            FF::to4(FF::add(FF::from4(prev[j * 2 * M + k]), FF::from4(prev[j * 2 * M + k + M])));
+      FF::V m[nm];
       m[2 * l] = FF::from4(cur[(2 * l) * M + k]);
       m[2 * l + 1] = FF::from4(cur[(2 * l + 1) * M + k]);
       bool peeled = false;
@@ -160,8 +164,6 @@ __device__ __forceinline__ bool fold_bin(const LevelArgs& g, int b, int64_t k) {
       const float t2 = theta2_f(g.zero_tol2_f, ymax_bits);
       active = t || above_ff(m[2 * l], t2, g.zero_tol, ymax_bits) ||
                above_ff(m[2 * l + 1], t2, g.zero_tol, ymax_bits);
-#pragma unroll
-      for (int j = 0; j < 2 * l; ++j) cur[j * M + k] = FF::to4(m[j]);
       if (peeled) {
         cur[(2 * l) * M + k] = FF::to4(m[2 * l]);
         cur[(2 * l + 1) * M + k] = FF::to4(m[2 * l + 1]);
