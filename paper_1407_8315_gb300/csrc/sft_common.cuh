@@ -31,6 +31,10 @@ __device__ __forceinline__ cdbl operator*(cdbl a, cdbl b) {
 }
 __device__ __forceinline__ cdbl operator*(cdbl a, double s) { return cdbl{a.x * s, a.y * s}; }
 __device__ __forceinline__ cdbl conjd(cdbl a) { return cdbl{a.x, -a.y}; }
+// a b + c in four FMAs
+__device__ __forceinline__ cdbl cfma(cdbl a, cdbl b, cdbl c) {
+  return cdbl{fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y))};
+}
 __device__ __forceinline__ double norm2(cdbl a) { return a.x * a.x + a.y * a.y; }
 __device__ __forceinline__ double absd(cdbl a) { return hypot(a.x, a.y); }
 __device__ __forceinline__ cdbl cdivd(cdbl a, cdbl b) {

@@ -26,12 +26,20 @@
 
 namespace sft {
 
-// 1/x: FP32 seed refined by two Newton steps r <- r + r (1 - x r) (each
-// doubles the correct bits: 2^-23 -> 2^-46 -> below an FP64 ulp); an exact
-// FP64 division when x lies outside the float range.
+// 1/x: an FP32 seed refined by two Newton steps r <- r + r (1 - x r) (each
+// doubles the correct bits: ~2^-22 -> 2^-44 -> below an FP64 ulp); an
+// exact FP64 division when |x| lies outside [2^-123, 2^124).  The seed's
+// operand is x truncated to float and its result widened back, both by
+// moving bits (sign, exponent rebiased by 896, top 23 significand bits) on
+// the integer pipes: a conversion instruction, like the range test on a
+// double, would occupy GB300's scarce FP64 unit.
 __device__ __forceinline__ double rcp_d(double x) {
-  double r = (double)__frcp_rn((float)x);
-  if (!(fabs(r) > 1e-37 && fabs(r) < 1e37)) return 1.0 / x;
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const uint32_t ex = (uint32_t)(u >> 52) & 0x7FFu;
+  if (ex < 900u || ex >= 1147u) return 1.0 / x;
+  const uint32_t fb = ((uint32_t)(u >> 63) << 31) | ((ex - 896u) << 23) |
+                      (uint32_t)((u >> 29) & 0x7FFFFFu);
+  double r = f2d_exact(__frcp_rn(__uint_as_float(fb)));
   double e = fma(-x, r, 1.0);
   r = fma(r, e, r);
   e = fma(-x, r, 1.0);
@@ -46,10 +54,10 @@ __device__ __forceinline__ cdbl csqrt_fast(cdbl v) {
   if (r == 0.0) return cdbl{0.0, 0.0};
   if (v.x >= 0.0) {
     const double t = sqrt(0.5 * (r + v.x));
-    return cdbl{t, v.y * (0.5 / t)};
+    return cdbl{t, v.y * (0.5 * rcp_d(t))};
   }
   const double t = sqrt(0.5 * (r - v.x));
-  return cdbl{fabs(v.y) * (0.5 / t), copysign(t, v.y)};
+  return cdbl{fabs(v.y) * (0.5 * rcp_d(t)), copysign(t, v.y)};
 }
 // a cube root of v: FP32 polar estimate, two FP64 Newton steps
 // u <- (2u + v / u^2) / 3
@@ -757,7 +765,9 @@ __device__ __forceinline__ bool decode_bin(cdbl* m, int64_t k, const BinGeom& g,
 
     // normal equations (Z^H Z) p = Z^H m over all nm equations, Z_ij = w_j^i.
     // Z^H Z is Hermitian with diagonal nm, and its (u, v) entry is the
-    // geometric sum sum_i q^i of q = conj(w_u) w_v: a(a-1)/2 sums.
+    // geometric sum sum_i q^i of q = conj(w_u) w_v: a(a-1)/2 sums.  Both
+    // the sums and Z^H m (sum_i conj(w_u)^i m_i) are polynomials evaluated
+    // by Horner's rule: one complex multiply-add per term.
     cdbl G[a * a], gr[a], wp[a];
 #pragma unroll
     for (int u = 0; u < a; ++u) {
@@ -765,28 +775,20 @@ __device__ __forceinline__ bool decode_bin(cdbl* m, int64_t k, const BinGeom& g,
 #pragma unroll
       for (int v = u + 1; v < a; ++v) {
         const cdbl q = conjd(w[u]) * w[v];
-        cdbl acc = mk(1.0, 0.0), qp = q;
+        cdbl acc = mk(1.0 + q.x, q.y);
 #pragma unroll
-        for (int i = 1; i < nm; ++i) {
-          acc = acc + qp;
-          if (i + 1 < nm) qp = qp * q;
-        }
+        for (int i = 2; i < nm; ++i) acc = cfma(acc, q, mk(1.0, 0.0));
         G[u * a + v] = acc;
         G[v * a + u] = conjd(acc);
       }
     }
 #pragma unroll
     for (int u = 0; u < a; ++u) {
-      gr[u] = m[0];
-      wp[u] = w[u];
-    }
+      const cdbl cw = conjd(w[u]);
+      cdbl acc = m[nm - 1];
 #pragma unroll
-    for (int i = 1; i < nm; ++i) {
-#pragma unroll
-      for (int u = 0; u < a; ++u) {
-        gr[u] = gr[u] + conjd(wp[u]) * m[i];
-        if (i + 1 < nm) wp[u] = wp[u] * w[u];
-      }
+      for (int i = nm - 2; i >= 0; --i) acc = cfma(acc, cw, m[i]);
+      gr[u] = acc;
     }
     if (!solve_small<a>(G, gr, p)) return false;
 #pragma unroll
