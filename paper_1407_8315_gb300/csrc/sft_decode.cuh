@@ -203,6 +203,16 @@ struct BinGeom {
   OmegaTab om;
 };
 
+// k / M in FP32 for a power of two M (< 2^30) and 0 <= k < M: k times the
+// exact reciprocal 2^-log2(M), formed from the exponent bits -- the same
+// value as the FP32 quotient, without a division
+__device__ __forceinline__ float k_over_M(int64_t k, int64_t M) {
+  return (float)(int)k * __int_as_float((127 - (__ffsll(M) - 1)) << 23);
+}
+// the candidate index t in [0, d) from its rounded value (d a power of two,
+// so the mask is the modulo for negative values too)
+__device__ __forceinline__ int64_t cand_of(int t, int64_t d) { return (int64_t)(t & (int)(d - 1)); }
+
 // Thresholds, squared: theta^2, root_tol^2, res_tol^2.
 struct Tol2 {
   double theta2, root2, res2;
@@ -220,20 +230,18 @@ struct Tol2f {
 __device__ __forceinline__ int64_t snap_root(cdbl z, int64_t k, const BinGeom& g) {
   const float inv2pi = 0.15915494309189533577f;
   const float ang = atan2f((float)z.y, (float)z.x);
-  const float df = (float)g.d;
-  const float q = fmaf(ang, df * inv2pi, -(float)k / (float)g.M);
+  const float df = (float)(int)g.d;
+  const float q = fmaf(ang, df * inv2pi, -k_over_M(k, g.M));
   const float fr = q - rintf(q);
   const float margin = fmaxf(1e-3f, 8e-7f * df);
-  double tf;
+  int t;
   if (fabsf(fabsf(fr) - 0.5f) < margin) {
     const double pos = atan2(z.y, z.x) * 0.15915494309189533577 * (double)g.N;
-    tf = rint((pos - (double)k) / (double)g.M);
+    t = (int)rint((pos - (double)k) / (double)g.M);
   } else {
-    tf = (double)rintf(q);
+    t = __float2int_rn(q);
   }
-  int64_t t = ((int64_t)tf) % g.d;
-  if (t < 0) t += g.d;
-  return k + t * g.M;
+  return k + cand_of(t, g.d) * g.M;
 }
 
 // snap_root for a root given in FP32 (z = m1 / m0 rounded): the FP64 root
@@ -242,14 +250,12 @@ __device__ __forceinline__ int64_t snap_root_f(float zx, float zy, int64_t k, co
                                                cdbl m0, cdbl m1) {
   const float inv2pi = 0.15915494309189533577f;
   const float ang = atan2f(zy, zx);
-  const float df = (float)g.d;
-  const float q = fmaf(ang, df * inv2pi, -(float)k / (float)g.M);
+  const float df = (float)(int)g.d;
+  const float q = fmaf(ang, df * inv2pi, -k_over_M(k, g.M));
   const float fr = q - rintf(q);
   const float margin = fmaxf(1e-3f, 8e-7f * df);
   if (fabsf(fabsf(fr) - 0.5f) < margin) return snap_root(m1 * crcp(m0), k, g);
-  int64_t t = ((int64_t)rintf(q)) % g.d;
-  if (t < 0) t += g.d;
-  return k + t * g.M;
+  return k + cand_of(__float2int_rn(q), g.d) * g.M;
 }
 
 // Validation (iii) in float-float on the FP32 pipes (mixed path): the
@@ -341,13 +347,11 @@ __device__ __forceinline__ int decode_a1_ff(const float4* raw, int64_t k, const 
   if (zx == 0.0f && zy == 0.0f) return 0;
   // the nearest candidate from the FP32 angle (as snap_root_f)
   const float ang = atan2f(zy, zx);
-  const float df = (float)g.d;
-  const float q = fmaf(ang, df * 0.15915494309189533577f, -(float)k / (float)g.M);
+  const float df = (float)(int)g.d;
+  const float q = fmaf(ang, df * 0.15915494309189533577f, -k_over_M(k, g.M));
   const float fr = q - rintf(q);
   if (fabsf(fabsf(fr) - 0.5f) < fmaxf(1e-3f, 8e-7f * df)) return -1;
-  int64_t t = ((int64_t)rintf(q)) % g.d;
-  if (t < 0) t += g.d;
-  s[0] = k + t * g.M;
+  s[0] = k + cand_of(__float2int_rn(q), g.d) * g.M;
   const FF::V w = omega_ff(omff, s[0]);
   const float dx = zx - ff_re(w), dy = zy - ff_im(w);
   const float dz = dx * dx + dy * dy, r2 = tol.root2;
@@ -531,15 +535,13 @@ __device__ __forceinline__ int decode_a2_ff(const float4* raw, int64_t k, const 
     const float err = root_polish<2>(cc, z[j], cond);
     const float zx = ff_re(z[j]), zy = ff_im(z[j]);
     if (!(zx * zx + zy * zy > 1e-30f && zx * zx + zy * zy < 1e30f)) return -1;
-    const float df = (float)g.d;
-    const float qa = fmaf(atan2f(zy, zx), df * 0.15915494309189533577f, -(float)k / (float)g.M);
+    const float df = (float)(int)g.d;
+    const float qa = fmaf(atan2f(zy, zx), df * 0.15915494309189533577f, -k_over_M(k, g.M));
     const float fr = qa - rintf(qa);
     const float err_t = 10.0f * err * df * 0.15915494309189533577f;
     if (!(err_t < 0.25f)) return -1;
     if (fabsf(fabsf(fr) - 0.5f) < fmaxf(fmaxf(1e-3f, 8e-7f * df), err_t)) return -1;
-    int64_t t = ((int64_t)rintf(qa)) % g.d;
-    if (t < 0) t += g.d;
-    s[j] = k + t * g.M;
+    s[j] = k + cand_of(__float2int_rn(qa), g.d) * g.M;
     w[j] = omega_ff(omff, s[j]);
     const float dx = zx - ff_re(w[j]), dy = zy - ff_im(w[j]);
     const float dz = dx * dx + dy * dy;

@@ -633,9 +633,9 @@ __device__ void solve_bin(const GenArgs& g, int b, int64_t k, int e) {
         const float fl = floorf(u), fr = u - fl;
         const float margin = fmaxf(1e-3f, 8e-7f * df);
         if (fr > margin && fr < 1.0f - margin) {
-          int64_t t0 = ((int64_t)fl) % d;
-          if (t0 < 0) t0 += d;
-          const int64_t t1 = (t0 + 1) % d;
+          // d is a power of two: the masks are the modulo, negatives too
+          const int64_t t0 = (int64_t)((int)fl & (int)(d - 1));
+          const int64_t t1 = (t0 + 1) & (d - 1);
           bt[0] = (int)min(t0, t1);
           bt[1] = (int)max(t0, t1);
           have = 2;
