@@ -238,11 +238,13 @@ __global__ void __launch_bounds__(256) k_extract(const In* __restrict__ x, int64
                                                  int64_t n_flat) {
   if constexpr (!kNarrow) {
     if (n_flat > 0) {
-      // grid-stride over the n_flat = signals x M0 rows (row f: signal f / M0)
+      // grid-stride over the n_flat = signals x M0 rows (row f: signal f / M0,
+      // M0 a power of two)
+      const int lm0 = __ffsll(M0) - 1;
       for (int64_t f = (int64_t)blockIdx.x * 256 + threadIdx.x; f < n_flat;
            f += (int64_t)gridDim.x * 256)
         extract_row<In, kNarrow>(x, x_stride, x_table, N, d, M0, levels, fixed_nsh, C, c_sig,
-                                 (int)(f / M0), f % M0);
+                                 (int)(f >> lm0), f & (M0 - 1));
       return;
     }
   }
@@ -309,8 +311,9 @@ __global__ void __launch_bounds__(8192 / PTS) k_fft4_cols(
     __syncthreads();
   }
   typename F::Out* Wo = W + (int64_t)b * w_sig + (int64_t)js * ((int64_t)M1 * M2);
+  const int lcb = __ffs(CB) - 1;  // CB, M1, M2, RB are powers of two: shifts and masks
   for (int idx = tid; idx < CB * M1; idx += blockDim.x) {
-    const int k1 = idx / CB, c = idx % CB;
+    const int k1 = idx >> lcb, c = idx & (CB - 1);
     const char* bc = smem + (size_t)c * padded(M1) * F::kBytesPerPoint;
     Wo[(int64_t)k1 * M2 + c0 + c] = F::out(F::ld(bc, M1, k1), 1);
   }
@@ -330,8 +333,9 @@ __global__ void __launch_bounds__(8192 / PTS) k_fft4_rows(
   const int tid = threadIdx.x, g = tid / tpg, t = tid % tpg;
   const int r0 = blockIdx.x * RB;
   const Out* Wi = W + (int64_t)b * w_sig + (int64_t)js * ((int64_t)M1 * M2);
+  const int lrb = __ffs(RB) - 1;  // RB and M2 are powers of two: shifts and masks
   for (int idx = tid; idx < RB * M2; idx += blockDim.x) {
-    const int gg = idx / M2, c = idx % M2;
+    const int gg = idx >> log2M2, c = idx & (M2 - 1);
     char* bg = smem + (size_t)gg * padded(M2) * F::kBytesPerPoint;
     F::st(bg, M2, c, F::from_out(Wi[(int64_t)(r0 + gg) * M2 + c]));
   }
@@ -345,7 +349,7 @@ __global__ void __launch_bounds__(8192 / PTS) k_fft4_rows(
   typename std::conditional<std::is_same<F, F64>::value, double, float>::type lmax_t = 0;
   const auto scale = (typename std::conditional<std::is_same<F, F64>::value, double, float>::type)d;
   for (int idx = tid; idx < RB * M2; idx += blockDim.x) {
-    const int k2 = idx / RB, gg = idx % RB;
+    const int k2 = idx >> lrb, gg = idx & (RB - 1);
     const char* bg = smem + (size_t)gg * padded(M2) * F::kBytesPerPoint;
     const Out w = F::out(F::ld(bg, M2, k2), scale);
     o[(int64_t)(r0 + gg) + (int64_t)M1 * k2] = w;

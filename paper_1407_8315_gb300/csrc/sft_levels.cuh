@@ -85,7 +85,7 @@ __device__ __forceinline__ bool fold_bin(const LevelArgs& g, int b, int64_t k) {
     uint8_t t = 0;
     if (l > 0) t = (uint8_t)(g.Tprev[(int64_t)b * M0 + k] | g.Tprev[(int64_t)b * M0 + k + M]);
     const unsigned long long ymax_bits = g.ymax2[b];
-    const int64_t nsub = M0 / M;
+    const int64_t nsub = int64_t(1) << l;  // M0 / M
     if constexpr (std::is_same<F, F64>::value) {
       cdbl m[nm];
       // fold the syndromes held from level l-1 (length 2M) to length M
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kFoldThreads, FoldOccupancy<F>::kMinBlocks)
   int64_t k;
   if (n_flat > 0) {
     const int64_t f = (int64_t)blockIdx.x * kFoldThreads + threadIdx.x;
-    b = (int)(f / g.M);
+    b = (int)(f >> (__ffsll(g.M) - 1));  // M is a power of two
     k = f < n_flat ? f - (int64_t)b * g.M : g.M;  // past the end: no bin
   } else {
     b = blockIdx.y;
