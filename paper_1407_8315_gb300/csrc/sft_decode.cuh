@@ -26,6 +26,15 @@
 
 namespace sft {
 
+// Squared magnitudes (non-negative doubles) order like their bit patterns
+// as integers, NaN above +inf: their maxima and comparisons run on the
+// integer pipes instead of occupying GB300's scarce FP64 unit.
+__device__ __forceinline__ long long ordbits(double v) { return __double_as_longlong(v); }
+// z == 0 (either sign of zero in both parts), on the bit patterns
+__device__ __forceinline__ bool is_zero_c(cdbl z) {
+  return ((__double_as_longlong(z.x) | __double_as_longlong(z.y)) << 1) == 0;
+}
+
 // 1/x: an FP32 seed refined by two Newton steps r <- r + r (1 - x r) (each
 // doubles the correct bits: ~2^-22 -> 2^-44 -> below an FP64 ulp); an
 // exact FP64 division when |x| lies outside [2^-123, 2^124).  The seed's
@@ -62,7 +71,7 @@ __device__ __forceinline__ cdbl csqrt_fast(cdbl v) {
 // a cube root of v: FP32 polar estimate, two FP64 Newton steps
 // u <- (2u + v / u^2) / 3
 __device__ __forceinline__ cdbl ccbrt_any(cdbl v) {
-  if (v.x == 0.0 && v.y == 0.0) return cdbl{0.0, 0.0};
+  if (is_zero_c(v)) return cdbl{0.0, 0.0};
   const float rf = cbrtf((float)sqrt(norm2(v)));
   const float th = atan2f((float)v.y, (float)v.x) * (1.0f / 3.0f);
   float sf, cf;
@@ -80,23 +89,25 @@ __device__ __forceinline__ cdbl ccbrt_any(cdbl v) {
 // A is row-major and destroyed.  Fails on a pivot below 1e-14 of max |A|.
 template <int n>
 __device__ __forceinline__ bool solve_small(cdbl* A, cdbl* b, cdbl* x) {
-  double amax2 = 0.0;
+  long long amax_b = 0;
 #pragma unroll
-  for (int i = 0; i < n * n; ++i) amax2 = fmax(amax2, norm2(A[i]));
+  for (int i = 0; i < n * n; ++i) amax_b = max(amax_b, ordbits(norm2(A[i])));
+  const double amax2 = __longlong_as_double(amax_b);
   if (!(amax2 > 0.0)) return false;
   cdbl inv[n];
 #pragma unroll
   for (int col = 0; col < n; ++col) {
     int piv = col;
-    double best = norm2(A[col * n + col]);
+    long long best_b = ordbits(norm2(A[col * n + col]));
 #pragma unroll
     for (int r = col + 1; r < n; ++r) {
-      const double v = norm2(A[r * n + col]);
-      if (v > best) {
-        best = v;
+      const long long v = ordbits(norm2(A[r * n + col]));
+      if (v > best_b) {
+        best_b = v;
         piv = r;
       }
     }
+    const double best = __longlong_as_double(best_b);
     if (!(best > 1e-28 * amax2)) return false;
 #pragma unroll
     for (int r = col + 1; r < n; ++r) {
@@ -112,7 +123,8 @@ __device__ __forceinline__ bool solve_small(cdbl* A, cdbl* b, cdbl* x) {
         b[r] = t;
       }
     }
-    inv[col] = crcp(A[col * n + col]);
+    // 1 / pivot = conj(pivot) / |pivot|^2, |pivot|^2 being `best`
+    inv[col] = conjd(A[col * n + col]) * rcp_d(best);
 #pragma unroll
     for (int r = col + 1; r < n; ++r) {
       const cdbl f = A[r * n + col] * inv[col];
@@ -136,8 +148,8 @@ __device__ __forceinline__ bool solve_small(cdbl* A, cdbl* b, cdbl* x) {
 __device__ __forceinline__ void quad_roots(cdbl b, cdbl c, cdbl* z) {
   const cdbl sq = csqrt_fast(b * b - c * 4.0);
   const cdbl qp = b + sq, qm = b - sq;
-  const cdbl q = (norm2(qp) >= norm2(qm) ? qp : qm) * -0.5;
-  if (q.x == 0.0 && q.y == 0.0) {
+  const cdbl q = (ordbits(norm2(qp)) >= ordbits(norm2(qm)) ? qp : qm) * -0.5;
+  if (is_zero_c(q)) {
     z[0] = z[1] = mk(0.0, 0.0);
     return;
   }
@@ -154,13 +166,13 @@ __device__ __forceinline__ void cubic_roots(cdbl c2, cdbl c1, cdbl c0, cdbl* z) 
   const cdbl q = c2 * c2 * c2 * (2.0 / 27.0) - c2 * c1 * (1.0 / 3.0) + c0;
   const cdbl sD = csqrt_fast(q * q * 0.25 + p * p * p * (1.0 / 27.0));
   const cdbl w1 = q * -0.5 + sD, w2 = q * -0.5 - sD;
-  const cdbl u = ccbrt_any(norm2(w1) >= norm2(w2) ? w1 : w2);
+  const cdbl u = ccbrt_any(ordbits(norm2(w1)) >= ordbits(norm2(w2)) ? w1 : w2);
   const cdbl br[3] = {mk(1.0, 0.0), mk(-0.5, 0.86602540378443864676),
                       mk(-0.5, -0.86602540378443864676)};
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     const cdbl uj = u * br[j];
-    const cdbl vj = (uj.x == 0.0 && uj.y == 0.0) ? mk(0.0, 0.0) : (-p) * crcp(uj * 3.0);
+    const cdbl vj = is_zero_c(uj) ? mk(0.0, 0.0) : (-p) * crcp(uj * 3.0);
     z[j] = uj + vj - sh;
   }
 }
@@ -177,11 +189,11 @@ __device__ __forceinline__ void quartic_roots(cdbl c3, cdbl c2, cdbl c1, cdbl c0
   cdbl mr[3];
   cubic_roots(p, (p * p * 2.0 - r * 8.0) * (1.0 / 8.0), q * q * (-1.0 / 8.0), mr);
   int best = 0;
-  if (norm2(mr[1]) > norm2(mr[best])) best = 1;
-  if (norm2(mr[2]) > norm2(mr[best])) best = 2;
+  if (ordbits(norm2(mr[1])) > ordbits(norm2(mr[best]))) best = 1;
+  if (ordbits(norm2(mr[2])) > ordbits(norm2(mr[best]))) best = 2;
   const cdbl m = mr[best];
   cdbl y[4];
-  if (m.x == 0.0 && m.y == 0.0) {
+  if (is_zero_c(m)) {
     cdbl w[2];
     quad_roots(p, r, w);
     y[0] = csqrt_fast(w[0]);
@@ -732,7 +744,7 @@ __device__ __forceinline__ bool decode_bin(cdbl* m, int64_t k, const BinGeom& g,
     cdbl w[a];
 #pragma unroll
     for (int j = 0; j < a; ++j) {
-      if (!(isfinite(z[j].x) && isfinite(z[j].y)) || (z[j].x == 0.0 && z[j].y == 0.0)) return false;
+      if (!(isfinite(z[j].x) && isfinite(z[j].y)) || is_zero_c(z[j])) return false;
       s[j] = snap_root(z[j], k, g);
       w[j] = omega_pow(g.om, s[j]);
       if (!(norm2(z[j] - w[j]) <= tol.root2)) return false;
