@@ -68,8 +68,11 @@ __device__ __forceinline__ cdbl csqrt_fast(cdbl v) {
   const double t = sqrt(0.5 * (r - v.x));
   return cdbl{fabs(v.y) * (0.5 * rcp_d(t)), copysign(t, v.y)};
 }
-// a cube root of v: FP32 polar estimate, two FP64 Newton steps
-// u <- (2u + v / u^2) / 3
+// a cube root of v: FP32 polar estimate (relative error ~1e-6), one FP64
+// Newton step u <- (2u + v / u^2) / 3 (quadratic: ~1e-12).  The roots it
+// yields only choose candidates (an angle against margins of 1e-3 of a
+// candidate spacing) and pass the 0.1 root tolerance; the values come from
+// the candidates themselves.
 __device__ __forceinline__ cdbl ccbrt_any(cdbl v) {
   if (is_zero_c(v)) return cdbl{0.0, 0.0};
   const float rf = cbrtf((float)sqrt(norm2(v)));
@@ -77,11 +80,8 @@ __device__ __forceinline__ cdbl ccbrt_any(cdbl v) {
   float sf, cf;
   sincosf(th, &sf, &cf);
   cdbl u{(double)(rf * cf), (double)(rf * sf)};
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const cdbl u2 = u * u;
-    u = (u * 2.0 + v * crcp(u2)) * (1.0 / 3.0);
-  }
+  const cdbl u2 = u * u;
+  u = (u * 2.0 + v * crcp(u2)) * (1.0 / 3.0);
   return u;
 }
 
@@ -309,7 +309,7 @@ __device__ __forceinline__ int ff_residual_ok(const float4* raw, const int64_t* 
     rmax2 = fmaxf(rmax2, rx * rx + ry * ry);
   }
   if (!(mmax2 < 1e36f) || !(rmax2 < 1e36f)) return -1;
-  if (!((double)rmax2 <= res2 * (double)mmax2)) return 0;
+  if (!(f2d_exact(rmax2) <= res2 * f2d_exact(mmax2))) return 0;
   if (res_out != nullptr) {
 #pragma unroll
     for (int i = 0; i < nm; ++i) res_out[i] = FF::to4(r[i]);
