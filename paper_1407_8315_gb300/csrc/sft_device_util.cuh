@@ -37,11 +37,15 @@ __device__ __forceinline__ void file_solution(const int64_t* s, const cdbl* p, i
   }
 }
 
-// File one recovered frequency whose value is already float-float.
+// File one recovered frequency whose value is already float-float.  With
+// kFirst the bin is known to hold nothing yet (level 0 of ITER: the counts
+// are zeroed per call and only bin k's own thread files under k), so its
+// count is not read -- one dependent load fewer per decoded bin.
+template <bool kFirst = false>
 __device__ __forceinline__ void file_one_ff(int64_t s, float4 p, int64_t M0, uint8_t* cnt,
                                             int64_t* ss, float4* sp, int32_t* flag) {
   const int64_t k0 = s & (M0 - 1);
-  const int c = cnt[k0];
+  const int c = kFirst ? 0 : cnt[k0];
   if (c < kSlots) {
     ss[slot_ix(k0, c, M0)] = s;
     sp[slot_ix(k0, c, M0)] = p;

@@ -237,11 +237,14 @@ __device__ __forceinline__ void decode_level_bin(const LevelArgs& g, int b, int6
       else
         fast = decode_a2_ff<nm>(raw, k, geom, tolf, g.omff, s, pf, res);
       if (fast == 1) {
+        // level 0 (one alias): nothing is filed under a level-0 bin before
+        // its own decode
 #pragma unroll
         for (int j = 0; j < A; ++j)
-          file_one_ff(s[j], pf[j], M0, g.slot_cnt + (int64_t)b * M0,
-                      g.slot_s + (int64_t)b * M0 * kSlots,
-                      reinterpret_cast<float4*>(g.slot_p) + (int64_t)b * M0 * kSlots, g.flags + b);
+          file_one_ff<A == 1>(s[j], pf[j], M0, g.slot_cnt + (int64_t)b * M0,
+                              g.slot_s + (int64_t)b * M0 * kSlots,
+                              reinterpret_cast<float4*>(g.slot_p) + (int64_t)b * M0 * kSlots,
+                              g.flags + b);
         ok = filed = true;
       }
     }
@@ -406,9 +409,10 @@ __global__ void __launch_bounds__(kDecThreads) k_fixed_round(FixedArgs g, const 
         if (fast == 1) {
 #pragma unroll
           for (int j = 0; j < A; ++j)
-            file_one_ff(s[j], pf[j], M, g.slot_cnt + (int64_t)b * M,
-                        g.slot_s + (int64_t)b * M * kSlots,
-                        reinterpret_cast<float4*>(g.slot_p) + (int64_t)b * M * kSlots, g.flags + b);
+            file_one_ff<A == 1>(s[j], pf[j], M, g.slot_cnt + (int64_t)b * M,
+                                g.slot_s + (int64_t)b * M * kSlots,
+                                reinterpret_cast<float4*>(g.slot_p) + (int64_t)b * M * kSlots,
+                                g.flags + b);
           ok = filed = true;
         }
       }
