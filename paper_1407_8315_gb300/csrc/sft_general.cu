@@ -70,7 +70,9 @@ __device__ void hankel_svals(const cdbl* m, double* sv) {
 #pragma unroll
     for (int j = 0; j < n; ++j) A[i * n + j] = m[i + j];
   for (int sweep = 0; sweep < 30; ++sweep) {
-    double off = 0.0;
+    // a sweep that rotates no pair (every |gamma| <= 1e-15 sqrt(alpha beta),
+    // compared squared) ends the iteration
+    bool rotated = false;
 #pragma unroll
     for (int p = 0; p < n; ++p) {
 #pragma unroll
@@ -85,14 +87,15 @@ __device__ void hankel_svals(const cdbl* m, double* sv) {
         }
         const double g2 = norm2(gamma), ab = alpha * beta;
         if (!(g2 > 0.0) || !(ab > 0.0)) continue;
-        const double g = sqrt(g2), sab = sqrt(ab);
-        off = fmax(off, g / sab);
-        if (!(g > 1e-15 * sab)) continue;
-        const double ig = 1.0 / g;
+        if (!(g2 > 1e-30 * ab)) continue;
+        rotated = true;
+        // 1/|gamma| and the rotation's cosine as reciprocal square roots,
+        // tan by the reciprocal (fewer FP64 square roots and divisions)
+        const double ig = rsqrt(g2);
         const cdbl phc = mk(gamma.x * ig, -gamma.y * ig);  // conj(gamma / |gamma|)
         const double zeta = (beta - alpha) * (0.5 * ig);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) * rcp_d(fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = rsqrt(1.0 + t * t), s = c * t;
 #pragma unroll
         for (int i = 0; i < n; ++i) {
           const cdbl ap = A[i * n + p], aq = A[i * n + q] * phc;
@@ -101,7 +104,7 @@ __device__ void hankel_svals(const cdbl* m, double* sv) {
         }
       }
     }
-    if (off <= 1e-15) break;
+    if (!rotated) break;
   }
 #pragma unroll
   for (int j = 0; j < n; ++j) {
@@ -453,21 +456,24 @@ __device__ __noinline__ double ls_cols(int rows, int cols, const cdbl* phi, cons
       for (int v = 0; v < nT; ++v) G[u * C + v] = G[u * C + v] + cu * phi[i * cols + T[v]];
     }
   }
-  double amax2 = 0.0;
+  // squared magnitudes compared on their bit patterns (integer pipes)
+  long long amax_b = 0;
   for (int u = 0; u < nT; ++u)
-    for (int v = 0; v < nT; ++v) amax2 = fmax(amax2, norm2(G[u * C + v]));
+    for (int v = 0; v < nT; ++v) amax_b = max(amax_b, ordbits(norm2(G[u * C + v])));
+  const double amax2 = __longlong_as_double(amax_b);
   if (!(amax2 > 0.0)) return -1.0;
   cdbl inv[C];
   for (int c = 0; c < nT; ++c) {
     int piv = c;
-    double best = norm2(G[c * C + c]);
+    long long best_b = ordbits(norm2(G[c * C + c]));
     for (int rr = c + 1; rr < nT; ++rr) {
-      const double v = norm2(G[rr * C + c]);
-      if (v > best) {
-        best = v;
+      const long long v = ordbits(norm2(G[rr * C + c]));
+      if (v > best_b) {
+        best_b = v;
         piv = rr;
       }
     }
+    const double best = __longlong_as_double(best_b);
     if (!(best > 1e-28 * amax2)) return -1.0;
     if (piv != c) {
       for (int q = 0; q < nT; ++q) {
@@ -479,7 +485,7 @@ __device__ __noinline__ double ls_cols(int rows, int cols, const cdbl* phi, cons
       gv[c] = gv[piv];
       gv[piv] = t;
     }
-    inv[c] = crcp(G[c * C + c]);
+    inv[c] = conjd(G[c * C + c]) * rcp_d(best);  // 1 / pivot
     for (int rr = c + 1; rr < nT; ++rr) {
       const cdbl f = G[rr * C + c] * inv[c];
       for (int q = c + 1; q < nT; ++q) G[rr * C + q] = G[rr * C + q] - f * G[c * C + q];
