@@ -486,6 +486,27 @@ sft_status sft_plan_stage_times(sft_plan_t plan, int32_t cap, const char** names
 sft_status sft_plan_stage_timeline(sft_plan_t plan, int32_t cap, const char** names, int32_t* sub,
                                    double* t0_ms, double* t1_ms, int32_t* n);
 
+/* The device arithmetic the FP64 decoders build on, evaluated elementwise,
+ * so that it can be checked against correctly rounded references.  x and
+ * out are device arrays of n doubles (which = 0, 1) or n complex values as
+ * (re, im) pairs, 2n doubles (which = 2), owned by the caller; the call is
+ * enqueued on `stream` (NULL: the default stream) and returns without
+ * waiting.
+ *   which = 0: the reciprocal 1/x (an FP32 seed whose operand is x
+ *              truncated to float and whose result is widened back, both
+ *              by moving bits, then two Newton steps r <- r + r (1 - x r);
+ *              an FP64 division for |x| outside [2^-123, 2^124));
+ *   which = 1: the float nearest x widened back to double by moving bits
+ *              (exact);
+ *   which = 2: the principal complex square root of the closed-form roots
+ *              (cancellation-free form, the reciprocal above for its
+ *              quotient), for values whose squared magnitude is a normal
+ *              double.
+ * SFT_EINVAL on n < 0, which outside 0..2, or NULL arrays with n > 0;
+ * SFT_ECUDA if the launch fails. */
+sft_status sft_device_math_check(const double* x, int64_t n, double* out, int32_t which,
+                                 void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* sft_strerror(sft_status s);
 

@@ -609,6 +609,19 @@ sft_status sft_plan_stage_timeline(sft_plan_t P, int32_t cap, const char** names
   return SFT_OK;
 }
 
+sft_status sft_device_math_check(const double* x, int64_t n, double* out, int32_t which,
+                                 void* stream) {
+  if (n < 0 || which < 0 || which > 2 || (n > 0 && (x == nullptr || out == nullptr)))
+    return SFT_EINVAL;
+  if (n == 0) return SFT_OK;
+  const cudaError_t e = sft::launch_selfcheck(x, n, out, which, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    note_cuda(e);
+    return SFT_ECUDA;
+  }
+  return SFT_OK;
+}
+
 const char* sft_strerror(sft_status s) {
   switch (s) {
     case SFT_OK: return "SFT_OK";

@@ -305,6 +305,8 @@ void launch_general_features(sft_plan_s* P, int64_t B, const void* x, int64_t x_
 // largest support logits of every queued voted bin into P->mlp_prop; and
 // the features alone, written out.
 void mlp_propose(sft_plan_s* P, int64_t B, int nsm, cudaStream_t st);
+cudaError_t launch_selfcheck(const double* x, int64_t n, double* out, int which,
+                             cudaStream_t st);
 void mlp_features(sft_plan_s* P, int64_t B, int nsm, float* feat, int32_t* rows, int64_t cap_rows,
                   cudaStream_t st);
 // Sets the calling thread's error detail returned by sft_last_cuda_error.

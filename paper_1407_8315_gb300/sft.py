@@ -56,7 +56,7 @@ EXPORTS = ["sft_params_default", "sft_plan_create", "sft_plan_destroy", "sft_pla
            "sft_mlp_forward", "sft_mlp_grad", "sft_mlp_train", "sft_plan_attach_mlp",
            "sft_exact_auto", "sft_alias_histogram", "sft_plan_set_sub_batches",
            "sft_plan_sub_batches", "sft_plan_set_quad_decoders", "sft_plan_queue_lengths",
-           "sft_plan_stage_timeline"]
+           "sft_plan_stage_timeline", "sft_device_math_check"]
 
 _lib = None
 
@@ -108,6 +108,8 @@ def load(build_if_missing: bool = False):
     lib.sft_plan_set_profiling.argtypes = [C.c_void_p, C.c_int32]
     lib.sft_plan_stage_times.argtypes = [C.c_void_p, C.c_int32, P(C.c_char_p), P(C.c_double),
                                          P(C.c_int64), P(C.c_int32)]
+    lib.sft_device_math_check.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32,
+                                          C.c_void_p]
     lib.sft_plan_stage_timeline.argtypes = [C.c_void_p, C.c_int32, P(C.c_char_p), P(C.c_int32),
                                             P(C.c_double), P(C.c_double), P(C.c_int32)]
     lib.sft_exact_noalloc.argtypes = [P(sft_params), C.c_int64, C.c_void_p, C.c_int64,
@@ -370,6 +372,15 @@ def sft_plan_stage_times(handle: int) -> dict:
     _check(load().sft_plan_stage_times(C.c_void_p(handle), cap, names, ms, cnt, C.byref(n)),
            "sft_plan_stage_times")
     return {names[i].decode(): (ms[i], int(cnt[i])) for i in range(min(n.value, cap))}
+
+
+def sft_device_math_check(x_ptr: int, n: int, out_ptr: int, which: int, stream: int = 0):
+    """The decoders' device arithmetic on n elements (device pointers; see
+    the header): 0 the reciprocal, 1 the float-to-double widening, 2 the
+    complex square root (n complex values)."""
+    _check(load().sft_device_math_check(C.c_void_p(x_ptr), int(n), C.c_void_p(out_ptr),
+                                        int(which), C.c_void_p(stream)),
+           "sft_device_math_check")
 
 
 def sft_plan_stage_timeline(handle: int, cap: int = 4096) -> list:

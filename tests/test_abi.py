@@ -191,3 +191,12 @@ def test_product_code_never_reaches_the_oracle():
     for f in files:
         m = bad.search(f.read_text())
         assert m is None, (str(f), m.group(0))
+
+
+def test_device_math_check_validates_before_launching(lib):
+    """Bad arguments are refused before any CUDA call; n = 0 is a no-op."""
+    from paper_1407_8315_gb300 import sft
+    assert lib.sft_device_math_check(None, -1, None, 0, None) == sft.SFT_EINVAL
+    assert lib.sft_device_math_check(None, 4, None, 0, None) == sft.SFT_EINVAL
+    assert lib.sft_device_math_check(None, 0, None, 3, None) == sft.SFT_EINVAL
+    assert lib.sft_device_math_check(None, 0, None, 1, None) == sft.SFT_OK
