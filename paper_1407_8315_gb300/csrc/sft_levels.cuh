@@ -285,6 +285,14 @@ template <class F>
 struct DecOccupancy {
   template <int A>
   static constexpr int min_blocks() { return std::is_same<F, FF>::value && A == 2 ? 4 : 1; }
+  // FIXED rounds 1 and 2 on the mixed path (all 2 a_max syndromes held):
+  // five and four CTAs per SM (96 and 128 registers, a few bytes spilled;
+  // 128 and 168 uncapped): round 1 0.185 -> 0.169, round 2 0.263 -> 0.212 ms
+  // per call at 608 signals
+  template <int A>
+  static constexpr int min_blocks_fixed() {
+    return !std::is_same<F, FF>::value ? 1 : (A == 1 ? 5 : (A == 2 ? 4 : 1));
+  }
 };
 template <class F, int A>
 __global__ void __launch_bounds__(kDecThreads, DecOccupancy<F>::template min_blocks<A>())
@@ -382,7 +390,8 @@ __global__ void __launch_bounds__(kFoldThreads) k_fixed_scan(FixedArgs g, int2* 
 // round a: decode the queued bins with a aliases; failures go to the next
 // round's queue, or are marked unsolved after the last round (a = a_max)
 template <class F, int A, int NM>
-__global__ void __launch_bounds__(kDecThreads) k_fixed_round(FixedArgs g, const int2* qin,
+__global__ void __launch_bounds__(kDecThreads, DecOccupancy<F>::template min_blocks_fixed<A>())
+    k_fixed_round(FixedArgs g, const int2* qin,
                                                              const int* nin, int2* qout,
                                                              int* nout, int n_quad_max = -1) {
   typedef typename Store<F>::T T;
