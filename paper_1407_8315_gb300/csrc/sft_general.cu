@@ -21,6 +21,8 @@
 //                  Steps 2-3), Subspace Pursuit on the pruned sensing matrix
 //                  Phi_p (Algorithm 2, Parts 3-4)
 //   k_finalize     as for the exact transform
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cstdio>
 #include <type_traits>
@@ -293,14 +295,21 @@ __device__ __forceinline__ int gen_block_scan(int v, int* total) {
 }
 
 // K-th largest of the n non-negative doubles `keys` (as bit patterns) of
-// one CTA's signal: MSB-first radix select, 8 passes of 8 bits.  Returns the
-// K-th largest key and, in *rem_out, how many of the keys equal to it are
-// among the K largest (0 < K <= n).
+// one signal: MSB-first radix select, 8 passes of 8 bits.  Returns the K-th
+// largest key and, in *rem_out, how many of the keys equal to it are among
+// the K largest (0 < K <= n).
 //
-// The histogram counts are aggregated per warp (one shared atomic per
-// distinct digit in a warp, not one per key), and once the keys still
-// matching the selected prefix fit in shared memory they are copied there,
-// so that the remaining passes read no global memory.
+// The signal is the work of one thread-block cluster (one CTA when the
+// signals alone fill the GPU, up to eight when they are few): each CTA
+// histograms a strided slice of the keys, and after a cluster barrier every
+// CTA sums the cluster's histograms through distributed shared memory and
+// takes the same digit.  The counts are integers, so the result does not
+// depend on the cluster size.  The histogram counts are aggregated per warp
+// (one shared atomic per distinct digit in a warp, not one per key), and
+// once the keys still matching the selected prefix fit in shared memory
+// (cluster-wide) each CTA copies its slice's there, so that the remaining
+// passes read no global memory.  Every thread of every CTA of the cluster
+// must call this.
 constexpr int kSelCand = 4096;
 
 __device__ __forceinline__ void hist_add(unsigned* hist, unsigned digit, bool pred) {
@@ -314,19 +323,25 @@ __device__ __forceinline__ void hist_add(unsigned* hist, unsigned digit, bool pr
 
 __device__ unsigned long long radix_select_desc(const unsigned long long* keys, int64_t n,
                                                 long long K, long long* rem_out) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   __shared__ unsigned hist[256];
+  __shared__ unsigned tot[256];
   __shared__ unsigned long long s_prefix;
   __shared__ long long s_rem;
   __shared__ unsigned s_sel_count;
   __shared__ int s_nc;
   __shared__ unsigned long long cand[kSelCand];
   const int tid = threadIdx.x, nthr = blockDim.x;
+  const int64_t gtid = (int64_t)rank * nthr + tid, gstride = (int64_t)C * nthr;
   unsigned long long prefix = 0ull, mask = 0ull;
   long long rem = K;  // rank (from the top) still to find among keys matching prefix
   bool in_smem = false;
   int nc = 0;
   for (int pass = 0; pass < 8; ++pass) {
     const int shift = 56 - 8 * pass;
+    cl.sync();  // no CTA still reads this CTA's previous histogram
     for (int i = tid; i < 256; i += nthr) hist[i] = 0u;
     __syncthreads();
     if (in_smem) {
@@ -335,34 +350,41 @@ __device__ unsigned long long radix_select_desc(const unsigned long long* keys, 
         hist_add(hist, (unsigned)((key >> shift) & 255ull), (key & mask) == prefix);
       }
     } else {
-      for (int64_t i = tid; i < n; i += nthr) {
+      for (int64_t i = gtid; i < n; i += gstride) {
         const unsigned long long key = keys[i];
         hist_add(hist, (unsigned)((key >> shift) & 255ull), (key & mask) == prefix);
       }
+    }
+    cl.sync();  // every CTA's histogram complete
+    for (int i = tid; i < 256; i += nthr) {
+      unsigned t = 0u;
+      for (int r = 0; r < C; ++r) t += cl.map_shared_rank(hist, r)[i];
+      tot[i] = t;
     }
     __syncthreads();
     if (tid == 0) {
       long long cum = 0;
       int sel = 0;
       for (int dg = 255; dg >= 0; --dg) {
-        if (cum + (long long)hist[dg] >= rem) {
+        if (cum + (long long)tot[dg] >= rem) {
           sel = dg;
           break;
         }
-        cum += hist[dg];
+        cum += tot[dg];
       }
       s_prefix = prefix | ((unsigned long long)sel << shift);
       s_rem = rem - cum;
-      s_sel_count = hist[sel];
+      s_sel_count = tot[sel];
       s_nc = 0;
     }
     __syncthreads();
     prefix = s_prefix;
     rem = s_rem;
     mask |= 255ull << shift;
-    // gather the keys matching the new prefix into shared memory once they fit
+    // gather this CTA's keys matching the new prefix into shared memory once
+    // the cluster's fit (this CTA's are a part of them)
     if (!in_smem && pass < 7 && s_sel_count <= (unsigned)kSelCand) {
-      for (int64_t i = tid; i < n; i += nthr) {
+      for (int64_t i = gtid; i < n; i += gstride) {
         const unsigned long long key = keys[i];
         if ((key & mask) == prefix) cand[atomicAdd(&s_nc, 1)] = key;
       }
@@ -372,14 +394,18 @@ __device__ unsigned long long radix_select_desc(const unsigned long long* keys, 
     }
     __syncthreads();
   }
+  cl.sync();  // the last histograms have been read: CTAs may go on (and exit)
   *rem_out = rem;
   return prefix;
 }
 
 // tau_L per signal: the K-th largest of the M bins' lower bounds (0 when K
 // is 0 or not below M, which disables pruning)
-__global__ void __launch_bounds__(1024) k_gen_tau(GenArgs g) {
-  const int b = blockIdx.x;
+// (one cluster per signal, launched by launch_per_signal)
+__global__ void __launch_bounds__(1024, 1) k_gen_tau(GenArgs g) {
+  namespace cg = cooperative_groups;
+  const cg::cluster_group cl = cg::this_cluster();
+  const int b = (int)(blockIdx.x / cl.num_blocks());
   const int64_t Kb = g.K_table != nullptr ? g.K_table[b] : g.K;
   double tau = 0.0;
   if (Kb > 0 && Kb < g.M) {
@@ -388,14 +414,21 @@ __global__ void __launch_bounds__(1024) k_gen_tau(GenArgs g) {
         reinterpret_cast<const unsigned long long*>(g.lbound + (int64_t)b * g.M), g.M, Kb, &rem);
     tau = __longlong_as_double((long long)key);
   }
-  if (threadIdx.x == 0) g.tau_lo[b] = tau;
+  if (threadIdx.x == 0 && cl.block_rank() == 0) g.tau_lo[b] = tau;
 }
 
 // Algorithm 2, the vote: the K largest of the M a_m singular values of one signal
 // (radix select on their bit patterns); of the values equal to the K-th
 // largest tau, those of lowest index are selected.
-__global__ void __launch_bounds__(1024) k_gen_vote(GenArgs g) {
-  const int b = blockIdx.x;
+// One cluster per signal (launched by launch_per_signal): CTA rank r of C
+// assigns the bins of the r-th of C consecutive chunks; the ties' order
+// across CTAs comes from the lower ranks' tie counts (distributed shared
+// memory).
+__global__ void __launch_bounds__(1024, 1) k_gen_vote(GenArgs g) {
+  namespace cg = cooperative_groups;
+  const cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int b = (int)(blockIdx.x / C);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int am = g.a_max;
   const int64_t n = g.M * am;
@@ -408,14 +441,24 @@ __global__ void __launch_bounds__(1024) k_gen_vote(GenArgs g) {
   long long rem = 0;
   if (K > 0) prefix = radix_select_desc(keys, n, K, &rem);
   const unsigned long long tau = prefix;  // K-th largest key
-  // per-thread chunk of whole bins, in index order
-  const int64_t chunk = (g.M + nthr - 1) / nthr;
-  const int64_t k_lo = min((int64_t)tid * chunk, g.M), k_hi = min(k_lo + chunk, g.M);
+  // this CTA's chunk of bins, then a per-thread chunk of it, in index order
+  const int64_t cchunk = (g.M + C - 1) / C;
+  const int64_t c_lo = min((int64_t)rank * cchunk, g.M), c_hi = min(c_lo + cchunk, g.M);
+  const int64_t chunk = (c_hi - c_lo + nthr - 1) / nthr;
+  const int64_t k_lo = min(c_lo + (int64_t)tid * chunk, c_hi), k_hi = min(k_lo + chunk, c_hi);
   int ties = 0;
   if (K > 0)
     for (int64_t i = k_lo * am; i < k_hi * am; ++i) ties += keys[i] == tau;
   int tie_total = 0;
   int tie_before = gen_block_scan(ties, &tie_total);
+  // ties in the chunks of the lower ranks come first
+  __shared__ int s_ties;
+  if (tid == 0) s_ties = tie_total;
+  cl.sync();
+  int tie_lower = 0;
+  for (int r = 0; r < rank; ++r) tie_lower += *cl.map_shared_rank(&s_ties, r);
+  cl.sync();  // every CTA has read the counts it needs
+  tie_before += tie_lower;
   for (int64_t k = k_lo; k < k_hi; ++k) {
     int a = 0;
     if (K > 0) {
@@ -435,6 +478,28 @@ __global__ void __launch_bounds__(1024) k_gen_vote(GenArgs g) {
     else if (a > 1)
       g.queue[g.qcap - 1 - atomicAdd(g.qcount_hi, 1)] = make_int2(b, (int)k);
   }
+}
+
+// One thread-block cluster of 1024-thread CTAs per signal: one CTA when the
+// signals fill the GPU, else up to eight (a power of two), so that a few
+// signals' selections still spread over the SMs.
+static void launch_per_signal(void (*kernel)(GenArgs), int64_t B, int nsm, cudaStream_t st,
+                              const GenArgs& g) {
+  int C = 1;
+  while (C < 8 && (int64_t)(2 * C) * B <= nsm) C *= 2;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(B * C), 1, 1);
+  cfg.blockDim = dim3(1024, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, g);
 }
 
 // Subspace Pursuit on at most C = 2 a_k candidate columns and 16 rows; the
@@ -797,8 +862,11 @@ static GenArgs general_front(sft_plan_s* P, int64_t B, const void* x, int64_t x_
     default: k_gen_bound<F, 4><<<sgrid, 256, 0, st>>>(g); break;
   }
   stage_end(P, st);
+  int dev = 0, nsm = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   stage_begin(P, "gen_tau", st);
-  k_gen_tau<<<(unsigned)B, 1024, 0, st>>>(g);
+  launch_per_signal(k_gen_tau, B, nsm, st, g);
   stage_end(P, st);
   stage_begin(P, "gen_prune", st);
   switch (am) {
@@ -808,9 +876,6 @@ static GenArgs general_front(sft_plan_s* P, int64_t B, const void* x, int64_t x_
     default: k_gen_prune<F, 4><<<sgrid, 256, 0, st>>>(g); break;
   }
   stage_end(P, st);
-  int dev = 0, nsm = 152;
-  if (cudaGetDevice(&dev) == cudaSuccess)
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const unsigned vgrid = (unsigned)std::max<int64_t>(
       1, std::min<int64_t>((B * P->M0 + 127) / 128, (int64_t)P->dec_ctas_per_sm * nsm));
   stage_begin(P, "gen_svals", st);
@@ -822,7 +887,7 @@ static GenArgs general_front(sft_plan_s* P, int64_t B, const void* x, int64_t x_
   }
   stage_end(P, st);
   stage_begin(P, "gen_vote", st);
-  k_gen_vote<<<(unsigned)B, 1024, 0, st>>>(g);
+  launch_per_signal(k_gen_vote, B, nsm, st, g);
   stage_end(P, st);
   return g;
 }
